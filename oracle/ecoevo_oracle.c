@@ -1,0 +1,590 @@
+/*
+ * ecoevo_oracle.c -- plain, slow, single-threaded CPU simulator.
+ *
+ * TEST INFRASTRUCTURE ONLY (see ecoevo_oracle.h).  Every function below
+ * follows one passage of the paper, cited in its comment, in the order the
+ * step is stated; no blocking, fusion or reordering.  Build:
+ *   gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared ecoevo_oracle.c -lm
+ */
+#include "ecoevo_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, as defined by Salmon et al. (SC'11): ten rounds of two    */
+/* 32x32->64 multiplies with the Weyl key schedule between rounds.          */
+/* ------------------------------------------------------------------------ */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                      uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u; /* golden ratio            */
+      k1 += 0xBB67AE85u; /* sqrt(3) - 1             */
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void key_of(uint64_t seed, uint32_t key[2]) {
+  key[0] = (uint32_t)(seed & 0xFFFFFFFFu);
+  key[1] = (uint32_t)(seed >> 32);
+}
+
+static uint32_t philox_word(uint64_t seed, uint32_t c0, uint32_t c1,
+                            uint32_t c2, uint32_t c3, int lane) {
+  uint32_t ctr[4] = {c0, c1, c2, c3}, key[2], out[4];
+  key_of(seed, key);
+  or_philox4x32_10(ctr, key, out);
+  return out[lane];
+}
+
+/* Box-Muller on u = (x + 1/2) 2^-32, computed in double. */
+void or_box_muller(uint32_t x1, uint32_t x2, double *z0, double *z1) {
+  const double two_m32 = 1.0 / 4294967296.0;
+  double u1 = ((double)x1 + 0.5) * two_m32;
+  double u2 = ((double)x2 + 0.5) * two_m32;
+  double r = sqrt(-2.0 * log(u1));
+  double a = 2.0 * M_PI * u2;
+  *z0 = r * cos(a);
+  *z1 = r * sin(a);
+}
+
+/* One Philox draw {j/4, t, tag, id} gives four normals: lanes (0,1) and
+ * (2,3) are two Box-Muller pairs; normal j takes pair (j%4)/2, and the cos
+ * (even j) or sin (odd j) member. */
+double or_normal(uint64_t seed, uint32_t tag, uint32_t t, uint32_t id,
+                 uint32_t j) {
+  uint32_t ctr[4] = {j >> 2, t, tag, id}, key[2], out[4];
+  key_of(seed, key);
+  or_philox4x32_10(ctr, key, out);
+  int pair = (int)((j & 3u) >> 1);
+  double z0, z1;
+  or_box_muller(out[2 * pair], out[2 * pair + 1], &z0, &z1);
+  return (j & 1u) ? z1 : z0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* App. B.1: regrowth probability p(x,y) = p_I(x,y) c(x) + c, Eq. (1).      */
+/* ------------------------------------------------------------------------ */
+
+/* Climate value of row y (rows are the latitude axis, y = 0 at the top).
+ * Linear form: lat_top at the top row to lat_bottom at the bottom row.
+ * Paper form: c = (alpha^x + 1) / (alpha + 1) with x = y / (H - 1). */
+static double climate(const OrParams *p, int y) {
+  double frac = (p->H > 1) ? (double)y / (double)(p->H - 1) : 0.0;
+  if (p->lat_mode == 1) return (pow(p->lat_alpha, frac) + 1.0) / (p->lat_alpha + 1.0);
+  return p->lat_top + (p->lat_bottom - p->lat_top) * frac;
+}
+
+static uint32_t prob_to_threshold(double prob) {
+  if (!(prob > 0.0)) return 0u;
+  if (prob >= 1.0) return 0xFFFFFFFFu;
+  return (uint32_t)floor(prob * 4294967296.0);
+}
+
+int or_threshold_table(const OrParams *p, uint32_t *thr) {
+  for (int y = 0; y < p->H; ++y) {
+    double cy = climate(p, y);
+    for (int cls = 0; cls < 4; ++cls) {
+      double prob = p->p_class[cls] * cy + p->p_spont;
+      thr[y * 4 + cls] = prob_to_threshold(prob);
+    }
+  }
+  return 0;
+}
+
+static int in_neighbourhood(const OrParams *p, int dy, int dx) {
+  if (dy == 0 && dx == 0) return 0;
+  int ady = dy < 0 ? -dy : dy, adx = dx < 0 ? -dx : dx;
+  if (p->nbr_shape == 1) return ady + adx <= p->nbr_radius;
+  return ady <= p->nbr_radius && adx <= p->nbr_radius;
+}
+
+static int count_class(const OrParams *p, int n) {
+  int cls = 0;
+  for (int e = 0; e < 3; ++e)
+    if (n >= p->class_edges[e]) cls = e + 1;
+  return cls;
+}
+
+/* Synchronous pass: every count reads res_old only.  A cell that is a wall
+ * or already holds a resource is copied; an empty cell counts the resources
+ * in its neighbourhood (cells off the grid count zero), picks its count
+ * class and grows iff its Philox word is below the row/class threshold. */
+void or_regrow(const OrParams *p, uint64_t seed, uint32_t t,
+               const uint32_t *thr, const uint8_t *res_old,
+               const uint8_t *wall, uint8_t *res_new) {
+  const int H = p->H, W = p->W, R = p->nbr_radius;
+  for (int y = 0; y < H; ++y) {
+    for (int x = 0; x < W; ++x) {
+      int cell = y * W + x;
+      if (wall[cell] || res_old[cell]) {
+        res_new[cell] = res_old[cell];
+        continue;
+      }
+      int n = 0;
+      for (int dy = -R; dy <= R; ++dy) {
+        for (int dx = -R; dx <= R; ++dx) {
+          if (!in_neighbourhood(p, dy, dx)) continue;
+          int yy = y + dy, xx = x + dx;
+          if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+          n += res_old[yy * W + xx] ? 1 : 0;
+        }
+      }
+      int cls = count_class(p, n);
+      uint32_t u = philox_word(seed, (uint32_t)cell >> 2, t, OR_TAG_REGROW, 0u,
+                               cell & 3);
+      res_new[cell] = (u < thr[y * 4 + cls]) ? 1 : 0;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* App. B.2: the agents.                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Sensorimotor ability: the 7x7 square centred on the agent, three channels
+ * (resource, other agent, wall), channel-major then row-major, and the
+ * agent's own energy last.  Off-grid cells read as wall. */
+void or_observe(const OrParams *p, const uint8_t *res, const uint8_t *wall,
+                const int32_t *slot_map, int32_t y, int32_t x, float energy,
+                double *obs) {
+  const int H = p->H, W = p->W, half = OR_VIEW / 2;
+  for (int dy = -half; dy <= half; ++dy) {
+    for (int dx = -half; dx <= half; ++dx) {
+      int k = (dy + half) * OR_VIEW + (dx + half);
+      int yy = y + dy, xx = x + dx;
+      double r = 0.0, a = 0.0, wl = 1.0;
+      if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+        int cell = yy * W + xx;
+        r = res[cell] ? 1.0 : 0.0;
+        a = (slot_map[cell] >= 0 && !(dy == 0 && dx == 0)) ? 1.0 : 0.0;
+        wl = wall[cell] ? 1.0 : 0.0;
+      }
+      obs[0 * 49 + k] = r;
+      obs[1 * 49 + k] = a;
+      obs[2 * 49 + k] = wl;
+    }
+  }
+  obs[147] = (double)energy;
+}
+
+static double sigmoid(double z) { return 1.0 / (1.0 + exp(-z)); }
+
+/* Cognitive capacity: z = W [obs; h] + b with gates i, f, g, o in blocks of
+ * 32 rows; c' = s(f) c + s(i) tanh(g); h' = s(o) tanh(c'); logits =
+ * Wo h' + bo; the action is the first index of the largest logit. */
+int or_lstm_step(const float *w, const double *obs, double *h, double *c,
+                 double *logits) {
+  double v[OR_NIN];
+  for (int k = 0; k < OR_NOBS; ++k) v[k] = obs[k];
+  for (int k = 0; k < OR_HID; ++k) v[OR_NOBS + k] = h[k];
+  double z[OR_NGATE];
+  for (int r = 0; r < OR_NGATE; ++r) {
+    double acc = 0.0;
+    for (int k = 0; k < OR_NIN; ++k) acc += (double)w[r * OR_NIN + k] * v[k];
+    z[r] = acc + (double)w[OR_OFF_B + r];
+  }
+  for (int j = 0; j < OR_HID; ++j) {
+    double gi = sigmoid(z[0 * OR_HID + j]);
+    double gf = sigmoid(z[1 * OR_HID + j]);
+    double gg = tanh(z[2 * OR_HID + j]);
+    double go = sigmoid(z[3 * OR_HID + j]);
+    c[j] = gf * c[j] + gi * gg;
+    h[j] = go * tanh(c[j]);
+  }
+  int best = 0;
+  for (int a = 0; a < OR_NACT; ++a) {
+    double acc = 0.0;
+    for (int j = 0; j < OR_HID; ++j)
+      acc += (double)w[OR_OFF_WO + a * OR_HID + j] * h[j];
+    logits[a] = acc + (double)w[OR_OFF_BO + a];
+    if (logits[a] > logits[best]) best = a;
+  }
+  return best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The world.                                                               */
+/* ------------------------------------------------------------------------ */
+struct OrWorld {
+  OrParams p;
+  uint64_t seed;
+  uint8_t *res, *wall, *res_tmp;
+  int32_t *slot_map;
+  uint8_t *alive, *ate, *killed, *wants;
+  int32_t *y, *x, *repr_ctr, *low_ctr, *age, *action, *target, *cand;
+  int32_t *claim, *birth_parent, *birth_child, *free_list;
+  float *energy, *weights;
+  double *h, *c, *logits;
+  uint32_t *thr;
+  int64_t counters[8];
+};
+
+static const int DY[5] = {0, -1, 1, 0, 0}; /* stay, N, S, E, W */
+static const int DX[5] = {0, 0, 0, 1, -1};
+
+void *or_world_field(OrWorld *w, int f) {
+  switch (f) {
+    case OR_F_RES: return w->res;
+    case OR_F_WALL: return w->wall;
+    case OR_F_SLOT_MAP: return w->slot_map;
+    case OR_F_ALIVE: return w->alive;
+    case OR_F_Y: return w->y;
+    case OR_F_X: return w->x;
+    case OR_F_ENERGY: return w->energy;
+    case OR_F_REPR_CTR: return w->repr_ctr;
+    case OR_F_LOW_CTR: return w->low_ctr;
+    case OR_F_AGE: return w->age;
+    case OR_F_H: return w->h;
+    case OR_F_C: return w->c;
+    case OR_F_ACTION: return w->action;
+    case OR_F_LOGITS: return w->logits;
+    case OR_F_ATE: return w->ate;
+    case OR_F_WEIGHTS: return w->weights;
+    case OR_F_COUNTERS: return w->counters;
+    case OR_F_THR: return w->thr;
+    case OR_F_BIRTH_PARENT: return w->birth_parent;
+    case OR_F_BIRTH_CHILD: return w->birth_child;
+    default: return NULL;
+  }
+}
+
+void or_world_destroy(OrWorld *w) {
+  if (!w) return;
+  free(w->res); free(w->wall); free(w->res_tmp); free(w->slot_map);
+  free(w->alive); free(w->ate); free(w->killed); free(w->wants);
+  free(w->y); free(w->x); free(w->repr_ctr); free(w->low_ctr); free(w->age);
+  free(w->action); free(w->target); free(w->cand); free(w->claim);
+  free(w->birth_parent); free(w->birth_child); free(w->free_list);
+  free(w->energy); free(w->weights); free(w->h); free(w->c); free(w->logits);
+  free(w->thr);
+  free(w);
+}
+
+static int valid_params(const OrParams *p) {
+  if (p->H < 1 || p->W < 1 || p->capacity < 0 || p->n_agents0 < 0) return 0;
+  if (p->n_agents0 > p->capacity) return 0;
+  if (p->nbr_radius < 1 || p->nbr_radius > 3) return 0;
+  if (p->nbr_shape != 0 && p->nbr_shape != 1) return 0;
+  if (p->lat_mode != 0 && p->lat_mode != 1) return 0;
+  return 1;
+}
+
+static int cmp_u64(const void *a, const void *b) {
+  uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+  return (x > y) - (x < y);
+}
+
+/* out[j] = base[j] + scale * N_j for j < 23333 (base NULL reads as zero),
+ * with N_j normal j of the stream (seed, tag, t, id); one Philox draw serves
+ * the four normals 4q..4q+3, as or_normal defines them. */
+static void fill_normals(uint64_t seed, uint32_t tag, uint32_t t, uint32_t id,
+                         float scale, const float *base, float *out) {
+  uint32_t key[2];
+  key_of(seed, key);
+  for (uint32_t q = 0; 4 * q < OR_NPARAM; ++q) {
+    uint32_t ctr[4] = {q, t, tag, id}, r[4];
+    or_philox4x32_10(ctr, key, r);
+    double z[4];
+    or_box_muller(r[0], r[1], &z[0], &z[1]);
+    or_box_muller(r[2], r[3], &z[2], &z[3]);
+    for (uint32_t i = 0; i < 4 && 4 * q + i < OR_NPARAM; ++i) {
+      uint32_t j = 4 * q + i;
+      double b = base ? (double)base[j] : 0.0;
+      out[j] = (float)(b + (double)scale * z[i]);
+    }
+  }
+}
+
+int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
+  *out = NULL;
+  if (!valid_params(p)) return -1;
+  OrWorld *w = (OrWorld *)calloc(1, sizeof(OrWorld));
+  if (!w) return -2;
+  w->p = *p;
+  w->seed = seed;
+  const size_t HW = (size_t)p->H * (size_t)p->W, C = (size_t)p->capacity;
+  const size_t C1 = C ? C : 1;
+  w->res = calloc(HW, 1); w->wall = calloc(HW, 1); w->res_tmp = calloc(HW, 1);
+  w->slot_map = malloc(HW * sizeof(int32_t));
+  w->claim = malloc(HW * sizeof(int32_t));
+  w->alive = calloc(C1, 1); w->ate = calloc(C1, 1);
+  w->killed = calloc(C1, 1); w->wants = calloc(C1, 1);
+  w->y = calloc(C1, 4); w->x = calloc(C1, 4); w->repr_ctr = calloc(C1, 4);
+  w->low_ctr = calloc(C1, 4); w->age = calloc(C1, 4); w->action = calloc(C1, 4);
+  w->target = calloc(C1, 4); w->cand = calloc(C1, 4);
+  w->birth_parent = calloc(C1, 4); w->birth_child = calloc(C1, 4);
+  w->free_list = calloc(C1, 4);
+  w->energy = calloc(C1, sizeof(float));
+  w->weights = calloc(C1 * OR_NPARAM, sizeof(float));
+  w->h = calloc(C1 * OR_HID, sizeof(double));
+  w->c = calloc(C1 * OR_HID, sizeof(double));
+  w->logits = calloc(C1 * OR_NACT, sizeof(double));
+  w->thr = calloc((size_t)p->H * 4, sizeof(uint32_t));
+  if (!w->res || !w->wall || !w->res_tmp || !w->slot_map || !w->claim ||
+      !w->alive || !w->ate || !w->killed || !w->wants || !w->y || !w->x ||
+      !w->repr_ctr || !w->low_ctr || !w->age || !w->action || !w->target ||
+      !w->cand || !w->birth_parent || !w->birth_child || !w->free_list ||
+      !w->energy || !w->weights || !w->h || !w->c || !w->logits || !w->thr) {
+    or_world_destroy(w);
+    return -2;
+  }
+  or_threshold_table(p, w->thr);
+  const int H = p->H, W = p->W;
+
+  /* Border walls (App. B.1 environment: walls are cells agents cannot
+   * cross). */
+  for (int yy = 0; yy < H; ++yy)
+    for (int xx = 0; xx < W; ++xx)
+      if (p->border_walls && (yy == 0 || yy == H - 1 || xx == 0 || xx == W - 1))
+        w->wall[yy * W + xx] = 1;
+
+  /* Initial resources: Bernoulli(res_init_p) on every non-wall cell. */
+  uint32_t thr_init = prob_to_threshold(p->res_init_p);
+  for (size_t cell = 0; cell < HW; ++cell) {
+    w->slot_map[cell] = -1;
+    w->claim[cell] = -1;
+    if (w->wall[cell]) continue;
+    uint32_t u = philox_word(seed, (uint32_t)cell >> 2, 0u, OR_TAG_RES_INIT, 0u,
+                             (int)(cell & 3));
+    w->res[cell] = (u < thr_init) ? 1 : 0;
+  }
+
+  /* Random placement: the non-wall cells sorted by (Philox word, cell); the
+   * first n_agents0 cells receive slots 0.. in that order. */
+  size_t nfree = 0;
+  for (size_t cell = 0; cell < HW; ++cell) nfree += w->wall[cell] ? 0 : 1;
+  if ((size_t)p->n_agents0 > nfree) {
+    or_world_destroy(w);
+    return -1;
+  }
+  if (p->n_agents0 > 0) {
+    uint64_t *keys = malloc(nfree * sizeof(uint64_t));
+    if (!keys) { or_world_destroy(w); return -2; }
+    size_t k = 0;
+    for (size_t cell = 0; cell < HW; ++cell) {
+      if (w->wall[cell]) continue;
+      uint32_t u = philox_word(seed, (uint32_t)cell >> 2, 0u, OR_TAG_PLACE, 0u,
+                               (int)(cell & 3));
+      keys[k++] = ((uint64_t)u << 32) | (uint64_t)cell;
+    }
+    qsort(keys, nfree, sizeof(uint64_t), cmp_u64);
+    for (int s = 0; s < p->n_agents0; ++s) {
+      uint32_t cell = (uint32_t)(keys[s] & 0xFFFFFFFFu);
+      w->alive[s] = 1;
+      w->y[s] = (int32_t)(cell / (uint32_t)W);
+      w->x[s] = (int32_t)(cell % (uint32_t)W);
+      w->slot_map[cell] = s;
+      w->energy[s] = p->e0;
+      /* weights drawn once at the start of the simulation, App. B.2 */
+      fill_normals(seed, OR_TAG_INIT_W, 0u, (uint32_t)s, p->w_init_std, NULL,
+                   w->weights + (size_t)s * OR_NPARAM);
+    }
+    free(keys);
+  }
+  w->counters[OR_C_POP] = p->n_agents0;
+  *out = w;
+  return 0;
+}
+
+int or_world_sync(OrWorld *w) {
+  const OrParams *p = &w->p;
+  const int H = p->H, W = p->W;
+  or_threshold_table(p, w->thr);
+  for (int i = 0; i < H * W; ++i) w->slot_map[i] = -1;
+  int64_t pop = 0;
+  for (int s = 0; s < p->capacity; ++s) {
+    if (!w->alive[s]) continue;
+    int yy = w->y[s], xx = w->x[s];
+    if (yy < 0 || yy >= H || xx < 0 || xx >= W) return -1;
+    int cell = yy * W + xx;
+    if (w->wall[cell] || w->slot_map[cell] >= 0) return -1;
+    w->slot_map[cell] = s;
+    ++pop;
+  }
+  w->counters[OR_C_POP] = pop;
+  return 0;
+}
+
+static int in_grid(const OrParams *p, int yy, int xx) {
+  return yy >= 0 && yy < p->H && xx >= 0 && xx < p->W;
+}
+
+/* One simulation step.  Order of the parts: regrowth (App. B.1), observation
+ * and controller (App. B.2), moves with one claim round, eating, physiology
+ * (App. B.2 physiology), death and reproduction (App. B.3). */
+int or_world_step(OrWorld *w, const int32_t *forced) {
+  const OrParams *p = &w->p;
+  const int H = p->H, W = p->W, C = p->capacity;
+  const uint32_t t = (uint32_t)w->counters[OR_C_T];
+
+  /* 1. regrowth from the grid as it stood at the start of the step */
+  or_regrow(p, w->seed, t, w->thr, w->res, w->wall, w->res_tmp);
+  memcpy(w->res, w->res_tmp, (size_t)H * W);
+
+  /* 2-3. observation (new resources, start-of-step occupancy) and one
+   * controller step per living agent */
+  for (int s = 0; s < C; ++s) {
+    w->ate[s] = 0;
+    w->killed[s] = 0;
+    w->wants[s] = 0;
+    w->target[s] = -1;
+    w->cand[s] = -1;
+    if (!w->alive[s]) continue;
+    double obs[OR_NOBS];
+    or_observe(p, w->res, w->wall, w->slot_map, w->y[s], w->x[s], w->energy[s],
+               obs);
+    w->action[s] = or_lstm_step(w->weights + (size_t)s * OR_NPARAM, obs,
+                                w->h + (size_t)s * OR_HID,
+                                w->c + (size_t)s * OR_HID,
+                                w->logits + (size_t)s * OR_NACT);
+  }
+
+  /* 4. moves: a target is valid if on the grid, not a wall and empty at the
+   * start of the phase; among valid claimants of a cell the lowest slot
+   * moves, every other agent stays. */
+  for (int i = 0; i < H * W; ++i) w->claim[i] = -1;
+  for (int s = 0; s < C; ++s) {
+    if (!w->alive[s]) continue;
+    int a = forced ? forced[s] : w->action[s];
+    if (a <= 0 || a >= OR_NACT) continue;
+    int ty = w->y[s] + DY[a], tx = w->x[s] + DX[a];
+    if (!in_grid(p, ty, tx) || w->wall[ty * W + tx]) {
+      if (p->wall_kills) w->killed[s] = 1;
+      continue;
+    }
+    int cell = ty * W + tx;
+    if (w->slot_map[cell] != -1) continue;
+    w->target[s] = cell;
+    if (w->claim[cell] == -1 || s < w->claim[cell]) w->claim[cell] = s;
+  }
+  for (int s = 0; s < C; ++s) {
+    int cell = w->target[s];
+    if (cell < 0 || w->claim[cell] != s) continue;
+    w->slot_map[w->y[s] * W + w->x[s]] = -1;
+    w->slot_map[cell] = s;
+    w->y[s] = cell / W;
+    w->x[s] = cell % W;
+  }
+
+  /* 5. eating: an agent on a resource cell consumes it */
+  for (int s = 0; s < C; ++s) {
+    if (!w->alive[s] || w->killed[s]) continue;
+    int cell = w->y[s] * W + w->x[s];
+    if (w->res[cell]) {
+      w->res[cell] = 0;
+      w->ate[s] = 1;
+    }
+  }
+
+  /* 6. physiology: gain when eating, linear decay, clip at e_max; death
+   * after t_death consecutive steps at or below e_death (at least one) or
+   * past the maximum age; reproduction counter above e_repr. */
+  int64_t deaths = 0;
+  for (int s = 0; s < C; ++s) {
+    if (!w->alive[s]) continue;
+    int dead = 0;
+    if (w->killed[s]) {
+      dead = 1;
+    } else {
+      float e = w->energy[s];
+      if (w->ate[s]) e = e + p->e_gain;
+      e = e - p->e_decay;
+      if (e > p->e_max) e = p->e_max;
+      w->energy[s] = e;
+      w->age[s] += 1;
+      w->low_ctr[s] = (e <= p->e_death) ? w->low_ctr[s] + 1 : 0;
+      int need = p->t_death > 1 ? p->t_death : 1;
+      if (w->low_ctr[s] >= need || w->age[s] > p->max_age) dead = 1;
+    }
+    if (dead) {
+      w->alive[s] = 0;
+      w->slot_map[w->y[s] * W + w->x[s]] = -1;
+      ++deaths;
+      continue;
+    }
+    w->repr_ctr[s] = (w->energy[s] > p->e_repr) ? w->repr_ctr[s] + 1 : 0;
+    w->wants[s] = (w->repr_ctr[s] >= p->t_repr) ? 1 : 0;
+  }
+
+  /* 7. reproduction: each parent takes its first free neighbour in the order
+   * N, S, E, W (occupancy after moves and deaths); the lowest parent slot
+   * wins a contested cell; the k-th successful parent (ascending) gets the
+   * k-th free slot (ascending); births past the free slots are dropped. */
+  for (int i = 0; i < H * W; ++i) w->claim[i] = -1;
+  for (int s = 0; s < C; ++s) {
+    if (!w->alive[s] || !w->wants[s]) continue;
+    for (int a = 1; a < OR_NACT; ++a) {
+      int ny = w->y[s] + DY[a], nx = w->x[s] + DX[a];
+      if (!in_grid(p, ny, nx)) continue;
+      int cell = ny * W + nx;
+      if (w->wall[cell] || w->slot_map[cell] != -1) continue;
+      w->cand[s] = cell;
+      break;
+    }
+    int cell = w->cand[s];
+    if (cell >= 0 && (w->claim[cell] == -1 || s < w->claim[cell]))
+      w->claim[cell] = s;
+  }
+  int nfree = 0;
+  for (int s = 0; s < C; ++s)
+    if (!w->alive[s]) w->free_list[nfree++] = s;
+  int k = 0;
+  int64_t dropped = 0;
+  for (int parent = 0; parent < C; ++parent) {
+    int cell = w->cand[parent];
+    if (cell < 0 || w->claim[cell] != parent) continue;
+    if (k >= nfree) {
+      ++dropped;
+      continue;
+    }
+    int child = w->free_list[k];
+    w->birth_parent[k] = parent;
+    w->birth_child[k] = child;
+    ++k;
+    w->alive[child] = 1;
+    w->y[child] = cell / W;
+    w->x[child] = cell % W;
+    w->slot_map[cell] = child;
+    w->energy[child] = p->e0;
+    w->repr_ctr[child] = 0;
+    w->low_ctr[child] = 0;
+    w->age[child] = 0;
+    w->action[child] = 0;
+    w->ate[child] = 0;
+    for (int j = 0; j < OR_HID; ++j) {
+      w->h[(size_t)child * OR_HID + j] = 0.0;
+      w->c[(size_t)child * OR_HID + j] = 0.0;
+    }
+    for (int a = 0; a < OR_NACT; ++a) w->logits[(size_t)child * OR_NACT + a] = 0.0;
+    /* asexual reproduction: parent weights plus N(0, sigma) noise, App. B.3 */
+    fill_normals(w->seed, OR_TAG_MUT, t, (uint32_t)parent, p->mut_std,
+                 w->weights + (size_t)parent * OR_NPARAM,
+                 w->weights + (size_t)child * OR_NPARAM);
+    w->repr_ctr[parent] = 0;
+  }
+
+  w->counters[OR_C_T] += 1;
+  w->counters[OR_C_POP] += (int64_t)k - deaths;
+  w->counters[OR_C_BIRTHS] += k;
+  w->counters[OR_C_DEATHS] += deaths;
+  w->counters[OR_C_DROPPED] += dropped;
+  w->counters[OR_C_BIRTHS_LAST] = k;
+  w->counters[OR_C_DEATHS_LAST] = deaths;
+  w->counters[OR_C_DROPPED_LAST] = dropped;
+  return 0;
+}

@@ -1,0 +1,147 @@
+/*
+ * ecoevo_oracle.h -- plain, slow, single-threaded CPU simulator of the
+ * non-episodic simulation step of "Eco-evolutionary Dynamics of
+ * Non-episodic Neuroevolution in Large Multi-agent Environments"
+ * (Hamon, Nisioti, Moulin-Frier, 2023).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This oracle exists to check the CUDA library.
+ * Only the test-suite, the smoke check and the CPU-baseline leg of the
+ * benchmark may load it.  It shares no code, header, table or constant
+ * generator with the CUDA path; it carries its own Philox4x32-10, its own
+ * Box-Muller transform and its own LSTM, all written in plain loops.
+ *
+ * Precision: energies and weights are FP32 state (the step is FP32
+ * throughout), so they are stored as float and every energy operation is a
+ * single IEEE float add/sub (build with -ffp-contract=off).  Everything the
+ * paper leaves to a network (gates, cell state, logits) is computed in
+ * double and kept in double.
+ *
+ * Parity status per function (the pins live in tests/test_oracle_*.py):
+ *   or_philox4x32_10   pinned: published known-answer vectors
+ *   or_box_muller      pinned: moments + Kolmogorov-Smirnov vs N(0,1)
+ *   or_threshold_table pinned: per-class growth frequencies (binomial bound)
+ *   or_regrow          pinned: convolution-count reconstruction, invariants
+ *   or_observe         pinned: numpy padded-slice reconstruction
+ *   or_lstm_step       pinned: torch.nn.LSTMCell (float64), bias-only closed form
+ *   or_world_step      pinned: invariants, float32 energy closed forms,
+ *                      brute force on <=4x4 worlds, slot-assignment rules
+ */
+#ifndef ECOEVO_ORACLE_H
+#define ECOEVO_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Fixed controller shape: 7x7x3 observation + energy, LSTM hidden 32,
+ * 5 actions (App. B.2; controller of the 200x400 workloads). */
+#define OR_VIEW 7
+#define OR_NOBS 148              /* 7*7*3 + 1 */
+#define OR_HID 32
+#define OR_NIN (OR_NOBS + OR_HID) /* 180 */
+#define OR_NGATE (4 * OR_HID)    /* 128 */
+#define OR_NACT 5
+/* Logical parameter vector of one agent. */
+#define OR_OFF_B (OR_NGATE * OR_NIN)          /* 23040: gate biases   */
+#define OR_OFF_WO (OR_OFF_B + OR_NGATE)       /* 23168: output matrix */
+#define OR_OFF_BO (OR_OFF_WO + OR_NACT * OR_HID) /* 23328: output bias */
+#define OR_NPARAM (OR_OFF_BO + OR_NACT)       /* 23333 */
+
+/* Philox stream tags (second-to-last counter word). */
+#define OR_TAG_REGROW 1u
+#define OR_TAG_PLACE 2u
+#define OR_TAG_RES_INIT 3u
+#define OR_TAG_INIT_W 4u
+#define OR_TAG_MUT 5u
+
+typedef struct OrParams {
+  int32_t H, W, capacity, n_agents0;
+  int32_t border_walls;     /* 1: rows 0,H-1 and cols 0,W-1 are walls     */
+  double res_init_p;        /* Bernoulli density of initial resources      */
+  int32_t nbr_shape;        /* 0: square (Chebyshev) radius, 1: diamond    */
+  int32_t nbr_radius;       /* 1..3                                        */
+  int32_t class_edges[3];   /* class = #edges <= n                         */
+  double p_class[4];        /* p_I per class                               */
+  int32_t lat_mode;         /* 0: linear top->bottom, 1: (a^x+1)/(a+1)     */
+  double lat_top, lat_bottom, lat_alpha;
+  double p_spont;           /* spontaneous growth c                        */
+  float e0, e_decay, e_gain, e_max;
+  float e_repr;
+  int32_t t_repr;
+  float e_death;
+  int32_t t_death, max_age;
+  int32_t wall_kills;       /* 1: an agent moving into a wall dies         */
+  float w_init_std, mut_std;
+} OrParams;
+
+typedef struct OrWorld OrWorld;
+
+/* Field ids for or_world_field(); each returns a pointer into the world.   */
+enum {
+  OR_F_RES = 0,      /* uint8  [H*W]  resource present                       */
+  OR_F_WALL,         /* uint8  [H*W]                                         */
+  OR_F_SLOT_MAP,     /* int32  [H*W]  slot of the agent on the cell, -1 none */
+  OR_F_ALIVE,        /* uint8  [C]                                           */
+  OR_F_Y,            /* int32  [C]                                           */
+  OR_F_X,            /* int32  [C]                                           */
+  OR_F_ENERGY,       /* float  [C]                                           */
+  OR_F_REPR_CTR,     /* int32  [C]  consecutive steps with energy > e_repr   */
+  OR_F_LOW_CTR,      /* int32  [C]  consecutive steps with energy <= e_death */
+  OR_F_AGE,          /* int32  [C]                                           */
+  OR_F_H,            /* double [C*32]                                        */
+  OR_F_C,            /* double [C*32]                                        */
+  OR_F_ACTION,       /* int32  [C]  argmax of the last step                  */
+  OR_F_LOGITS,       /* double [C*5]                                         */
+  OR_F_ATE,          /* uint8  [C]  ate during the last step                 */
+  OR_F_WEIGHTS,      /* float  [C*23333] logical parameter vectors           */
+  OR_F_COUNTERS,     /* int64  [8]  see OR_C_*                               */
+  OR_F_THR,          /* uint32 [H*4] growth thresholds                       */
+  OR_F_BIRTH_PARENT, /* int32  [C]  parents of the last step's births        */
+  OR_F_BIRTH_CHILD,  /* int32  [C]  child slots of the last step's births    */
+  OR_NFIELDS
+};
+enum {
+  OR_C_T = 0, OR_C_POP, OR_C_BIRTHS, OR_C_DEATHS, OR_C_DROPPED,
+  OR_C_BIRTHS_LAST, OR_C_DEATHS_LAST, OR_C_DROPPED_LAST
+};
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                      uint32_t out[4]);
+/* Two standard normals from two uniform words (Box and Muller, 1958). */
+void or_box_muller(uint32_t x1, uint32_t x2, double *z0, double *z1);
+/* Normal number j of the stream (seed, tag, t, id). */
+double or_normal(uint64_t seed, uint32_t tag, uint32_t t, uint32_t id,
+                 uint32_t j);
+/* Growth thresholds thr[y*4+cls] = floor(p * 2^32), App. B.1 Eq. (1). */
+int or_threshold_table(const OrParams *p, uint32_t *thr);
+/* One synchronous regrowth pass, App. B.1 Eq. (1). */
+void or_regrow(const OrParams *p, uint64_t seed, uint32_t t,
+               const uint32_t *thr, const uint8_t *res_old,
+               const uint8_t *wall, uint8_t *res_new);
+/* Observation of the agent at (y, x), App. B.2 (sensorimotor ability). */
+void or_observe(const OrParams *p, const uint8_t *res, const uint8_t *wall,
+                const int32_t *slot_map, int32_t y, int32_t x, float energy,
+                double *obs /* [148] */);
+/* One LSTM step + linear read-out + argmax, App. B.2 (cognitive capacity).
+ * h and c are updated in place; returns the action. */
+int or_lstm_step(const float *w /* [23333] */, const double *obs,
+                 double *h, double *c, double *logits);
+
+int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out);
+void or_world_destroy(OrWorld *w);
+/* One step.  forced: NULL, or [C] actions used for moving instead of the
+ * controller's own argmax (the controller still runs). */
+int or_world_step(OrWorld *w, const int32_t *forced);
+void *or_world_field(OrWorld *w, int field);
+/* Rebuild slot_map from alive/y/x and the threshold table from the params,
+ * after a caller has written state into the fields.  Returns 0, or -1 if
+ * two agents share a cell or an agent sits on a wall or off the grid. */
+int or_world_sync(OrWorld *w);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,241 @@
+"""ctypes view of the CPU oracle (test infrastructure only).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg import
+this module.  It shares nothing with the CUDA library: parameters come in as
+a plain mapping of field names to numbers.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NOBS, HID, NACT = 148, 32, 5
+NPARAM = 23333
+OFF_B, OFF_WO, OFF_BO = 23040, 23168, 23328
+TAG_REGROW, TAG_PLACE, TAG_RES_INIT, TAG_INIT_W, TAG_MUT = 1, 2, 3, 4, 5
+
+(F_RES, F_WALL, F_SLOT_MAP, F_ALIVE, F_Y, F_X, F_ENERGY, F_REPR_CTR, F_LOW_CTR,
+ F_AGE, F_H, F_C, F_ACTION, F_LOGITS, F_ATE, F_WEIGHTS, F_COUNTERS, F_THR,
+ F_BIRTH_PARENT, F_BIRTH_CHILD) = range(20)
+(C_T, C_POP, C_BIRTHS, C_DEATHS, C_DROPPED, C_BIRTHS_LAST, C_DEATHS_LAST,
+ C_DROPPED_LAST) = range(8)
+
+
+class OrParams(ctypes.Structure):
+    _fields_ = [
+        ("H", ctypes.c_int32), ("W", ctypes.c_int32),
+        ("capacity", ctypes.c_int32), ("n_agents0", ctypes.c_int32),
+        ("border_walls", ctypes.c_int32),
+        ("res_init_p", ctypes.c_double),
+        ("nbr_shape", ctypes.c_int32), ("nbr_radius", ctypes.c_int32),
+        ("class_edges", ctypes.c_int32 * 3),
+        ("p_class", ctypes.c_double * 4),
+        ("lat_mode", ctypes.c_int32),
+        ("lat_top", ctypes.c_double), ("lat_bottom", ctypes.c_double),
+        ("lat_alpha", ctypes.c_double),
+        ("p_spont", ctypes.c_double),
+        ("e0", ctypes.c_float), ("e_decay", ctypes.c_float),
+        ("e_gain", ctypes.c_float), ("e_max", ctypes.c_float),
+        ("e_repr", ctypes.c_float), ("t_repr", ctypes.c_int32),
+        ("e_death", ctypes.c_float), ("t_death", ctypes.c_int32),
+        ("max_age", ctypes.c_int32),
+        ("wall_kills", ctypes.c_int32),
+        ("w_init_std", ctypes.c_float), ("mut_std", ctypes.c_float),
+    ]
+
+
+def make_params(values) -> OrParams:
+    """Fill OrParams from a mapping (or an object with attributes)."""
+    get = values.get if hasattr(values, "get") else (lambda k: getattr(values, k))
+    p = OrParams()
+    for name, ctype in OrParams._fields_:
+        v = get(name)
+        if name == "class_edges":
+            p.class_edges = (ctypes.c_int32 * 3)(*[int(e) for e in v])
+        elif name == "p_class":
+            p.p_class = (ctypes.c_double * 4)(*[float(e) for e in v])
+        elif ctype in (ctypes.c_float, ctypes.c_double):
+            setattr(p, name, float(v))
+        else:
+            setattr(p, name, int(v))
+    return p
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.or_box_muller.argtypes = [ctypes.c_uint32, ctypes.c_uint32,
+                                    ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double)]
+        L.or_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                ctypes.c_uint32, ctypes.c_uint32]
+        L.or_normal.restype = ctypes.c_double
+        L.or_threshold_table.argtypes = [ctypes.POINTER(OrParams), u32p]
+        L.or_regrow.argtypes = [ctypes.POINTER(OrParams), ctypes.c_uint64,
+                                ctypes.c_uint32, u32p, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_void_p]
+        L.or_observe.argtypes = [ctypes.POINTER(OrParams), ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                 ctypes.c_int32, ctypes.c_float, ctypes.c_void_p]
+        L.or_lstm_step.argtypes = [ctypes.c_void_p] * 5
+        L.or_lstm_step.restype = ctypes.c_int
+        L.or_world_create.argtypes = [ctypes.POINTER(OrParams), ctypes.c_uint64,
+                                      ctypes.POINTER(ctypes.c_void_p)]
+        L.or_world_destroy.argtypes = [ctypes.c_void_p]
+        L.or_world_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.or_world_field.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.or_world_field.restype = ctypes.c_void_p
+        L.or_world_sync.argtypes = [ctypes.c_void_p]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def philox4x32_10(ctr, key):
+    c = (ctypes.c_uint32 * 4)(*ctr)
+    k = (ctypes.c_uint32 * 2)(*key)
+    o = (ctypes.c_uint32 * 4)()
+    lib().or_philox4x32_10(c, k, o)
+    return list(o)
+
+
+def box_muller(x1, x2):
+    z0, z1 = ctypes.c_double(), ctypes.c_double()
+    lib().or_box_muller(x1, x2, ctypes.byref(z0), ctypes.byref(z1))
+    return z0.value, z1.value
+
+
+def normal(seed, tag, t, ident, j):
+    return lib().or_normal(seed, tag, t, ident, j)
+
+
+def threshold_table(params) -> np.ndarray:
+    p = make_params(params)
+    thr = np.zeros((p.H, 4), np.uint32)
+    lib().or_threshold_table(ctypes.byref(p),
+                             thr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    return thr
+
+
+def regrow(params, seed, t, res_old, wall, thr=None) -> np.ndarray:
+    p = make_params(params)
+    if thr is None:
+        thr = threshold_table(params)
+    thr = np.ascontiguousarray(thr, np.uint32)
+    res_old = np.ascontiguousarray(res_old, np.uint8)
+    wall = np.ascontiguousarray(wall, np.uint8)
+    out = np.zeros_like(res_old)
+    lib().or_regrow(ctypes.byref(p), seed, t,
+                    thr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                    _ptr(res_old), _ptr(wall), _ptr(out))
+    return out
+
+
+def observe(params, res, wall, slot_map, y, x, energy) -> np.ndarray:
+    p = make_params(params)
+    res = np.ascontiguousarray(res, np.uint8)
+    wall = np.ascontiguousarray(wall, np.uint8)
+    slot_map = np.ascontiguousarray(slot_map, np.int32)
+    out = np.zeros(NOBS, np.float64)
+    lib().or_observe(ctypes.byref(p), _ptr(res), _ptr(wall), _ptr(slot_map),
+                     int(y), int(x), float(energy), _ptr(out))
+    return out
+
+
+def lstm_step(w, obs, h, c):
+    """Returns (action, h', c', logits) without touching the inputs."""
+    w = np.ascontiguousarray(w, np.float32)
+    obs = np.ascontiguousarray(obs, np.float64)
+    h2 = np.array(h, np.float64)
+    c2 = np.array(c, np.float64)
+    logits = np.zeros(NACT, np.float64)
+    a = lib().or_lstm_step(_ptr(w), _ptr(obs), _ptr(h2), _ptr(c2), _ptr(logits))
+    return a, h2, c2, logits
+
+
+class OracleWorld:
+    """One oracle world; the fields are numpy views into the C arrays."""
+
+    def __init__(self, params, seed: int):
+        self.p = make_params(params)
+        self.seed = int(seed)
+        h = ctypes.c_void_p()
+        rc = lib().or_world_create(ctypes.byref(self.p), self.seed, ctypes.byref(h))
+        if rc != 0:
+            raise ValueError(f"or_world_create failed ({rc})")
+        self._h = h
+        H, W, C = self.p.H, self.p.W, max(self.p.capacity, 1)
+        f = self._field
+        self.res = f(F_RES, np.uint8, (H, W))
+        self.wall = f(F_WALL, np.uint8, (H, W))
+        self.slot_map = f(F_SLOT_MAP, np.int32, (H, W))
+        self.alive = f(F_ALIVE, np.uint8, (C,))
+        self.y = f(F_Y, np.int32, (C,))
+        self.x = f(F_X, np.int32, (C,))
+        self.energy = f(F_ENERGY, np.float32, (C,))
+        self.repr_ctr = f(F_REPR_CTR, np.int32, (C,))
+        self.low_ctr = f(F_LOW_CTR, np.int32, (C,))
+        self.age = f(F_AGE, np.int32, (C,))
+        self.h = f(F_H, np.float64, (C, HID))
+        self.c = f(F_C, np.float64, (C, HID))
+        self.action = f(F_ACTION, np.int32, (C,))
+        self.logits = f(F_LOGITS, np.float64, (C, NACT))
+        self.ate = f(F_ATE, np.uint8, (C,))
+        self.weights = f(F_WEIGHTS, np.float32, (C, NPARAM))
+        self.counters = f(F_COUNTERS, np.int64, (8,))
+        self.thr = f(F_THR, np.uint32, (H, 4))
+        self.birth_parent = f(F_BIRTH_PARENT, np.int32, (C,))
+        self.birth_child = f(F_BIRTH_CHILD, np.int32, (C,))
+
+    def _field(self, fid, dtype, shape):
+        addr = lib().or_world_field(self._h, fid)
+        n = int(np.prod(shape))
+        buf = (ctypes.c_char * (n * np.dtype(dtype).itemsize)).from_address(addr)
+        return np.frombuffer(buf, dtype=dtype, count=n).reshape(shape)
+
+    @property
+    def t(self):
+        return int(self.counters[C_T])
+
+    @property
+    def population(self):
+        return int(self.counters[C_POP])
+
+    def step(self, forced=None):
+        if forced is None:
+            rc = lib().or_world_step(self._h, None)
+        else:
+            fa = np.ascontiguousarray(forced, np.int32)
+            assert fa.shape[0] >= self.p.capacity
+            rc = lib().or_world_step(self._h, _ptr(fa))
+        if rc != 0:
+            raise RuntimeError(f"or_world_step failed ({rc})")
+
+    def sync(self):
+        """Rebuild slot_map/thresholds after fields were written directly."""
+        if lib().or_world_sync(self._h) != 0:
+            raise ValueError("inconsistent agent placement")
+
+    def close(self):
+        if self._h:
+            lib().or_world_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

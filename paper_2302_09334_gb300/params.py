@@ -1,0 +1,78 @@
+"""World parameters and the named workloads.
+
+`EcoParams` mirrors the C struct of the library header field for field; the
+presets are the synthetic worlds shaped like the paper's natural environment
+(App. B.4 hyper-parameters: a 200x400 grid, thousands of agents, runs meant
+for 10^6 steps) at three scales.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+INT32_MAX = 2**31 - 1
+
+
+@dataclasses.dataclass
+class EcoParams:
+    H: int = 20
+    W: int = 40
+    capacity: int = 256
+    n_agents0: int = 64
+    border_walls: int = 1
+    res_init_p: float = 0.1
+    nbr_shape: int = 0            # 0: square (Chebyshev) radius, 1: diamond
+    nbr_radius: int = 2
+    class_edges: tuple = (1, 3, 5)  # classes 0 | 1-2 | 3-4 | >=5
+    p_class: tuple = (0.0, 0.001, 0.005, 0.025)
+    lat_mode: int = 0             # 0: linear, 1: (alpha^x + 1)/(alpha + 1)
+    lat_top: float = 0.2
+    lat_bottom: float = 1.0
+    lat_alpha: float = 200.0
+    p_spont: float = 1e-5
+    e0: float = 1.0
+    e_decay: float = 0.01
+    e_gain: float = 0.2
+    e_max: float = math.inf
+    e_repr: float = 0.5
+    t_repr: int = 50
+    e_death: float = 0.0
+    t_death: int = 0
+    max_age: int = INT32_MAX
+    wall_kills: int = 0
+    w_init_std: float = 0.1
+    mut_std: float = 0.02
+
+    def replace(self, **kw) -> "EcoParams":
+        return dataclasses.replace(self, **kw)
+
+    def asdict(self) -> dict:
+        return dataclasses.asdict(self)
+
+
+def small_20x40() -> EcoParams:
+    """20x40 grid, 64 agents (capacity 256); the parity world."""
+    return EcoParams()
+
+
+def paper_200x400() -> EcoParams:
+    """Paper-scale 200x400 grid (App. B.4), 1000 agents, capacity 8192."""
+    return EcoParams(H=200, W=400, capacity=8192, n_agents0=1000)
+
+
+def large_1000x2000() -> EcoParams:
+    """1000x2000 grid, 20,000 agents, capacity 131,072 (12.2 GB of weights)."""
+    return EcoParams(H=1000, W=2000, capacity=131072, n_agents0=20000)
+
+
+def held(p: EcoParams) -> EcoParams:
+    """Held population: no energy decay and no reproduction, so the agent
+    count stays at n_agents0 (roofline microbenchmark)."""
+    return p.replace(e_decay=0.0, t_repr=INT32_MAX)
+
+
+PRESETS = {
+    "small_20x40": small_20x40,
+    "paper_200x400": paper_200x400,
+    "large_1000x2000": large_1000x2000,
+}
