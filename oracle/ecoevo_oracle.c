@@ -123,7 +123,9 @@ static int count_class(const OrParams *p, int n) {
 /* Synchronous pass: every count reads res_old only.  A cell that is a wall
  * or already holds a resource is copied; an empty cell counts the resources
  * in its neighbourhood (cells off the grid count zero), picks its count
- * class and grows iff its Philox word is below the row/class threshold. */
+ * class and grows iff its Philox word is below the row/class threshold.
+ * The word of cell (y, x) at step t is lane x%4 of the draw
+ * {x/4, t, TAG_REGROW, y}; every cell-keyed stream uses this layout. */
 void or_regrow(const OrParams *p, uint64_t seed, uint32_t t,
                const uint32_t *thr, const uint8_t *res_old,
                const uint8_t *wall, uint8_t *res_new) {
@@ -145,8 +147,8 @@ void or_regrow(const OrParams *p, uint64_t seed, uint32_t t,
         }
       }
       int cls = count_class(p, n);
-      uint32_t u = philox_word(seed, (uint32_t)cell >> 2, t, OR_TAG_REGROW, 0u,
-                               cell & 3);
+      uint32_t u = philox_word(seed, (uint32_t)x >> 2, t, OR_TAG_REGROW,
+                               (uint32_t)y, x & 3);
       res_new[cell] = (u < thr[y * 4 + cls]) ? 1 : 0;
     }
   }
@@ -359,8 +361,8 @@ int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
     w->slot_map[cell] = -1;
     w->claim[cell] = -1;
     if (w->wall[cell]) continue;
-    uint32_t u = philox_word(seed, (uint32_t)cell >> 2, 0u, OR_TAG_RES_INIT, 0u,
-                             (int)(cell & 3));
+    uint32_t u = philox_word(seed, (uint32_t)(cell % W) >> 2, 0u, OR_TAG_RES_INIT,
+                             (uint32_t)(cell / W), (int)(cell % W) & 3);
     w->res[cell] = (u < thr_init) ? 1 : 0;
   }
 
@@ -378,8 +380,8 @@ int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
     size_t k = 0;
     for (size_t cell = 0; cell < HW; ++cell) {
       if (w->wall[cell]) continue;
-      uint32_t u = philox_word(seed, (uint32_t)cell >> 2, 0u, OR_TAG_PLACE, 0u,
-                               (int)(cell & 3));
+      uint32_t u = philox_word(seed, (uint32_t)(cell % W) >> 2, 0u, OR_TAG_PLACE,
+                               (uint32_t)(cell / W), (int)(cell % W) & 3);
       keys[k++] = ((uint64_t)u << 32) | (uint64_t)cell;
     }
     qsort(keys, nfree, sizeof(uint64_t), cmp_u64);

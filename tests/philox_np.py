@@ -33,10 +33,10 @@ def philox(c0, c1, c2, c3, k0, k1):
     return c0, c1, c2, c3
 
 
-def cell_words(seed: int, n_cells: int, c1: int, tag: int) -> np.ndarray:
-    """Word cell%4 of the draw {cell/4, c1, tag, 0} for every cell."""
-    cells = np.arange(n_cells, dtype=np.uint64)
-    q = (cells >> np.uint64(2)).astype(np.uint32)
-    out = philox(q, c1, tag, 0, seed & 0xFFFFFFFF, seed >> 32)
+def grid_words(seed: int, H: int, W: int, c1: int, tag: int) -> np.ndarray:
+    """[H, W] array: word x%4 of the draw {x/4, c1, tag, y} for every cell."""
+    ys, xs = np.mgrid[0:H, 0:W]
+    out = philox((xs >> 2).astype(np.uint32), c1, tag, ys.astype(np.uint32),
+                 seed & 0xFFFFFFFF, seed >> 32)
     lanes = np.stack(out, axis=-1)
-    return lanes[np.arange(n_cells), (cells & np.uint64(3)).astype(np.int64)]
+    return np.take_along_axis(lanes, (xs & 3)[..., None], axis=-1)[..., 0]

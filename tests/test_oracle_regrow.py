@@ -42,7 +42,7 @@ def _reconstruct(p: EcoParams, seed, t, res, wall, thr):
     counts = signal.convolve2d(res.astype(np.int64), _kernel(p.nbr_shape, p.nbr_radius),
                                mode="same", boundary="fill", fillvalue=0)
     cls = (counts[..., None] >= np.array(p.class_edges)[None, None, :]).sum(-1)
-    u = philox_np.cell_words(seed, p.H * p.W, t, 1).reshape(p.H, p.W)
+    u = philox_np.grid_words(seed, p.H, p.W, t, 1)
     rows = np.arange(p.H)[:, None].repeat(p.W, 1)
     grow = u < thr[rows, cls]
     empty = (res == 0) & (wall == 0)

@@ -39,10 +39,10 @@ def test_initial_state_reconstruction(oracle):
     wall = np.zeros((H, W), np.uint8)
     wall[0, :] = wall[-1, :] = wall[:, 0] = wall[:, -1] = 1
     np.testing.assert_array_equal(w.wall, wall)
-    u = philox_np.cell_words(seed, H * W, 0, 3).reshape(H, W)
+    u = philox_np.grid_words(seed, H, W, 0, 3)
     res = ((u < math.floor(0.1 * 2**32)) & (wall == 0)).astype(np.uint8)
     np.testing.assert_array_equal(w.res, res)
-    key = philox_np.cell_words(seed, H * W, 0, 2).astype(np.uint64)
+    key = philox_np.grid_words(seed, H, W, 0, 2).ravel().astype(np.uint64)
     cells = np.arange(H * W, dtype=np.uint64)
     free = wall.ravel() == 0
     order = np.argsort((key[free] << np.uint64(32)) | cells[free], kind="stable")
