@@ -1,0 +1,300 @@
+"""Throughput of the simulation step on GB300: agent-steps/s at 200x400.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--workload paper_200x400|large_1000x2000|small_20x40]
+
+A step is one pass of the whole path (regrowth, observation + LSTM, moves,
+physiology, births) over one world.  The world is synthetic (seeded), shaped
+like the paper's natural environment: a 200x400 grid, 1000 agents at the
+start, capacity 8192, free-running population.  Inputs fit in L2 (129 MB),
+so L2 is flushed (256 MB write) before every timed step; each step is timed
+with CUDA events on the world's stream and the step times are summed.
+
+Under torchrun (N > 1) every rank steps its own world (seed = rank): worlds
+are independent, there is no collective on the data path ("replicas only").
+--impl reference times the CPU oracle on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# algorithmic bytes of the observation + LSTM kernel per agent:
+# 93,332 B of weights (4 blocks + read-out), h and c read and written
+# (4 x 128 B), position, energy, action and logits (36 B)
+LSTM_BYTES_PER_AGENT = 93332 + 512 + 36
+L2_FLUSH_BYTES = 256 << 20
+
+
+def lstm_bytes(n_agents: int, H: int, W: int) -> int:
+    # + the three observation channels of the grid, one bit per cell
+    return n_agents * LSTM_BYTES_PER_AGENT + 3 * H * W // 8
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_oracle_sample(params, seed: int, budget_s: float, max_steps: int):
+    """Time the CPU oracle stepping the same world; returns (agent-steps/s,
+    steps, seconds)."""
+    from oracle import pyoracle
+    ow = pyoracle.OracleWorld(params.asdict(), seed)
+    agent_steps, steps = 0, 0
+    t0 = time.perf_counter()
+    while steps < max_steps and (time.perf_counter() - t0) < budget_s:
+        agent_steps += ow.population
+        ow.step()
+        steps += 1
+    dt = time.perf_counter() - t0
+    ow.close()
+    return agent_steps / dt, steps, dt
+
+
+def bench_reference(args, params, rank, world_size):
+    if rank != 0:
+        return
+    from oracle import build as oracle_build
+    oracle_build.build()
+    from oracle import pyoracle
+    ow = pyoracle.OracleWorld(params.asdict(), 0)
+    for _ in range(args.warmup):
+        ow.step()
+    agent_steps = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        agent_steps += ow.population
+        ow.step()
+    dt = time.perf_counter() - t0
+    v = agent_steps / dt
+    line = {
+        "impl": "reference", "metric": "agent-steps/s at 200x400", "value": v,
+        "unit": "agent-steps/s", "n_gpus": world_size, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(args, params),
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "agent-steps/s",
+                         "sample": f"{args.workload} seed 0, steps {args.warmup + 1}.."
+                                   f"{args.warmup + args.steps}, single-threaded C oracle"},
+        "e2e": {"value": v, "unit": "agent-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args, params):
+    return {"workload": args.workload, "H": params.H, "W": params.W,
+            "n_agents0": params.n_agents0, "capacity": params.capacity, "seed": "rank",
+            "population": "free-running", "l2": "flushed (256 MB write) before every step",
+            "parallelism": f"replicas{args.gpus}"}
+
+
+def bench_ours(args, params, rank, world_size, dist):
+    import torch
+    from paper_2302_09334_gb300 import build as lib_build
+    lib_build.build()
+    from paper_2302_09334_gb300._lib import lib
+    from paper_2302_09334_gb300.world import World
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    world = World(params, seed=rank, device=local)
+    stream = world.stream
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    kps = lib().eco_kernels_per_step()
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+
+    for _ in range(args.warmup):
+        flush_l2()
+        world.step(1)
+    world.sync()
+
+    world.profile(True, max_steps=args.steps)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    pops = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            pops.append(int(world.counters()[1]))
+            flush_l2()
+            starts[k].record(stream)
+            world.step(1)
+            ends[k].record(stream)
+        world.sync()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    prof = world.profile_read()
+    world.profile(False)
+    agent_steps = sum(pops)
+    cell_steps = params.H * params.W * args.steps
+
+    # e2e through the C ABI with host buffers: upload the start state from
+    # host memory, then every step read counters and agent positions and
+    # energies back to host memory.
+    alive_slots = world.read_state(fields=("alive",))["alive"].nonzero()[0]
+    hi = int(alive_slots.max()) + 1 if alive_slots.size else 0
+    e2e_state = world.read_state(weights=(0, hi))
+    read_fields = ("alive", "y", "x", "energy")
+    h2d = sum(v.nbytes for k, v in e2e_state.items() if k not in ("slot_map",))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    world.load_state(e2e_state)
+    e2e_agent_steps = 0
+    d2h = 0
+    for _ in range(args.steps):
+        world.step(1)
+        out = world.read_state(fields=read_fields)
+        e2e_agent_steps += int(out["counters"][1])
+        d2h = sum(v.nbytes for v in out.values())
+    e2e_dt = time.perf_counter() - t0
+
+    stats = torch.tensor([total_ms, float(agent_steps), float(cell_steps), e2e_dt,
+                          float(e2e_agent_steps)], dtype=torch.float64, device=dev)
+    if dist:
+        mx = stats.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = stats.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        total_ms, e2e_dt = float(mx[0]), float(mx[3])
+        agent_steps, cell_steps, e2e_agent_steps = float(sm[1]), float(sm[2]), float(sm[4])
+    if rank != 0:
+        return
+    value = agent_steps / (total_ms / 1e3)
+    lstm_ms, lstm_n = prof["observe_lstm"]
+    peak, peak_kind = load_peaks()
+    bytes_lstm = sum(lstm_bytes(n, params.H, params.W) for n in pops)
+    achieved = bytes_lstm / (lstm_ms / 1e3) / 1e9 if lstm_ms > 0 else None
+    line = {
+        "metric": "agent-steps/s at 200x400", "value": value, "unit": "agent-steps/s",
+        "n_gpus": world_size, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_of(args, params),
+        "cell_steps_per_s": cell_steps / (total_ms / 1e3),
+        "mean_population": agent_steps / max(args.steps * world_size, 1),
+        "kernel_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
+        "roofline": {"kernel": "observe_lstm", "bound": "hbm", "achieved": achieved,
+                     "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "bytes_per_launch": bytes_lstm / max(lstm_n, 1)},
+        "gpu_launches": kps * args.steps,
+        "e2e": {"value": e2e_agent_steps / e2e_dt, "unit": "agent-steps/s",
+                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h},
+        "clocks": clocks.summary(),
+    }
+    if not args.no_cpu_baseline:
+        v, n, dt = run_oracle_sample(params, 0, args.cpu_budget, 100000)
+        line["cpu_baseline"] = {"value": v, "unit": "agent-steps/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{args.workload} seed 0, first {n} steps "
+                                          f"({dt:.1f} s, single-threaded C oracle)"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="paper_200x400")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    from paper_2302_09334_gb300.params import PRESETS
+    params = PRESETS[args.workload]()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world_size = int(os.environ.get("WORLD_SIZE", "1"))
+    dist = None
+    if world_size > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    try:
+        if args.impl == "reference":
+            bench_reference(args, params, rank, world_size)
+        else:
+            bench_ours(args, params, rank, world_size, dist)
+    finally:
+        if dist:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

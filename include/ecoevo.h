@@ -1,0 +1,213 @@
+/*
+ * ecoevo.h -- C ABI of libecoevo, the GB300 (sm_103a) simulation step of
+ * non-episodic neuroevolution in a large multi-agent common-pool-resource
+ * grid world (Hamon, Nisioti, Moulin-Frier, 2023).
+ *
+ * One call of eco_world_step advances a world by whole steps.  A step is,
+ * in order (each part is a CUDA kernel of this library):
+ *   a1 regrowth of the resource field      App. B.1, Eq. (1)
+ *   a2 observation of the 7x7x3 window      App. B.2, sensorimotor ability
+ *   a3 one LSTM step per agent + argmax     App. B.2, cognitive capacity
+ *   a4 moves (one claim round) and eating   App. B.2
+ *   a5 physiology and death                 App. B.2 physiology, App. B.3 death
+ *   a6 reproduction: slot compaction and    App. B.3 reproduction
+ *      Gaussian mutation of the parent's weights
+ *
+ * Conventions, for every entry point:
+ *   - Return ECO_OK (0) on success or a negative ECO_E* code.
+ *   - Pointers named *_host are host memory; everything else handed to the
+ *     library is a device pointer of the current CUDA device.
+ *   - Work is enqueued on the world's CUDA stream and is asynchronous unless
+ *     the comment says "synchronous".
+ *   - A world is not thread-safe; distinct worlds may be used from distinct
+ *     host threads.
+ *   - Device-side waits are bounded: a wait that runs out sets a status bit
+ *     that eco_world_sync / eco_batch_sync return as ECO_ETIMEOUT.
+ */
+#ifndef ECOEVO_H
+#define ECOEVO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ECO_ABI_V1 0x45434F01u
+
+/* Error codes. */
+#define ECO_OK 0
+#define ECO_EINVAL -1    /* invalid argument or parameter block            */
+#define ECO_ENOMEM -2    /* arena too small, or an allocation failed       */
+#define ECO_ECUDA -3     /* a CUDA runtime call failed                     */
+#define ECO_ETIMEOUT -4  /* a bounded device wait ran out                  */
+#define ECO_ESTATE -5    /* loaded state is inconsistent (shared cell ...) */
+
+/* Fixed controller shape (7x7 view, 3 channels + energy, hidden 32). */
+#define ECO_NOBS 148
+#define ECO_HIDDEN 32
+#define ECO_NACT 5
+#define ECO_NPARAM 23333 /* logical parameter vector of one agent */
+
+/* World parameters; all plain data.  Field meanings:
+ *   H, W            grid rows (latitude axis, row 0 = top) and columns
+ *   capacity        agent slots; births past the free slots are dropped
+ *   n_agents0       agents placed at random free cells at creation
+ *   border_walls    1: the outer ring of cells is wall (App. B.1)
+ *   res_init_p      Bernoulli density of the initial resources
+ *   nbr_shape       0: square (Chebyshev) neighbourhood, 1: diamond
+ *   nbr_radius      1..3, the centre cell is never counted
+ *   class_edges     count class = number of edges <= count (4 classes)
+ *   p_class         p_I per count class                    Eq. (1)
+ *   lat_mode        0: linear climate lat_top -> lat_bottom over the rows;
+ *                   1: c = (alpha^x + 1)/(alpha + 1), x = row/(H-1)
+ *   p_spont         spontaneous growth probability c        Eq. (1)
+ *   e0, e_decay, e_gain, e_max   initial energy, decay per step, gain per
+ *                   resource eaten, clip                    App. B.2
+ *   e_repr, t_repr  reproduce after t_repr consecutive steps above e_repr
+ *   e_death, t_death  die after max(t_death,1) consecutive steps at or below
+ *                   e_death;  max_age: die when age exceeds it   App. B.3
+ *   wall_kills      1: an agent moving into a wall or off the grid dies
+ *                   (App. B.1); 0: the move is blocked
+ *   w_init_std      std of the initial weights; mut_std: std sigma of the
+ *                   mutation noise N(0, sigma)                  App. B.3
+ * Sizes: 3 <= H, W <= 16384 with H*W <= 2^26; capacity <= 2^24. */
+typedef struct EcoParams {
+  uint32_t abi_version; /* must be ECO_ABI_V1 */
+  int32_t H, W, capacity, n_agents0;
+  int32_t border_walls;
+  double res_init_p;
+  int32_t nbr_shape, nbr_radius;
+  int32_t class_edges[3];
+  double p_class[4];
+  int32_t lat_mode;
+  double lat_top, lat_bottom, lat_alpha;
+  double p_spont;
+  float e0, e_decay, e_gain, e_max;
+  float e_repr;
+  int32_t t_repr;
+  float e_death;
+  int32_t t_death, max_age;
+  int32_t wall_kills;
+  float w_init_std, mut_std;
+} EcoParams;
+
+/* Counters (int64), indices into EcoState.counters. */
+#define ECO_C_T 0            /* steps taken                       */
+#define ECO_C_POP 1          /* living agents                     */
+#define ECO_C_BIRTHS 2       /* births so far                     */
+#define ECO_C_DEATHS 3       /* deaths so far                     */
+#define ECO_C_DROPPED 4      /* births dropped for lack of a slot */
+#define ECO_C_BIRTHS_LAST 5  /* births of the last step           */
+#define ECO_C_DEATHS_LAST 6
+#define ECO_C_DROPPED_LAST 7
+#define ECO_NCOUNTERS 8
+
+/* Host-side view of a world's state.  Every pointer is caller-owned host
+ * memory and may be NULL to skip that field.  Grid fields are unpacked
+ * uint8 [H*W] row-major; per-slot fields have `capacity` entries; h, c are
+ * [capacity*32]; logits [capacity*5]; weights are logical parameter
+ * vectors [weights_count * 23333] for slots weights_first ..
+ * weights_first + weights_count - 1, laid out as
+ *   W[r][k]  r < 128 gate rows (i, f, g, o blocks of 32), k < 180
+ *            (148 observation inputs, then 32 hidden inputs)   [0, 23040)
+ *   b[r]                                                    [23040, 23168)
+ *   Wo[a][j] a < 5, j < 32                                  [23168, 23328)
+ *   bo[a]                                                   [23328, 23333) */
+typedef struct EcoState {
+  int64_t counters[ECO_NCOUNTERS];
+  uint8_t *res_host, *wall_host;
+  int32_t *slot_map_host;  /* read only: -1 or the slot on the cell */
+  uint8_t *alive_host;
+  int32_t *y_host, *x_host;
+  float *energy_host;
+  int32_t *repr_ctr_host, *low_ctr_host, *age_host;
+  float *h_host, *c_host;
+  int32_t *action_host;    /* the controller's argmax of the last step */
+  float *logits_host;
+  float *weights_host;
+  int32_t weights_first, weights_count;
+} EcoState;
+
+typedef struct EcoWorld EcoWorld;
+typedef struct EcoBatch EcoBatch;
+
+/* Device bytes a world of these parameters needs (0 if they are invalid).
+ * Synchronous, host only. */
+size_t eco_world_bytes(const EcoParams *params);
+
+/* Create a world (App. B.4: random walls border, random resources, random
+ * placement of n_agents0 agents, random weights, all drawn from `seed`).
+ *   arena, arena_bytes: caller-owned device memory of at least
+ *     eco_world_bytes(params), 256-byte aligned, kept alive until
+ *     eco_world_destroy; or NULL/0 to let the library allocate and own it.
+ *   stream: cudaStream_t all work of the world is enqueued on; must not be
+ *     the legacy default stream (0), since steps are replayed as CUDA graphs.
+ * Synchronous (returns once the initial state is on the device).
+ * Errors: ECO_EINVAL (params, alignment, stream), ECO_ENOMEM, ECO_ECUDA. */
+int eco_world_create(const EcoParams *params, uint64_t seed, void *arena,
+                     size_t arena_bytes, void *stream, EcoWorld **out);
+
+/* Release the world (and its arena if the library allocated it). */
+void eco_world_destroy(EcoWorld *world);
+
+/* Advance the world by n_steps >= 0 whole steps (a1..a6 each step).
+ * Asynchronous.  Errors: ECO_EINVAL, ECO_ECUDA. */
+int eco_world_step(EcoWorld *world, int64_t n_steps);
+
+/* One step in which moves use the given actions instead of the controller's
+ * argmax; the controller still runs and its argmax is kept as `action`.
+ * actions: int32 [capacity] (values 0..4; 0 = stay, 1 N, 2 S, 3 E, 4 W),
+ * on the host if actions_on_host != 0, else on the device.  Synchronous
+ * when actions_on_host.  Test hook for multi-step parity runs. */
+int eco_world_step_forced(EcoWorld *world, const int32_t *actions,
+                          int actions_on_host);
+
+/* Copy the state into `out` (see EcoState).  Synchronous. */
+int eco_world_read_state(EcoWorld *world, EcoState *out);
+
+/* Replace the state by `in`: every non-NULL field is written; slot_map,
+ * the population and the free/alive lists are rebuilt from alive, y, x.
+ * counters[ECO_C_T] and the cumulative counters are taken from `in` when
+ * set_counters != 0.  h and c become the recurrent state for the next step.
+ * Synchronous.  Errors: ECO_EINVAL, ECO_ESTATE (two agents on one cell, an
+ * agent on a wall or off the grid, res set on a wall), ECO_ECUDA. */
+int eco_world_load_state(EcoWorld *world, const EcoState *in, int set_counters);
+
+/* Wait for the world's stream; returns ECO_ETIMEOUT if a device wait ran
+ * out, ECO_ECUDA on a CUDA error, else ECO_OK.  Synchronous. */
+int eco_world_sync(EcoWorld *world);
+
+/* The world's parameters and CUDA stream. */
+const EcoParams *eco_world_params(const EcoWorld *world);
+void *eco_world_stream(const EcoWorld *world);
+
+/* Batch of independent worlds stepped together: every kernel of a step is
+ * launched once for all of them (work lists over worlds and agents).  The
+ * worlds must live on the current device; the batch uses the first
+ * world's stream.  The worlds must outlive the batch. */
+int eco_batch_create(EcoWorld *const *worlds, int n_worlds, EcoBatch **out);
+int eco_batch_step(EcoBatch *batch, int64_t n_steps);
+int eco_batch_sync(EcoBatch *batch);
+void eco_batch_destroy(EcoBatch *batch);
+
+/* Per-kernel timing with CUDA events on the world's stream.  While enabled,
+ * steps are launched kernel by kernel with an event between kernels;
+ * eco_world_profile_read sums the elapsed times since enabling:
+ * ms[k], launches[k] for k < ECO_NKERNELS (names: eco_kernel_name).
+ * Synchronous read.  max_steps bounds the recorded steps. */
+#define ECO_NKERNELS 8
+int eco_world_profile(EcoWorld *world, int enable, int max_steps);
+int eco_world_profile_read(EcoWorld *world, double *ms, int64_t *launches);
+const char *eco_kernel_name(int k);
+
+/* Number of the library's kernels one step launches. */
+int eco_kernels_per_step(void);
+
+const char *eco_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,216 @@
+// ecoevo_dev.cuh -- device-side data layout and helpers shared by the
+// kernels of libecoevo (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ecoevo.h"
+
+namespace eco {
+
+// ---------------------------------------------------------------------------
+// Controller shape and the physical weight layout in HBM.
+// ---------------------------------------------------------------------------
+constexpr int NOBS = 148;            // 7*7*3 + energy
+constexpr int HID = 32;
+constexpr int NIN = NOBS + HID;      // 180
+constexpr int NGATE = 4 * HID;       // 128
+constexpr int NACT = 5;
+constexpr int NPARAM = 23333;        // logical parameter vector
+constexpr int OFF_B = NGATE * NIN;   // 23040
+constexpr int OFF_WO = OFF_B + NGATE;     // 23168
+constexpr int OFF_BO = OFF_WO + NACT * HID; // 23328
+
+// An agent's weights are stored as four hidden-unit blocks followed by the
+// read-out.  Block q holds the 32 gate rows of hidden units 8q..8q+7, row l
+// of the block being gate (l % 4) of hidden unit 8q + l/4, each row the 180
+// input weights, then the 32 biases of those rows.  One block is the unit of
+// work of the LSTM kernel: it carries every gate of its hidden units, so the
+// cell update needs nothing from the other blocks.
+constexpr int BLK_ROWS = 32;
+constexpr int BLK_FLOATS = BLK_ROWS * NIN + BLK_ROWS;   // 5792
+constexpr int BLK_BYTES = BLK_FLOATS * 4;               // 23168 (16-B multiple)
+constexpr int NBLK = 4;
+constexpr int TAIL = NBLK * BLK_FLOATS;                 // 23168 == OFF_WO
+constexpr int WSTRIDE = 23360;                          // floats, 128-B multiple
+static_assert(TAIL == OFF_WO, "read-out sits at its logical offset");
+static_assert((WSTRIDE * 4) % 128 == 0 && WSTRIDE >= NPARAM, "stride");
+
+// Logical gate row of row l of block q.
+__host__ __device__ inline int blk_row_to_logical(int q, int l) {
+  return (l & 3) * HID + 8 * q + (l >> 2);
+}
+// Physical float offset of logical parameter j.
+__host__ __device__ inline int phys_of_logical(int j) {
+  if (j >= OFF_WO) return j;
+  int r = (j < OFF_B) ? j / NIN : j - OFF_B;
+  int gate = r / HID, jj = r % HID;
+  int q = jj >> 3, l = ((jj & 7) << 2) | gate;
+  if (j < OFF_B) return q * BLK_FLOATS + l * NIN + (j % NIN);
+  return q * BLK_FLOATS + BLK_ROWS * NIN + l;
+}
+// Logical parameter of physical float offset p, or -1 for padding.
+__host__ __device__ inline int logical_of_phys(int p) {
+  if (p >= TAIL) return p < NPARAM ? p : -1;
+  int q = p / BLK_FLOATS, o = p % BLK_FLOATS;
+  if (o < BLK_ROWS * NIN) {
+    int l = o / NIN, k = o % NIN;
+    return blk_row_to_logical(q, l) * NIN + k;
+  }
+  return OFF_B + blk_row_to_logical(q, o - BLK_ROWS * NIN);
+}
+
+// Philox stream tags (third counter word).
+constexpr uint32_t TAG_REGROW = 1u, TAG_PLACE = 2u, TAG_RES_INIT = 3u,
+                   TAG_INIT_W = 4u, TAG_MUT = 5u;
+
+// Status bits written by kernels.
+constexpr int ST_TIMEOUT = 1;
+constexpr int ST_STATE = 2;
+
+// ---------------------------------------------------------------------------
+// Per-world device structures.
+// ---------------------------------------------------------------------------
+struct Counters {            // mutable, updated by the kernels
+  long long t, pop, births, deaths, dropped, births_last, deaths_last,
+      dropped_last;
+  int deaths_step;           // atomically accumulated during a step
+  int n_births;              // births of the step, read by the spawn kernel
+  unsigned births_t;         // step index the births belong to
+  int use_forced;            // moves read `forced` instead of `action`
+  int status;                // ST_* bits
+  int pad[3];
+};
+
+struct WorldDev {            // read-only while kernels run
+  int H, W, Wp, C;
+  int nbr_shape, nbr_radius;
+  int class_edges[3];
+  int t_repr, t_death, max_age, wall_kills;
+  float e0, e_decay, e_gain, e_max, e_repr, e_death, mut_std, w_init_std;
+  uint32_t key0, key1;
+  uint32_t *thr;             // [H][4]
+  uint32_t *res0, *res1;     // bit planes [H][Wp]; current = t even ? res0 : res1
+  uint32_t *wall;            // [H][Wp]
+  int32_t *slot_map;         // [H*W]  -1 free
+  int32_t *claim;            // [H*W]  INT32_MAX free (move claims)
+  int32_t *bclaim;           // [H*W]  INT32_MAX free (birth claims)
+  uint8_t *alive, *killed, *ate, *flag;
+  int32_t *y, *x;
+  float *energy;
+  int32_t *repr_ctr, *low_ctr, *age;
+  int32_t *action, *forced, *target, *birth_cell;
+  uint32_t *arrive;          // LSTM block arrivals per slot
+  float *h0, *h1;            // [C][32]; h read at step t = t even ? h0 : h1
+  float *c;                  // [C][32]
+  float *logits;             // [C][8]
+  int32_t *alive_list;       // [C] slots alive at the start of the step
+  int32_t *free_list, *birth_parent, *birth_child;  // [C]
+  float *weights;            // [C][WSTRIDE], 256-B aligned
+  Counters *ctr;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11) and normals.
+// ---------------------------------------------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__host__ __device__ inline U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+#ifdef __CUDA_ARCH__
+    uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+#else
+    uint64_t p0 = 0xD2511F53ull * c.x, p1 = 0xCD9E8D57ull * c.z;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+    c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+  }
+  return c;
+}
+
+#ifdef __CUDACC__
+// Box-Muller pair from two words, in float.  ln(u1) is taken on the side of
+// 1/2 where it is well conditioned (log of u1, or log1p of -(1 - u1) built
+// from the complement word), and the angle is reduced by quadrant from the
+// top two bits of x2 so that sincospi sees an argument below 1/2.
+__device__ inline void box_muller_f(uint32_t x1, uint32_t x2, float &z0,
+                                    float &z1) {
+  const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
+  float ln_u1;
+  if (x1 < 0x80000000u)
+    ln_u1 = logf(((float)x1 + 0.5f) * two_m32);
+  else
+    ln_u1 = log1pf(-(((float)(~x1) + 0.5f) * two_m32));
+  float r = sqrtf(-2.0f * ln_u1);
+  uint32_t quad = x2 >> 30;
+  float f = ((float)(x2 & 0x3FFFFFFFu) + 0.5f) * 9.313225746154785e-10f;  // 2^-30
+  float s, c;
+  sincospif(0.5f * f, &s, &c);  // angle = pi/2 * (quad + f)
+  float cs, sn;
+  switch (quad) {
+    case 0: cs = c; sn = s; break;
+    case 1: cs = -s; sn = c; break;
+    case 2: cs = -c; sn = -s; break;
+    default: cs = s; sn = -c; break;
+  }
+  z0 = r * cs;
+  z1 = r * sn;
+}
+
+// Four normals of the draw {q, t, tag, id}: (cos, sin) of lanes (0,1), then
+// of lanes (2,3).
+__device__ inline void normals4(uint32_t k0, uint32_t k1, uint32_t q,
+                                uint32_t t, uint32_t tag, uint32_t id,
+                                float z[4]) {
+  U4 r = philox4x32_10(U4{q, t, tag, id}, k0, k1);
+  box_muller_f(r.x, r.y, z[0], z[1]);
+  box_muller_f(r.z, r.w, z[2], z[3]);
+}
+
+__device__ inline bool bit_at(const uint32_t *plane, int Wp, int y, int x) {
+  return (plane[y * Wp + (x >> 5)] >> (x & 31)) & 1u;
+}
+#endif
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (one per kernel source).
+// ---------------------------------------------------------------------------
+struct BatchDev {
+  WorldDev *const *worlds;   // device array [n]
+  int n;
+  int *tile_prefix;          // device [n+1]: regrowth tiles per world
+  int *slot_block_prefix;    // device [n+1]: 256-slot blocks per world
+  int total_tiles, total_slot_blocks;
+  int max_capacity;
+  int n_sms;
+};
+
+void launch_regrow(const BatchDev &b, cudaStream_t s);
+void launch_lstm(const BatchDev &b, cudaStream_t s);
+void launch_move_claim(const BatchDev &b, cudaStream_t s);
+void launch_move_apply(const BatchDev &b, cudaStream_t s);
+void launch_physio(const BatchDev &b, cudaStream_t s);
+void launch_birth_claim(const BatchDev &b, cudaStream_t s);
+void launch_scan(const BatchDev &b, cudaStream_t s);
+void launch_spawn(const BatchDev &b, cudaStream_t s);
+void configure_lstm();   // once per device, before the first launch
+// Load every step kernel's code before a step is captured in a graph.
+void preload_regrow();
+void preload_lstm();
+void preload_agents();
+// set-up and state I/O
+void launch_init_world(const WorldDev *wd_host, WorldDev *wd_dev, int n0,
+                       const int32_t *place_y, const int32_t *place_x,
+                       int border, uint32_t thr_init, int n_sms, cudaStream_t s);
+void launch_rebuild(const WorldDev *wd_host, int n_sms, cudaStream_t s);
+
+constexpr int SCAN_THREADS = 1024;
+constexpr int SLOT_BLOCK = 256;
+constexpr int REGROW_ROWS = 8, REGROW_WORDS = 4;
+
+}  // namespace eco

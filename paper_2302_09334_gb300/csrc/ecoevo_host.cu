@@ -1,0 +1,758 @@
+// ecoevo_host.cu -- the C ABI of libecoevo (include/ecoevo.h): world
+// layout in one device arena, creation, stepping (CUDA graphs of whole
+// steps), state I/O, batches and per-kernel profiling.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ecoevo_dev.cuh"
+
+using namespace eco;
+
+namespace {
+
+constexpr int STEPS_PER_GRAPH = 16;
+
+// ---------------------------------------------------------------------------
+// Parameters and the arena layout.
+// ---------------------------------------------------------------------------
+bool params_ok(const EcoParams *p) {
+  if (!p || p->abi_version != ECO_ABI_V1) return false;
+  if (p->H < 1 || p->W < 1 || p->H > 16384 || p->W > 16384) return false;
+  if ((long long)p->H * p->W > (1ll << 26)) return false;
+  if (p->capacity < 0 || p->capacity > (1 << 24)) return false;
+  if (p->n_agents0 < 0 || p->n_agents0 > p->capacity) return false;
+  if (p->nbr_shape != 0 && p->nbr_shape != 1) return false;
+  if (p->nbr_radius < 1 || p->nbr_radius > 3) return false;
+  if (!(p->class_edges[0] <= p->class_edges[1] && p->class_edges[1] <= p->class_edges[2]))
+    return false;
+  if (p->lat_mode != 0 && p->lat_mode != 1) return false;
+  if (p->t_repr < 0 || p->t_death < 0 || p->max_age < 0) return false;
+  if (p->border_walls != 0 && p->border_walls != 1) return false;
+  return true;
+}
+
+struct Layout {
+  size_t ctr, wdev, tab_worlds, tab_tiles, tab_blocks, thr, res0, res1, wall,
+      slot_map, claim, bclaim, alive, killed, ate, flag, y, x, energy, repr_ctr,
+      low_ctr, age, action, forced, target, birth_cell, arrive, h0, h1, c,
+      logits, alive_list, free_list, birth_parent, birth_child, weights, total;
+};
+
+Layout layout_of(const EcoParams *p) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return at;
+  };
+  const size_t H = p->H, W = p->W, Wp = (p->W + 31) / 32, C = p->capacity;
+  const size_t C1 = C ? C : 1;
+  L.ctr = take(sizeof(Counters));
+  L.wdev = take(sizeof(WorldDev));
+  L.tab_worlds = take(sizeof(WorldDev *));
+  L.tab_tiles = take(2 * sizeof(int));
+  L.tab_blocks = take(2 * sizeof(int));
+  L.thr = take(H * 4 * 4);
+  L.res0 = take(H * Wp * 4);
+  L.res1 = take(H * Wp * 4);
+  L.wall = take(H * Wp * 4);
+  L.slot_map = take(H * W * 4);
+  L.claim = take(H * W * 4);
+  L.bclaim = take(H * W * 4);
+  L.alive = take(C1);
+  L.killed = take(C1);
+  L.ate = take(C1);
+  L.flag = take(C1);
+  L.y = take(C1 * 4);
+  L.x = take(C1 * 4);
+  L.energy = take(C1 * 4);
+  L.repr_ctr = take(C1 * 4);
+  L.low_ctr = take(C1 * 4);
+  L.age = take(C1 * 4);
+  L.action = take(C1 * 4);
+  L.forced = take(C1 * 4);
+  L.target = take(C1 * 4);
+  L.birth_cell = take(C1 * 4);
+  L.arrive = take(C1 * 4);
+  L.h0 = take(C1 * HID * 4);
+  L.h1 = take(C1 * HID * 4);
+  L.c = take(C1 * HID * 4);
+  L.logits = take(C1 * 8 * 4);
+  L.alive_list = take(C1 * 4);
+  L.free_list = take(C1 * 4);
+  L.birth_parent = take(C1 * 4);
+  L.birth_child = take(C1 * 4);
+  L.weights = take(C1 * (size_t)WSTRIDE * 4);
+  L.total = off;
+  return L;
+}
+
+// Growth thresholds, App. B.1 Eq. (1): p = p_I[class] * climate(row) + c,
+// threshold floor(p * 2^32) (0 when p <= 0, 2^32 - 1 when p >= 1); a cell
+// grows when its Philox word is below the threshold.
+uint32_t threshold_of(double prob) {
+  if (!(prob > 0.0)) return 0u;
+  if (prob >= 1.0) return 0xFFFFFFFFu;
+  return (uint32_t)std::floor(prob * 4294967296.0);
+}
+
+std::vector<uint32_t> threshold_table(const EcoParams *p) {
+  std::vector<uint32_t> thr((size_t)p->H * 4);
+  for (int y = 0; y < p->H; ++y) {
+    const double frac = (p->H > 1) ? (double)y / (double)(p->H - 1) : 0.0;
+    double climate;
+    if (p->lat_mode == 1)
+      climate = (std::pow(p->lat_alpha, frac) + 1.0) / (p->lat_alpha + 1.0);
+    else
+      climate = p->lat_top + (p->lat_bottom - p->lat_top) * frac;
+    for (int k = 0; k < 4; ++k) thr[(size_t)y * 4 + k] = threshold_of(p->p_class[k] * climate + p->p_spont);
+  }
+  return thr;
+}
+
+struct Profile {
+  bool on = false;
+  int max_steps = 0, used = 0;
+  std::vector<cudaEvent_t> ev;  // (ECO_NKERNELS + 1) per step
+  double ms[ECO_NKERNELS] = {0};
+  long long launches[ECO_NKERNELS] = {0};
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Opaque handles.
+// ---------------------------------------------------------------------------
+struct EcoBatch {
+  std::vector<EcoWorld *> worlds;
+  BatchDev bd{};
+  cudaStream_t stream = nullptr;
+  void *table = nullptr;  // device: worlds[], tile prefix, block prefix
+  bool owns_table = false;
+  cudaGraphExec_t g1 = nullptr, gk = nullptr;
+  Profile *prof = nullptr;  // the first world's profiler
+};
+
+struct EcoWorld {
+  EcoParams p{};
+  uint64_t seed = 0;
+  int device = 0;
+  int n_sms = 0;
+  cudaStream_t stream = nullptr;
+  char *arena = nullptr;
+  size_t arena_bytes = 0;
+  bool owns_arena = false;
+  Layout L{};
+  WorldDev hd{};          // host copy of the device descriptor
+  WorldDev *dd = nullptr; // device descriptor
+  EcoBatch self;          // batch of one: this world
+  Profile prof;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return ECO_OK;
+  std::fprintf(stderr, "libecoevo: CUDA error %s\n", cudaGetErrorString(e));
+  return ECO_ECUDA;
+}
+#define ECO_CU(call)                                  \
+  do {                                                \
+    int rc__ = cuda_err(call);                        \
+    if (rc__ != ECO_OK) return rc__;                  \
+  } while (0)
+
+int tiles_of(const WorldDev &wd) {
+  return ((wd.H + REGROW_ROWS - 1) / REGROW_ROWS) *
+         ((wd.Wp + REGROW_WORDS - 1) / REGROW_WORDS);
+}
+int slot_blocks_of(const WorldDev &wd) { return (wd.C + SLOT_BLOCK - 1) / SLOT_BLOCK; }
+
+void launch_step(const EcoBatch &b, cudaStream_t s, Profile *prof, int step_ev) {
+  typedef void (*Launcher)(const BatchDev &, cudaStream_t);
+  static const Launcher order[ECO_NKERNELS] = {
+      launch_regrow, launch_lstm,        launch_move_claim, launch_move_apply,
+      launch_physio, launch_birth_claim, launch_scan,       launch_spawn};
+  for (int k = 0; k < ECO_NKERNELS; ++k) {
+    if (prof) cudaEventRecord(prof->ev[(size_t)step_ev * (ECO_NKERNELS + 1) + k], s);
+    order[k](b.bd, s);
+  }
+  if (prof) cudaEventRecord(prof->ev[(size_t)step_ev * (ECO_NKERNELS + 1) + ECO_NKERNELS], s);
+}
+
+void destroy_graphs(EcoBatch &b) {
+  if (b.g1) cudaGraphExecDestroy(b.g1);
+  if (b.gk) cudaGraphExecDestroy(b.gk);
+  b.g1 = b.gk = nullptr;
+}
+
+int capture(EcoBatch &b, int steps, cudaGraphExec_t *out) {
+  cudaGraph_t g = nullptr;
+  ECO_CU(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < steps; ++i) launch_step(b, b.stream, nullptr, 0);
+  cudaError_t e = cudaStreamEndCapture(b.stream, &g);
+  if (e != cudaSuccess) return cuda_err(e);
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return cuda_err(e);
+}
+
+// Host side of a batch: device table of descriptors and work prefixes.
+int batch_init(EcoBatch &b, EcoWorld *const *worlds, int n, void *table_dev) {
+  b.worlds.assign(worlds, worlds + n);
+  b.stream = worlds[0]->stream;
+  const size_t tab_bytes = n * sizeof(WorldDev *) + 2 * (n + 1) * sizeof(int);
+  if (table_dev) {
+    b.table = table_dev;
+    b.owns_table = false;
+  } else {
+    ECO_CU(cudaMalloc(&b.table, tab_bytes));
+    b.owns_table = true;
+  }
+  std::vector<char> host(tab_bytes);
+  WorldDev **wp = reinterpret_cast<WorldDev **>(host.data());
+  int *tiles = reinterpret_cast<int *>(host.data() + n * sizeof(WorldDev *));
+  int *blocks = tiles + (n + 1);
+  int tt = 0, bb = 0, maxc = 0;
+  for (int i = 0; i < n; ++i) {
+    wp[i] = worlds[i]->dd;
+    tiles[i] = tt;
+    blocks[i] = bb;
+    tt += tiles_of(worlds[i]->hd);
+    bb += slot_blocks_of(worlds[i]->hd);
+    maxc = std::max(maxc, worlds[i]->hd.C);
+  }
+  tiles[n] = tt;
+  blocks[n] = bb;
+  ECO_CU(cudaMemcpy(b.table, host.data(), tab_bytes, cudaMemcpyHostToDevice));
+  b.bd.worlds = reinterpret_cast<WorldDev *const *>(b.table);
+  b.bd.n = n;
+  b.bd.tile_prefix = reinterpret_cast<int *>((char *)b.table + n * sizeof(WorldDev *));
+  b.bd.slot_block_prefix = b.bd.tile_prefix + (n + 1);
+  b.bd.total_tiles = tt;
+  b.bd.total_slot_blocks = bb;
+  b.bd.max_capacity = maxc;
+  b.bd.n_sms = worlds[0]->n_sms;
+  b.prof = &worlds[0]->prof;
+  return ECO_OK;
+}
+
+int batch_step(EcoBatch &b, int64_t n) {
+  if (n < 0) return ECO_EINVAL;
+  Profile *prof = b.prof;
+  if (prof && prof->on) {
+    for (int64_t i = 0; i < n; ++i) {
+      if (prof->used < prof->max_steps) {
+        launch_step(b, b.stream, prof, prof->used);
+        prof->used += 1;
+      } else {
+        launch_step(b, b.stream, nullptr, 0);
+      }
+    }
+    return cuda_err(cudaGetLastError());
+  }
+  if (n >= STEPS_PER_GRAPH && !b.gk) {
+    int rc = capture(b, STEPS_PER_GRAPH, &b.gk);
+    if (rc) return rc;
+  }
+  if (n % STEPS_PER_GRAPH && !b.g1) {
+    int rc = capture(b, 1, &b.g1);
+    if (rc) return rc;
+  }
+  for (int64_t i = 0; i < n / STEPS_PER_GRAPH; ++i) ECO_CU(cudaGraphLaunch(b.gk, b.stream));
+  for (int64_t i = 0; i < n % STEPS_PER_GRAPH; ++i) ECO_CU(cudaGraphLaunch(b.g1, b.stream));
+  return ECO_OK;
+}
+
+int read_status(EcoWorld *w, int *status) {
+  ECO_CU(cudaMemcpy(status, &w->hd.ctr->status, sizeof(int), cudaMemcpyDeviceToHost));
+  return ECO_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+size_t eco_world_bytes(const EcoParams *p) {
+  if (!params_ok(p)) return 0;
+  return layout_of(p).total;
+}
+
+static void fill_descriptor(EcoWorld *w) {
+  const EcoParams &p = w->p;
+  const Layout &L = w->L;
+  char *a = w->arena;
+  WorldDev &d = w->hd;
+  d.H = p.H; d.W = p.W; d.Wp = (p.W + 31) / 32; d.C = p.capacity;
+  d.nbr_shape = p.nbr_shape; d.nbr_radius = p.nbr_radius;
+  for (int i = 0; i < 3; ++i) d.class_edges[i] = p.class_edges[i];
+  d.t_repr = p.t_repr; d.t_death = p.t_death; d.max_age = p.max_age;
+  d.wall_kills = p.wall_kills;
+  d.e0 = p.e0; d.e_decay = p.e_decay; d.e_gain = p.e_gain; d.e_max = p.e_max;
+  d.e_repr = p.e_repr; d.e_death = p.e_death; d.mut_std = p.mut_std;
+  d.w_init_std = p.w_init_std;
+  d.key0 = (uint32_t)(w->seed & 0xFFFFFFFFu);
+  d.key1 = (uint32_t)(w->seed >> 32);
+  d.thr = (uint32_t *)(a + L.thr);
+  d.res0 = (uint32_t *)(a + L.res0);
+  d.res1 = (uint32_t *)(a + L.res1);
+  d.wall = (uint32_t *)(a + L.wall);
+  d.slot_map = (int32_t *)(a + L.slot_map);
+  d.claim = (int32_t *)(a + L.claim);
+  d.bclaim = (int32_t *)(a + L.bclaim);
+  d.alive = (uint8_t *)(a + L.alive);
+  d.killed = (uint8_t *)(a + L.killed);
+  d.ate = (uint8_t *)(a + L.ate);
+  d.flag = (uint8_t *)(a + L.flag);
+  d.y = (int32_t *)(a + L.y);
+  d.x = (int32_t *)(a + L.x);
+  d.energy = (float *)(a + L.energy);
+  d.repr_ctr = (int32_t *)(a + L.repr_ctr);
+  d.low_ctr = (int32_t *)(a + L.low_ctr);
+  d.age = (int32_t *)(a + L.age);
+  d.action = (int32_t *)(a + L.action);
+  d.forced = (int32_t *)(a + L.forced);
+  d.target = (int32_t *)(a + L.target);
+  d.birth_cell = (int32_t *)(a + L.birth_cell);
+  d.arrive = (uint32_t *)(a + L.arrive);
+  d.h0 = (float *)(a + L.h0);
+  d.h1 = (float *)(a + L.h1);
+  d.c = (float *)(a + L.c);
+  d.logits = (float *)(a + L.logits);
+  d.alive_list = (int32_t *)(a + L.alive_list);
+  d.free_list = (int32_t *)(a + L.free_list);
+  d.birth_parent = (int32_t *)(a + L.birth_parent);
+  d.birth_child = (int32_t *)(a + L.birth_child);
+  d.weights = (float *)(a + L.weights);
+  d.ctr = (Counters *)(a + L.ctr);
+  w->dd = (WorldDev *)(a + L.wdev);
+}
+
+// Cells of the initial agents: the non-wall cells in ascending order of
+// (word x%4 of the Philox draw {x/4, 0, TAG_PLACE, y}, cell index).
+static bool initial_cells(const EcoParams &p, uint64_t seed, std::vector<int32_t> &py,
+                          std::vector<int32_t> &px) {
+  const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
+  std::vector<uint64_t> keys;
+  keys.reserve((size_t)p.H * p.W);
+  for (int y = 0; y < p.H; ++y) {
+    for (int xq = 0; xq < p.W; xq += 4) {
+      const U4 u = philox4x32_10(U4{(uint32_t)xq >> 2, 0u, TAG_PLACE, (uint32_t)y}, k0, k1);
+      const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
+      for (int i = 0; i < 4 && xq + i < p.W; ++i) {
+        const int x = xq + i;
+        const bool wall = p.border_walls && (y == 0 || y == p.H - 1 || x == 0 || x == p.W - 1);
+        if (wall) continue;
+        keys.push_back(((uint64_t)uw[i] << 32) | (uint64_t)((size_t)y * p.W + x));
+      }
+    }
+  }
+  const size_t n0 = (size_t)p.n_agents0;
+  if (n0 > keys.size()) return false;
+  std::partial_sort(keys.begin(), keys.begin() + n0, keys.end());
+  py.resize(n0);
+  px.resize(n0);
+  for (size_t s = 0; s < n0; ++s) {
+    const uint32_t cell = (uint32_t)(keys[s] & 0xFFFFFFFFu);
+    py[s] = (int32_t)(cell / (uint32_t)p.W);
+    px[s] = (int32_t)(cell % (uint32_t)p.W);
+  }
+  return true;
+}
+
+int eco_world_create(const EcoParams *params, uint64_t seed, void *arena,
+                     size_t arena_bytes, void *stream, EcoWorld **out) {
+  if (!out) return ECO_EINVAL;
+  *out = nullptr;
+  if (!params_ok(params) || !stream) return ECO_EINVAL;
+  const Layout L = layout_of(params);
+  if (arena && ((uintptr_t)arena & 255u)) return ECO_EINVAL;
+  if (arena && arena_bytes < L.total) return ECO_ENOMEM;
+  std::vector<int32_t> py, px;
+  if (!initial_cells(*params, seed, py, px)) return ECO_EINVAL;
+
+  EcoWorld *w = new (std::nothrow) EcoWorld;
+  if (!w) return ECO_ENOMEM;
+  w->p = *params;
+  w->seed = seed;
+  w->stream = (cudaStream_t)stream;
+  w->L = L;
+  int rc = ECO_OK;
+  do {
+    if ((rc = cuda_err(cudaGetDevice(&w->device)))) break;
+    if ((rc = cuda_err(cudaDeviceGetAttribute(&w->n_sms, cudaDevAttrMultiProcessorCount,
+                                              w->device)))) break;
+    configure_lstm();
+    preload_regrow();
+    preload_lstm();
+    preload_agents();
+    if (arena) {
+      w->arena = (char *)arena;
+      w->arena_bytes = arena_bytes;
+    } else {
+      if (cudaMalloc((void **)&w->arena, L.total) != cudaSuccess) {
+        cudaGetLastError();
+        rc = ECO_ENOMEM;
+        break;
+      }
+      w->owns_arena = true;
+      w->arena_bytes = L.total;
+    }
+    fill_descriptor(w);
+    const std::vector<uint32_t> thr = threshold_table(params);
+    cudaStream_t s = w->stream;
+    if ((rc = cuda_err(cudaMemsetAsync(w->hd.ctr, 0, sizeof(Counters), s)))) break;
+    if ((rc = cuda_err(cudaMemcpyAsync(w->hd.thr, thr.data(), thr.size() * 4,
+                                       cudaMemcpyHostToDevice, s)))) break;
+    if ((rc = cuda_err(cudaMemcpyAsync(w->dd, &w->hd, sizeof(WorldDev),
+                                       cudaMemcpyHostToDevice, s)))) break;
+    if (!py.empty()) {
+      if ((rc = cuda_err(cudaMemcpyAsync(w->hd.free_list, py.data(), py.size() * 4,
+                                         cudaMemcpyHostToDevice, s)))) break;
+      if ((rc = cuda_err(cudaMemcpyAsync(w->hd.birth_parent, px.data(), px.size() * 4,
+                                         cudaMemcpyHostToDevice, s)))) break;
+    }
+    launch_init_world(&w->hd, w->dd, params->n_agents0, w->hd.free_list,
+                      w->hd.birth_parent, params->border_walls,
+                      threshold_of(params->res_init_p), w->n_sms, s);
+    if ((rc = cuda_err(cudaGetLastError()))) break;
+    if ((rc = cuda_err(cudaStreamSynchronize(s)))) break;
+    EcoWorld *self[1] = {w};
+    if ((rc = batch_init(w->self, self, 1, w->arena + L.tab_worlds))) break;
+  } while (0);
+  if (rc != ECO_OK) {
+    if (w->owns_arena && w->arena) cudaFree(w->arena);
+    delete w;
+    return rc;
+  }
+  *out = w;
+  return ECO_OK;
+}
+
+void eco_world_destroy(EcoWorld *w) {
+  if (!w) return;
+  cudaStreamSynchronize(w->stream);
+  destroy_graphs(w->self);
+  for (cudaEvent_t e : w->prof.ev) cudaEventDestroy(e);
+  if (w->owns_arena) cudaFree(w->arena);
+  delete w;
+}
+
+int eco_world_step(EcoWorld *w, int64_t n_steps) {
+  if (!w) return ECO_EINVAL;
+  return batch_step(w->self, n_steps);
+}
+
+int eco_world_step_forced(EcoWorld *w, const int32_t *actions, int actions_on_host) {
+  if (!w || (!actions && w->p.capacity > 0)) return ECO_EINVAL;
+  cudaStream_t s = w->stream;
+  const size_t bytes = (size_t)w->p.capacity * 4;
+  if (bytes)
+    ECO_CU(cudaMemcpyAsync(w->hd.forced, actions, bytes,
+                           actions_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  static const int one = 1;
+  ECO_CU(cudaMemcpyAsync(&w->hd.ctr->use_forced, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+  launch_step(w->self, s, nullptr, 0);
+  ECO_CU(cudaGetLastError());
+  ECO_CU(cudaMemsetAsync(&w->hd.ctr->use_forced, 0, sizeof(int), s));
+  if (actions_on_host) ECO_CU(cudaStreamSynchronize(s));
+  return ECO_OK;
+}
+
+int eco_world_sync(EcoWorld *w) {
+  if (!w) return ECO_EINVAL;
+  ECO_CU(cudaStreamSynchronize(w->stream));
+  int st = 0;
+  int rc = read_status(w, &st);
+  if (rc) return rc;
+  if (st & ST_TIMEOUT) return ECO_ETIMEOUT;
+  return ECO_OK;
+}
+
+const EcoParams *eco_world_params(const EcoWorld *w) { return w ? &w->p : nullptr; }
+void *eco_world_stream(const EcoWorld *w) { return w ? (void *)w->stream : nullptr; }
+
+static void counters_to_array(const Counters &c, int64_t *out) {
+  out[ECO_C_T] = c.t;
+  out[ECO_C_POP] = c.pop;
+  out[ECO_C_BIRTHS] = c.births;
+  out[ECO_C_DEATHS] = c.deaths;
+  out[ECO_C_DROPPED] = c.dropped;
+  out[ECO_C_BIRTHS_LAST] = c.births_last;
+  out[ECO_C_DEATHS_LAST] = c.deaths_last;
+  out[ECO_C_DROPPED_LAST] = c.dropped_last;
+}
+
+static int download(void *dst, const void *src, size_t bytes) {
+  if (!dst || !bytes) return ECO_OK;
+  return cuda_err(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+}
+static int upload(void *dst, const void *src, size_t bytes) {
+  if (!src || !bytes) return ECO_OK;
+  return cuda_err(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+}
+
+static int read_plane(const uint32_t *plane, const EcoParams &p, uint8_t *out) {
+  if (!out) return ECO_OK;
+  const int Wp = (p.W + 31) / 32;
+  std::vector<uint32_t> words((size_t)p.H * Wp);
+  int rc = download(words.data(), plane, words.size() * 4);
+  if (rc) return rc;
+  for (int y = 0; y < p.H; ++y)
+    for (int x = 0; x < p.W; ++x)
+      out[(size_t)y * p.W + x] = (words[(size_t)y * Wp + (x >> 5)] >> (x & 31)) & 1u;
+  return ECO_OK;
+}
+static int write_plane(uint32_t *plane, const EcoParams &p, const uint8_t *in) {
+  if (!in) return ECO_OK;
+  const int Wp = (p.W + 31) / 32;
+  std::vector<uint32_t> words((size_t)p.H * Wp, 0u);
+  for (int y = 0; y < p.H; ++y)
+    for (int x = 0; x < p.W; ++x)
+      if (in[(size_t)y * p.W + x]) words[(size_t)y * Wp + (x >> 5)] |= 1u << (x & 31);
+  return upload(plane, words.data(), words.size() * 4);
+}
+
+int eco_world_read_state(EcoWorld *w, EcoState *out) {
+  if (!w || !out) return ECO_EINVAL;
+  const EcoParams &p = w->p;
+  const WorldDev &d = w->hd;
+  const size_t C = p.capacity, HW = (size_t)p.H * p.W;
+  if (out->weights_host &&
+      (out->weights_first < 0 || out->weights_count < 0 ||
+       (size_t)out->weights_first + out->weights_count > C))
+    return ECO_EINVAL;
+  ECO_CU(cudaStreamSynchronize(w->stream));
+  Counters c;
+  int rc = download(&c, d.ctr, sizeof(Counters));
+  if (rc) return rc;
+  counters_to_array(c, out->counters);
+  const bool odd = (c.t & 1) != 0;
+  if ((rc = read_plane(odd ? d.res1 : d.res0, p, out->res_host))) return rc;
+  if ((rc = read_plane(d.wall, p, out->wall_host))) return rc;
+  if ((rc = download(out->slot_map_host, d.slot_map, HW * 4))) return rc;
+  if ((rc = download(out->alive_host, d.alive, C))) return rc;
+  if ((rc = download(out->y_host, d.y, C * 4))) return rc;
+  if ((rc = download(out->x_host, d.x, C * 4))) return rc;
+  if ((rc = download(out->energy_host, d.energy, C * 4))) return rc;
+  if ((rc = download(out->repr_ctr_host, d.repr_ctr, C * 4))) return rc;
+  if ((rc = download(out->low_ctr_host, d.low_ctr, C * 4))) return rc;
+  if ((rc = download(out->age_host, d.age, C * 4))) return rc;
+  if ((rc = download(out->h_host, odd ? d.h1 : d.h0, C * HID * 4))) return rc;
+  if ((rc = download(out->c_host, d.c, C * HID * 4))) return rc;
+  if ((rc = download(out->action_host, d.action, C * 4))) return rc;
+  if (out->logits_host && C) {
+    std::vector<float> lg(C * 8);
+    if ((rc = download(lg.data(), d.logits, lg.size() * 4))) return rc;
+    for (size_t s = 0; s < C; ++s)
+      for (int a = 0; a < NACT; ++a) out->logits_host[s * NACT + a] = lg[s * 8 + a];
+  }
+  if (out->weights_host && out->weights_count > 0) {
+    const int chunk = 64;
+    std::vector<float> phys((size_t)chunk * WSTRIDE);
+    for (int s0 = 0; s0 < out->weights_count; s0 += chunk) {
+      const int n = std::min(chunk, out->weights_count - s0);
+      if ((rc = download(phys.data(), d.weights + (size_t)(out->weights_first + s0) * WSTRIDE,
+                         (size_t)n * WSTRIDE * 4)))
+        return rc;
+      for (int i = 0; i < n; ++i) {
+        float *dst = out->weights_host + (size_t)(s0 + i) * NPARAM;
+        const float *src = phys.data() + (size_t)i * WSTRIDE;
+        for (int j = 0; j < NPARAM; ++j) dst[j] = src[phys_of_logical(j)];
+      }
+    }
+  }
+  return ECO_OK;
+}
+
+int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
+  if (!w || !in) return ECO_EINVAL;
+  const EcoParams &p = w->p;
+  const WorldDev &d = w->hd;
+  const size_t C = p.capacity;
+  if (in->weights_host &&
+      (in->weights_first < 0 || in->weights_count < 0 ||
+       (size_t)in->weights_first + in->weights_count > C))
+    return ECO_EINVAL;
+  ECO_CU(cudaStreamSynchronize(w->stream));
+  Counters c;
+  int rc = download(&c, d.ctr, sizeof(Counters));
+  if (rc) return rc;
+  if (set_counters) {
+    c.t = in->counters[ECO_C_T];
+    c.births = in->counters[ECO_C_BIRTHS];
+    c.deaths = in->counters[ECO_C_DEATHS];
+    c.dropped = in->counters[ECO_C_DROPPED];
+    c.births_last = in->counters[ECO_C_BIRTHS_LAST];
+    c.deaths_last = in->counters[ECO_C_DEATHS_LAST];
+    c.dropped_last = in->counters[ECO_C_DROPPED_LAST];
+    if (c.t < 0 || c.t > 0xFFFFFFFFll) return ECO_EINVAL;
+  }
+  c.deaths_step = 0;
+  c.n_births = 0;
+  c.use_forced = 0;
+  if ((rc = upload(d.ctr, &c, sizeof(Counters)))) return rc;
+  const bool odd = (c.t & 1) != 0;
+  if ((rc = write_plane(odd ? d.res1 : d.res0, p, in->res_host))) return rc;
+  if ((rc = write_plane(d.wall, p, in->wall_host))) return rc;
+  if ((rc = upload(d.alive, in->alive_host, C))) return rc;
+  if ((rc = upload(d.y, in->y_host, C * 4))) return rc;
+  if ((rc = upload(d.x, in->x_host, C * 4))) return rc;
+  if ((rc = upload(d.energy, in->energy_host, C * 4))) return rc;
+  if ((rc = upload(d.repr_ctr, in->repr_ctr_host, C * 4))) return rc;
+  if ((rc = upload(d.low_ctr, in->low_ctr_host, C * 4))) return rc;
+  if ((rc = upload(d.age, in->age_host, C * 4))) return rc;
+  if ((rc = upload(odd ? d.h1 : d.h0, in->h_host, C * HID * 4))) return rc;
+  if ((rc = upload(d.c, in->c_host, C * HID * 4))) return rc;
+  if ((rc = upload(d.action, in->action_host, C * 4))) return rc;
+  if (in->logits_host && C) {
+    std::vector<float> lg(C * 8, 0.f);
+    for (size_t s = 0; s < C; ++s)
+      for (int a = 0; a < NACT; ++a) lg[s * 8 + a] = in->logits_host[s * NACT + a];
+    if ((rc = upload(d.logits, lg.data(), lg.size() * 4))) return rc;
+  }
+  if (in->weights_host && in->weights_count > 0) {
+    const int chunk = 64;
+    std::vector<float> phys((size_t)chunk * WSTRIDE);
+    for (int s0 = 0; s0 < in->weights_count; s0 += chunk) {
+      const int n = std::min(chunk, in->weights_count - s0);
+      std::fill(phys.begin(), phys.end(), 0.f);
+      for (int i = 0; i < n; ++i) {
+        const float *src = in->weights_host + (size_t)(s0 + i) * NPARAM;
+        float *dst = phys.data() + (size_t)i * WSTRIDE;
+        for (int j = 0; j < NPARAM; ++j) dst[phys_of_logical(j)] = src[j];
+      }
+      if ((rc = upload(d.weights + (size_t)(in->weights_first + s0) * WSTRIDE, phys.data(),
+                       (size_t)n * WSTRIDE * 4)))
+        return rc;
+    }
+  }
+  launch_rebuild(&w->hd, w->n_sms, w->stream);
+  ECO_CU(cudaGetLastError());
+  ECO_CU(cudaStreamSynchronize(w->stream));
+  int st = 0;
+  if ((rc = read_status(w, &st))) return rc;
+  if (st & ST_STATE) {
+    st &= ~ST_STATE;
+    upload(&d.ctr->status, &st, sizeof(int));
+    return ECO_ESTATE;
+  }
+  return ECO_OK;
+}
+
+int eco_batch_create(EcoWorld *const *worlds, int n, EcoBatch **out) {
+  if (!out) return ECO_EINVAL;
+  *out = nullptr;
+  if (!worlds || n < 1 || n > 1024) return ECO_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!worlds[i] || worlds[i]->device != worlds[0]->device) return ECO_EINVAL;
+  EcoBatch *b = new (std::nothrow) EcoBatch;
+  if (!b) return ECO_ENOMEM;
+  int rc = batch_init(*b, worlds, n, nullptr);
+  if (rc) {
+    if (b->owns_table && b->table) cudaFree(b->table);
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return ECO_OK;
+}
+
+int eco_batch_step(EcoBatch *b, int64_t n_steps) {
+  if (!b) return ECO_EINVAL;
+  return batch_step(*b, n_steps);
+}
+
+int eco_batch_sync(EcoBatch *b) {
+  if (!b) return ECO_EINVAL;
+  ECO_CU(cudaStreamSynchronize(b->stream));
+  for (EcoWorld *w : b->worlds) {
+    int st = 0;
+    int rc = read_status(w, &st);
+    if (rc) return rc;
+    if (st & ST_TIMEOUT) return ECO_ETIMEOUT;
+  }
+  return ECO_OK;
+}
+
+void eco_batch_destroy(EcoBatch *b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  destroy_graphs(*b);
+  if (b->owns_table) cudaFree(b->table);
+  delete b;
+}
+
+int eco_world_profile(EcoWorld *w, int enable, int max_steps) {
+  if (!w || (enable && max_steps < 1)) return ECO_EINVAL;
+  Profile &pr = w->prof;
+  ECO_CU(cudaStreamSynchronize(w->stream));
+  for (cudaEvent_t e : pr.ev) cudaEventDestroy(e);
+  pr.ev.clear();
+  pr.on = false;
+  pr.used = 0;
+  for (int k = 0; k < ECO_NKERNELS; ++k) {
+    pr.ms[k] = 0.0;
+    pr.launches[k] = 0;
+  }
+  if (!enable) return ECO_OK;
+  pr.ev.resize((size_t)max_steps * (ECO_NKERNELS + 1));
+  for (auto &e : pr.ev) ECO_CU(cudaEventCreate(&e));
+  pr.max_steps = max_steps;
+  pr.on = true;
+  return ECO_OK;
+}
+
+int eco_world_profile_read(EcoWorld *w, double *ms, int64_t *launches) {
+  if (!w || !ms || !launches) return ECO_EINVAL;
+  Profile &pr = w->prof;
+  ECO_CU(cudaStreamSynchronize(w->stream));
+  for (int s = 0; s < pr.used; ++s) {
+    for (int k = 0; k < ECO_NKERNELS; ++k) {
+      float t = 0.f;
+      ECO_CU(cudaEventElapsedTime(&t, pr.ev[(size_t)s * (ECO_NKERNELS + 1) + k],
+                                  pr.ev[(size_t)s * (ECO_NKERNELS + 1) + k + 1]));
+      pr.ms[k] += t;
+      pr.launches[k] += 1;
+    }
+  }
+  pr.used = 0;
+  for (int k = 0; k < ECO_NKERNELS; ++k) {
+    ms[k] = pr.ms[k];
+    launches[k] = pr.launches[k];
+  }
+  return ECO_OK;
+}
+
+const char *eco_kernel_name(int k) {
+  static const char *names[ECO_NKERNELS] = {"regrow",  "observe_lstm", "move_claim",
+                                            "move_apply", "physio",   "birth_claim",
+                                            "scan",    "spawn"};
+  return (k >= 0 && k < ECO_NKERNELS) ? names[k] : "?";
+}
+
+int eco_kernels_per_step(void) { return ECO_NKERNELS; }
+
+const char *eco_strerror(int code) {
+  switch (code) {
+    case ECO_OK: return "ok";
+    case ECO_EINVAL: return "invalid argument";
+    case ECO_ENOMEM: return "out of memory";
+    case ECO_ECUDA: return "CUDA error";
+    case ECO_ETIMEOUT: return "device wait timed out";
+    case ECO_ESTATE: return "inconsistent state";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

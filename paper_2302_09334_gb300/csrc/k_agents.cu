@@ -1,0 +1,374 @@
+// k_agents.cu -- step parts a4..a6: moves and eating, physiology and death,
+// reproduction (slot compaction + mutation), App. B.2 and B.3.
+//
+// Per-slot kernels run one thread per agent slot of every world (blocks of
+// 256 slots, world found from a block prefix).  Conflicts are settled with
+// order-independent atomics only (atomicMin on claim cells, atomicAnd on
+// resource words), so results do not depend on thread scheduling:
+//   move_claim  target cell; a valid target (on the grid, not a wall, empty
+//               at the start of the phase) gets atomicMin(claim, slot)
+//   move_apply  the lowest claimant moves and resets the claim cell
+//   physio      eat (atomicAnd clears the resource bit), energy update with
+//               exactly rounded float add/sub, death, reproduction counter
+//   birth_claim first free N/S/E/W cell of each parent, atomicMin(bclaim)
+//   scan        one CTA per world: successful parents, free slots, the k-th
+//               parent gets the k-th free slot, children initialised, the
+//               alive list for the next step rebuilt, counters, t += 1
+//   spawn       child weights = parent weights + sigma * N(0,1), eight work
+//               items per birth across the grid
+#include <climits>
+
+#include "ecoevo_dev.cuh"
+
+namespace eco {
+
+__device__ inline int find_world_a(const int *prefix, int n, int item) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Slot handled by this thread, or -1; sets wd.
+__device__ inline int slot_of_thread(const BatchDev &b, const WorldDev *&wd) {
+  const int w = find_world_a(b.slot_block_prefix, b.n, blockIdx.x);
+  wd = b.worlds[w];
+  const int s = (blockIdx.x - b.slot_block_prefix[w]) * SLOT_BLOCK + threadIdx.x;
+  return s < wd->C ? s : -1;
+}
+
+__constant__ int kDY[5] = {0, -1, 1, 0, 0};  // stay, N, S, E, W
+__constant__ int kDX[5] = {0, 0, 0, 1, -1};
+
+// ---------------------------------------------------------------- a4 ------
+__global__ void __launch_bounds__(SLOT_BLOCK) k_move_claim(BatchDev b) {
+  const WorldDev *wd;
+  const int s = slot_of_thread(b, wd);
+  if (s < 0) return;
+  wd->killed[s] = 0;
+  wd->target[s] = -1;
+  if (!wd->alive[s]) return;
+  const int a = wd->ctr->use_forced ? wd->forced[s] : wd->action[s];
+  if (a <= 0 || a >= NACT) return;
+  const int ty = wd->y[s] + kDY[a], tx = wd->x[s] + kDX[a];
+  if (ty < 0 || ty >= wd->H || tx < 0 || tx >= wd->W ||
+      bit_at(wd->wall, wd->Wp, ty, tx)) {
+    if (wd->wall_kills) wd->killed[s] = 1;
+    return;
+  }
+  const int cell = ty * wd->W + tx;
+  if (wd->slot_map[cell] != -1) return;
+  wd->target[s] = cell;
+  atomicMin(&wd->claim[cell], s);
+}
+
+__global__ void __launch_bounds__(SLOT_BLOCK) k_move_apply(BatchDev b) {
+  const WorldDev *wd;
+  const int s = slot_of_thread(b, wd);
+  if (s < 0) return;
+  const int cell = wd->target[s];
+  if (cell < 0 || wd->claim[cell] != s) return;
+  wd->claim[cell] = INT_MAX;  // only the winner resets; losers compare != s
+  wd->slot_map[wd->y[s] * wd->W + wd->x[s]] = -1;
+  wd->slot_map[cell] = s;
+  wd->y[s] = cell / wd->W;
+  wd->x[s] = cell % wd->W;
+}
+
+// ---------------------------------------------------------------- a5 ------
+__global__ void __launch_bounds__(SLOT_BLOCK) k_physio(BatchDev b) {
+  const WorldDev *wd;
+  const int s = slot_of_thread(b, wd);
+  if (s < 0) return;
+  wd->ate[s] = 0;
+  if (!wd->alive[s]) return;
+  const int y = wd->y[s], x = wd->x[s];
+  bool dead;
+  if (wd->killed[s]) {
+    dead = true;
+  } else {
+    const uint32_t t = (uint32_t)wd->ctr->t;
+    uint32_t *res = (t & 1u) ? wd->res0 : wd->res1;  // plane after regrowth
+    const uint32_t bit = 1u << (x & 31);
+    const uint32_t old = atomicAnd(&res[y * wd->Wp + (x >> 5)], ~bit);
+    const bool ate = (old & bit) != 0u;
+    wd->ate[s] = ate ? 1 : 0;
+    float e = wd->energy[s];
+    if (ate) e = __fadd_rn(e, wd->e_gain);
+    e = __fsub_rn(e, wd->e_decay);
+    e = fminf(e, wd->e_max);
+    wd->energy[s] = e;
+    const int age = wd->age[s] + 1;
+    wd->age[s] = age;
+    const int low = (e <= wd->e_death) ? wd->low_ctr[s] + 1 : 0;
+    wd->low_ctr[s] = low;
+    dead = low >= max(wd->t_death, 1) || age > wd->max_age;
+    if (!dead) wd->repr_ctr[s] = (e > wd->e_repr) ? wd->repr_ctr[s] + 1 : 0;
+  }
+  if (dead) {
+    wd->alive[s] = 0;
+    wd->slot_map[y * wd->W + x] = -1;
+    atomicAdd(&wd->ctr->deaths_step, 1);
+  }
+}
+
+// ---------------------------------------------------------------- a6 ------
+__global__ void __launch_bounds__(SLOT_BLOCK) k_birth_claim(BatchDev b) {
+  const WorldDev *wd;
+  const int s = slot_of_thread(b, wd);
+  if (s < 0) return;
+  wd->birth_cell[s] = -1;
+  if (!wd->alive[s] || wd->repr_ctr[s] < wd->t_repr) return;
+  const int y = wd->y[s], x = wd->x[s];
+  for (int a = 1; a < NACT; ++a) {
+    const int ny = y + kDY[a], nx = x + kDX[a];
+    if (ny < 0 || ny >= wd->H || nx < 0 || nx >= wd->W) continue;
+    if (bit_at(wd->wall, wd->Wp, ny, nx)) continue;
+    const int cell = ny * wd->W + nx;
+    if (wd->slot_map[cell] != -1) continue;
+    wd->birth_cell[s] = cell;
+    atomicMin(&wd->bclaim[cell], s);
+    return;
+  }
+}
+
+// Exclusive block scan of two counters over SCAN_THREADS threads.
+__device__ inline void block_scan2(int a, int b, int &ea, int &eb, int &ta,
+                                   int &tb, int *sh /* [2*32] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int xa = __shfl_up_sync(0xFFFFFFFFu, ia, o);
+    const int xb = __shfl_up_sync(0xFFFFFFFFu, ib, o);
+    if (lane >= o) { ia += xa; ib += xb; }
+  }
+  if (lane == 31) { sh[warp] = ia; sh[32 + warp] = ib; }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    int va = lane < nw ? sh[lane] : 0, vb = lane < nw ? sh[32 + lane] : 0;
+    int sa = va, sb = vb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int xa = __shfl_up_sync(0xFFFFFFFFu, sa, o);
+      const int xb = __shfl_up_sync(0xFFFFFFFFu, sb, o);
+      if (lane >= o) { sa += xa; sb += xb; }
+    }
+    if (lane < nw) { sh[lane] = sa - va; sh[32 + lane] = sb - vb; }
+    if (lane == 31) { sh[64] = sa; sh[65] = sb; }
+  }
+  __syncthreads();
+  ea = sh[warp] + ia - a;
+  eb = sh[32 + warp] + ib - b;
+  ta = sh[64];
+  tb = sh[65];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan(BatchDev b) {
+  __shared__ int sh[66];
+  const WorldDev &wd = *b.worlds[blockIdx.x];
+  const int C = wd.C;
+  const int per = (C + SCAN_THREADS - 1) / SCAN_THREADS;
+  const int s0 = min(C, (int)threadIdx.x * per), s1 = min(C, s0 + per);
+  const uint32_t t = (uint32_t)wd.ctr->t;
+  float *h_next = (t & 1u) ? wd.h0 : wd.h1;
+
+  // 1. successful parents: lowest claimant of their birth cell
+  int n_free = 0, n_succ = 0;
+  for (int s = s0; s < s1; ++s) {
+    const int cell = wd.birth_cell[s];
+    const bool ok = wd.alive[s] && cell >= 0 && wd.bclaim[cell] == s;
+    wd.flag[s] = ok ? 1 : 0;
+    n_succ += ok;
+    n_free += wd.alive[s] ? 0 : 1;
+  }
+  int free_off, succ_off, F, S;
+  block_scan2(n_free, n_succ, free_off, succ_off, F, S, sh);
+
+  // 2. reset the claim cells; list the free slots the births will take
+  for (int s = s0; s < s1; ++s) {
+    const int cell = wd.birth_cell[s];
+    if (cell >= 0) wd.bclaim[cell] = INT_MAX;
+    if (!wd.alive[s]) {
+      if (free_off < S) wd.free_list[free_off] = s;
+      ++free_off;
+    }
+  }
+  __syncthreads();
+
+  // 3. birth k (ascending parent) takes free slot k; past the free list the
+  //    birth is dropped and the parent keeps its counter
+  for (int s = s0; s < s1; ++s) {
+    if (!wd.flag[s]) continue;
+    const int k = succ_off++;
+    if (k >= F) continue;
+    const int child = wd.free_list[k];
+    const int cell = wd.birth_cell[s];
+    wd.birth_parent[k] = s;
+    wd.birth_child[k] = child;
+    wd.repr_ctr[s] = 0;
+    wd.alive[child] = 1;
+    wd.y[child] = cell / wd.W;
+    wd.x[child] = cell % wd.W;
+    wd.slot_map[cell] = child;
+    wd.energy[child] = wd.e0;
+    wd.repr_ctr[child] = 0;
+    wd.low_ctr[child] = 0;
+    wd.age[child] = 0;
+    wd.action[child] = 0;
+    wd.ate[child] = 0;
+    wd.arrive[child] = 0u;
+    wd.birth_cell[child] = -1;
+    for (int j = 0; j < HID; ++j) {
+      h_next[(size_t)child * HID + j] = 0.f;
+      wd.c[(size_t)child * HID + j] = 0.f;
+    }
+    for (int a = 0; a < 8; ++a) wd.logits[(size_t)child * 8 + a] = 0.f;
+  }
+  __syncthreads();
+
+  // 4. alive list of the next step (ascending slots)
+  int n_alive = 0;
+  for (int s = s0; s < s1; ++s) n_alive += wd.alive[s];
+  int alive_off, dummy, pop, dummy2;
+  block_scan2(n_alive, 0, alive_off, dummy, pop, dummy2, sh);
+  for (int s = s0; s < s1; ++s)
+    if (wd.alive[s]) wd.alive_list[alive_off++] = s;
+
+  if (threadIdx.x == 0) {
+    Counters &c = *wd.ctr;
+    const int births = min(S, F);
+    c.births_last = births;
+    c.dropped_last = S - births;
+    c.deaths_last = c.deaths_step;
+    c.births += births;
+    c.dropped += S - births;
+    c.deaths += c.deaths_step;
+    c.deaths_step = 0;
+    c.n_births = births;
+    c.births_t = t;
+    c.pop = pop;
+    c.t = (long long)t + 1;
+  }
+}
+
+// Child weights, physical layout: W[child][p] = W[parent][p] + sigma * N_j
+// with N_j normal j = logical index of p of the stream (TAG_MUT, t, parent).
+// A float4 of a weight row or of the read-out holds four consecutive logical
+// indices starting at a multiple of 4, so one Philox draw serves it; the
+// bias rows of a block are permuted and take one draw per element.
+constexpr int SPAWN_SPLIT = 8;
+constexpr int SPAWN_THREADS = 256;
+constexpr int NVEC = WSTRIDE / 4;  // 5840 float4 per agent
+
+__device__ inline void mutate_copy(const WorldDev &wd, int parent, int child,
+                                   uint32_t tag, uint32_t t, uint32_t id,
+                                   float scale, bool from_parent, int v0, int v1) {
+  const float4 *src = reinterpret_cast<const float4 *>(wd.weights + (size_t)parent * WSTRIDE);
+  float4 *dst = reinterpret_cast<float4 *>(wd.weights + (size_t)child * WSTRIDE);
+  for (int vi = v0 + threadIdx.x; vi < v1; vi += blockDim.x) {
+    const int p = vi * 4;
+    float4 base = from_parent ? src[vi] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float out[4] = {base.x, base.y, base.z, base.w};
+    const int o = p % BLK_FLOATS;
+    const bool bias_vec = p < TAIL && o >= BLK_ROWS * NIN;
+    if (!bias_vec) {
+      const int j = logical_of_phys(p);  // multiple of 4, or -1 for padding
+      if (j >= 0) {
+        float z[4];
+        normals4(wd.key0, wd.key1, (uint32_t)j >> 2, t, tag, id, z);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (j + i < NPARAM)
+            out[i] = __fadd_rn(out[i], __fmul_rn(scale, z[i]));
+          else
+            out[i] = 0.f;
+        }
+      } else {
+        out[0] = out[1] = out[2] = out[3] = 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int j = logical_of_phys(p + i);
+        float z[4];
+        normals4(wd.key0, wd.key1, (uint32_t)j >> 2, t, tag, id, z);
+        out[i] = __fadd_rn(out[i], __fmul_rn(scale, z[j & 3]));
+      }
+    }
+    dst[vi] = make_float4(out[0], out[1], out[2], out[3]);
+  }
+}
+
+__global__ void __launch_bounds__(SPAWN_THREADS) k_spawn(BatchDev b) {
+  __shared__ int pre[1025];
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int w = 0; w < b.n; ++w) {
+      pre[w] = run;
+      run += b.worlds[w]->ctr->n_births;
+    }
+    pre[b.n] = run;
+  }
+  __syncthreads();
+  const int total = pre[b.n] * SPAWN_SPLIT;
+  int w = 0;
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int bi = item / SPAWN_SPLIT, part = item % SPAWN_SPLIT;
+    while (bi >= pre[w + 1]) ++w;
+    const WorldDev &wd = *b.worlds[w];
+    const int k = bi - pre[w];
+    const int parent = wd.birth_parent[k], child = wd.birth_child[k];
+    const int v0 = (NVEC * part) / SPAWN_SPLIT, v1 = (NVEC * (part + 1)) / SPAWN_SPLIT;
+    mutate_copy(wd, parent, child, TAG_MUT, wd.ctr->births_t, (uint32_t)parent,
+                wd.mut_std, true, v0, v1);
+  }
+}
+
+// Initial weights of slots [0, n0): w_init_std * N_j of (TAG_INIT_W, 0, slot).
+__global__ void __launch_bounds__(SPAWN_THREADS) k_init_weights(const WorldDev *wdp, int n0) {
+  const WorldDev &wd = *wdp;
+  for (int item = blockIdx.x; item < n0 * SPAWN_SPLIT; item += gridDim.x) {
+    const int s = item / SPAWN_SPLIT, part = item % SPAWN_SPLIT;
+    const int v0 = (NVEC * part) / SPAWN_SPLIT, v1 = (NVEC * (part + 1)) / SPAWN_SPLIT;
+    mutate_copy(wd, s, s, TAG_INIT_W, 0u, (uint32_t)s, wd.w_init_std, false, v0, v1);
+  }
+}
+
+void preload_agents() {
+  cudaFuncAttributes a;
+  cudaFuncGetAttributes(&a, k_move_claim);
+  cudaFuncGetAttributes(&a, k_move_apply);
+  cudaFuncGetAttributes(&a, k_physio);
+  cudaFuncGetAttributes(&a, k_birth_claim);
+  cudaFuncGetAttributes(&a, k_scan);
+  cudaFuncGetAttributes(&a, k_spawn);
+}
+
+void launch_move_claim(const BatchDev &b, cudaStream_t s) {
+  k_move_claim<<<b.total_slot_blocks, SLOT_BLOCK, 0, s>>>(b);
+}
+void launch_move_apply(const BatchDev &b, cudaStream_t s) {
+  k_move_apply<<<b.total_slot_blocks, SLOT_BLOCK, 0, s>>>(b);
+}
+void launch_physio(const BatchDev &b, cudaStream_t s) {
+  k_physio<<<b.total_slot_blocks, SLOT_BLOCK, 0, s>>>(b);
+}
+void launch_birth_claim(const BatchDev &b, cudaStream_t s) {
+  k_birth_claim<<<b.total_slot_blocks, SLOT_BLOCK, 0, s>>>(b);
+}
+void launch_scan(const BatchDev &b, cudaStream_t s) {
+  k_scan<<<b.n, SCAN_THREADS, 0, s>>>(b);
+}
+void launch_spawn(const BatchDev &b, cudaStream_t s) {
+  k_spawn<<<2 * b.n_sms, SPAWN_THREADS, 0, s>>>(b);
+}
+void launch_init_weights(const WorldDev *wd_dev, int n0, int n_sms, cudaStream_t s) {
+  if (n0 > 0) k_init_weights<<<2 * n_sms, SPAWN_THREADS, 0, s>>>(wd_dev, n0);
+}
+
+}  // namespace eco

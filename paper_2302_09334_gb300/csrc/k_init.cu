@@ -1,0 +1,162 @@
+// k_init.cu -- world set-up and state rebuild (not part of the timed step).
+//
+// Initial state (App. B.4: walls on the border, resources and agents placed
+// at random, weights drawn once at the start of the simulation):
+//   walls       the outer ring of cells when border_walls
+//   resources   cell (y, x) off the walls holds one iff word x%4 of the
+//               Philox draw {x/4, 0, TAG_RES_INIT, y} is below
+//               floor(res_init_p * 2^32)
+//   agents      slots 0..n0-1 on the cells chosen by the host (ascending
+//               order of the words of {x/4, 0, TAG_PLACE, y})
+//   weights     w_init_std * N_j of the stream (TAG_INIT_W, 0, slot)
+#include <climits>
+
+#include "ecoevo_dev.cuh"
+
+namespace eco {
+
+void launch_init_weights(const WorldDev *wd_dev, int n0, int n_sms, cudaStream_t s);
+
+__global__ void k_init_planes(WorldDev wd, int border, uint32_t thr_init) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= wd.H * wd.Wp) return;
+  const int y = i / wd.Wp, ww = i % wd.Wp;
+  uint32_t wall = 0, res = 0;
+  for (int q = 0; q < 8; ++q) {
+    const int xq = ww * 32 + q * 4;
+    if (xq >= wd.W) break;
+    const U4 u = philox4x32_10(U4{(uint32_t)xq >> 2, 0u, TAG_RES_INIT, (uint32_t)y},
+                               wd.key0, wd.key1);
+    const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
+    for (int k = 0; k < 4; ++k) {
+      const int x = xq + k;
+      if (x >= wd.W) break;
+      const bool is_wall = border && (y == 0 || y == wd.H - 1 || x == 0 || x == wd.W - 1);
+      if (is_wall) wall |= 1u << (x & 31);
+      else if (uw[k] < thr_init) res |= 1u << (x & 31);
+    }
+  }
+  wd.wall[i] = wall;
+  wd.res0[i] = res;
+  wd.res1[i] = 0u;
+}
+
+__global__ void k_clear_cells(WorldDev wd) {
+  const size_t n = (size_t)wd.H * wd.W;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    wd.slot_map[i] = -1;
+    wd.claim[i] = INT_MAX;
+    wd.bclaim[i] = INT_MAX;
+  }
+}
+
+// Fresh agents in slots [0, n0) at the given cells; every other slot empty.
+__global__ void k_init_agents(WorldDev wd, int n0, const int32_t *py,
+                              const int32_t *px) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= wd.C) return;
+  const bool live = s < n0;
+  wd.alive[s] = live ? 1 : 0;
+  wd.y[s] = live ? py[s] : 0;
+  wd.x[s] = live ? px[s] : 0;
+  wd.energy[s] = live ? wd.e0 : 0.f;
+  wd.repr_ctr[s] = 0;
+  wd.low_ctr[s] = 0;
+  wd.age[s] = 0;
+  wd.action[s] = 0;
+  wd.forced[s] = 0;
+  wd.killed[s] = 0;
+  wd.ate[s] = 0;
+  wd.target[s] = -1;
+  wd.birth_cell[s] = -1;
+  wd.arrive[s] = 0u;
+  for (int j = 0; j < HID; ++j) {
+    wd.h0[(size_t)s * HID + j] = 0.f;
+    wd.h1[(size_t)s * HID + j] = 0.f;
+    wd.c[(size_t)s * HID + j] = 0.f;
+  }
+  for (int a = 0; a < 8; ++a) wd.logits[(size_t)s * 8 + a] = 0.f;
+}
+
+// Put every living agent on slot_map; a second agent on a cell, an agent on
+// a wall or off the grid, or a resource on a wall sets ST_STATE.
+__global__ void k_place_agents(WorldDev wd) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < wd.C) {
+    wd.arrive[s] = 0u;
+    wd.birth_cell[s] = -1;
+    wd.target[s] = -1;
+    if (wd.alive[s]) {
+      const int y = wd.y[s], x = wd.x[s];
+      if (y < 0 || y >= wd.H || x < 0 || x >= wd.W || bit_at(wd.wall, wd.Wp, y, x)) {
+        atomicOr(&wd.ctr->status, ST_STATE);
+      } else if (atomicCAS(&wd.slot_map[y * wd.W + x], -1, s) != -1) {
+        atomicOr(&wd.ctr->status, ST_STATE);
+      }
+    }
+  }
+  const int i = s;
+  if (i < wd.H * wd.Wp) {
+    const uint32_t t = (uint32_t)wd.ctr->t;
+    const uint32_t *res = (t & 1u) ? wd.res1 : wd.res0;
+    if (res[i] & wd.wall[i]) atomicOr(&wd.ctr->status, ST_STATE);
+  }
+}
+
+// Alive list (ascending slots) and population, one CTA.
+__global__ void __launch_bounds__(SCAN_THREADS) k_alive_list(WorldDev wd) {
+  __shared__ int sh[33];
+  const int C = wd.C;
+  const int per = (C + SCAN_THREADS - 1) / SCAN_THREADS;
+  const int s0 = min(C, (int)threadIdx.x * per), s1 = min(C, s0 + per);
+  int n = 0;
+  for (int s = s0; s < s1; ++s) n += wd.alive[s];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc = n;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) sh[warp] = inc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int k = 0; k < SCAN_THREADS / 32; ++k) {
+      const int v = sh[k];
+      sh[k] = run;
+      run += v;
+    }
+    sh[32] = run;
+  }
+  __syncthreads();
+  int off = sh[warp] + inc - n;
+  for (int s = s0; s < s1; ++s)
+    if (wd.alive[s]) wd.alive_list[off++] = s;
+  if (threadIdx.x == 0) wd.ctr->pop = sh[32];
+}
+
+void launch_init_world(const WorldDev *wd_host, WorldDev *wd_dev, int n0,
+                       const int32_t *place_y, const int32_t *place_x,
+                       int border, uint32_t thr_init, int n_sms, cudaStream_t s) {
+  const WorldDev &wd = *wd_host;
+  const int nw = wd.H * wd.Wp;
+  k_init_planes<<<(nw + 255) / 256, 256, 0, s>>>(wd, border, thr_init);
+  k_clear_cells<<<4 * n_sms, 256, 0, s>>>(wd);
+  if (wd.C > 0) {
+    k_init_agents<<<(wd.C + 255) / 256, 256, 0, s>>>(wd, n0, place_y, place_x);
+    k_place_agents<<<(max(wd.C, nw) + 255) / 256, 256, 0, s>>>(wd);
+  }
+  k_alive_list<<<1, SCAN_THREADS, 0, s>>>(wd);
+  launch_init_weights(wd_dev, n0, n_sms, s);
+}
+
+void launch_rebuild(const WorldDev *wd_host, int n_sms, cudaStream_t s) {
+  const WorldDev &wd = *wd_host;
+  const int nw = wd.H * wd.Wp;
+  k_clear_cells<<<4 * n_sms, 256, 0, s>>>(wd);
+  k_place_agents<<<(max(wd.C, nw) + 255) / 256, 256, 0, s>>>(wd);
+  k_alive_list<<<1, SCAN_THREADS, 0, s>>>(wd);
+}
+
+}  // namespace eco

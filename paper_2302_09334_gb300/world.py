@@ -1,0 +1,171 @@
+"""Python view of the C ABI: worlds and batches.
+
+PyTorch provides the device memory (one uint8 arena per world, from its
+caching allocator) and the CUDA stream; every part of the simulation step
+runs in libecoevo's kernels.  Functions here only marshal arguments.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import check, lib, to_c_params
+from .params import EcoParams
+
+NPARAM = 23333
+HID = 32
+NACT = 5
+
+# state field -> (dtype, per-slot width or "grid")
+_GRID = {"res": np.uint8, "wall": np.uint8, "slot_map": np.int32}
+_SLOT = {
+    "alive": (np.uint8, 1), "y": (np.int32, 1), "x": (np.int32, 1),
+    "energy": (np.float32, 1), "repr_ctr": (np.int32, 1), "low_ctr": (np.int32, 1),
+    "age": (np.int32, 1), "h": (np.float32, HID), "c": (np.float32, HID),
+    "action": (np.int32, 1), "logits": (np.float32, NACT),
+}
+ALL_FIELDS = tuple(_GRID) + tuple(_SLOT)
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+class World:
+    """One simulated world resident on a CUDA device."""
+
+    def __init__(self, params: EcoParams, seed: int = 0, device=None, stream=None):
+        import torch
+        self.p = params
+        self.seed = int(seed)
+        self._c = to_c_params(params)
+        L = lib()
+        nbytes = L.eco_world_bytes(ctypes.byref(self._c))
+        if nbytes == 0:
+            raise ValueError(f"invalid world parameters: {params}")
+        self.nbytes = nbytes
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.device = dev
+        self._h = None
+        with torch.cuda.device(dev):
+            self.stream = stream if stream is not None else torch.cuda.Stream(dev)
+            self.arena = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+            base = (self.arena.data_ptr() + 255) & ~255
+            h = ctypes.c_void_p()
+            check(L.eco_world_create(ctypes.byref(self._c), self.seed, ctypes.c_void_p(base),
+                                     nbytes, ctypes.c_void_p(self.stream.cuda_stream),
+                                     ctypes.byref(h)), "eco_world_create")
+            self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def step(self, n: int = 1) -> None:
+        check(lib().eco_world_step(self._h, int(n)), "eco_world_step")
+
+    def step_forced(self, actions) -> None:
+        a = np.ascontiguousarray(actions, dtype=np.int32)
+        if a.shape != (self.p.capacity,):
+            raise ValueError("actions must have one entry per slot")
+        check(lib().eco_world_step_forced(self._h, _ptr(a), 1), "eco_world_step_forced")
+
+    def sync(self) -> None:
+        check(lib().eco_world_sync(self._h), "eco_world_sync")
+
+    def read_state(self, fields=ALL_FIELDS, weights=None) -> dict:
+        """Copy state to host numpy arrays.  weights: None, or (first, count)
+        slot range of logical parameter vectors."""
+        st = _lib.CEcoState()
+        out = {}
+        H, W, C = self.p.H, self.p.W, self.p.capacity
+        for f in fields:
+            if f in _GRID:
+                out[f] = np.zeros((H, W), _GRID[f])
+            else:
+                dt, width = _SLOT[f]
+                out[f] = np.zeros((C, width) if width > 1 else (C,), dt)
+            setattr(st, f + "_host", out[f].ctypes.data)
+        if weights is not None:
+            first, count = weights
+            out["weights"] = np.zeros((count, NPARAM), np.float32)
+            st.weights_host = out["weights"].ctypes.data
+            st.weights_first, st.weights_count = int(first), int(count)
+        check(lib().eco_world_read_state(self._h, ctypes.byref(st)), "eco_world_read_state")
+        out["counters"] = np.array(st.counters[:], np.int64)
+        return out
+
+    def load_state(self, state: dict, set_counters: bool = True, weights_first: int = 0) -> None:
+        st = _lib.CEcoState()
+        keep = []
+        for f in ALL_FIELDS:
+            if f == "slot_map" or f not in state:
+                continue
+            a = np.ascontiguousarray(state[f], dtype=(_GRID[f] if f in _GRID else _SLOT[f][0]))
+            keep.append(a)
+            setattr(st, f + "_host", a.ctypes.data)
+        if "weights" in state:
+            wts = np.ascontiguousarray(state["weights"], np.float32).reshape(-1, NPARAM)
+            keep.append(wts)
+            st.weights_host = wts.ctypes.data
+            st.weights_first, st.weights_count = int(weights_first), wts.shape[0]
+        if "counters" in state:
+            for i, v in enumerate(state["counters"]):
+                st.counters[i] = int(v)
+        check(lib().eco_world_load_state(self._h, ctypes.byref(st), 1 if set_counters else 0),
+              "eco_world_load_state")
+
+    def counters(self) -> np.ndarray:
+        return self.read_state(fields=())["counters"]
+
+    def profile(self, enable: bool, max_steps: int = 1024) -> None:
+        check(lib().eco_world_profile(self._h, 1 if enable else 0, int(max_steps)),
+              "eco_world_profile")
+
+    def profile_read(self) -> dict:
+        ms = (ctypes.c_double * _lib.NKERNELS)()
+        n = (ctypes.c_int64 * _lib.NKERNELS)()
+        check(lib().eco_world_profile_read(self._h, ms, n), "eco_world_profile_read")
+        return {lib().eco_kernel_name(k).decode(): (ms[k], n[k]) for k in range(_lib.NKERNELS)}
+
+    def close(self) -> None:
+        if self._h is not None:
+            lib().eco_world_destroy(self._h)
+            self._h = None
+            self.arena = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent worlds stepped together, one launch per kernel per step."""
+
+    def __init__(self, worlds):
+        self.worlds = list(worlds)
+        arr = (ctypes.c_void_p * len(self.worlds))(*[w.handle.value for w in self.worlds])
+        h = ctypes.c_void_p()
+        check(lib().eco_batch_create(arr, len(self.worlds), ctypes.byref(h)), "eco_batch_create")
+        self._h = h
+
+    def step(self, n: int = 1) -> None:
+        check(lib().eco_batch_step(self._h, int(n)), "eco_batch_step")
+
+    def sync(self) -> None:
+        check(lib().eco_batch_sync(self._h), "eco_batch_sync")
+
+    def close(self) -> None:
+        if self._h is not None:
+            lib().eco_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,149 @@
+"""Parity of the CUDA step with the CPU oracle (GPU tests).
+
+Every case starts both sides from the same seed (or the same loaded state),
+steps them with the oracle's actions forced on the GPU, and compares the
+full state after each step under the rules in tests/parity.py.
+"""
+import numpy as np
+import pytest
+
+from paper_2302_09334_gb300.params import INT32_MAX, EcoParams, paper_200x400, small_20x40
+from tests import inputs
+from tests.parity import compare, run_forced, weights_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eco():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_09334_gb300 import build, world
+    build.build()
+    return world
+
+
+def _pair(eco, oracle, p, seed):
+    gw = eco.World(p, seed)
+    ow = oracle.OracleWorld(p.asdict(), seed)
+    return gw, ow
+
+
+def test_initial_state_matches(eco, oracle):
+    p = small_20x40()
+    gw, ow = _pair(eco, oracle, p, 0)
+    gs = gw.read_state(weights=(0, p.capacity))
+    compare(gs, ow, "init")
+    weights_close(gs["weights"][:p.n_agents0], ow.weights[:p.n_agents0], p.w_init_std, "init weights")
+
+
+def test_small_world_500_steps_forced(eco, oracle):
+    p = small_20x40()
+    gw, ow = _pair(eco, oracle, p, 0)
+    st = run_forced(gw, ow, 500, "20x40", p.mut_std)
+    assert st["births"] > 0
+    assert ow.counters[3] > 0  # deaths happened too
+
+
+EDGE_CASES = {
+    "ragged_9x33": EcoParams(H=9, W=33, capacity=40, n_agents0=20),
+    "paper_forms_24x100": EcoParams(H=24, W=100, capacity=120, n_agents0=60, nbr_shape=1,
+                                    nbr_radius=1, class_edges=(1, 2, 5),
+                                    p_class=(0.0, 0.05, 0.0, 0.0), lat_mode=1,
+                                    p_spont=5e-4, wall_kills=1, t_death=3, max_age=80,
+                                    e_max=1.2, e_gain=1.0, t_repr=10, e_decay=0.025),
+    "no_agents": EcoParams(H=16, W=70, capacity=8, n_agents0=0, p_class=(0.0, 0.05, 0.1, 0.2)),
+    "full_capacity": EcoParams(H=12, W=40, capacity=30, n_agents0=30, t_repr=5),
+    "tiny_3x3": EcoParams(H=3, W=3, capacity=4, n_agents0=1, t_repr=3),
+    "radius3_open": EcoParams(H=17, W=65, capacity=64, n_agents0=40, border_walls=0,
+                              nbr_radius=3, class_edges=(1, 4, 9), e_decay=0.02),
+    "word_multiple_8x64": EcoParams(H=8, W=64, capacity=64, n_agents0=32, t_repr=7),
+}
+
+
+@pytest.mark.parametrize("name", list(EDGE_CASES))
+def test_edge_cases_forced(eco, oracle, name):
+    p = EDGE_CASES[name]
+    gw, ow = _pair(eco, oracle, p, 11)
+    compare(gw.read_state(), ow, f"{name} init")
+    run_forced(gw, ow, 120, name, p.mut_std)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_from_identical_random_state(eco, oracle, seed):
+    p = EcoParams(H=30, W=75, capacity=300, n_agents0=0, t_repr=3, e_decay=0.01)
+    state = inputs.random_state(p, seed, n_agents=180, t=1000 + seed)
+    gw, ow = _pair(eco, oracle, p, 5)
+    inputs.load_into_oracle(ow, state)
+    gw.load_state(state)
+    compare(gw.read_state(), ow, "loaded")
+    st = run_forced(gw, ow, 25, f"random state {seed}", p.mut_std)
+    assert st["births"] > 0
+
+
+def test_paper_scale_world_forced(eco, oracle):
+    p = paper_200x400()
+    gw, ow = _pair(eco, oracle, p, 0)
+    gs = gw.read_state(weights=(0, 64))
+    compare(gs, ow, "200x400 init")
+    weights_close(gs["weights"], ow.weights[:64], p.w_init_std, "200x400 init weights")
+    run_forced(gw, ow, 60, "200x400", p.mut_std, compare_every=10)
+
+
+def test_free_run_is_deterministic(eco):
+    p = small_20x40()
+    a = eco.World(p, 3)
+    b = eco.World(p, 3)
+    a.step(200)
+    b.step(57)
+    b.step(143)
+    sa, sb = a.read_state(), b.read_state()
+    for k in sa:
+        np.testing.assert_array_equal(sa[k], sb[k], err_msg=k)
+
+
+def test_batch_equals_alone(eco):
+    import torch
+    ps = [small_20x40(), EcoParams(H=33, W=90, capacity=200, n_agents0=100),
+          EcoParams(H=50, W=100, capacity=400, n_agents0=150, lat_bottom=0.6)]
+    stream = torch.cuda.Stream()
+    alone = [eco.World(p, 10 + i) for i, p in enumerate(ps)]
+    mixed = [eco.World(p, 10 + i, stream=stream) for i, p in enumerate(ps)]
+    for w in alone:
+        w.step(150)
+    batch = eco.Batch(mixed)
+    batch.step(150)
+    batch.sync()
+    for wa, wb in zip(alone, mixed):
+        sa, sb = wa.read_state(), wb.read_state()
+        for k in sa:
+            np.testing.assert_array_equal(sa[k], sb[k], err_msg=k)
+
+
+def test_load_rejects_inconsistent_state(eco):
+    from paper_2302_09334_gb300._lib import EcoError, ECO_ESTATE
+    p = EcoParams(H=8, W=8, capacity=4, n_agents0=2)
+    w = eco.World(p, 0)
+    st = w.read_state()
+    st["alive"][:] = [1, 1, 0, 0]
+    st["y"][:2] = 3
+    st["x"][:2] = 4
+    with pytest.raises(EcoError) as e:
+        w.load_state(st)
+    assert e.value.code == ECO_ESTATE
+    st["y"][1] = 0  # on the border wall
+    with pytest.raises(EcoError):
+        w.load_state(st)
+    st["y"][1] = 2
+    w.load_state(st)  # consistent again
+    w.step(3)
+    w.sync()
+
+
+def test_held_population_stays_constant(eco):
+    p = small_20x40().replace(e_decay=0.0, t_repr=INT32_MAX)
+    w = eco.World(p, 4)
+    w.step(100)
+    c = w.counters()
+    assert c[1] == p.n_agents0 and c[2] == 0 and c[3] == 0
