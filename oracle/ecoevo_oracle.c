@@ -294,8 +294,8 @@ static int cmp_u64(const void *a, const void *b) {
 /* out[j] = base[j] + scale * N_j for j < 23333 (base NULL reads as zero),
  * with N_j normal j of the stream (seed, tag, t, id); one Philox draw serves
  * the four normals 4q..4q+3, as or_normal defines them. */
-static void fill_normals(uint64_t seed, uint32_t tag, uint32_t t, uint32_t id,
-                         float scale, const float *base, float *out) {
+void or_fill_normals(uint64_t seed, uint32_t tag, uint32_t t, uint32_t id,
+                     float scale, const float *base, float *out) {
   uint32_t key[2];
   key_of(seed, key);
   for (uint32_t q = 0; 4 * q < OR_NPARAM; ++q) {
@@ -393,7 +393,7 @@ int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
       w->slot_map[cell] = s;
       w->energy[s] = p->e0;
       /* weights drawn once at the start of the simulation, App. B.2 */
-      fill_normals(seed, OR_TAG_INIT_W, 0u, (uint32_t)s, p->w_init_std, NULL,
+      or_fill_normals(seed, OR_TAG_INIT_W, 0u, (uint32_t)s, p->w_init_std, NULL,
                    w->weights + (size_t)s * OR_NPARAM);
     }
     free(keys);
@@ -574,7 +574,7 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
     }
     for (int a = 0; a < OR_NACT; ++a) w->logits[(size_t)child * OR_NACT + a] = 0.0;
     /* asexual reproduction: parent weights plus N(0, sigma) noise, App. B.3 */
-    fill_normals(w->seed, OR_TAG_MUT, t, (uint32_t)parent, p->mut_std,
+    or_fill_normals(w->seed, OR_TAG_MUT, t, (uint32_t)parent, p->mut_std,
                  w->weights + (size_t)parent * OR_NPARAM,
                  w->weights + (size_t)child * OR_NPARAM);
     w->repr_ctr[parent] = 0;

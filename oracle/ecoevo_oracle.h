@@ -115,6 +115,12 @@ void or_box_muller(uint32_t x1, uint32_t x2, double *z0, double *z1);
 /* Normal number j of the stream (seed, tag, t, id). */
 double or_normal(uint64_t seed, uint32_t tag, uint32_t t, uint32_t id,
                  uint32_t j);
+/* out[j] = base[j] + scale * N_j for the 23333 parameters (base NULL reads
+ * as zero), N_j = or_normal(seed, tag, t, id, j); the mutation of App. B.3
+ * (tag OR_TAG_MUT, t = step, id = parent) and the initial weights (tag
+ * OR_TAG_INIT_W, t = 0, id = slot, base NULL). */
+void or_fill_normals(uint64_t seed, uint32_t tag, uint32_t t, uint32_t id,
+                     float scale, const float *base, float *out);
 /* Growth thresholds thr[y*4+cls] = floor(p * 2^32), App. B.1 Eq. (1). */
 int or_threshold_table(const OrParams *p, uint32_t *thr);
 /* One synchronous regrowth pass, App. B.1 Eq. (1). */

@@ -79,6 +79,9 @@ def lib():
         L.or_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                 ctypes.c_uint32, ctypes.c_uint32]
         L.or_normal.restype = ctypes.c_double
+        L.or_fill_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                      ctypes.c_uint32, ctypes.c_float, ctypes.c_void_p,
+                                      ctypes.c_void_p]
         L.or_threshold_table.argtypes = [ctypes.POINTER(OrParams), u32p]
         L.or_regrow.argtypes = [ctypes.POINTER(OrParams), ctypes.c_uint64,
                                 ctypes.c_uint32, u32p, ctypes.c_void_p,
@@ -120,6 +123,14 @@ def box_muller(x1, x2):
 
 def normal(seed, tag, t, ident, j):
     return lib().or_normal(seed, tag, t, ident, j)
+
+
+def fill_normals(seed, tag, t, ident, scale, base=None) -> np.ndarray:
+    """base + scale * N(0,1) over one parameter vector (float32)."""
+    out = np.zeros(NPARAM, np.float32)
+    b = None if base is None else np.ascontiguousarray(base, np.float32)
+    lib().or_fill_normals(seed, tag, t, ident, scale, None if b is None else _ptr(b), _ptr(out))
+    return out
 
 
 def threshold_table(params) -> np.ndarray:
