@@ -229,7 +229,7 @@ struct OrWorld {
   int32_t *slot_map;
   uint8_t *alive, *ate, *killed, *wants;
   int32_t *y, *x, *repr_ctr, *low_ctr, *age, *action, *target, *cand;
-  int32_t *claim, *birth_parent, *birth_child, *free_list;
+  int32_t *claim, *birth_parent, *birth_child, *free_list, *move_action;
   float *energy, *weights;
   double *h, *c, *logits;
   uint32_t *thr;
@@ -261,6 +261,7 @@ void *or_world_field(OrWorld *w, int f) {
     case OR_F_THR: return w->thr;
     case OR_F_BIRTH_PARENT: return w->birth_parent;
     case OR_F_BIRTH_CHILD: return w->birth_child;
+    case OR_F_MOVE_ACTION: return w->move_action;
     default: return NULL;
   }
 }
@@ -272,6 +273,7 @@ void or_world_destroy(OrWorld *w) {
   free(w->y); free(w->x); free(w->repr_ctr); free(w->low_ctr); free(w->age);
   free(w->action); free(w->target); free(w->cand); free(w->claim);
   free(w->birth_parent); free(w->birth_child); free(w->free_list);
+  free(w->move_action);
   free(w->energy); free(w->weights); free(w->h); free(w->c); free(w->logits);
   free(w->thr);
   free(w);
@@ -331,6 +333,7 @@ int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
   w->target = calloc(C1, 4); w->cand = calloc(C1, 4);
   w->birth_parent = calloc(C1, 4); w->birth_child = calloc(C1, 4);
   w->free_list = calloc(C1, 4);
+  w->move_action = calloc(C1, 4);
   w->energy = calloc(C1, sizeof(float));
   w->weights = calloc(C1 * OR_NPARAM, sizeof(float));
   w->h = calloc(C1 * OR_HID, sizeof(double));
@@ -340,7 +343,7 @@ int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
   if (!w->res || !w->wall || !w->res_tmp || !w->slot_map || !w->claim ||
       !w->alive || !w->ate || !w->killed || !w->wants || !w->y || !w->x ||
       !w->repr_ctr || !w->low_ctr || !w->age || !w->action || !w->target ||
-      !w->cand || !w->birth_parent || !w->birth_child || !w->free_list ||
+      !w->cand || !w->birth_parent || !w->birth_child || !w->free_list || !w->move_action ||
       !w->energy || !w->weights || !w->h || !w->c || !w->logits || !w->thr) {
     or_world_destroy(w);
     return -2;
@@ -461,8 +464,10 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
    * moves, every other agent stays. */
   for (int i = 0; i < H * W; ++i) w->claim[i] = -1;
   for (int s = 0; s < C; ++s) {
+    w->move_action[s] = 0;
     if (!w->alive[s]) continue;
     int a = forced ? forced[s] : w->action[s];
+    w->move_action[s] = a;
     if (a <= 0 || a >= OR_NACT) continue;
     int ty = w->y[s] + DY[a], tx = w->x[s] + DX[a];
     if (!in_grid(p, ty, tx) || w->wall[ty * W + tx]) {

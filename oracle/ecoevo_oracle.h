@@ -100,6 +100,8 @@ enum {
   OR_F_THR,          /* uint32 [H*4] growth thresholds                       */
   OR_F_BIRTH_PARENT, /* int32  [C]  parents of the last step's births        */
   OR_F_BIRTH_CHILD,  /* int32  [C]  child slots of the last step's births    */
+  OR_F_MOVE_ACTION,  /* int32  [C]  action each agent alive at the start of the
+                                    last step moved with (0 for the others)  */
   OR_NFIELDS
 };
 enum {

@@ -18,7 +18,7 @@ TAG_REGROW, TAG_PLACE, TAG_RES_INIT, TAG_INIT_W, TAG_MUT = 1, 2, 3, 4, 5
 
 (F_RES, F_WALL, F_SLOT_MAP, F_ALIVE, F_Y, F_X, F_ENERGY, F_REPR_CTR, F_LOW_CTR,
  F_AGE, F_H, F_C, F_ACTION, F_LOGITS, F_ATE, F_WEIGHTS, F_COUNTERS, F_THR,
- F_BIRTH_PARENT, F_BIRTH_CHILD) = range(20)
+ F_BIRTH_PARENT, F_BIRTH_CHILD, F_MOVE_ACTION) = range(21)
 (C_T, C_POP, C_BIRTHS, C_DEATHS, C_DROPPED, C_BIRTHS_LAST, C_DEATHS_LAST,
  C_DROPPED_LAST) = range(8)
 
@@ -210,6 +210,7 @@ class OracleWorld:
         self.thr = f(F_THR, np.uint32, (H, 4))
         self.birth_parent = f(F_BIRTH_PARENT, np.int32, (C,))
         self.birth_child = f(F_BIRTH_CHILD, np.int32, (C,))
+        self.move_action = f(F_MOVE_ACTION, np.int32, (C,))
 
     def _field(self, fid, dtype, shape):
         addr = lib().or_world_field(self._h, fid)

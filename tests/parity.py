@@ -103,29 +103,63 @@ def check_births(gw, ow, nb, sigma, where):
         weights_drift_close(wc, ow.weights[ch], ow.weights[par], sigma, f"{where} child {ch}")
 
 
+def _diagnose(prev, gs, ow, forced, where):
+    """Describe the agents around every cell where the slot maps differ."""
+    lines = [f"{where}: slot_map differs"]
+    cells = np.argwhere(gs["slot_map"] != ow.slot_map)
+    near = set()
+    for (y, x) in cells:
+        for s in (int(gs["slot_map"][y, x]), int(ow.slot_map[y, x])):
+            if s >= 0:
+                near.add(s)
+        for s in np.flatnonzero(prev["alive"]):
+            if abs(int(prev["y"][s]) - y) + abs(int(prev["x"][s]) - x) <= 2:
+                near.add(int(s))
+    for s in sorted(near):
+        lines.append(
+            f"  slot {s}: before ({prev['y'][s]},{prev['x'][s]}) alive {prev['alive'][s]} "
+            f"forced {forced[s]} gpu_action {gs['action'][s]} oracle_move {ow.move_action[s]} "
+            f"after gpu ({gs['y'][s]},{gs['x'][s]}) alive {gs['alive'][s]} "
+            f"oracle ({ow.y[s]},{ow.x[s]}) alive {ow.alive[s]}")
+    lines.append(f"  births {ow.birth_parent[:ow.counters[5]]} -> {ow.birth_child[:ow.counters[5]]}")
+    return "\n".join(lines)
+
+
 def run_forced(gw, ow, steps: int, where: str, weight_std: float,
                compare_every: int = 1) -> dict:
-    """Step both worlds `steps` times, the GPU with the oracle's actions, and
-    compare after every `compare_every` steps (always after births)."""
-    C = ow.p.capacity
+    """Step both worlds `steps` times, the GPU with the actions the oracle
+    moved with, and compare after every `compare_every` steps (always after
+    births)."""
     flagged = 0
     worst = {"h": 0.0, "c": 0.0}
     births = 0
+    prev = gw.read_state()
     for k in range(steps):
         acted = ow.alive.copy().astype(bool)
         ow.step()
-        forced = np.where(acted, ow.action, 0).astype(np.int32)
+        forced = ow.move_action.copy()
         gw.step_forced(forced)
         nb = int(ow.counters[5])
         births += nb
         if (k + 1) % compare_every and nb == 0 and k != steps - 1:
             continue
         gs = gw.read_state()
-        st = compare(gs, ow, f"{where} step {k + 1}")
+        label = f"{where} step {k + 1}"
+        if not np.array_equal(gs["slot_map"], ow.slot_map):
+            raise AssertionError(_diagnose(prev, gs, ow, forced, label))
+        st = compare(gs, ow, label)
         for key in st:
             worst[key] = max(worst[key], st[key])
-        flagged += compare_actions(gs["action"], gs["logits"], ow, acted, f"{where} step {k + 1}")
+        # a slot reused by a newborn this step has its action and logits reset
+        reborn = np.zeros_like(acted)
+        reborn[ow.birth_child[:nb]] = True
+        ow_action_saved = ow.action.copy()
+        try:
+            ow.action[:] = ow.move_action
+            flagged += compare_actions(gs["action"], gs["logits"], ow, acted & ~reborn, label)
+        finally:
+            ow.action[:] = ow_action_saved
         if nb:
-            check_births(gw, ow, nb, weight_std, f"{where} step {k + 1}")
-    assert C >= 0
+            check_births(gw, ow, nb, weight_std, label)
+        prev = gs
     return {"flagged": flagged, "births": births, **worst}
