@@ -11,8 +11,9 @@ Tolerances (derived from the arithmetic; see the design notes):
     (w' = w_parent + sigma N_j, noise from the oracle's stream):
     |gpu - expected| <= 1e-6 * (|expected| + sigma); and the drift against
     the oracle's child after several generations, relative to the operands
-    of the mutation: |gpu - oracle| <= 1e-6 * (|oracle| + |parent| + sigma)
-    (each generation may round the parent differently by one ulp);
+    of the mutation and scaled by the child's generation g (each mutation
+    adds its own rounding, the initial draw one more):
+    |gpu - oracle| <= (g + 1) 1e-6 (|oracle| + |parent| + sigma);
   * actions: equal, except where the oracle's top-two logit margin is below
     1e-5 * max(1, max|logit|) (flagged, not counted as a mismatch).
 """
@@ -42,10 +43,11 @@ def weights_close(gpu, ref, std, what):
                            f"{(np.abs(gpu - ref) / (np.abs(ref) + std)).max():.3g}")
 
 
-def weights_drift_close(gpu, ref, parent, std, what):
+def weights_drift_close(gpu, ref, parent, std, generation, what):
     gpu = np.asarray(gpu, np.float64)
     ref = np.asarray(ref, np.float64)
-    bound = W_TOL * (np.abs(ref) + np.abs(np.asarray(parent, np.float64)) + std)
+    # the initial draw counts as one more rounding step
+    bound = (generation + 1) * W_TOL * (np.abs(ref) + np.abs(np.asarray(parent, np.float64)) + std)
     bad = np.abs(gpu - ref) > bound
     assert not bad.any(), f"{what}: {int(bad.sum())} weights drifted"
 
@@ -89,8 +91,9 @@ def compare_actions(g_action, g_logits, ow, acted, where: str) -> int:
     return int((diff & flagged).sum())
 
 
-def check_births(gw, ow, nb, sigma, where):
-    """Weights of this step's children (see the tolerance rules above)."""
+def check_births(gw, ow, nb, sigma, where, gen):
+    """Weights of this step's children (see the tolerance rules above);
+    gen[slot] is the generation of the agent in the slot (updated here)."""
     from oracle import pyoracle
     t = int(ow.counters[0]) - 1
     parents = ow.birth_parent[:nb].copy()
@@ -100,7 +103,9 @@ def check_births(gw, ow, nb, sigma, where):
         wc = gw.read_state(fields=(), weights=(int(ch), 1))["weights"][0]
         expected = pyoracle.fill_normals(ow.seed, pyoracle.TAG_MUT, t, int(par), sigma, wp)
         weights_close(wc, expected, sigma, f"{where} child {ch} (mutation)")
-        weights_drift_close(wc, ow.weights[ch], ow.weights[par], sigma, f"{where} child {ch}")
+        gen[ch] = gen[par] + 1
+        weights_drift_close(wc, ow.weights[ch], ow.weights[par], sigma, gen[ch],
+                            f"{where} child {ch} (generation {gen[ch]})")
 
 
 def _diagnose(prev, gs, ow, forced, where):
@@ -134,6 +139,7 @@ def run_forced(gw, ow, steps: int, where: str, weight_std: float,
     worst = {"h": 0.0, "c": 0.0}
     births = 0
     prev = gw.read_state()
+    gen = np.zeros(ow.p.capacity, np.int64)   # loaded/initial agents: generation 0
     for k in range(steps):
         acted = ow.alive.copy().astype(bool)
         ow.step()
@@ -160,6 +166,6 @@ def run_forced(gw, ow, steps: int, where: str, weight_std: float,
         finally:
             ow.action[:] = ow_action_saved
         if nb:
-            check_births(gw, ow, nb, weight_std, label)
+            check_births(gw, ow, nb, weight_std, label, gen)
         prev = gs
     return {"flagged": flagged, "births": births, **worst}
