@@ -3,43 +3,57 @@
 //
 // Every agent has its own 93 KB of FP32 weights, used once per step, so the
 // step is a batched GEMV bound by HBM bandwidth (about 0.5 flop per byte).
-// Design:
-//   * unit of work = one weight block of one agent (32 gate rows = all four
-//     gates of 8 hidden units, 23,168 bytes); an agent is 4 units;
-//   * a persistent grid of one CTA per SM; CTA b owns a contiguous range of
-//     the units of all worlds of the batch (world-major, alive list order);
-//   * a producer lane streams the blocks with plain (non-multicast)
-//     cp.async.bulk copies into an 8-stage shared-memory ring guarded by
-//     mbarriers, so about 180 KB per SM are in flight;
-//   * four consumer warps take the units round-robin: each gathers the
-//     agent's 7x7x3 observation (bit planes staged through shared memory)
-//     and previous hidden state into a 180-float input vector while the
-//     copy is in flight, then each lane computes one gate row with 128-bit
-//     shared loads (conflict-free: rows are 720 B apart), applies the gate
-//     nonlinearity, and lanes 0, 4, .., 28 update the cell state of their
-//     hidden unit;
-//   * the last of an agent's four units to finish (atomic arrival counter)
-//     computes the 5 logits from the new hidden state and takes the argmax.
-// Every mbarrier wait is bounded; a wait that runs out sets ST_TIMEOUT, the
-// CTA stops issuing copies, waits (bounded) for the copies in flight and
-// returns.
+// A persistent grid of one CTA per SM; CTA b owns a contiguous range of the
+// agents of all worlds of the batch (world-major, alive-list order) and runs
+// a warp-specialised pipeline with no global synchronisation:
+//   * producer warp: streams each agent's four weight blocks (a block = the
+//     32 gate rows of 8 hidden units, 23,168 B; the last block also carries
+//     the read-out) with plain (non-multicast) cp.async.bulk copies into an
+//     8-stage shared-memory ring (two agents in flight, ~190 KB per SM);
+//   * two gather warps: build each agent's input [obs(148); h(32)] and its
+//     cell state into a 4-entry ring: the 7x7x3 window is staged through
+//     shared memory as 7-bit row masks of the bit planes; agent slots and
+//     positions are prefetched 32 agents at a time, one lane per agent;
+//   * four compute warps, warp q on block q: lane l computes gate row l with
+//     128-bit shared loads (conflict-free: rows are 720 B apart), the gate
+//     nonlinearity, and lanes 0, 4, .., 28 update the cell of their hidden
+//     unit; warp 3 then takes the 32 new hidden values and computes the 5
+//     logits and the argmax (first maximum).
+// Every hand-off is an mbarrier with a bounded wait; a wait that runs out
+// sets ST_TIMEOUT, every role leaves its loop, and the CTA waits (bounded)
+// for the copies it issued before returning.
 #include "ecoevo_dev.cuh"
 
 namespace eco {
 
-constexpr int LSTAGES = 8;
-constexpr int NCONS = 4;
-constexpr int LTHREADS = (NCONS + 1) * 32;
+constexpr int LSTAGES = 8;                 // two agents of four blocks
+constexpr int VRING = 4;                   // gathered inputs in flight
+constexpr int NCOMP = 4;                   // compute warps (one per block)
+constexpr int NGATH = 2;                   // gather warps
+constexpr int W_PROD = NCOMP + NGATH;      // producer warp index
+constexpr int LTHREADS = (NCOMP + NGATH + 1) * 32;
 constexpr int MAX_BATCH = 1024;
-constexpr int VLEN = 184;  // 180 inputs padded to a 16-byte multiple
+constexpr int VLEN = 184;                  // 180 inputs padded to 16 B
+constexpr int STAGE_FLOATS = 5960;         // block + read-out (165) + pad
+static_assert((STAGE_FLOATS * 4) % 16 == 0, "bulk copies are 16-B multiples");
+static_assert(3 * BLK_FLOATS + STAGE_FLOATS <= WSTRIDE, "last copy stays in the slot");
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
 
+struct VEntry {
+  float v[VLEN];      // [obs; h_prev]
+  float c[HID];       // cell state before the step
+  float hn[HID];      // new hidden state, filled by the compute warps
+  float *c_row, *h_row, *logits_row;  // outputs of the agent
+  int32_t *action;
+  int slot, pad[3];
+};
+
 struct __align__(128) LstmSmem {
-  float stage[LSTAGES][BLK_FLOATS];
-  float v[NCONS][VLEN];
-  uint32_t masks[NCONS][16];
-  unsigned long long full[LSTAGES];
-  unsigned long long empty[LSTAGES];
+  float stage[LSTAGES][STAGE_FLOATS];
+  VEntry ring[VRING];
+  uint32_t masks[NGATH][16];
+  unsigned long long full[LSTAGES], empty[LSTAGES];
+  unsigned long long vfull[VRING], vempty[VRING], hready[VRING];
   int prefix[MAX_BATCH + 1];
   int issued;
   volatile int abort_flag;
@@ -111,15 +125,17 @@ __device__ inline uint32_t row7(const uint32_t *row, int Wp, int W, int xs,
   return m;
 }
 
-// Input vector [obs(148); h(32)] of `slot` into v, by one warp.  The grid is
-// the resource plane after this step's regrowth, the agent channel is the
-// start-of-step occupancy without the agent itself, off-grid cells read as
-// wall, the last observation is the agent's energy.
-__device__ inline void gather_input(const WorldDev &wd, int slot,
-                                    const uint32_t *res, const float *h_prev,
-                                    float *v, uint32_t *masks, int lane) {
+// Input of one agent into a ring entry, by one warp: [obs(148); h(32)] and
+// the cell state.  The grid is the resource plane after this step's
+// regrowth, the agent channel is the start-of-step occupancy without the
+// agent itself, off-grid cells read as wall, the last observation is the
+// agent's energy.
+__device__ inline void gather_input(const WorldDev &wd, int slot, int y, int x,
+                                    float energy, uint32_t t, VEntry &e,
+                                    uint32_t *masks, int lane) {
   const int H = wd.H, W = wd.W, Wp = wd.Wp;
-  const int y = wd.y[slot], x = wd.x[slot];
+  const uint32_t *res = (t & 1u) ? wd.res0 : wd.res1;
+  const float *h_prev = (t & 1u) ? wd.h1 : wd.h0;
   if (lane < 14) {
     const bool is_wall = lane >= 7;
     const int yy = y - 3 + (is_wall ? lane - 7 : lane);
@@ -130,61 +146,86 @@ __device__ inline void gather_input(const WorldDev &wd, int slot,
       m = row7((is_wall ? wd.wall : res) + (size_t)yy * Wp, Wp, W, x - 3, is_wall);
     masks[lane] = m;
   }
-  for (int k = lane; k < 49; k += 32) {
+  float occ[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int k = lane + 32 * r;
     const int yy = y + k / 7 - 3, xx = x + k % 7 - 3;
-    float a = 0.f;
-    if (k != 24 && yy >= 0 && yy < H && xx >= 0 && xx < W)
-      a = wd.slot_map[(size_t)yy * W + xx] >= 0 ? 1.f : 0.f;
-    v[49 + k] = a;
+    occ[r] = 0.f;
+    if (k < 49 && k != 24 && yy >= 0 && yy < H && xx >= 0 && xx < W)
+      occ[r] = wd.slot_map[(size_t)yy * W + xx] >= 0 ? 1.f : 0.f;
   }
-  if (lane == 0) v[147] = wd.energy[slot];
-  v[NOBS + lane] = h_prev[(size_t)slot * HID + lane];
+  const float hp = h_prev[(size_t)slot * HID + lane];
+  const float cp = wd.c[(size_t)slot * HID + lane];
   __syncwarp();
+  e.v[49 + lane] = occ[0];
+  if (lane + 32 < 49) e.v[49 + 32 + lane] = occ[1];
   for (int k = lane; k < 49; k += 32) {
     const int r = k / 7, cc = k % 7;
-    v[k] = (float)((masks[r] >> cc) & 1u);
-    v[98 + k] = (float)((masks[7 + r] >> cc) & 1u);
+    e.v[k] = (float)((masks[r] >> cc) & 1u);
+    e.v[98 + k] = (float)((masks[7 + r] >> cc) & 1u);
   }
-  __syncwarp();
+  if (lane == 0) {
+    e.v[147] = energy;
+    e.slot = slot;
+    e.c_row = wd.c + (size_t)slot * HID;
+    e.h_row = ((t & 1u) ? wd.h0 : wd.h1) + (size_t)slot * HID;
+    e.logits_row = wd.logits + (size_t)slot * 8;
+    e.action = wd.action + slot;
+  }
+  e.v[NOBS + lane] = hp;
+  e.c[lane] = cp;
 }
 
-__device__ inline void advance_world(const int *prefix, int &w, int u) {
-  while (u >= prefix[w + 1]) ++w;
+// World of global agent index a (prefix over worlds in shared memory).
+__device__ inline int world_of(const int *prefix, int n, int a) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= a) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
 __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(BatchDev b) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   LstmSmem &sm = *reinterpret_cast<LstmSmem *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned FULL = 0xFFFFFFFFu;
 
-  // units per world: 4 * population (= alive-list length at step start)
+  // agents per world (= alive-list length at the start of the step)
   if (warp == 0) {
     const int per = (b.n + 31) / 32;
     int local = 0;
     for (int i = 0; i < per; ++i) {
       const int w = lane * per + i;
-      if (w < b.n) local += NBLK * (int)b.worlds[w]->ctr->pop;
+      if (w < b.n) local += (int)b.worlds[w]->ctr->pop;
     }
     int incl = local;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= o) incl += t;
+      const int v = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += v;
     }
     int run = incl - local;
     for (int i = 0; i < per; ++i) {
       const int w = lane * per + i;
       if (w < b.n) {
         sm.prefix[w] = run;
-        run += NBLK * (int)b.worlds[w]->ctr->pop;
+        run += (int)b.worlds[w]->ctr->pop;
       }
     }
     if (lane == 31) sm.prefix[b.n] = incl;
   }
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < LSTAGES; ++s) {
-      mbar_init(&sm.full[s], 1);
-      mbar_init(&sm.empty[s], 1);
+  if (threadIdx.x == 32) {
+    for (int i = 0; i < LSTAGES; ++i) {
+      mbar_init(&sm.full[i], 1);
+      mbar_init(&sm.empty[i], 1);
+    }
+    for (int i = 0; i < VRING; ++i) {
+      mbar_init(&sm.vfull[i], 1);
+      mbar_init(&sm.vempty[i], 1);
+      mbar_init(&sm.hready[i], NCOMP);
     }
     sm.issued = 0;
     sm.abort_flag = 0;
@@ -192,65 +233,109 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(BatchDev b) {
   }
   __syncthreads();
 
-  const long long U = sm.prefix[b.n];
-  const int u_begin = (int)(U * blockIdx.x / gridDim.x);
-  const int u_end = (int)(U * (blockIdx.x + 1) / gridDim.x);
+  const long long A = sm.prefix[b.n];
+  const int a_begin = (int)(A * blockIdx.x / gridDim.x);
+  const int a_end = (int)(A * (blockIdx.x + 1) / gridDim.x);
+  const int n_agents = a_end - a_begin;
   int *status = &b.worlds[0]->ctr->status;
 
-  if (warp == NCONS) {
-    // ---------------- producer: one lane issues the bulk copies ----------
-    if (lane == 0 && u_begin < u_end) {
-      int w = 0;
-      advance_world(sm.prefix, w, u_begin);
-      int n = 0;
-      for (int u = u_begin; u < u_end; ++u, ++n) {
-        advance_world(sm.prefix, w, u);
-        const WorldDev &wd = *b.worlds[w];
-        const int lu = u - sm.prefix[w];
-        const int slot = wd.alive_list[lu >> 2];
-        const int st = n % LSTAGES;
-        if (n >= LSTAGES && !mbar_wait(&sm.empty[st], ((n / LSTAGES) - 1) & 1)) {
-          atomicOr(status, ST_TIMEOUT);
-          sm.abort_flag = 1;
-          break;
+  if (warp == W_PROD) {
+    // ------------------------------------------------ producer -------------
+    int my_slot = 0;
+    const float *my_w = nullptr;
+    int issued = 0;
+    for (int n = 0; n < n_agents; ++n) {
+      if ((n & 31) == 0) {
+        const int a = a_begin + n + lane;
+        if (a < a_end) {
+          const int w = world_of(sm.prefix, b.n, a);
+          const WorldDev *wd = b.worlds[w];
+          my_slot = wd->alive_list[a - sm.prefix[w]];
+          my_w = wd->weights;
         }
-        if (sm.abort_flag) break;
-        const float *src = wd.weights + (size_t)slot * WSTRIDE + (lu & 3) * BLK_FLOATS;
-        mbar_expect_tx(&sm.full[st], BLK_BYTES);
-        bulk_copy_g2s(sm.stage[st], src, BLK_BYTES, &sm.full[st]);
-        sm.issued = n + 1;
       }
-    }
-  } else {
-    // ---------------- consumers ------------------------------------------
-    float *v = sm.v[warp];
-    uint32_t *masks = sm.masks[warp];
-    int w = 0;
-    if (u_begin < u_end) advance_world(sm.prefix, w, u_begin);
-    for (int n = warp; u_begin + n < u_end; n += NCONS) {
+      const int slot = __shfl_sync(FULL, my_slot, n & 31);
+      const float *wts = reinterpret_cast<const float *>(
+          __shfl_sync(FULL, reinterpret_cast<unsigned long long>(my_w), n & 31));
+      if (lane == 0) {
+        for (int q = 0; q < NBLK; ++q) {
+          const int u = NBLK * n + q, st = u % LSTAGES, k = u / LSTAGES;
+          if (k > 0 && !mbar_wait(&sm.empty[st], (k - 1) & 1)) {
+            atomicOr(status, ST_TIMEOUT);
+            sm.abort_flag = 1;
+            break;
+          }
+          const uint32_t bytes = (q == NBLK - 1) ? STAGE_FLOATS * 4 : BLK_BYTES;
+          mbar_expect_tx(&sm.full[st], bytes);
+          bulk_copy_g2s(sm.stage[st], wts + (size_t)slot * WSTRIDE + q * BLK_FLOATS, bytes,
+                        &sm.full[st]);
+          issued = u + 1;
+        }
+      }
+      __syncwarp();
       if (sm.abort_flag) break;
-      const int u = u_begin + n;
-      advance_world(sm.prefix, w, u);
-      const WorldDev &wd = *b.worlds[w];
-      const int lu = u - sm.prefix[w];
-      const int slot = wd.alive_list[lu >> 2];
-      const int q = lu & 3;
-      const uint32_t t = (uint32_t)wd.ctr->t;
-      const uint32_t *res_new = (t & 1u) ? wd.res0 : wd.res1;
-      const float *h_prev = (t & 1u) ? wd.h1 : wd.h0;
-      float *h_next = (t & 1u) ? wd.h0 : wd.h1;
-
-      gather_input(wd, slot, res_new, h_prev, v, masks, lane);
-
-      const int st = n % LSTAGES;
-      if (!mbar_wait(&sm.full[st], (n / LSTAGES) & 1)) {
+    }
+    if (lane == 0) sm.issued = issued;
+  } else if (warp >= NCOMP) {
+    // ------------------------------------------------ gather ---------------
+    const int gw = warp - NCOMP;
+    int my_slot = 0, my_y = 0, my_x = 0;
+    float my_e = 0.f;
+    uint32_t my_t = 0;
+    const WorldDev *my_wd = nullptr;
+    for (int m = 0;; ++m) {
+      const int n = gw + NGATH * m;
+      if (n >= n_agents) break;
+      if ((m & 31) == 0) {
+        const int a = a_begin + gw + NGATH * (m + lane);
+        if (a < a_end) {
+          const int w = world_of(sm.prefix, b.n, a);
+          my_wd = b.worlds[w];
+          my_slot = my_wd->alive_list[a - sm.prefix[w]];
+          my_y = my_wd->y[my_slot];
+          my_x = my_wd->x[my_slot];
+          my_e = my_wd->energy[my_slot];
+          my_t = (uint32_t)my_wd->ctr->t;
+        }
+      }
+      const int src = m & 31;
+      const int slot = __shfl_sync(FULL, my_slot, src);
+      const int y = __shfl_sync(FULL, my_y, src);
+      const int x = __shfl_sync(FULL, my_x, src);
+      const float e = __shfl_sync(FULL, my_e, src);
+      const uint32_t t = __shfl_sync(FULL, my_t, src);
+      const WorldDev *wd = reinterpret_cast<const WorldDev *>(
+          __shfl_sync(FULL, reinterpret_cast<unsigned long long>(my_wd), src));
+      const int ei = n % VRING, k = n / VRING;
+      bool ok = true;
+      if (lane == 0 && k > 0) ok = mbar_wait(&sm.vempty[ei], (k - 1) & 1);
+      if (!__shfl_sync(FULL, ok ? 1 : 0, 0)) {
         if (lane == 0) atomicOr(status, ST_TIMEOUT);
         sm.abort_flag = 1;
         break;
       }
+      gather_input(*wd, slot, y, x, e, t, sm.ring[ei], sm.masks[gw], lane);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.vfull[ei]);
+      if (sm.abort_flag) break;
+    }
+  } else {
+    // ------------------------------------------------ compute --------------
+    const int q = warp;
+    for (int n = 0; n < n_agents; ++n) {
+      if (sm.abort_flag) break;
+      const int ei = n % VRING, kv = n / VRING;
+      const int u = NBLK * n + q, st = u % LSTAGES, ks = u / LSTAGES;
+      if (!mbar_wait(&sm.vfull[ei], kv & 1) || !mbar_wait(&sm.full[st], ks & 1)) {
+        if (lane == 0) atomicOr(status, ST_TIMEOUT);
+        sm.abort_flag = 1;
+        break;
+      }
+      VEntry &E = sm.ring[ei];
+      const float *stg = sm.stage[st];
       // gate row `lane` of block q: z = W_row . [obs; h] + b_row
-      const float4 *W4 = reinterpret_cast<const float4 *>(sm.stage[st] + lane * NIN);
-      const float4 *V4 = reinterpret_cast<const float4 *>(v);
+      const float4 *W4 = reinterpret_cast<const float4 *>(stg + lane * NIN);
+      const float4 *V4 = reinterpret_cast<const float4 *>(E.v);
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll 9
       for (int k = 0; k < NIN / 4; ++k) {
@@ -260,54 +345,59 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(BatchDev b) {
         a2 = fmaf(wv.z, xv.z, a2);
         a3 = fmaf(wv.w, xv.w, a3);
       }
-      const float z = ((a0 + a1) + (a2 + a3)) + sm.stage[st][BLK_ROWS * NIN + lane];
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sm.empty[st]);
-
+      const float z = ((a0 + a1) + (a2 + a3)) + stg[BLK_ROWS * NIN + lane];
+      if (q < NCOMP - 1) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.empty[st]);
+      }
       // gate (lane % 4): 0 input, 1 forget, 2 candidate (tanh), 3 output
       const int g = lane & 3;
       const float act = (g == 2) ? tanhf(z) : 1.0f / (1.0f + expf(-z));
       const int base = lane & ~3;
-      const float gi = __shfl_sync(0xFFFFFFFFu, act, base);
-      const float gf = __shfl_sync(0xFFFFFFFFu, act, base + 1);
-      const float gg = __shfl_sync(0xFFFFFFFFu, act, base + 2);
-      const float go = __shfl_sync(0xFFFFFFFFu, act, base + 3);
+      const float gi = __shfl_sync(FULL, act, base);
+      const float gf = __shfl_sync(FULL, act, base + 1);
+      const float gg = __shfl_sync(FULL, act, base + 2);
+      const float go = __shfl_sync(FULL, act, base + 3);
       if (g == 0) {
-        const size_t j = (size_t)slot * HID + 8 * q + (lane >> 2);
-        const float cn = gf * wd.c[j] + gi * gg;
-        wd.c[j] = cn;
-        h_next[j] = go * tanhf(cn);
+        const int j = 8 * q + (lane >> 2);
+        const float cn = gf * E.c[j] + gi * gg;
+        const float hn = go * tanhf(cn);
+        E.hn[j] = hn;
+        E.c_row[j] = cn;
+        E.h_row[j] = hn;
       }
-      __threadfence();
       __syncwarp();
-      unsigned old = 0;
-      if (lane == 0) old = atomicAdd(&wd.arrive[slot], 1u);
-      old = __shfl_sync(0xFFFFFFFFu, old, 0);
-      if (old == NBLK - 1) {
-        // last block of the agent: read-out and argmax (first maximum)
-        __threadfence();
-        const float hj = __ldcg(&h_next[(size_t)slot * HID + lane]);
-        const float *tail = wd.weights + (size_t)slot * WSTRIDE + TAIL;
+      if (lane == 0) mbar_arrive(&sm.hready[ei]);
+      if (q == NCOMP - 1) {
+        // read-out: logits = Wo h' + bo over the whole hidden state
+        if (!mbar_wait(&sm.hready[ei], kv & 1)) {
+          if (lane == 0) atomicOr(status, ST_TIMEOUT);
+          sm.abort_flag = 1;
+          break;
+        }
+        const float hj = E.hn[lane];
+        const float *tail = stg + BLK_FLOATS;
         float lg[NACT];
 #pragma unroll
         for (int a = 0; a < NACT; ++a) {
           float p = tail[a * HID + lane] * hj;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xFFFFFFFFu, p, o);
+          for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
           lg[a] = p + tail[NACT * HID + a];
         }
         int best = 0;
-#pragma unroll
-        for (int a = 1; a < NACT; ++a)
-          if (lg[a] > lg[best]) best = a;
         float mine = lg[0];
 #pragma unroll
-        for (int a = 1; a < NACT; ++a)
+        for (int a = 1; a < NACT; ++a) {
+          if (lg[a] > lg[best]) best = a;
           if (lane == a) mine = lg[a];
-        if (lane < NACT) wd.logits[(size_t)slot * 8 + lane] = mine;
+        }
+        if (lane < NACT) E.logits_row[lane] = mine;
+        if (lane == 0) *E.action = best;
+        __syncwarp();
         if (lane == 0) {
-          wd.action[slot] = best;
-          wd.arrive[slot] = 0u;
+          mbar_arrive(&sm.empty[st]);
+          mbar_arrive(&sm.vempty[ei]);
         }
       }
     }
