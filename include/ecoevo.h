@@ -207,6 +207,38 @@ int eco_kernels_per_step(void);
 
 const char *eco_strerror(int code);
 
+/* Move resolution that allocates no device memory.  The paper has no
+ * counterpart to this entry point: it exists for callers that cannot call
+ * cudaMalloc -- for example code that runs under another allocator which
+ * owns all of the device's memory, or a loop that must not stall on the
+ * device-wide synchronisation an allocation can cause.
+ *
+ * Applies one round of moves with the rule of the simulation step: agent s
+ * (alive[s] != 0) with action a in {1 N, 2 S, 3 E, 4 W} moves to its target
+ * cell iff the cell is on the grid, not a wall, empty in slot_map at the
+ * start of the call, and s is the lowest slot claiming it; every other agent
+ * stays.  With wall_kills != 0, killed[s] = 1 for an agent whose target is a
+ * wall or off the grid (killed may be NULL; the caller removes such agents).
+ *   wall      uint8 [H*W]  row-major, nonzero = wall              (device)
+ *   alive     uint8 [capacity]                                    (device)
+ *   actions   int32 [capacity], values 0..4 (others mean stay)    (device)
+ *   y, x      int32 [capacity], in/out positions                  (device)
+ *   slot_map  int32 [H*W], in/out: -1 or the slot on the cell     (device)
+ *   killed    uint8 [capacity] or NULL, out                       (device)
+ *   stream    cudaStream_t the work is enqueued on (asynchronous)
+ * The per-cell claims live in one fixed array inside the library, sized for
+ * at most 2^21 cells (H*W <= 2,097,152; larger grids return ECO_EINVAL with a
+ * message on stderr); every GPU that loads the library keeps those 8 MiB
+ * until the process exits.  The first call on each device looks up the
+ * array's device address; make that first call before any stream capture.
+ * Each call resets the claims it uses, but all calls share the one array:
+ * calls that overlap on the GPU (other streams, other threads) race and must
+ * be serialised by the caller.  Errors: ECO_EINVAL, ECO_ECUDA. */
+int eco_moves_noalloc(int32_t H, int32_t W, int32_t capacity, int32_t wall_kills,
+                      const uint8_t *wall, const uint8_t *alive,
+                      const int32_t *actions, int32_t *y, int32_t *x,
+                      int32_t *slot_map, uint8_t *killed, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

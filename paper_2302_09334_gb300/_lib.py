@@ -98,6 +98,8 @@ SIGNATURES = {
     "eco_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
     "eco_kernels_per_step": (ctypes.c_int, []),
     "eco_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "eco_moves_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 
 _lib = None
