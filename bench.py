@@ -147,7 +147,8 @@ def bench_reference(args, params, rank, world_size):
 def config_of(args, params):
     return {"workload": args.workload, "H": params.H, "W": params.W,
             "n_agents0": params.n_agents0, "capacity": params.capacity, "seed": "rank",
-            "population": "free-running", "l2": "flushed (256 MB write) before every step",
+            "population": "held" if args.held else "free-running",
+            "l2": "flushed (256 MB write) before every step",
             "parallelism": f"replicas{args.gpus}"}
 
 
@@ -164,7 +165,7 @@ def bench_ours(args, params, rank, world_size, dist):
     world = World(params, seed=rank, device=local)
     stream = world.stream
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    kps = lib().eco_kernels_per_step()
+    kps = lib().eco_kernels_per_step(world.handle)
 
     def flush_l2():
         with torch.cuda.stream(stream):
@@ -244,7 +245,7 @@ def bench_ours(args, params, rank, world_size, dist):
         "config": config_of(args, params),
         "cell_steps_per_s": cell_steps / (total_ms / 1e3),
         "mean_population": agent_steps / max(args.steps * world_size, 1),
-        "kernel_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
+        "kernel_ms_per_step": {k: v[0] / v[1] for k, v in prof.items() if v[1]},
         "roofline": {"kernel": "observe_lstm", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
@@ -271,11 +272,19 @@ def main():
     ap.add_argument("--workload", default="paper_200x400")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--held", action="store_true",
+                    help="no energy decay and no births: the population stays at n_agents0")
+    ap.add_argument("--n-agents", type=int, default=None, help="override n_agents0")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     from paper_2302_09334_gb300.params import PRESETS
     params = PRESETS[args.workload]()
+    if args.n_agents is not None:
+        params = params.replace(n_agents0=args.n_agents)
+    if args.held:
+        from paper_2302_09334_gb300.params import held
+        params = held(params)
 
     rank = int(os.environ.get("RANK", "0"))
     world_size = int(os.environ.get("WORLD_SIZE", "1"))

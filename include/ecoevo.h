@@ -195,15 +195,18 @@ void eco_batch_destroy(EcoBatch *batch);
 /* Per-kernel timing with CUDA events on the world's stream.  While enabled,
  * steps are launched kernel by kernel with an event between kernels;
  * eco_world_profile_read sums the elapsed times since enabling:
- * ms[k], launches[k] for k < ECO_NKERNELS (names: eco_kernel_name).
- * Synchronous read.  max_steps bounds the recorded steps. */
-#define ECO_NKERNELS 8
+ * ms[k], launches[k] for k < ECO_NKERNELS (names: eco_kernel_name; a kernel
+ * the world's step does not launch keeps 0 launches).  Synchronous read.
+ * max_steps bounds the recorded steps.  Worlds of capacity <= 16384 run the
+ * slot phases (moves, physiology, birth claims, compaction) as one kernel
+ * "agents_fused"; larger ones as five kernels. */
+#define ECO_NKERNELS 9
 int eco_world_profile(EcoWorld *world, int enable, int max_steps);
 int eco_world_profile_read(EcoWorld *world, double *ms, int64_t *launches);
 const char *eco_kernel_name(int k);
 
-/* Number of the library's kernels one step launches. */
-int eco_kernels_per_step(void);
+/* Number of the library's kernels one step of this world launches. */
+int eco_kernels_per_step(const EcoWorld *world);
 
 const char *eco_strerror(int code);
 

@@ -13,7 +13,7 @@ from .params import EcoParams
 ECO_ABI_V1 = 0x45434F01
 ECO_OK, ECO_EINVAL, ECO_ENOMEM, ECO_ECUDA, ECO_ETIMEOUT, ECO_ESTATE = 0, -1, -2, -3, -4, -5
 NCOUNTERS = 8
-NKERNELS = 8
+NKERNELS = 9
 (C_T, C_POP, C_BIRTHS, C_DEATHS, C_DROPPED, C_BIRTHS_LAST, C_DEATHS_LAST,
  C_DROPPED_LAST) = range(8)
 
@@ -96,7 +96,7 @@ SIGNATURES = {
     "eco_world_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_int64)]),
     "eco_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
-    "eco_kernels_per_step": (ctypes.c_int, []),
+    "eco_kernels_per_step": (ctypes.c_int, [_P]),
     "eco_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "eco_moves_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]),

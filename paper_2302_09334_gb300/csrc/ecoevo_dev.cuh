@@ -188,7 +188,11 @@ struct BatchDev {
   int total_tiles, total_slot_blocks;
   int max_capacity;
   int n_sms;
+  int fused;                 // every world has capacity <= FUSED_MAX_C
 };
+
+// Worlds up to this capacity run all slot phases of a step in one CTA.
+constexpr int FUSED_MAX_C = 16384;
 
 void launch_regrow(const BatchDev &b, cudaStream_t s);
 void launch_lstm(const BatchDev &b, cudaStream_t s);
@@ -198,6 +202,7 @@ void launch_physio(const BatchDev &b, cudaStream_t s);
 void launch_birth_claim(const BatchDev &b, cudaStream_t s);
 void launch_scan(const BatchDev &b, cudaStream_t s);
 void launch_spawn(const BatchDev &b, cudaStream_t s);
+void launch_agents_fused(const BatchDev &b, cudaStream_t s);
 void configure_lstm();   // once per device, before the first launch
 // Load every step kernel's code before a step is captured in a graph.
 void preload_regrow();

@@ -175,16 +175,41 @@ int tiles_of(const WorldDev &wd) {
 }
 int slot_blocks_of(const WorldDev &wd) { return (wd.C + SLOT_BLOCK - 1) / SLOT_BLOCK; }
 
-void launch_step(const EcoBatch &b, cudaStream_t s, Profile *prof, int step_ev) {
-  typedef void (*Launcher)(const BatchDev &, cudaStream_t);
-  static const Launcher order[ECO_NKERNELS] = {
-      launch_regrow, launch_lstm,        launch_move_claim, launch_move_apply,
-      launch_physio, launch_birth_claim, launch_scan,       launch_spawn};
-  for (int k = 0; k < ECO_NKERNELS; ++k) {
-    if (prof) cudaEventRecord(prof->ev[(size_t)step_ev * (ECO_NKERNELS + 1) + k], s);
-    order[k](b.bd, s);
+// Kernel ids for profiling (names: eco_kernel_name).
+enum { K_REGROW, K_LSTM, K_MOVE_CLAIM, K_MOVE_APPLY, K_PHYSIO, K_BIRTH_CLAIM, K_SCAN,
+       K_SPAWN, K_AGENTS_FUSED };
+typedef void (*Launcher)(const BatchDev &, cudaStream_t);
+struct StepKernel { int id; Launcher fn; };
+const StepKernel kSplitStep[] = {
+    {K_REGROW, launch_regrow},         {K_LSTM, launch_lstm},
+    {K_MOVE_CLAIM, launch_move_claim}, {K_MOVE_APPLY, launch_move_apply},
+    {K_PHYSIO, launch_physio},         {K_BIRTH_CLAIM, launch_birth_claim},
+    {K_SCAN, launch_scan},             {K_SPAWN, launch_spawn}};
+const StepKernel kFusedStep[] = {{K_REGROW, launch_regrow},
+                                 {K_LSTM, launch_lstm},
+                                 {K_AGENTS_FUSED, launch_agents_fused},
+                                 {K_SPAWN, launch_spawn}};
+
+int step_kernels(const BatchDev &bd, const StepKernel **list) {
+  if (bd.fused) {
+    *list = kFusedStep;
+    return (int)(sizeof(kFusedStep) / sizeof(kFusedStep[0]));
   }
-  if (prof) cudaEventRecord(prof->ev[(size_t)step_ev * (ECO_NKERNELS + 1) + ECO_NKERNELS], s);
+  *list = kSplitStep;
+  return (int)(sizeof(kSplitStep) / sizeof(kSplitStep[0]));
+}
+
+// One step; with a profiler, an event before every kernel and after the
+// last (events of step slot `step_ev`).
+void launch_step(const EcoBatch &b, cudaStream_t s, Profile *prof, int step_ev) {
+  const StepKernel *list;
+  const int nk = step_kernels(b.bd, &list);
+  cudaEvent_t *ev = prof ? &prof->ev[(size_t)step_ev * (ECO_NKERNELS + 1)] : nullptr;
+  for (int k = 0; k < nk; ++k) {
+    if (ev) cudaEventRecord(ev[k], s);
+    list[k].fn(b.bd, s);
+  }
+  if (ev) cudaEventRecord(ev[nk], s);
 }
 
 void destroy_graphs(EcoBatch &b) {
@@ -240,6 +265,7 @@ int batch_init(EcoBatch &b, EcoWorld *const *worlds, int n, void *table_dev) {
   b.bd.total_slot_blocks = bb;
   b.bd.max_capacity = maxc;
   b.bd.n_sms = worlds[0]->n_sms;
+  b.bd.fused = maxc <= FUSED_MAX_C ? 1 : 0;
   b.prof = &worlds[0]->prof;
   return ECO_OK;
 }
@@ -717,13 +743,15 @@ int eco_world_profile_read(EcoWorld *w, double *ms, int64_t *launches) {
   if (!w || !ms || !launches) return ECO_EINVAL;
   Profile &pr = w->prof;
   ECO_CU(cudaStreamSynchronize(w->stream));
+  const StepKernel *list;
+  const int nk = step_kernels(w->self.bd, &list);
   for (int s = 0; s < pr.used; ++s) {
-    for (int k = 0; k < ECO_NKERNELS; ++k) {
+    for (int k = 0; k < nk; ++k) {
       float t = 0.f;
       ECO_CU(cudaEventElapsedTime(&t, pr.ev[(size_t)s * (ECO_NKERNELS + 1) + k],
                                   pr.ev[(size_t)s * (ECO_NKERNELS + 1) + k + 1]));
-      pr.ms[k] += t;
-      pr.launches[k] += 1;
+      pr.ms[list[k].id] += t;
+      pr.launches[list[k].id] += 1;
     }
   }
   pr.used = 0;
@@ -735,13 +763,17 @@ int eco_world_profile_read(EcoWorld *w, double *ms, int64_t *launches) {
 }
 
 const char *eco_kernel_name(int k) {
-  static const char *names[ECO_NKERNELS] = {"regrow",  "observe_lstm", "move_claim",
-                                            "move_apply", "physio",   "birth_claim",
-                                            "scan",    "spawn"};
+  static const char *names[ECO_NKERNELS] = {
+      "regrow", "observe_lstm", "move_claim", "move_apply", "physio",
+      "birth_claim", "scan", "spawn", "agents_fused"};
   return (k >= 0 && k < ECO_NKERNELS) ? names[k] : "?";
 }
 
-int eco_kernels_per_step(void) { return ECO_NKERNELS; }
+int eco_kernels_per_step(const EcoWorld *w) {
+  if (!w) return ECO_EINVAL;
+  const StepKernel *list;
+  return step_kernels(w->self.bd, &list);
+}
 
 const char *eco_strerror(int code) {
   switch (code) {

@@ -43,10 +43,7 @@ __constant__ int kDY[5] = {0, -1, 1, 0, 0};  // stay, N, S, E, W
 __constant__ int kDX[5] = {0, 0, 0, 1, -1};
 
 // ---------------------------------------------------------------- a4 ------
-__global__ void __launch_bounds__(SLOT_BLOCK) k_move_claim(BatchDev b) {
-  const WorldDev *wd;
-  const int s = slot_of_thread(b, wd);
-  if (s < 0) return;
+__device__ inline void slot_move_claim(const WorldDev *wd, int s) {
   wd->killed[s] = 0;
   wd->target[s] = -1;
   if (!wd->alive[s]) return;
@@ -64,10 +61,7 @@ __global__ void __launch_bounds__(SLOT_BLOCK) k_move_claim(BatchDev b) {
   atomicMin(&wd->claim[cell], s);
 }
 
-__global__ void __launch_bounds__(SLOT_BLOCK) k_move_apply(BatchDev b) {
-  const WorldDev *wd;
-  const int s = slot_of_thread(b, wd);
-  if (s < 0) return;
+__device__ inline void slot_move_apply(const WorldDev *wd, int s) {
   const int cell = wd->target[s];
   if (cell < 0 || wd->claim[cell] != s) return;
   wd->claim[cell] = INT_MAX;  // only the winner resets; losers compare != s
@@ -78,10 +72,7 @@ __global__ void __launch_bounds__(SLOT_BLOCK) k_move_apply(BatchDev b) {
 }
 
 // ---------------------------------------------------------------- a5 ------
-__global__ void __launch_bounds__(SLOT_BLOCK) k_physio(BatchDev b) {
-  const WorldDev *wd;
-  const int s = slot_of_thread(b, wd);
-  if (s < 0) return;
+__device__ inline void slot_physio(const WorldDev *wd, int s) {
   wd->ate[s] = 0;
   if (!wd->alive[s]) return;
   const int y = wd->y[s], x = wd->x[s];
@@ -115,10 +106,7 @@ __global__ void __launch_bounds__(SLOT_BLOCK) k_physio(BatchDev b) {
 }
 
 // ---------------------------------------------------------------- a6 ------
-__global__ void __launch_bounds__(SLOT_BLOCK) k_birth_claim(BatchDev b) {
-  const WorldDev *wd;
-  const int s = slot_of_thread(b, wd);
-  if (s < 0) return;
+__device__ inline void slot_birth_claim(const WorldDev *wd, int s) {
   wd->birth_cell[s] = -1;
   if (!wd->alive[s] || wd->repr_ctr[s] < wd->t_repr) return;
   const int y = wd->y[s], x = wd->x[s];
@@ -168,9 +156,8 @@ __device__ inline void block_scan2(int a, int b, int &ea, int &eb, int &ta,
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan(BatchDev b) {
-  __shared__ int sh[66];
-  const WorldDev &wd = *b.worlds[blockIdx.x];
+// Births and the next alive list of one world, by one CTA of SCAN_THREADS.
+__device__ void scan_world(const WorldDev &wd, int *sh) {
   const int C = wd.C;
   const int per = (C + SCAN_THREADS - 1) / SCAN_THREADS;
   const int s0 = min(C, (int)threadIdx.x * per), s1 = min(C, s0 + per);
@@ -254,6 +241,50 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(BatchDev b) {
     c.pop = pop;
     c.t = (long long)t + 1;
   }
+}
+
+__global__ void __launch_bounds__(SLOT_BLOCK) k_move_claim(BatchDev b) {
+  const WorldDev *wd;
+  const int s = slot_of_thread(b, wd);
+  if (s >= 0) slot_move_claim(wd, s);
+}
+__global__ void __launch_bounds__(SLOT_BLOCK) k_move_apply(BatchDev b) {
+  const WorldDev *wd;
+  const int s = slot_of_thread(b, wd);
+  if (s >= 0) slot_move_apply(wd, s);
+}
+__global__ void __launch_bounds__(SLOT_BLOCK) k_physio(BatchDev b) {
+  const WorldDev *wd;
+  const int s = slot_of_thread(b, wd);
+  if (s >= 0) slot_physio(wd, s);
+}
+__global__ void __launch_bounds__(SLOT_BLOCK) k_birth_claim(BatchDev b) {
+  const WorldDev *wd;
+  const int s = slot_of_thread(b, wd);
+  if (s >= 0) slot_birth_claim(wd, s);
+}
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan(BatchDev b) {
+  __shared__ int sh[66];
+  scan_world(*b.worlds[blockIdx.x], sh);
+}
+
+// Worlds of capacity <= FUSED_MAX_C: all slot phases of a step (moves,
+// eating and physiology, birth claims, compaction) in one CTA per world,
+// each phase separated by a block barrier, which orders the global memory
+// the next phase reads.
+__global__ void __launch_bounds__(SCAN_THREADS) k_agents_fused(BatchDev b) {
+  __shared__ int sh[66];
+  const WorldDev *wd = b.worlds[blockIdx.x];
+  const int C = wd->C;
+  for (int s = threadIdx.x; s < C; s += blockDim.x) slot_move_claim(wd, s);
+  __syncthreads();
+  for (int s = threadIdx.x; s < C; s += blockDim.x) slot_move_apply(wd, s);
+  __syncthreads();
+  for (int s = threadIdx.x; s < C; s += blockDim.x) slot_physio(wd, s);
+  __syncthreads();
+  for (int s = threadIdx.x; s < C; s += blockDim.x) slot_birth_claim(wd, s);
+  __syncthreads();
+  scan_world(*wd, sh);
 }
 
 // Child weights, physical layout: W[child][p] = W[parent][p] + sigma * N_j
@@ -347,6 +378,7 @@ void preload_agents() {
   cudaFuncGetAttributes(&a, k_birth_claim);
   cudaFuncGetAttributes(&a, k_scan);
   cudaFuncGetAttributes(&a, k_spawn);
+  cudaFuncGetAttributes(&a, k_agents_fused);
 }
 
 void launch_move_claim(const BatchDev &b, cudaStream_t s) {
@@ -363,6 +395,9 @@ void launch_birth_claim(const BatchDev &b, cudaStream_t s) {
 }
 void launch_scan(const BatchDev &b, cudaStream_t s) {
   k_scan<<<b.n, SCAN_THREADS, 0, s>>>(b);
+}
+void launch_agents_fused(const BatchDev &b, cudaStream_t s) {
+  k_agents_fused<<<b.n, SCAN_THREADS, 0, s>>>(b);
 }
 void launch_spawn(const BatchDev &b, cudaStream_t s) {
   k_spawn<<<2 * b.n_sms, SPAWN_THREADS, 0, s>>>(b);

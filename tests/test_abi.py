@@ -68,9 +68,10 @@ def test_world_bytes_and_validation(L):
 def test_strerror_and_kernel_names(L):
     assert L.eco_strerror(0) == b"ok"
     assert L.eco_strerror(_lib.ECO_ETIMEOUT) == b"device wait timed out"
-    assert L.eco_kernels_per_step() == 8
-    names = [L.eco_kernel_name(k) for k in range(8)]
-    assert names[1] == b"observe_lstm" and len(set(names)) == 8
+    assert L.eco_kernels_per_step(None) == _lib.ECO_EINVAL
+    names = [L.eco_kernel_name(k) for k in range(_lib.NKERNELS)]
+    assert names[1] == b"observe_lstm" and names[8] == b"agents_fused"
+    assert len(set(names)) == _lib.NKERNELS
 
 
 def test_create_rejects_bad_arguments_without_gpu(L):

@@ -59,6 +59,8 @@ EDGE_CASES = {
     "radius3_open": EcoParams(H=17, W=65, capacity=64, n_agents0=40, border_walls=0,
                               nbr_radius=3, class_edges=(1, 4, 9), e_decay=0.02),
     "word_multiple_8x64": EcoParams(H=8, W=64, capacity=64, n_agents0=32, t_repr=7),
+    # capacity above 16384: the slot phases run as five multi-CTA kernels
+    "split_path_cap20000": EcoParams(H=40, W=80, capacity=20000, n_agents0=400, t_repr=20),
 }
 
 
