@@ -193,7 +193,8 @@ int eco_batch_sync(EcoBatch *batch);
 void eco_batch_destroy(EcoBatch *batch);
 
 /* Per-kernel timing with CUDA events on the world's stream.  While enabled,
- * steps are launched kernel by kernel with an event between kernels;
+ * each step runs as a one-step CUDA graph with an event-record node before
+ * every kernel and after the last, pointed at fresh events every step;
  * eco_world_profile_read sums the elapsed times since enabling:
  * ms[k], launches[k] for k < ECO_NKERNELS (names: eco_kernel_name; a kernel
  * the world's step does not launch keeps 0 launches).  Synchronous read.

@@ -181,6 +181,7 @@ __device__ inline bool bit_at(const uint32_t *plane, int Wp, int y, int x) {
 // Kernel launchers (one per kernel source).
 // ---------------------------------------------------------------------------
 struct BatchDev {
+  WorldDev w0;               // descriptor of worlds[0], carried in the launch
   WorldDev *const *worlds;   // device array [n]
   int n;
   int *tile_prefix;          // device [n+1]: regrowth tiles per world
@@ -191,7 +192,16 @@ struct BatchDev {
   int fused;                 // every world has capacity <= FUSED_MAX_C
 };
 
-// Worlds up to this capacity run all slot phases of a step in one CTA.
+#ifdef __CUDACC__
+// Descriptor of world w.  Kernels take the batch as a __grid_constant__
+// parameter, so for a batch of one the descriptor is read from the launch's
+// constant bank instead of global memory.
+__device__ inline const WorldDev *world_ptr(const BatchDev &b, int w) {
+  return b.n == 1 ? &b.w0 : b.worlds[w];
+}
+#endif
+
+// Worlds up to this capacity run all slot phases of a step in one cluster.
 constexpr int FUSED_MAX_C = 16384;
 
 void launch_regrow(const BatchDev &b, cudaStream_t s);

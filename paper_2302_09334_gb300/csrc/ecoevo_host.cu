@@ -117,12 +117,18 @@ std::vector<uint32_t> threshold_table(const EcoParams *p) {
   return thr;
 }
 
+// Per-kernel timing of graph-launched steps: the one-step graph is captured
+// with an event-record node before every kernel and after the last; before
+// each launch those nodes are pointed at the next unused set of events.
 struct Profile {
   bool on = false;
   int max_steps = 0, used = 0;
   std::vector<cudaEvent_t> ev;  // (ECO_NKERNELS + 1) per step
   double ms[ECO_NKERNELS] = {0};
   long long launches[ECO_NKERNELS] = {0};
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t nodes[ECO_NKERNELS + 1] = {nullptr};
+  int n_nodes = 0;
 };
 
 }  // namespace
@@ -257,6 +263,7 @@ int batch_init(EcoBatch &b, EcoWorld *const *worlds, int n, void *table_dev) {
   tiles[n] = tt;
   blocks[n] = bb;
   ECO_CU(cudaMemcpy(b.table, host.data(), tab_bytes, cudaMemcpyHostToDevice));
+  b.bd.w0 = worlds[0]->hd;
   b.bd.worlds = reinterpret_cast<WorldDev *const *>(b.table);
   b.bd.n = n;
   b.bd.tile_prefix = reinterpret_cast<int *>((char *)b.table + n * sizeof(WorldDev *));
@@ -270,14 +277,63 @@ int batch_init(EcoBatch &b, EcoWorld *const *worlds, int n, void *table_dev) {
   return ECO_OK;
 }
 
+// One-step graph with external event-record nodes around every kernel.
+int capture_profiled(EcoBatch &b, Profile &pr) {
+  const StepKernel *list;
+  const int nk = step_kernels(b.bd, &list);
+  cudaEvent_t cap[ECO_NKERNELS + 1];
+  for (int k = 0; k <= nk; ++k) ECO_CU(cudaEventCreate(&cap[k]));
+  cudaGraph_t g = nullptr;
+  int rc = cuda_err(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
+  if (rc == ECO_OK) {
+    for (int k = 0; k < nk; ++k) {
+      cudaEventRecordWithFlags(cap[k], b.stream, cudaEventRecordExternal);
+      list[k].fn(b.bd, b.stream);
+    }
+    cudaEventRecordWithFlags(cap[nk], b.stream, cudaEventRecordExternal);
+    rc = cuda_err(cudaStreamEndCapture(b.stream, &g));
+  }
+  if (rc == ECO_OK) {
+    size_t n = 0;
+    rc = cuda_err(cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> all(n);
+    if (rc == ECO_OK && n) rc = cuda_err(cudaGraphGetNodes(g, all.data(), &n));
+    pr.n_nodes = 0;
+    for (size_t i = 0; rc == ECO_OK && i < n; ++i) {
+      cudaGraphNodeType type;
+      if ((rc = cuda_err(cudaGraphNodeGetType(all[i], &type)))) break;
+      if (type != cudaGraphNodeTypeEventRecord) continue;
+      cudaEvent_t e;
+      if ((rc = cuda_err(cudaGraphEventRecordNodeGetEvent(all[i], &e)))) break;
+      for (int k = 0; k <= nk; ++k)
+        if (e == cap[k]) {
+          pr.nodes[k] = all[i];
+          ++pr.n_nodes;
+        }
+    }
+    if (rc == ECO_OK && pr.n_nodes != nk + 1) rc = ECO_ECUDA;
+    if (rc == ECO_OK) rc = cuda_err(cudaGraphInstantiate(&pr.exec, g, 0));
+  }
+  if (g) cudaGraphDestroy(g);
+  for (int k = 0; k <= nk; ++k) cudaEventDestroy(cap[k]);
+  return rc;
+}
+
 int batch_step(EcoBatch &b, int64_t n) {
   if (n < 0) return ECO_EINVAL;
   Profile *prof = b.prof;
   if (prof && prof->on) {
+    if (!prof->exec) {
+      int rc = capture_profiled(b, *prof);
+      if (rc) return rc;
+    }
     for (int64_t i = 0; i < n; ++i) {
       if (prof->used < prof->max_steps) {
-        launch_step(b, b.stream, prof, prof->used);
+        const cudaEvent_t *ev = &prof->ev[(size_t)prof->used * (ECO_NKERNELS + 1)];
+        for (int k = 0; k < prof->n_nodes; ++k)
+          ECO_CU(cudaGraphExecEventRecordNodeSetEvent(prof->exec, prof->nodes[k], ev[k]));
         prof->used += 1;
+        ECO_CU(cudaGraphLaunch(prof->exec, b.stream));
       } else {
         launch_step(b, b.stream, nullptr, 0);
       }
@@ -470,6 +526,7 @@ void eco_world_destroy(EcoWorld *w) {
   cudaStreamSynchronize(w->stream);
   destroy_graphs(w->self);
   for (cudaEvent_t e : w->prof.ev) cudaEventDestroy(e);
+  if (w->prof.exec) cudaGraphExecDestroy(w->prof.exec);
   if (w->owns_arena) cudaFree(w->arena);
   delete w;
 }
@@ -725,6 +782,9 @@ int eco_world_profile(EcoWorld *w, int enable, int max_steps) {
   ECO_CU(cudaStreamSynchronize(w->stream));
   for (cudaEvent_t e : pr.ev) cudaEventDestroy(e);
   pr.ev.clear();
+  if (pr.exec) cudaGraphExecDestroy(pr.exec);
+  pr.exec = nullptr;
+  pr.n_nodes = 0;
   pr.on = false;
   pr.used = 0;
   for (int k = 0; k < ECO_NKERNELS; ++k) {

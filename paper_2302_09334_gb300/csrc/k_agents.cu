@@ -14,15 +14,22 @@
 //   scan        one CTA per world: successful parents, free slots, the k-th
 //               parent gets the k-th free slot, children initialised, the
 //               alive list for the next step rebuilt, counters, t += 1
-//   spawn       child weights = parent weights + sigma * N(0,1), eight work
-//               items per birth across the grid
+//   agents_cluster  all of the above for worlds of capacity <= 16384, one
+//               thread-block cluster per world
+//   spawn       child weights = parent weights + sigma * N(0,1), a grid-
+//               stride pass over every float4 of every birth
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "ecoevo_dev.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace eco {
 
 __device__ inline int find_world_a(const int *prefix, int n, int item) {
+  if (n == 1) return 0;
   int lo = 0, hi = n - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
@@ -34,8 +41,8 @@ __device__ inline int find_world_a(const int *prefix, int n, int item) {
 // Slot handled by this thread, or -1; sets wd.
 __device__ inline int slot_of_thread(const BatchDev &b, const WorldDev *&wd) {
   const int w = find_world_a(b.slot_block_prefix, b.n, blockIdx.x);
-  wd = b.worlds[w];
-  const int s = (blockIdx.x - b.slot_block_prefix[w]) * SLOT_BLOCK + threadIdx.x;
+  wd = world_ptr(b, w);
+  const int s = (blockIdx.x - (b.n == 1 ? 0 : b.slot_block_prefix[w])) * SLOT_BLOCK + threadIdx.x;
   return s < wd->C ? s : -1;
 }
 
@@ -156,6 +163,50 @@ __device__ inline void block_scan2(int a, int b, int &ea, int &eb, int &ta,
   __syncthreads();
 }
 
+// Birth k of the step: parent s, child in free slot `child` on the parent's
+// claimed cell; the child starts with e0, zero counters and zero recurrent
+// state, the parent's reproduction counter restarts.
+__device__ inline void init_child(const WorldDev &wd, int s, int k, int child, float *h_next) {
+  const int cell = wd.birth_cell[s];
+  wd.birth_parent[k] = s;
+  wd.birth_child[k] = child;
+  wd.repr_ctr[s] = 0;
+  wd.alive[child] = 1;
+  wd.y[child] = cell / wd.W;
+  wd.x[child] = cell % wd.W;
+  wd.slot_map[cell] = child;
+  wd.energy[child] = wd.e0;
+  wd.repr_ctr[child] = 0;
+  wd.low_ctr[child] = 0;
+  wd.age[child] = 0;
+  wd.action[child] = 0;
+  wd.ate[child] = 0;
+  wd.arrive[child] = 0u;
+  wd.birth_cell[child] = -1;
+  for (int j = 0; j < HID; ++j) {
+    h_next[(size_t)child * HID + j] = 0.f;
+    wd.c[(size_t)child * HID + j] = 0.f;
+  }
+  for (int a = 0; a < 8; ++a) wd.logits[(size_t)child * 8 + a] = 0.f;
+}
+
+// Counters at the end of a step: S successful parents, F free slots.
+__device__ inline void finish_step(const WorldDev &wd, int S, int F, int pop, uint32_t t) {
+  Counters &c = *wd.ctr;
+  const int births = min(S, F);
+  c.births_last = births;
+  c.dropped_last = S - births;
+  c.deaths_last = c.deaths_step;
+  c.births += births;
+  c.dropped += S - births;
+  c.deaths += c.deaths_step;
+  c.deaths_step = 0;
+  c.n_births = births;
+  c.births_t = t;
+  c.pop = pop;
+  c.t = (long long)t + 1;
+}
+
 // Births and the next alive list of one world, by one CTA of SCAN_THREADS.
 __device__ void scan_world(const WorldDev &wd, int *sh) {
   const int C = wd.C;
@@ -193,28 +244,7 @@ __device__ void scan_world(const WorldDev &wd, int *sh) {
     if (!wd.flag[s]) continue;
     const int k = succ_off++;
     if (k >= F) continue;
-    const int child = wd.free_list[k];
-    const int cell = wd.birth_cell[s];
-    wd.birth_parent[k] = s;
-    wd.birth_child[k] = child;
-    wd.repr_ctr[s] = 0;
-    wd.alive[child] = 1;
-    wd.y[child] = cell / wd.W;
-    wd.x[child] = cell % wd.W;
-    wd.slot_map[cell] = child;
-    wd.energy[child] = wd.e0;
-    wd.repr_ctr[child] = 0;
-    wd.low_ctr[child] = 0;
-    wd.age[child] = 0;
-    wd.action[child] = 0;
-    wd.ate[child] = 0;
-    wd.arrive[child] = 0u;
-    wd.birth_cell[child] = -1;
-    for (int j = 0; j < HID; ++j) {
-      h_next[(size_t)child * HID + j] = 0.f;
-      wd.c[(size_t)child * HID + j] = 0.f;
-    }
-    for (int a = 0; a < 8; ++a) wd.logits[(size_t)child * 8 + a] = 0.f;
+    init_child(wd, s, k, wd.free_list[k], h_next);
   }
   __syncthreads();
 
@@ -226,65 +256,129 @@ __device__ void scan_world(const WorldDev &wd, int *sh) {
   for (int s = s0; s < s1; ++s)
     if (wd.alive[s]) wd.alive_list[alive_off++] = s;
 
-  if (threadIdx.x == 0) {
-    Counters &c = *wd.ctr;
-    const int births = min(S, F);
-    c.births_last = births;
-    c.dropped_last = S - births;
-    c.deaths_last = c.deaths_step;
-    c.births += births;
-    c.dropped += S - births;
-    c.deaths += c.deaths_step;
-    c.deaths_step = 0;
-    c.n_births = births;
-    c.births_t = t;
-    c.pop = pop;
-    c.t = (long long)t + 1;
-  }
+  if (threadIdx.x == 0) finish_step(wd, S, F, pop, t);
 }
 
-__global__ void __launch_bounds__(SLOT_BLOCK) k_move_claim(BatchDev b) {
+__global__ void __launch_bounds__(SLOT_BLOCK) k_move_claim(const __grid_constant__ BatchDev b) {
   const WorldDev *wd;
   const int s = slot_of_thread(b, wd);
   if (s >= 0) slot_move_claim(wd, s);
 }
-__global__ void __launch_bounds__(SLOT_BLOCK) k_move_apply(BatchDev b) {
+__global__ void __launch_bounds__(SLOT_BLOCK) k_move_apply(const __grid_constant__ BatchDev b) {
   const WorldDev *wd;
   const int s = slot_of_thread(b, wd);
   if (s >= 0) slot_move_apply(wd, s);
 }
-__global__ void __launch_bounds__(SLOT_BLOCK) k_physio(BatchDev b) {
+__global__ void __launch_bounds__(SLOT_BLOCK) k_physio(const __grid_constant__ BatchDev b) {
   const WorldDev *wd;
   const int s = slot_of_thread(b, wd);
   if (s >= 0) slot_physio(wd, s);
 }
-__global__ void __launch_bounds__(SLOT_BLOCK) k_birth_claim(BatchDev b) {
+__global__ void __launch_bounds__(SLOT_BLOCK) k_birth_claim(const __grid_constant__ BatchDev b) {
   const WorldDev *wd;
   const int s = slot_of_thread(b, wd);
   if (s >= 0) slot_birth_claim(wd, s);
 }
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan(BatchDev b) {
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan(const __grid_constant__ BatchDev b) {
   __shared__ int sh[66];
-  scan_world(*b.worlds[blockIdx.x], sh);
+  scan_world(*world_ptr(b, blockIdx.x), sh);
 }
 
-// Worlds of capacity <= FUSED_MAX_C: all slot phases of a step (moves,
-// eating and physiology, birth claims, compaction) in one CTA per world,
-// each phase separated by a block barrier, which orders the global memory
-// the next phase reads.
-__global__ void __launch_bounds__(SCAN_THREADS) k_agents_fused(BatchDev b) {
+// Worlds of capacity <= FUSED_MAX_C: every slot phase of a step (moves,
+// eating and physiology, birth claims, compaction) in one launch, one
+// thread-block cluster of CLUSTER CTAs per world.  Phases are separated by
+// the hardware cluster barrier (release/acquire at cluster scope, so the
+// global memory one phase writes is visible to the next); the compaction
+// exchanges per-CTA totals through distributed shared memory.
+constexpr int CLUSTER = 8;
+
+// Exclusive prefix over the cluster's CTAs of two per-CTA totals.
+__device__ inline void cluster_prefix2(cg::cluster_group &cl, int *pub, int *out, int a,
+                                       int b) {
+  if (threadIdx.x == 0) {
+    pub[0] = a;
+    pub[1] = b;
+  }
+  cl.sync();
+  if (threadIdx.x == 0) {
+    const int me = (int)cl.block_rank();
+    int ba = 0, bb = 0, ta = 0, tb = 0;
+    for (int r = 0; r < CLUSTER; ++r) {
+      const int *rp = cl.map_shared_rank(pub, r);
+      const int ra = rp[0], rb = rp[1];
+      if (r < me) { ba += ra; bb += rb; }
+      ta += ra;
+      tb += rb;
+    }
+    out[0] = ba; out[1] = bb; out[2] = ta; out[3] = tb;
+  }
+  __syncthreads();
+}
+
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
+    k_agents_cluster(const __grid_constant__ BatchDev b) {
   __shared__ int sh[66];
-  const WorldDev *wd = b.worlds[blockIdx.x];
-  const int C = wd->C;
-  for (int s = threadIdx.x; s < C; s += blockDim.x) slot_move_claim(wd, s);
-  __syncthreads();
-  for (int s = threadIdx.x; s < C; s += blockDim.x) slot_move_apply(wd, s);
-  __syncthreads();
-  for (int s = threadIdx.x; s < C; s += blockDim.x) slot_physio(wd, s);
-  __syncthreads();
-  for (int s = threadIdx.x; s < C; s += blockDim.x) slot_birth_claim(wd, s);
-  __syncthreads();
-  scan_world(*wd, sh);
+  __shared__ int pub1[2], pub2[2], ex[4];
+  cg::cluster_group cl = cg::this_cluster();
+  const WorldDev &wd = *world_ptr(b, blockIdx.x / CLUSTER);
+  const int rank = (int)cl.block_rank();
+  const int C = wd.C;
+  const int per_cta = (C + CLUSTER - 1) / CLUSTER;
+  const int c0 = min(C, rank * per_cta), c1 = min(C, c0 + per_cta);
+
+  for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) slot_move_claim(&wd, s);
+  cl.sync();
+  for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) slot_move_apply(&wd, s);
+  cl.sync();
+  for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) slot_physio(&wd, s);
+  cl.sync();
+  for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) slot_birth_claim(&wd, s);
+  cl.sync();
+
+  // compaction: contiguous slots per thread so ranks follow slot order
+  const int per = (c1 - c0 + SCAN_THREADS - 1) / SCAN_THREADS;
+  const int s0 = min(c1, c0 + (int)threadIdx.x * per), s1 = min(c1, s0 + per);
+  const uint32_t t = (uint32_t)wd.ctr->t;
+  float *h_next = (t & 1u) ? wd.h0 : wd.h1;
+  int n_free = 0, n_succ = 0;
+  for (int s = s0; s < s1; ++s) {
+    const int cell = wd.birth_cell[s];
+    const bool ok = wd.alive[s] && cell >= 0 && wd.bclaim[cell] == s;
+    wd.flag[s] = ok ? 1 : 0;
+    n_succ += ok;
+    n_free += wd.alive[s] ? 0 : 1;
+  }
+  int free_off, succ_off, Fb, Sb;
+  block_scan2(n_free, n_succ, free_off, succ_off, Fb, Sb, sh);
+  cluster_prefix2(cl, pub1, ex, Fb, Sb);  // every claim cell read before any reset
+  free_off += ex[0];
+  succ_off += ex[1];
+  const int F = ex[2], S = ex[3];
+  for (int s = s0; s < s1; ++s) {
+    const int cell = wd.birth_cell[s];
+    if (cell >= 0) wd.bclaim[cell] = INT_MAX;
+    if (!wd.alive[s]) {
+      if (free_off < S) wd.free_list[free_off] = s;
+      ++free_off;
+    }
+  }
+  cl.sync();
+  for (int s = s0; s < s1; ++s) {
+    if (!wd.flag[s]) continue;
+    const int k = succ_off++;
+    if (k < F) init_child(wd, s, k, wd.free_list[k], h_next);
+  }
+  cl.sync();
+  int n_alive = 0;
+  for (int s = s0; s < s1; ++s) n_alive += wd.alive[s];
+  int alive_off, dummy, Ab, dummy2;
+  block_scan2(n_alive, 0, alive_off, dummy, Ab, dummy2, sh);
+  cluster_prefix2(cl, pub2, ex, Ab, 0);
+  alive_off += ex[0];
+  for (int s = s0; s < s1; ++s)
+    if (wd.alive[s]) wd.alive_list[alive_off++] = s;
+  if (rank == 0 && threadIdx.x == 0) finish_step(wd, S, F, ex[2], t);
+  cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 // Child weights, physical layout: W[child][p] = W[parent][p] + sigma * N_j
@@ -292,81 +386,103 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_agents_fused(BatchDev b) {
 // A float4 of a weight row or of the read-out holds four consecutive logical
 // indices starting at a multiple of 4, so one Philox draw serves it; the
 // bias rows of a block are permuted and take one draw per element.
-constexpr int SPAWN_SPLIT = 8;
 constexpr int SPAWN_THREADS = 256;
 constexpr int NVEC = WSTRIDE / 4;  // 5840 float4 per agent
 
-__device__ inline void mutate_copy(const WorldDev &wd, int parent, int child,
-                                   uint32_t tag, uint32_t t, uint32_t id,
-                                   float scale, bool from_parent, int v0, int v1) {
-  const float4 *src = reinterpret_cast<const float4 *>(wd.weights + (size_t)parent * WSTRIDE);
-  float4 *dst = reinterpret_cast<float4 *>(wd.weights + (size_t)child * WSTRIDE);
-  for (int vi = v0 + threadIdx.x; vi < v1; vi += blockDim.x) {
-    const int p = vi * 4;
-    float4 base = from_parent ? src[vi] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float out[4] = {base.x, base.y, base.z, base.w};
-    const int o = p % BLK_FLOATS;
-    const bool bias_vec = p < TAIL && o >= BLK_ROWS * NIN;
-    if (!bias_vec) {
-      const int j = logical_of_phys(p);  // multiple of 4, or -1 for padding
-      if (j >= 0) {
-        float z[4];
-        normals4(wd.key0, wd.key1, (uint32_t)j >> 2, t, tag, id, z);
+// Float4 number vi of an agent's physical weights after adding scale * N_j
+// (stream tag, t, id) to `base`.
+__device__ inline float4 mutate4(const WorldDev &wd, int vi, float4 base, uint32_t tag,
+                                 uint32_t t, uint32_t id, float scale) {
+  const int p = vi * 4;
+  float out[4] = {base.x, base.y, base.z, base.w};
+  const int o = p % BLK_FLOATS;
+  const bool bias_vec = p < TAIL && o >= BLK_ROWS * NIN;
+  if (!bias_vec) {
+    const int j = logical_of_phys(p);  // multiple of 4, or -1 for padding
+    if (j >= 0) {
+      float z[4];
+      normals4(wd.key0, wd.key1, (uint32_t)j >> 2, t, tag, id, z);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          if (j + i < NPARAM)
-            out[i] = __fadd_rn(out[i], __fmul_rn(scale, z[i]));
-          else
-            out[i] = 0.f;
-        }
-      } else {
-        out[0] = out[1] = out[2] = out[3] = 0.f;
-      }
+      for (int i = 0; i < 4; ++i)
+        out[i] = (j + i < NPARAM) ? __fadd_rn(out[i], __fmul_rn(scale, z[i])) : 0.f;
     } else {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int j = logical_of_phys(p + i);
-        float z[4];
-        normals4(wd.key0, wd.key1, (uint32_t)j >> 2, t, tag, id, z);
-        out[i] = __fadd_rn(out[i], __fmul_rn(scale, z[j & 3]));
-      }
+      out[0] = out[1] = out[2] = out[3] = 0.f;
     }
-    dst[vi] = make_float4(out[0], out[1], out[2], out[3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = logical_of_phys(p + i);
+      float z[4];
+      normals4(wd.key0, wd.key1, (uint32_t)j >> 2, t, tag, id, z);
+      out[i] = __fadd_rn(out[i], __fmul_rn(scale, z[j & 3]));
+    }
   }
+  return make_float4(out[0], out[1], out[2], out[3]);
 }
 
-__global__ void __launch_bounds__(SPAWN_THREADS) k_spawn(BatchDev b) {
+// Grid-stride over every float4 of every birth of the batch; each thread
+// issues the loads of SPAWN_UNROLL elements before any of their arithmetic.
+constexpr int SPAWN_UNROLL = 4;
+
+__global__ void __launch_bounds__(SPAWN_THREADS) k_spawn(const __grid_constant__ BatchDev b) {
   __shared__ int pre[1025];
   if (threadIdx.x == 0) {
     int run = 0;
     for (int w = 0; w < b.n; ++w) {
       pre[w] = run;
-      run += b.worlds[w]->ctr->n_births;
+      run += world_ptr(b, w)->ctr->n_births;
     }
     pre[b.n] = run;
   }
   __syncthreads();
-  const int total = pre[b.n] * SPAWN_SPLIT;
-  int w = 0;
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int bi = item / SPAWN_SPLIT, part = item % SPAWN_SPLIT;
-    while (bi >= pre[w + 1]) ++w;
-    const WorldDev &wd = *b.worlds[w];
-    const int k = bi - pre[w];
-    const int parent = wd.birth_parent[k], child = wd.birth_child[k];
-    const int v0 = (NVEC * part) / SPAWN_SPLIT, v1 = (NVEC * (part + 1)) / SPAWN_SPLIT;
-    mutate_copy(wd, parent, child, TAG_MUT, wd.ctr->births_t, (uint32_t)parent,
-                wd.mut_std, true, v0, v1);
+  const long long total = (long long)pre[b.n] * NVEC;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; g0 < total;
+       g0 += SPAWN_UNROLL * stride) {
+    float4 in[SPAWN_UNROLL];
+    float4 *dst[SPAWN_UNROLL];
+    const WorldDev *wdu[SPAWN_UNROLL];
+    int vi[SPAWN_UNROLL], par[SPAWN_UNROLL];
+#pragma unroll
+    for (int u = 0; u < SPAWN_UNROLL; ++u) {
+      const long long g = g0 + u * stride;
+      dst[u] = nullptr;
+      if (g >= total) continue;
+      const int bi = (int)(g / NVEC);
+      vi[u] = (int)(g % NVEC);
+      int lo = 0, hi = b.n - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= bi) lo = mid; else hi = mid - 1;
+      }
+      const WorldDev &wd = *world_ptr(b, lo);
+      const int k = bi - pre[lo];
+      par[u] = wd.birth_parent[k];
+      const int child = wd.birth_child[k];
+      wdu[u] = &wd;
+      in[u] = reinterpret_cast<const float4 *>(wd.weights + (size_t)par[u] * WSTRIDE)[vi[u]];
+      dst[u] = reinterpret_cast<float4 *>(wd.weights + (size_t)child * WSTRIDE) + vi[u];
+    }
+#pragma unroll
+    for (int u = 0; u < SPAWN_UNROLL; ++u) {
+      if (!dst[u]) continue;
+      const WorldDev &wd = *wdu[u];
+      *dst[u] = mutate4(wd, vi[u], in[u], TAG_MUT, wd.ctr->births_t, (uint32_t)par[u],
+                        wd.mut_std);
+    }
   }
 }
 
 // Initial weights of slots [0, n0): w_init_std * N_j of (TAG_INIT_W, 0, slot).
 __global__ void __launch_bounds__(SPAWN_THREADS) k_init_weights(const WorldDev *wdp, int n0) {
   const WorldDev &wd = *wdp;
-  for (int item = blockIdx.x; item < n0 * SPAWN_SPLIT; item += gridDim.x) {
-    const int s = item / SPAWN_SPLIT, part = item % SPAWN_SPLIT;
-    const int v0 = (NVEC * part) / SPAWN_SPLIT, v1 = (NVEC * (part + 1)) / SPAWN_SPLIT;
-    mutate_copy(wd, s, s, TAG_INIT_W, 0u, (uint32_t)s, wd.w_init_std, false, v0, v1);
+  const long long total = (long long)n0 * NVEC;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(g / NVEC), vi = (int)(g % NVEC);
+    reinterpret_cast<float4 *>(wd.weights + (size_t)s * WSTRIDE)[vi] =
+        mutate4(wd, vi, make_float4(0.f, 0.f, 0.f, 0.f), TAG_INIT_W, 0u, (uint32_t)s,
+                wd.w_init_std);
   }
 }
 
@@ -378,7 +494,7 @@ void preload_agents() {
   cudaFuncGetAttributes(&a, k_birth_claim);
   cudaFuncGetAttributes(&a, k_scan);
   cudaFuncGetAttributes(&a, k_spawn);
-  cudaFuncGetAttributes(&a, k_agents_fused);
+  cudaFuncGetAttributes(&a, k_agents_cluster);
 }
 
 void launch_move_claim(const BatchDev &b, cudaStream_t s) {
@@ -397,13 +513,13 @@ void launch_scan(const BatchDev &b, cudaStream_t s) {
   k_scan<<<b.n, SCAN_THREADS, 0, s>>>(b);
 }
 void launch_agents_fused(const BatchDev &b, cudaStream_t s) {
-  k_agents_fused<<<b.n, SCAN_THREADS, 0, s>>>(b);
+  k_agents_cluster<<<b.n * CLUSTER, SCAN_THREADS, 0, s>>>(b);
 }
 void launch_spawn(const BatchDev &b, cudaStream_t s) {
-  k_spawn<<<2 * b.n_sms, SPAWN_THREADS, 0, s>>>(b);
+  k_spawn<<<4 * b.n_sms, SPAWN_THREADS, 0, s>>>(b);
 }
 void launch_init_weights(const WorldDev *wd_dev, int n0, int n_sms, cudaStream_t s) {
-  if (n0 > 0) k_init_weights<<<2 * n_sms, SPAWN_THREADS, 0, s>>>(wd_dev, n0);
+  if (n0 > 0) k_init_weights<<<8 * n_sms, SPAWN_THREADS, 0, s>>>(wd_dev, n0);
 }
 
 }  // namespace eco

@@ -187,7 +187,7 @@ __device__ inline int world_of(const int *prefix, int n, int a) {
   return lo;
 }
 
-__global__ void __launch_bounds__(LTHREADS, 1) k_lstm(BatchDev b) {
+__global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ BatchDev b) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   LstmSmem &sm = *reinterpret_cast<LstmSmem *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(BatchDev b) {
     int local = 0;
     for (int i = 0; i < per; ++i) {
       const int w = lane * per + i;
-      if (w < b.n) local += (int)b.worlds[w]->ctr->pop;
+      if (w < b.n) local += (int)world_ptr(b, w)->ctr->pop;
     }
     int incl = local;
 #pragma unroll
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(BatchDev b) {
       const int w = lane * per + i;
       if (w < b.n) {
         sm.prefix[w] = run;
-        run += (int)b.worlds[w]->ctr->pop;
+        run += (int)world_ptr(b, w)->ctr->pop;
       }
     }
     if (lane == 31) sm.prefix[b.n] = incl;
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(BatchDev b) {
   const int a_begin = (int)(A * blockIdx.x / gridDim.x);
   const int a_end = (int)(A * (blockIdx.x + 1) / gridDim.x);
   const int n_agents = a_end - a_begin;
-  int *status = &b.worlds[0]->ctr->status;
+  int *status = &world_ptr(b, 0)->ctr->status;
 
   if (warp == W_PROD) {
     // ------------------------------------------------ producer -------------
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(BatchDev b) {
         const int a = a_begin + n + lane;
         if (a < a_end) {
           const int w = world_of(sm.prefix, b.n, a);
-          const WorldDev *wd = b.worlds[w];
+          const WorldDev *wd = world_ptr(b, w);
           my_slot = wd->alive_list[a - sm.prefix[w]];
           my_w = wd->weights;
         }
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(BatchDev b) {
         const int a = a_begin + gw + NGATH * (m + lane);
         if (a < a_end) {
           const int w = world_of(sm.prefix, b.n, a);
-          my_wd = b.worlds[w];
+          my_wd = world_ptr(b, w);
           my_slot = my_wd->alive_list[a - sm.prefix[w]];
           my_y = my_wd->y[my_slot];
           my_x = my_wd->x[my_slot];

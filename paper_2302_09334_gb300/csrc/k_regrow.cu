@@ -13,6 +13,7 @@
 namespace eco {
 
 __device__ inline int find_world(const int *prefix, int n, int item) {
+  if (n == 1) return 0;
   int lo = 0, hi = n - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
@@ -35,13 +36,13 @@ __device__ inline uint32_t nbr_mask(int shape, int R, int dy) {
 constexpr int TILE_ROWS_MAX = REGROW_ROWS + 6;  // R <= 3
 constexpr int TILE_COLS = REGROW_WORDS + 2;
 
-__global__ void __launch_bounds__(256) k_regrow(BatchDev b) {
+__global__ void __launch_bounds__(256) k_regrow(const __grid_constant__ BatchDev b) {
   __shared__ uint32_t tile[TILE_ROWS_MAX][TILE_COLS];
   const int w = find_world(b.tile_prefix, b.n, blockIdx.x);
-  const WorldDev &wd = *b.worlds[w];
+  const WorldDev &wd = *world_ptr(b, w);
   const int H = wd.H, W = wd.W, Wp = wd.Wp, R = wd.nbr_radius;
   const int tiles_x = (Wp + REGROW_WORDS - 1) / REGROW_WORDS;
-  const int local = blockIdx.x - b.tile_prefix[w];
+  const int local = blockIdx.x - (b.n == 1 ? 0 : b.tile_prefix[w]);
   const int y0 = (local / tiles_x) * REGROW_ROWS;
   const int w0 = (local % tiles_x) * REGROW_WORDS;
   const uint32_t t = (uint32_t)wd.ctr->t;
