@@ -175,7 +175,7 @@ def bench_ours(args, params, rank, world_size, dist):
         # the step stays in L2 and the lines left there are clean
         with torch.cuda.stream(stream):
             flush.fill_(1)
-            torch.sum(flush_read, out=flush_sink)
+            torch.sum(flush_read, dim=0, out=flush_sink)
 
     for _ in range(args.warmup):
         flush_l2()
