@@ -126,6 +126,7 @@ struct Profile {
   std::vector<cudaEvent_t> ev;  // (ECO_NKERNELS + 1) per step
   double ms[ECO_NKERNELS] = {0};
   long long launches[ECO_NKERNELS] = {0};
+  cudaGraph_t graph = nullptr;  // kept: its node handles address the exec
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t nodes[ECO_NKERNELS + 1] = {nullptr};
   int n_nodes = 0;
@@ -314,7 +315,11 @@ int capture_profiled(EcoBatch &b, Profile &pr) {
     if (rc == ECO_OK && pr.n_nodes != nk + 1) rc = ECO_ECUDA;
     if (rc == ECO_OK) rc = cuda_err(cudaGraphInstantiate(&pr.exec, g, 0));
   }
-  if (g) cudaGraphDestroy(g);
+  if (rc == ECO_OK) {
+    pr.graph = g;
+  } else if (g) {
+    cudaGraphDestroy(g);
+  }
   for (int k = 0; k <= nk; ++k) cudaEventDestroy(cap[k]);
   return rc;
 }
@@ -527,6 +532,7 @@ void eco_world_destroy(EcoWorld *w) {
   destroy_graphs(w->self);
   for (cudaEvent_t e : w->prof.ev) cudaEventDestroy(e);
   if (w->prof.exec) cudaGraphExecDestroy(w->prof.exec);
+  if (w->prof.graph) cudaGraphDestroy(w->prof.graph);
   if (w->owns_arena) cudaFree(w->arena);
   delete w;
 }
@@ -783,7 +789,9 @@ int eco_world_profile(EcoWorld *w, int enable, int max_steps) {
   for (cudaEvent_t e : pr.ev) cudaEventDestroy(e);
   pr.ev.clear();
   if (pr.exec) cudaGraphExecDestroy(pr.exec);
+  if (pr.graph) cudaGraphDestroy(pr.graph);
   pr.exec = nullptr;
+  pr.graph = nullptr;
   pr.n_nodes = 0;
   pr.on = false;
   pr.used = 0;
