@@ -193,14 +193,15 @@ int eco_batch_sync(EcoBatch *batch);
 void eco_batch_destroy(EcoBatch *batch);
 
 /* Per-kernel timing with CUDA events on the world's stream.  While enabled,
- * each step runs as a one-step CUDA graph with an event-record node before
- * every kernel and after the last, pointed at fresh events every step;
- * eco_world_profile_read sums the elapsed times since enabling:
+ * each step (up to max_steps after each read) runs as a one-step CUDA graph
+ * with an event-record node before every kernel and after the last; the
+ * step call waits for the step to finish and adds the elapsed time between
+ * consecutive events to the kernel in between (profiled stepping is
+ * synchronous).  eco_world_profile_read returns the sums since enabling:
  * ms[k], launches[k] for k < ECO_NKERNELS (names: eco_kernel_name; a kernel
- * the world's step does not launch keeps 0 launches).  Synchronous read.
- * max_steps bounds the recorded steps.  Worlds of capacity <= 16384 run the
- * slot phases (moves, physiology, birth claims, compaction) as one kernel
- * "agents_fused"; larger ones as five kernels. */
+ * the world's step does not launch keeps 0 launches).  Worlds of capacity
+ * <= 16384 run the slot phases (moves, physiology, birth claims,
+ * compaction) as one kernel "agents_fused"; larger ones as five kernels. */
 #define ECO_NKERNELS 9
 int eco_world_profile(EcoWorld *world, int enable, int max_steps);
 int eco_world_profile_read(EcoWorld *world, double *ms, int64_t *launches);

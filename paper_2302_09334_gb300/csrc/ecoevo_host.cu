@@ -118,18 +118,17 @@ std::vector<uint32_t> threshold_table(const EcoParams *p) {
 }
 
 // Per-kernel timing of graph-launched steps: the one-step graph is captured
-// with an event-record node before every kernel and after the last; before
-// each launch those nodes are pointed at the next unused set of events.
+// with an event-record node before every kernel and after the last; after
+// each profiled launch the host waits for the last event and adds the
+// elapsed time between consecutive events to the kernel in between.
 struct Profile {
   bool on = false;
   int max_steps = 0, used = 0;
-  std::vector<cudaEvent_t> ev;  // (ECO_NKERNELS + 1) per step
   double ms[ECO_NKERNELS] = {0};
   long long launches[ECO_NKERNELS] = {0};
-  cudaGraph_t graph = nullptr;  // kept: its node handles address the exec
+  cudaEvent_t ev[ECO_NKERNELS + 1] = {nullptr};
+  int n_ev = 0;
   cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t nodes[ECO_NKERNELS + 1] = {nullptr};
-  int n_nodes = 0;
 };
 
 }  // namespace
@@ -165,14 +164,15 @@ struct EcoWorld {
 
 namespace {
 
-int cuda_err(cudaError_t e) {
+int cuda_err_at(cudaError_t e, const char *what) {
   if (e == cudaSuccess) return ECO_OK;
-  std::fprintf(stderr, "libecoevo: CUDA error %s\n", cudaGetErrorString(e));
+  std::fprintf(stderr, "libecoevo: CUDA error %s in %s\n", cudaGetErrorString(e), what);
   return ECO_ECUDA;
 }
+#define cuda_err(call) cuda_err_at((call), #call)
 #define ECO_CU(call)                                  \
   do {                                                \
-    int rc__ = cuda_err(call);                        \
+    int rc__ = cuda_err_at((call), #call);            \
     if (rc__ != ECO_OK) return rc__;                  \
   } while (0)
 
@@ -206,17 +206,11 @@ int step_kernels(const BatchDev &bd, const StepKernel **list) {
   return (int)(sizeof(kSplitStep) / sizeof(kSplitStep[0]));
 }
 
-// One step; with a profiler, an event before every kernel and after the
-// last (events of step slot `step_ev`).
-void launch_step(const EcoBatch &b, cudaStream_t s, Profile *prof, int step_ev) {
+// One step, kernel by kernel.
+void launch_step(const EcoBatch &b, cudaStream_t s, Profile *, int) {
   const StepKernel *list;
   const int nk = step_kernels(b.bd, &list);
-  cudaEvent_t *ev = prof ? &prof->ev[(size_t)step_ev * (ECO_NKERNELS + 1)] : nullptr;
-  for (int k = 0; k < nk; ++k) {
-    if (ev) cudaEventRecord(ev[k], s);
-    list[k].fn(b.bd, s);
-  }
-  if (ev) cudaEventRecord(ev[nk], s);
+  for (int k = 0; k < nk; ++k) list[k].fn(b.bd, s);
 }
 
 void destroy_graphs(EcoBatch &b) {
@@ -282,46 +276,47 @@ int batch_init(EcoBatch &b, EcoWorld *const *worlds, int n, void *table_dev) {
 int capture_profiled(EcoBatch &b, Profile &pr) {
   const StepKernel *list;
   const int nk = step_kernels(b.bd, &list);
-  cudaEvent_t cap[ECO_NKERNELS + 1];
-  for (int k = 0; k <= nk; ++k) ECO_CU(cudaEventCreate(&cap[k]));
+  for (int k = 0; k <= nk; ++k) ECO_CU(cudaEventCreate(&pr.ev[k]));
+  pr.n_ev = nk + 1;
   cudaGraph_t g = nullptr;
   int rc = cuda_err(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
   if (rc == ECO_OK) {
     for (int k = 0; k < nk; ++k) {
-      cudaEventRecordWithFlags(cap[k], b.stream, cudaEventRecordExternal);
+      if (rc == ECO_OK)
+        rc = cuda_err(cudaEventRecordWithFlags(pr.ev[k], b.stream, cudaEventRecordExternal));
       list[k].fn(b.bd, b.stream);
     }
-    cudaEventRecordWithFlags(cap[nk], b.stream, cudaEventRecordExternal);
-    rc = cuda_err(cudaStreamEndCapture(b.stream, &g));
+    if (rc == ECO_OK)
+      rc = cuda_err(cudaEventRecordWithFlags(pr.ev[nk], b.stream, cudaEventRecordExternal));
+    const int rc_end = cuda_err(cudaStreamEndCapture(b.stream, &g));
+    if (rc == ECO_OK) rc = rc_end;
   }
-  if (rc == ECO_OK) {
-    size_t n = 0;
-    rc = cuda_err(cudaGraphGetNodes(g, nullptr, &n));
-    std::vector<cudaGraphNode_t> all(n);
-    if (rc == ECO_OK && n) rc = cuda_err(cudaGraphGetNodes(g, all.data(), &n));
-    pr.n_nodes = 0;
-    for (size_t i = 0; rc == ECO_OK && i < n; ++i) {
-      cudaGraphNodeType type;
-      if ((rc = cuda_err(cudaGraphNodeGetType(all[i], &type)))) break;
-      if (type != cudaGraphNodeTypeEventRecord) continue;
-      cudaEvent_t e;
-      if ((rc = cuda_err(cudaGraphEventRecordNodeGetEvent(all[i], &e)))) break;
-      for (int k = 0; k <= nk; ++k)
-        if (e == cap[k]) {
-          pr.nodes[k] = all[i];
-          ++pr.n_nodes;
-        }
-    }
-    if (rc == ECO_OK && pr.n_nodes != nk + 1) rc = ECO_ECUDA;
-    if (rc == ECO_OK) rc = cuda_err(cudaGraphInstantiate(&pr.exec, g, 0));
-  }
-  if (rc == ECO_OK) {
-    pr.graph = g;
-  } else if (g) {
-    cudaGraphDestroy(g);
-  }
-  for (int k = 0; k <= nk; ++k) cudaEventDestroy(cap[k]);
+  if (rc == ECO_OK) rc = cuda_err(cudaGraphInstantiate(&pr.exec, g, 0));
+  if (g) cudaGraphDestroy(g);
   return rc;
+}
+
+void profile_release(Profile &pr) {
+  for (int k = 0; k < pr.n_ev; ++k) cudaEventDestroy(pr.ev[k]);
+  pr.n_ev = 0;
+  if (pr.exec) cudaGraphExecDestroy(pr.exec);
+  pr.exec = nullptr;
+}
+
+// One profiled step: launch, wait, add the per-kernel times.
+int profiled_step(EcoBatch &b, Profile &pr) {
+  const StepKernel *list;
+  const int nk = step_kernels(b.bd, &list);
+  ECO_CU(cudaGraphLaunch(pr.exec, b.stream));
+  ECO_CU(cudaEventSynchronize(pr.ev[nk]));
+  for (int k = 0; k < nk; ++k) {
+    float t = 0.f;
+    ECO_CU(cudaEventElapsedTime(&t, pr.ev[k], pr.ev[k + 1]));
+    pr.ms[list[k].id] += t;
+    pr.launches[list[k].id] += 1;
+  }
+  pr.used += 1;
+  return ECO_OK;
 }
 
 int batch_step(EcoBatch &b, int64_t n) {
@@ -334,11 +329,8 @@ int batch_step(EcoBatch &b, int64_t n) {
     }
     for (int64_t i = 0; i < n; ++i) {
       if (prof->used < prof->max_steps) {
-        const cudaEvent_t *ev = &prof->ev[(size_t)prof->used * (ECO_NKERNELS + 1)];
-        for (int k = 0; k < prof->n_nodes; ++k)
-          ECO_CU(cudaGraphExecEventRecordNodeSetEvent(prof->exec, prof->nodes[k], ev[k]));
-        prof->used += 1;
-        ECO_CU(cudaGraphLaunch(prof->exec, b.stream));
+        int rc = profiled_step(b, *prof);
+        if (rc) return rc;
       } else {
         launch_step(b, b.stream, nullptr, 0);
       }
@@ -530,9 +522,7 @@ void eco_world_destroy(EcoWorld *w) {
   if (!w) return;
   cudaStreamSynchronize(w->stream);
   destroy_graphs(w->self);
-  for (cudaEvent_t e : w->prof.ev) cudaEventDestroy(e);
-  if (w->prof.exec) cudaGraphExecDestroy(w->prof.exec);
-  if (w->prof.graph) cudaGraphDestroy(w->prof.graph);
+  profile_release(w->prof);
   if (w->owns_arena) cudaFree(w->arena);
   delete w;
 }
@@ -786,13 +776,7 @@ int eco_world_profile(EcoWorld *w, int enable, int max_steps) {
   if (!w || (enable && max_steps < 1)) return ECO_EINVAL;
   Profile &pr = w->prof;
   ECO_CU(cudaStreamSynchronize(w->stream));
-  for (cudaEvent_t e : pr.ev) cudaEventDestroy(e);
-  pr.ev.clear();
-  if (pr.exec) cudaGraphExecDestroy(pr.exec);
-  if (pr.graph) cudaGraphDestroy(pr.graph);
-  pr.exec = nullptr;
-  pr.graph = nullptr;
-  pr.n_nodes = 0;
+  profile_release(pr);
   pr.on = false;
   pr.used = 0;
   for (int k = 0; k < ECO_NKERNELS; ++k) {
@@ -800,8 +784,6 @@ int eco_world_profile(EcoWorld *w, int enable, int max_steps) {
     pr.launches[k] = 0;
   }
   if (!enable) return ECO_OK;
-  pr.ev.resize((size_t)max_steps * (ECO_NKERNELS + 1));
-  for (auto &e : pr.ev) ECO_CU(cudaEventCreate(&e));
   pr.max_steps = max_steps;
   pr.on = true;
   return ECO_OK;
@@ -811,17 +793,6 @@ int eco_world_profile_read(EcoWorld *w, double *ms, int64_t *launches) {
   if (!w || !ms || !launches) return ECO_EINVAL;
   Profile &pr = w->prof;
   ECO_CU(cudaStreamSynchronize(w->stream));
-  const StepKernel *list;
-  const int nk = step_kernels(w->self.bd, &list);
-  for (int s = 0; s < pr.used; ++s) {
-    for (int k = 0; k < nk; ++k) {
-      float t = 0.f;
-      ECO_CU(cudaEventElapsedTime(&t, pr.ev[(size_t)s * (ECO_NKERNELS + 1) + k],
-                                  pr.ev[(size_t)s * (ECO_NKERNELS + 1) + k + 1]));
-      pr.ms[list[k].id] += t;
-      pr.launches[list[k].id] += 1;
-    }
-  }
   pr.used = 0;
   for (int k = 0; k < ECO_NKERNELS; ++k) {
     ms[k] = pr.ms[k];

@@ -23,14 +23,14 @@ def test_profiled_steps_equal_plain_steps(eco):
     a = eco.World(p, 21)
     b = eco.World(p, 21)
     a.profile(True, max_steps=8)
-    a.step(12)          # 8 profiled, 4 past the event pool
+    a.step(12)          # 8 profiled, 4 past the cap
     b.step(12)
     prof = a.profile_read()
     assert prof["observe_lstm"][1] == 8 and prof["observe_lstm"][0] > 0
     assert prof["spawn"][1] == 8 and prof["agents_fused"][1] == 8
     a.step(3)
     prof2 = a.profile_read()
-    assert prof2["observe_lstm"][1] == 11   # pool reused after each read
+    assert prof2["observe_lstm"][1] == 11   # the cap restarts after each read
     a.profile(False)
     a.step(2)
     b.step(5)
