@@ -166,8 +166,8 @@ __device__ inline void block_scan2(int a, int b, int &ea, int &eb, int &ta,
 // Birth k of the step: parent s, child in free slot `child` on the parent's
 // claimed cell; the child starts with e0, zero counters and zero recurrent
 // state, the parent's reproduction counter restarts.
-__device__ inline void init_child(const WorldDev &wd, int s, int k, int child, float *h_next) {
-  const int cell = wd.birth_cell[s];
+__device__ inline void init_child(const WorldDev &wd, int s, int cell, int k, int child,
+                                  float *h_next) {
   wd.birth_parent[k] = s;
   wd.birth_child[k] = child;
   wd.repr_ctr[s] = 0;
@@ -244,7 +244,7 @@ __device__ void scan_world(const WorldDev &wd, int *sh) {
     if (!wd.flag[s]) continue;
     const int k = succ_off++;
     if (k >= F) continue;
-    init_child(wd, s, k, wd.free_list[k], h_next);
+    init_child(wd, s, wd.birth_cell[s], k, wd.free_list[k], h_next);
   }
   __syncthreads();
 
@@ -315,38 +315,141 @@ __device__ inline void cluster_prefix2(cg::cluster_group &cl, int *pub, int *out
   __syncthreads();
 }
 
+// Slots per thread of the cluster kernel (8 CTAs x 1024 threads).
+constexpr int CL_SPT = (FUSED_MAX_C + CLUSTER * SCAN_THREADS - 1) / (CLUSTER * SCAN_THREADS);
+
+// Every slot phase of a step for one world.  Each thread owns up to CL_SPT
+// consecutive slots and keeps their state in registers from phase to phase.
+// Phases: claims | moves, eating, physiology, death | birth claims |
+// compaction.  Moves and physiology share a phase: a winner's target was
+// empty at the start of the phase and a dying agent clears its own final
+// cell, so their slot-map writes never meet.
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
     k_agents_cluster(const __grid_constant__ BatchDev b) {
   __shared__ int sh[66];
   __shared__ int pub1[2], pub2[2], ex[4];
+  __shared__ int cta_deaths;
   cg::cluster_group cl = cg::this_cluster();
   const WorldDev &wd = *world_ptr(b, blockIdx.x / CLUSTER);
   const int rank = (int)cl.block_rank();
-  const int C = wd.C;
+  const int C = wd.C, H = wd.H, W = wd.W, Wp = wd.Wp;
   const int per_cta = (C + CLUSTER - 1) / CLUSTER;
   const int c0 = min(C, rank * per_cta), c1 = min(C, c0 + per_cta);
-
-  for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) slot_move_claim(&wd, s);
-  cl.sync();
-  for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) slot_move_apply(&wd, s);
-  cl.sync();
-  for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) slot_physio(&wd, s);
-  cl.sync();
-  for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) slot_birth_claim(&wd, s);
-  cl.sync();
-
-  // compaction: contiguous slots per thread so ranks follow slot order
   const int per = (c1 - c0 + SCAN_THREADS - 1) / SCAN_THREADS;
-  const int s0 = min(c1, c0 + (int)threadIdx.x * per), s1 = min(c1, s0 + per);
+  const int s0 = min(c1, c0 + (int)threadIdx.x * per);
+  const int ns = min(c1, s0 + per) - s0;
+  if (threadIdx.x == 0) cta_deaths = 0;
   const uint32_t t = (uint32_t)wd.ctr->t;
+  const int use_forced = wd.ctr->use_forced;
+  uint32_t *res = (t & 1u) ? wd.res0 : wd.res1;  // plane after this step's regrowth
   float *h_next = (t & 1u) ? wd.h0 : wd.h1;
+
+  int al[CL_SPT], py[CL_SPT], px[CL_SPT], act[CL_SPT], tgt[CL_SPT], age[CL_SPT],
+      low[CL_SPT], rep[CL_SPT], bcell[CL_SPT];
+  float en[CL_SPT];
+  bool kil[CL_SPT];
+#pragma unroll
+  for (int k = 0; k < CL_SPT; ++k) {
+    al[k] = 0;
+    if (k < ns) {
+      const int s = s0 + k;
+      al[k] = wd.alive[s];
+      py[k] = wd.y[s];
+      px[k] = wd.x[s];
+      act[k] = use_forced ? wd.forced[s] : wd.action[s];
+      en[k] = wd.energy[s];
+      age[k] = wd.age[s];
+      low[k] = wd.low_ctr[s];
+      rep[k] = wd.repr_ctr[s];
+    }
+  }
+  // ---- claims: a valid target is on the grid, not a wall, empty now
+#pragma unroll
+  for (int k = 0; k < CL_SPT; ++k) {
+    tgt[k] = -1;
+    kil[k] = false;
+    if (!al[k] || act[k] <= 0 || act[k] >= NACT) continue;
+    const int ty = py[k] + kDY[act[k]], tx = px[k] + kDX[act[k]];
+    if (ty < 0 || ty >= H || tx < 0 || tx >= W || bit_at(wd.wall, Wp, ty, tx)) {
+      kil[k] = wd.wall_kills != 0;
+      continue;
+    }
+    const int cell = ty * W + tx;
+    if (wd.slot_map[cell] != -1) continue;
+    tgt[k] = cell;
+    atomicMin(&wd.claim[cell], s0 + k);
+  }
+  cl.sync();
+  // ---- moves (lowest claimant wins), eating, physiology, death
+#pragma unroll
+  for (int k = 0; k < CL_SPT; ++k) {
+    if (!al[k]) continue;
+    const int s = s0 + k;
+    if (tgt[k] >= 0 && wd.claim[tgt[k]] == s) {
+      wd.claim[tgt[k]] = INT_MAX;  // only the winner resets its cell
+      wd.slot_map[py[k] * W + px[k]] = -1;
+      wd.slot_map[tgt[k]] = s;
+      py[k] = tgt[k] / W;
+      px[k] = tgt[k] % W;
+      wd.y[s] = py[k];
+      wd.x[s] = px[k];
+    }
+    bool dead;
+    if (kil[k]) {
+      dead = true;
+    } else {
+      const uint32_t bit = 1u << (px[k] & 31);
+      const uint32_t old = atomicAnd(&res[py[k] * Wp + (px[k] >> 5)], ~bit);
+      float e = en[k];
+      if (old & bit) e = __fadd_rn(e, wd.e_gain);
+      e = __fsub_rn(e, wd.e_decay);
+      e = fminf(e, wd.e_max);
+      wd.energy[s] = e;
+      age[k] += 1;
+      wd.age[s] = age[k];
+      low[k] = (e <= wd.e_death) ? low[k] + 1 : 0;
+      wd.low_ctr[s] = low[k];
+      dead = low[k] >= max(wd.t_death, 1) || age[k] > wd.max_age;
+      if (!dead) {
+        rep[k] = (e > wd.e_repr) ? rep[k] + 1 : 0;
+        wd.repr_ctr[s] = rep[k];
+      }
+    }
+    if (dead) {
+      al[k] = 0;
+      wd.alive[s] = 0;
+      wd.slot_map[py[k] * W + px[k]] = -1;
+      atomicAdd(&cta_deaths, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && cta_deaths) atomicAdd(&wd.ctr->deaths_step, cta_deaths);
+  cl.sync();
+  // ---- birth claims: first free N, S, E, W cell; lowest parent slot wins
+#pragma unroll
+  for (int k = 0; k < CL_SPT; ++k) {
+    bcell[k] = -1;
+    if (!al[k] || rep[k] < wd.t_repr) continue;
+    for (int a = 1; a < NACT; ++a) {
+      const int ny = py[k] + kDY[a], nx = px[k] + kDX[a];
+      if (ny < 0 || ny >= H || nx < 0 || nx >= W) continue;
+      if (bit_at(wd.wall, Wp, ny, nx)) continue;
+      const int cell = ny * W + nx;
+      if (wd.slot_map[cell] != -1) continue;
+      bcell[k] = cell;
+      atomicMin(&wd.bclaim[cell], s0 + k);
+      break;
+    }
+  }
+  cl.sync();
+  // ---- compaction: ranks follow slot order (contiguous slots per thread)
+  bool ok[CL_SPT];
   int n_free = 0, n_succ = 0;
-  for (int s = s0; s < s1; ++s) {
-    const int cell = wd.birth_cell[s];
-    const bool ok = wd.alive[s] && cell >= 0 && wd.bclaim[cell] == s;
-    wd.flag[s] = ok ? 1 : 0;
-    n_succ += ok;
-    n_free += wd.alive[s] ? 0 : 1;
+#pragma unroll
+  for (int k = 0; k < CL_SPT; ++k) {
+    ok[k] = al[k] && bcell[k] >= 0 && wd.bclaim[bcell[k]] == s0 + k;
+    n_succ += ok[k];
+    n_free += (k < ns && !al[k]) ? 1 : 0;
   }
   int free_off, succ_off, Fb, Sb;
   block_scan2(n_free, n_succ, free_off, succ_off, Fb, Sb, sh);
@@ -354,29 +457,39 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
   free_off += ex[0];
   succ_off += ex[1];
   const int F = ex[2], S = ex[3];
-  for (int s = s0; s < s1; ++s) {
-    const int cell = wd.birth_cell[s];
-    if (cell >= 0) wd.bclaim[cell] = INT_MAX;
-    if (!wd.alive[s]) {
-      if (free_off < S) wd.free_list[free_off] = s;
+  const int births = min(S, F);
+  int free_rank[CL_SPT];
+#pragma unroll
+  for (int k = 0; k < CL_SPT; ++k) {
+    free_rank[k] = INT_MAX;
+    if (bcell[k] >= 0) wd.bclaim[bcell[k]] = INT_MAX;
+    if (k < ns && !al[k]) {
+      free_rank[k] = free_off;
+      if (free_off < S) wd.free_list[free_off] = s0 + k;
       ++free_off;
     }
   }
   cl.sync();
-  for (int s = s0; s < s1; ++s) {
-    if (!wd.flag[s]) continue;
-    const int k = succ_off++;
-    if (k < F) init_child(wd, s, k, wd.free_list[k], h_next);
+#pragma unroll
+  for (int k = 0; k < CL_SPT; ++k) {
+    if (!ok[k]) continue;
+    const int kk = succ_off++;
+    if (kk < F) init_child(wd, s0 + k, bcell[k], kk, wd.free_list[kk], h_next);
   }
-  cl.sync();
+  // alive list of the next step: survivors and the slots that received a child
   int n_alive = 0;
-  for (int s = s0; s < s1; ++s) n_alive += wd.alive[s];
+#pragma unroll
+  for (int k = 0; k < CL_SPT; ++k) {
+    if (free_rank[k] < births) al[k] = 1;
+    n_alive += (k < ns && al[k]) ? 1 : 0;
+  }
   int alive_off, dummy, Ab, dummy2;
   block_scan2(n_alive, 0, alive_off, dummy, Ab, dummy2, sh);
   cluster_prefix2(cl, pub2, ex, Ab, 0);
   alive_off += ex[0];
-  for (int s = s0; s < s1; ++s)
-    if (wd.alive[s]) wd.alive_list[alive_off++] = s;
+#pragma unroll
+  for (int k = 0; k < CL_SPT; ++k)
+    if (k < ns && al[k]) wd.alive_list[alive_off++] = s0 + k;
   if (rank == 0 && threadIdx.x == 0) finish_step(wd, S, F, ex[2], t);
   cl.sync();  // no CTA leaves while another may still read its shared memory
 }
