@@ -33,6 +33,10 @@ sys.path.insert(0, ROOT)
 # (4 x 128 B), position, energy, action and logits (36 B)
 LSTM_BYTES_PER_AGENT = 93332 + 512 + 36
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of one observation+LSTM launch per agent, from the
+# ncu capture in profiles/k_lstm_paper_200x400_held3440.md (327.52 MB at 3,440
+# agents); traffic grows with the agents of a launch, so it is scaled by them.
+LSTM_TRAFFIC_PER_AGENT = 327.515e6 / 3440
 
 
 def lstm_bytes(n_agents: int, H: int, W: int) -> int:
@@ -254,7 +258,8 @@ def bench_ours(args, params, rank, world_size, dist):
         "kernel_ms_per_step": {k: v[0] / v[1] for k, v in prof.items() if v[1]},
         "roofline": {"kernel": "observe_lstm", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": LSTM_TRAFFIC_PER_AGENT * (sum(pops) / max(len(pops), 1)),
                      "bytes_per_launch": bytes_lstm / max(lstm_n, 1)},
         "gpu_launches": kps * args.steps,
         "e2e": {"value": e2e_agent_steps / e2e_dt, "unit": "agent-steps/s",
