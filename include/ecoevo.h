@@ -179,6 +179,17 @@ int eco_world_load_state(EcoWorld *world, const EcoState *in, int set_counters);
  * out, ECO_ECUDA on a CUDA error, else ECO_OK.  Synchronous. */
 int eco_world_sync(EcoWorld *world);
 
+/* Failure detection without a fault: enqueue a kernel that runs the same
+ * bounded mbarrier wait the step's pipeline uses, on a barrier whose phase
+ * never completes; after limit_ns (<= 10 s) it gives up and sets the
+ * world's timeout status, so the next eco_world_sync returns ECO_ETIMEOUT and
+ * the CUDA context stays usable.  Asynchronous.  Errors: ECO_EINVAL. */
+int eco_world_selftest_timeout(EcoWorld *world, uint64_t limit_ns);
+
+/* Clear the world's device status word (after ECO_ETIMEOUT was handled).
+ * Synchronous. */
+int eco_world_clear_status(EcoWorld *world);
+
 /* The world's parameters and CUDA stream. */
 const EcoParams *eco_world_params(const EcoWorld *world);
 void *eco_world_stream(const EcoWorld *world);

@@ -314,6 +314,50 @@ void or_fill_normals(uint64_t seed, uint32_t tag, uint32_t t, uint32_t id,
   }
 }
 
+int or_initial_layout(const OrParams *p, uint64_t seed, uint8_t *res, uint8_t *wall,
+                      int32_t *cells) {
+  if (!valid_params(p)) return -1;
+  const int H = p->H, W = p->W;
+  const size_t HW = (size_t)H * (size_t)W;
+
+  /* Border walls (App. B.1 environment: walls are cells agents cannot
+   * cross). */
+  for (int yy = 0; yy < H; ++yy)
+    for (int xx = 0; xx < W; ++xx)
+      wall[yy * W + xx] =
+          (p->border_walls && (yy == 0 || yy == H - 1 || xx == 0 || xx == W - 1)) ? 1 : 0;
+
+  /* Initial resources: Bernoulli(res_init_p) on every non-wall cell. */
+  uint32_t thr_init = prob_to_threshold(p->res_init_p);
+  for (size_t cell = 0; cell < HW; ++cell) {
+    res[cell] = 0;
+    if (wall[cell]) continue;
+    uint32_t u = philox_word(seed, (uint32_t)(cell % W) >> 2, 0u, OR_TAG_RES_INIT,
+                             (uint32_t)(cell / W), (int)(cell % W) & 3);
+    res[cell] = (u < thr_init) ? 1 : 0;
+  }
+
+  /* Random placement: the non-wall cells sorted by (Philox word, cell); the
+   * first n_agents0 cells receive slots 0.. in that order. */
+  size_t nfree = 0;
+  for (size_t cell = 0; cell < HW; ++cell) nfree += wall[cell] ? 0 : 1;
+  if ((size_t)p->n_agents0 > nfree) return -1;
+  if (p->n_agents0 == 0) return 0;
+  uint64_t *keys = malloc(nfree * sizeof(uint64_t));
+  if (!keys) return -2;
+  size_t k = 0;
+  for (size_t cell = 0; cell < HW; ++cell) {
+    if (wall[cell]) continue;
+    uint32_t u = philox_word(seed, (uint32_t)(cell % W) >> 2, 0u, OR_TAG_PLACE,
+                             (uint32_t)(cell / W), (int)(cell % W) & 3);
+    keys[k++] = ((uint64_t)u << 32) | (uint64_t)cell;
+  }
+  qsort(keys, nfree, sizeof(uint64_t), cmp_u64);
+  for (int s = 0; s < p->n_agents0; ++s) cells[s] = (int32_t)(keys[s] & 0xFFFFFFFFu);
+  free(keys);
+  return 0;
+}
+
 int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
   *out = NULL;
   if (!valid_params(p)) return -1;
@@ -349,58 +393,31 @@ int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
     return -2;
   }
   or_threshold_table(p, w->thr);
-  const int H = p->H, W = p->W;
-
-  /* Border walls (App. B.1 environment: walls are cells agents cannot
-   * cross). */
-  for (int yy = 0; yy < H; ++yy)
-    for (int xx = 0; xx < W; ++xx)
-      if (p->border_walls && (yy == 0 || yy == H - 1 || xx == 0 || xx == W - 1))
-        w->wall[yy * W + xx] = 1;
-
-  /* Initial resources: Bernoulli(res_init_p) on every non-wall cell. */
-  uint32_t thr_init = prob_to_threshold(p->res_init_p);
+  const int W = p->W;
   for (size_t cell = 0; cell < HW; ++cell) {
     w->slot_map[cell] = -1;
     w->claim[cell] = -1;
-    if (w->wall[cell]) continue;
-    uint32_t u = philox_word(seed, (uint32_t)(cell % W) >> 2, 0u, OR_TAG_RES_INIT,
-                             (uint32_t)(cell / W), (int)(cell % W) & 3);
-    w->res[cell] = (u < thr_init) ? 1 : 0;
   }
-
-  /* Random placement: the non-wall cells sorted by (Philox word, cell); the
-   * first n_agents0 cells receive slots 0.. in that order. */
-  size_t nfree = 0;
-  for (size_t cell = 0; cell < HW; ++cell) nfree += w->wall[cell] ? 0 : 1;
-  if ((size_t)p->n_agents0 > nfree) {
+  int32_t *cells = malloc(((size_t)p->n_agents0 + 1) * sizeof(int32_t));
+  if (!cells) { or_world_destroy(w); return -2; }
+  int rc = or_initial_layout(p, seed, w->res, w->wall, cells);
+  if (rc != 0) {
+    free(cells);
     or_world_destroy(w);
-    return -1;
+    return rc;
   }
-  if (p->n_agents0 > 0) {
-    uint64_t *keys = malloc(nfree * sizeof(uint64_t));
-    if (!keys) { or_world_destroy(w); return -2; }
-    size_t k = 0;
-    for (size_t cell = 0; cell < HW; ++cell) {
-      if (w->wall[cell]) continue;
-      uint32_t u = philox_word(seed, (uint32_t)(cell % W) >> 2, 0u, OR_TAG_PLACE,
-                               (uint32_t)(cell / W), (int)(cell % W) & 3);
-      keys[k++] = ((uint64_t)u << 32) | (uint64_t)cell;
-    }
-    qsort(keys, nfree, sizeof(uint64_t), cmp_u64);
-    for (int s = 0; s < p->n_agents0; ++s) {
-      uint32_t cell = (uint32_t)(keys[s] & 0xFFFFFFFFu);
-      w->alive[s] = 1;
-      w->y[s] = (int32_t)(cell / (uint32_t)W);
-      w->x[s] = (int32_t)(cell % (uint32_t)W);
-      w->slot_map[cell] = s;
-      w->energy[s] = p->e0;
-      /* weights drawn once at the start of the simulation, App. B.2 */
-      or_fill_normals(seed, OR_TAG_INIT_W, 0u, (uint32_t)s, p->w_init_std, NULL,
-                   w->weights + (size_t)s * OR_NPARAM);
-    }
-    free(keys);
+  for (int s = 0; s < p->n_agents0; ++s) {
+    const int32_t cell = cells[s];
+    w->alive[s] = 1;
+    w->y[s] = cell / W;
+    w->x[s] = cell % W;
+    w->slot_map[cell] = s;
+    w->energy[s] = p->e0;
+    /* weights drawn once at the start of the simulation, App. B.2 */
+    or_fill_normals(seed, OR_TAG_INIT_W, 0u, (uint32_t)s, p->w_init_std, NULL,
+                    w->weights + (size_t)s * OR_NPARAM);
   }
+  free(cells);
   w->counters[OR_C_POP] = p->n_agents0;
   *out = w;
   return 0;

@@ -138,6 +138,11 @@ void or_observe(const OrParams *p, const uint8_t *res, const uint8_t *wall,
 int or_lstm_step(const float *w /* [23333] */, const double *obs,
                  double *h, double *c, double *logits);
 
+/* Initial walls, resources and agent cells (cells[s] = y*W + x of slot s,
+ * s < n_agents0) of a world created from `seed`; the first part of
+ * or_world_create.  Returns 0, -1 (invalid / too many agents), -2. */
+int or_initial_layout(const OrParams *p, uint64_t seed, uint8_t *res, uint8_t *wall,
+                      int32_t *cells);
 int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out);
 void or_world_destroy(OrWorld *w);
 /* One step.  forced: NULL, or [C] actions used for moving instead of the

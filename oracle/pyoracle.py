@@ -91,6 +91,8 @@ def lib():
                                  ctypes.c_int32, ctypes.c_float, ctypes.c_void_p]
         L.or_lstm_step.argtypes = [ctypes.c_void_p] * 5
         L.or_lstm_step.restype = ctypes.c_int
+        L.or_initial_layout.argtypes = [ctypes.POINTER(OrParams), ctypes.c_uint64,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.or_world_create.argtypes = [ctypes.POINTER(OrParams), ctypes.c_uint64,
                                       ctypes.POINTER(ctypes.c_void_p)]
         L.or_world_destroy.argtypes = [ctypes.c_void_p]
@@ -175,6 +177,18 @@ def lstm_step(w, obs, h, c):
     logits = np.zeros(NACT, np.float64)
     a = lib().or_lstm_step(_ptr(w), _ptr(obs), _ptr(h2), _ptr(c2), _ptr(logits))
     return a, h2, c2, logits
+
+
+def initial_layout(params, seed):
+    """(res [H,W] u8, wall [H,W] u8, cells [n_agents0] int32) of a new world."""
+    p = make_params(params)
+    res = np.zeros((p.H, p.W), np.uint8)
+    wall = np.zeros((p.H, p.W), np.uint8)
+    cells = np.zeros(max(p.n_agents0, 1), np.int32)
+    rc = lib().or_initial_layout(ctypes.byref(p), int(seed), _ptr(res), _ptr(wall), _ptr(cells))
+    if rc != 0:
+        raise ValueError(f"or_initial_layout failed ({rc})")
+    return res, wall, cells[:p.n_agents0]
 
 
 class OracleWorld:

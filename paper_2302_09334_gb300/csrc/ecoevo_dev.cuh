@@ -214,6 +214,7 @@ void launch_scan(const BatchDev &b, cudaStream_t s);
 void launch_spawn(const BatchDev &b, cudaStream_t s);
 void launch_agents_fused(const BatchDev &b, cudaStream_t s);
 void configure_lstm();   // once per device, before the first launch
+void launch_wait_selftest(int *status, unsigned long long limit_ns, cudaStream_t s);
 // Load every step kernel's code before a step is captured in a graph.
 void preload_regrow();
 void preload_lstm();

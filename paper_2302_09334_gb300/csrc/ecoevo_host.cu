@@ -558,6 +558,20 @@ int eco_world_sync(EcoWorld *w) {
   return ECO_OK;
 }
 
+int eco_world_selftest_timeout(EcoWorld *w, uint64_t limit_ns) {
+  if (!w || limit_ns > 10000000000ull) return ECO_EINVAL;
+  launch_wait_selftest(&w->hd.ctr->status, (unsigned long long)limit_ns, w->stream);
+  ECO_CU(cudaGetLastError());
+  return ECO_OK;
+}
+
+int eco_world_clear_status(EcoWorld *w) {
+  if (!w) return ECO_EINVAL;
+  ECO_CU(cudaMemsetAsync(&w->hd.ctr->status, 0, sizeof(int), w->stream));
+  ECO_CU(cudaStreamSynchronize(w->stream));
+  return ECO_OK;
+}
+
 const EcoParams *eco_world_params(const EcoWorld *w) { return w ? &w->p : nullptr; }
 void *eco_world_stream(const EcoWorld *w) { return w ? (void *)w->stream : nullptr; }
 

@@ -94,11 +94,12 @@ __device__ inline bool mbar_try_wait(unsigned long long *bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait for the completion of the phase with the given parity.
-__device__ inline bool mbar_wait(unsigned long long *bar, uint32_t parity) {
+__device__ inline bool mbar_wait(unsigned long long *bar, uint32_t parity,
+                                 unsigned long long limit_ns = WAIT_NS) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > WAIT_NS) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   return true;
 }
 __device__ inline void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
@@ -413,6 +414,26 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
       if (!mbar_wait(&sm.full[st], (last / LSTAGES) & 1)) atomicOr(status, ST_TIMEOUT);
     }
   }
+}
+
+// Exercises the bounded wait on a barrier whose phase never completes (two
+// arrivals expected, one made): the wait gives up after limit_ns and sets
+// ST_TIMEOUT, exactly as a stalled pipeline stage would.
+__global__ void k_wait_selftest(int *status, unsigned long long limit_ns) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 2);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive(&bar);
+    if (!mbar_wait(&bar, 0, limit_ns)) atomicOr(status, ST_TIMEOUT);
+  }
+}
+
+void launch_wait_selftest(int *status, unsigned long long limit_ns, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(status, limit_ns);
 }
 
 void configure_lstm() {

@@ -76,3 +76,56 @@ PRESETS = {
     "paper_200x400": paper_200x400,
     "large_1000x2000": large_1000x2000,
 }
+
+
+# ---------------------------------------------------------------------------
+# Many-world workloads.  Their shapes are drawn from a host Philox stream
+# (numpy's Philox bit generator, seed 12345) so that runs are reproducible;
+# these draws are inputs, not part of the simulation.
+# ---------------------------------------------------------------------------
+def _host_rng(seed: int = 12345):
+    import numpy as np
+    return np.random.Generator(np.random.Philox(seed))
+
+
+def batched_64(n_worlds: int = 64, seed: int = 12345) -> list:
+    """64 independent worlds stepped in one launch per kernel: grid sides
+    log-uniform between 50x100 and 200x400 (aspect 1:2), initial populations
+    uniform in 100..4000, capacity 4x the initial population, bottom-row
+    climate factor uniform in [0.5, 1.0] (top 0.2).  World i uses seed i.
+    Returns [(EcoParams, seed)]."""
+    import math
+    rng = _host_rng(seed)
+    out = []
+    for i in range(n_worlds):
+        h = int(round(math.exp(rng.uniform(math.log(50), math.log(200)))))
+        n0 = int(rng.integers(100, 4001))
+        free = (h - 2) * (2 * h - 2)
+        n0 = min(n0, free // 2)
+        p = EcoParams(H=h, W=2 * h, n_agents0=n0, capacity=4 * n0,
+                      lat_bottom=float(rng.uniform(0.5, 1.0)))
+        out.append((p, i))
+    return out
+
+
+SERVE_GRIDS = ((50, 100), (100, 200), (200, 400))
+
+
+def serve_trace(rate_per_s: float = 20.0, duration_s: float = 600.0, seed: int = 12345) -> list:
+    """Simulation requests with Poisson arrivals: grid one of 50x100,
+    100x200, 200x400; initial population uniform in 200..3000 (at most half
+    the free cells); capacity 4x; steps uniform in 1000..20000; request k
+    uses seed k.  Returns [dict(arrival, params, seed, steps)]."""
+    rng = _host_rng(seed)
+    out, t, k = [], 0.0, 0
+    while True:
+        t += float(rng.exponential(1.0 / rate_per_s))
+        if t >= duration_s:
+            break
+        h, w = SERVE_GRIDS[int(rng.integers(0, len(SERVE_GRIDS)))]
+        n0 = min(int(rng.integers(200, 3001)), (h - 2) * (w - 2) // 2)
+        steps = int(rng.integers(1000, 20001))
+        p = EcoParams(H=h, W=w, n_agents0=n0, capacity=4 * n0)
+        out.append({"arrival": t, "params": p, "seed": k, "steps": steps})
+        k += 1
+    return out

@@ -1,0 +1,73 @@
+"""Batched and served forms: the 64-world batch and the serving loop give
+every world the result it has when stepped alone, and the alone runs match
+the oracle (worlds 0-3 of the batch)."""
+import numpy as np
+import pytest
+
+from paper_2302_09334_gb300.params import EcoParams, batched_64
+from tests.parity import compare, run_forced
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eco():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_09334_gb300 import build, world
+    build.build()
+    return world
+
+
+def test_batched_64_worlds_equal_alone(eco):
+    import torch
+    specs = batched_64()
+    stream = torch.cuda.Stream()
+    worlds = [eco.World(p, s, stream=stream) for p, s in specs]
+    batch = eco.Batch(worlds)
+    batch.step(30)
+    batch.sync()
+    for i in (0, 1, 2, 3, 63):
+        p, s = specs[i]
+        alone = eco.World(p, s)
+        alone.step(30)
+        a, b = alone.read_state(), worlds[i].read_state()
+        for k in a:
+            np.testing.assert_array_equal(a[k], b[k], err_msg=f"world {i} {k}")
+        alone.close()
+    batch.close()
+    for w in worlds:
+        w.close()
+
+
+@pytest.mark.parametrize("i", [0, 1, 2, 3])
+def test_batched_64_worlds_0_to_3_match_oracle(eco, oracle, i):
+    p, s = batched_64()[i]
+    gw = eco.World(p, s)
+    ow = oracle.OracleWorld(p.asdict(), s)
+    compare(gw.read_state(), ow, f"batched world {i} init")
+    run_forced(gw, ow, 20, f"batched world {i}", p.mut_std, compare_every=5)
+
+
+def test_served_results_equal_alone(eco):
+    from paper_2302_09334_gb300.serve import Server
+    trace = []
+    for k, (arr, h, w, n0, steps) in enumerate([(0.0, 20, 40, 60, 250), (0.0, 30, 60, 150, 420),
+                                                (0.05, 12, 70, 40, 130), (0.1, 20, 40, 64, 300),
+                                                (0.15, 50, 100, 300, 210)]):
+        trace.append({"arrival": arr, "params": EcoParams(H=h, W=w, n_agents0=n0, capacity=4 * n0),
+                      "seed": 100 + k, "steps": steps})
+    srv = Server(budget_bytes=3 * 2**30, chunk=100, keep_final=True)
+    rep = srv.run(trace)
+    srv.close()
+    assert rep["requests_completed"] == len(trace)
+    assert rep["chunk_latency_p99_s"] is not None
+    for r in srv.finished:
+        alone = eco.World(r.params, r.seed)
+        alone.step(r.steps)
+        a = alone.read_state()
+        assert int(a["counters"][0]) == r.steps
+        for k in a:
+            np.testing.assert_array_equal(a[k], r.final[k], err_msg=f"request {r.rid} {k}")
+        alone.close()
