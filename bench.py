@@ -266,12 +266,87 @@ def bench_ours(args, params, rank, world_size, dist):
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h},
         "clocks": clocks.summary(),
     }
+    if world_size == 1 and not args.no_many:
+        line["batched"] = bench_batched(args, local)
+        line["served"] = bench_served(args, local)
     if not args.no_cpu_baseline:
         v, n, dt = run_oracle_sample(params, 0, args.cpu_budget, 100000)
         line["cpu_baseline"] = {"value": v, "unit": "agent-steps/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{args.workload} seed 0, first {n} steps "
                                           f"({dt:.1f} s, single-threaded C oracle)"}
     print(json.dumps(line), flush=True)
+
+
+def bench_batched(args, local):
+    """64 worlds of mixed sizes stepped together (one launch per kernel per
+    step).  ~12 GB of weights per step: inputs far larger than L2, no flush."""
+    import torch
+    from paper_2302_09334_gb300.params import batched_64
+    from paper_2302_09334_gb300.world import Batch, World
+    specs = batched_64()
+    stream = torch.cuda.Stream(local)
+    worlds = [World(p, s, device=local, stream=stream) for p, s in specs]
+    batch = Batch(worlds)
+    batch.step(args.batched_warmup)
+    batch.sync()
+    pops0 = [int(w.counters()[1]) for w in worlds]
+    worlds[0].profile(True, max_steps=args.batched_steps)
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pops = []
+    total_ms = 0.0
+    for _ in range(args.batched_steps):
+        pops.append(sum(int(w.counters()[1]) for w in worlds))
+        start.record(stream)
+        batch.step(1)
+        end.record(stream)
+        end.synchronize()
+        total_ms += start.elapsed_time(end)
+    prof = worlds[0].profile_read()
+    worlds[0].profile(False)
+    lstm_ms, _ = prof["observe_lstm"]
+    cells = sum(p.H * p.W for p, _ in specs)
+    bytes_lstm = sum(n * LSTM_BYTES_PER_AGENT for n in pops) + \
+        args.batched_steps * sum(3 * p.H * p.W // 8 for p, _ in specs)
+    peak, kind = load_peaks()
+    achieved = bytes_lstm / (lstm_ms / 1e3) / 1e9 if lstm_ms > 0 else None
+    out = {"workload": "batched_64", "worlds": len(specs), "steps": args.batched_steps,
+           "warmup": args.batched_warmup, "value": sum(pops) / (total_ms / 1e3),
+           "unit": "agent-steps/s", "ms_per_step": total_ms / args.batched_steps,
+           "cell_steps_per_s": cells * args.batched_steps / (total_ms / 1e3),
+           "mean_population": sum(pops) / len(pops), "initial_population": sum(pops0),
+           "kernel_ms_per_step": {k: v[0] / v[1] for k, v in prof.items() if v[1]},
+           "roofline": {"kernel": "observe_lstm", "bound": "hbm", "achieved": achieved,
+                        "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak if achieved else None},
+           "l2": "inputs larger than L2 (about 12 GB of weights per step)"}
+    batch.close()
+    for w in worlds:
+        w.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_served(args, local):
+    """Serving: Poisson request arrivals (20/s), admission by a 120 GB
+    device-memory budget, continuous batching in chunks of 100 steps; the
+    same arrival trace processed one request at a time as the comparison."""
+    import torch
+    from paper_2302_09334_gb300.params import serve_trace
+    from paper_2302_09334_gb300.serve import Server, serve_sequential
+    trace = serve_trace(duration_s=args.serve_seconds)
+    srv = Server(budget_bytes=120e9, chunk=100, device=local)
+    rep = srv.run(trace, duration_s=args.serve_seconds, max_wall_s=args.serve_seconds)
+    srv.close()
+    torch.cuda.empty_cache()
+    seq = serve_sequential(trace, duration_s=args.serve_seconds,
+                           max_wall_s=args.serve_seconds / 2, device=local)
+    torch.cuda.empty_cache()
+    rep.update({"trace": f"Poisson 20/s arrivals over the first {args.serve_seconds:.0f} s "
+                         "(grids 50x100/100x200/200x400, 200-3000 agents, 1000-20000 steps)",
+                "budget_gb": 120, "chunk_steps": 100,
+                "sequential": seq})
+    return rep
 
 
 def main():
@@ -286,6 +361,11 @@ def main():
     ap.add_argument("--held", action="store_true",
                     help="no energy decay and no births: the population stays at n_agents0")
     ap.add_argument("--n-agents", type=int, default=None, help="override n_agents0")
+    ap.add_argument("--no-many", action="store_true",
+                    help="skip the batched (64 worlds) and served measurements")
+    ap.add_argument("--batched-steps", type=int, default=100)
+    ap.add_argument("--batched-warmup", type=int, default=10)
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
