@@ -187,13 +187,16 @@ enum { K_REGROW, K_LSTM, K_MOVE_CLAIM, K_MOVE_APPLY, K_PHYSIO, K_BIRTH_CLAIM, K_
        K_SPAWN, K_AGENTS_FUSED };
 typedef void (*Launcher)(const BatchDev &, cudaStream_t);
 struct StepKernel { int id; Launcher fn; };
+// A step starts with the resource plane of this step already regrown (by
+// the previous step, or at creation/loading) and ends by regrowing the
+// plane of the next step: in the agents cluster kernel for worlds up to the
+// fused capacity, in the grid-wide regrowth kernel otherwise.
 const StepKernel kSplitStep[] = {
-    {K_REGROW, launch_regrow},         {K_LSTM, launch_lstm},
-    {K_MOVE_CLAIM, launch_move_claim}, {K_MOVE_APPLY, launch_move_apply},
-    {K_PHYSIO, launch_physio},         {K_BIRTH_CLAIM, launch_birth_claim},
-    {K_SCAN, launch_scan},             {K_SPAWN, launch_spawn}};
-const StepKernel kFusedStep[] = {{K_REGROW, launch_regrow},
-                                 {K_LSTM, launch_lstm},
+    {K_LSTM, launch_lstm},           {K_MOVE_CLAIM, launch_move_claim},
+    {K_MOVE_APPLY, launch_move_apply}, {K_PHYSIO, launch_physio},
+    {K_BIRTH_CLAIM, launch_birth_claim}, {K_SCAN, launch_scan},
+    {K_SPAWN, launch_spawn},         {K_REGROW, launch_regrow}};
+const StepKernel kFusedStep[] = {{K_LSTM, launch_lstm},
                                  {K_AGENTS_FUSED, launch_agents_fused},
                                  {K_SPAWN, launch_spawn}};
 
@@ -508,6 +511,9 @@ int eco_world_create(const EcoParams *params, uint64_t seed, void *arena,
     if ((rc = cuda_err(cudaStreamSynchronize(s)))) break;
     EcoWorld *self[1] = {w};
     if ((rc = batch_init(w->self, self, 1, w->arena + L.tab_worlds))) break;
+    launch_regrow(w->self.bd, s);  // the plane the first step observes
+    if ((rc = cuda_err(cudaGetLastError()))) break;
+    if ((rc = cuda_err(cudaStreamSynchronize(s)))) break;
   } while (0);
   if (rc != ECO_OK) {
     if (w->owns_arena && w->arena) cudaFree(w->arena);
@@ -731,6 +737,7 @@ int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
     }
   }
   launch_rebuild(&w->hd, w->n_sms, w->stream);
+  launch_regrow(w->self.bd, w->stream);  // the plane the next step observes
   ECO_CU(cudaGetLastError());
   ECO_CU(cudaStreamSynchronize(w->stream));
   int st = 0;

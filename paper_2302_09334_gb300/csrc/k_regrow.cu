@@ -1,4 +1,7 @@
-// k_regrow.cu -- step part a1: resource regrowth, App. B.1, Eq. (1).
+// k_regrow.cu -- step part a1: resource regrowth, App. B.1, Eq. (1), as a
+// grid-wide kernel (worlds above the fused capacity, and the first regrowth
+// after creating or loading a world; smaller worlds regrow inside the agents
+// cluster kernel of the previous step).
 //
 // The resource field is a bit plane (one uint32 word = 32 cells of a row).
 // A CTA owns a tile of 8 rows x 4 words (8 x 128 cells) and stages the rows
@@ -20,17 +23,6 @@ __device__ inline int find_world(const int *prefix, int n, int item) {
     if (prefix[mid] <= item) lo = mid; else hi = mid - 1;
   }
   return lo;
-}
-
-// Bits [dx_lo, dx_hi] of a (2R+1)-bit row window that belong to the
-// neighbourhood at row offset dy (centre excluded).
-__device__ inline uint32_t nbr_mask(int shape, int R, int dy) {
-  int ady = dy < 0 ? -dy : dy;
-  int reach = (shape == 1) ? R - ady : R;
-  uint32_t m = 0;
-  if (reach >= 0) m = ((1u << (2 * reach + 1)) - 1u) << (R - reach);
-  if (dy == 0) m &= ~(1u << R);
-  return m;
 }
 
 constexpr int TILE_ROWS_MAX = REGROW_ROWS + 6;  // R <= 3
