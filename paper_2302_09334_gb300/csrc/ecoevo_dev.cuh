@@ -187,55 +187,6 @@ __device__ inline uint32_t nbr_mask(int shape, int R, int dy) {
   return m;
 }
 
-// Regrowth (App. B.1, Eq. (1)) of the 32 cells of word ww of row y: an empty
-// non-wall cell grows iff word x%4 of the Philox draw {x/4, t, TAG_REGROW, y}
-// is below the threshold of its row and neighbour-count class.  Reads the
-// plane `rin` through L2 (it may have been written earlier in the same
-// kernel) and writes the word of `rout`.
-__device__ inline void regrow_word(const WorldDev &wd, int y, int ww, uint32_t t,
-                                   const uint32_t *rin, uint32_t *rout) {
-  const int H = wd.H, W = wd.W, Wp = wd.Wp, R = wd.nbr_radius;
-  const uint32_t own = __ldcg(&rin[y * Wp + ww]);
-  const uint32_t wl = wd.wall[y * Wp + ww];
-  const int nvalid = min(32, W - ww * 32);
-  const uint32_t valid = nvalid >= 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
-  const uint32_t cand = ~own & ~wl & valid;
-  uint32_t out = own;
-  if (cand) {
-    uint32_t rows[7][3];
-    for (int dy = -R; dy <= R; ++dy) {
-      const int yy = y + dy;
-      for (int c = 0; c < 3; ++c) {
-        const int w2 = ww - 1 + c;
-        rows[dy + R][c] =
-            (yy >= 0 && yy < H && w2 >= 0 && w2 < Wp) ? __ldcg(&rin[yy * Wp + w2]) : 0u;
-      }
-    }
-    const uint32_t *thr = wd.thr + y * 4;
-    const uint32_t win = (1u << (2 * R + 1)) - 1u;
-    for (int q = 0; q < 8; ++q) {
-      const uint32_t cq = (cand >> (4 * q)) & 0xFu;
-      if (!cq) continue;
-      const U4 u = philox4x32_10(U4{(uint32_t)(ww * 8 + q), t, TAG_REGROW, (uint32_t)y},
-                                 wd.key0, wd.key1);
-      const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
-      for (int i = 0; i < 4; ++i) {
-        if (!((cq >> i) & 1u)) continue;
-        const int start = 32 + 4 * q + i - R;  // window start in the 96-bit row
-        const int c0 = start >> 5, off = start & 31;
-        int n = 0;
-        for (int dy = -R; dy <= R; ++dy) {
-          const uint64_t v = (uint64_t)rows[dy + R][c0] | ((uint64_t)rows[dy + R][c0 + 1] << 32);
-          n += __popc((uint32_t)(v >> off) & win & nbr_mask(wd.nbr_shape, R, dy));
-        }
-        const int cls = (n >= wd.class_edges[0]) + (n >= wd.class_edges[1]) +
-                        (n >= wd.class_edges[2]);
-        if (uw[i] < thr[cls]) out |= 1u << (4 * q + i);
-      }
-    }
-  }
-  rout[y * Wp + ww] = out;
-}
 #endif
 
 // ---------------------------------------------------------------------------

@@ -126,7 +126,7 @@ struct Profile {
   int max_steps = 0, used = 0;
   double ms[ECO_NKERNELS] = {0};
   long long launches[ECO_NKERNELS] = {0};
-  cudaEvent_t ev[ECO_NKERNELS + 1] = {nullptr};
+  cudaEvent_t ev[2 * ECO_NKERNELS] = {nullptr};
   int n_ev = 0;
   cudaGraphExec_t exec = nullptr;
 };
@@ -144,6 +144,8 @@ struct EcoBatch {
   bool owns_table = false;
   cudaGraphExec_t g1 = nullptr, gk = nullptr;
   Profile *prof = nullptr;  // the first world's profiler
+  cudaStream_t side = nullptr;        // forked stream of a step
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 struct EcoWorld {
@@ -186,19 +188,21 @@ int slot_blocks_of(const WorldDev &wd) { return (wd.C + SLOT_BLOCK - 1) / SLOT_B
 enum { K_REGROW, K_LSTM, K_MOVE_CLAIM, K_MOVE_APPLY, K_PHYSIO, K_BIRTH_CLAIM, K_SCAN,
        K_SPAWN, K_AGENTS_FUSED };
 typedef void (*Launcher)(const BatchDev &, cudaStream_t);
-struct StepKernel { int id; Launcher fn; };
-// A step starts with the resource plane of this step already regrown (by
-// the previous step, or at creation/loading) and ends by regrowing the
-// plane of the next step: in the agents cluster kernel for worlds up to the
-// fused capacity, in the grid-wide regrowth kernel otherwise.
+struct StepKernel { int id; Launcher fn; int side; };  // side: on the forked stream
+// A step starts with its resource plane already regrown (by the previous
+// step, or at creation/loading) and ends by regrowing the plane of the next
+// step on a forked stream, concurrently with the mutation kernel: regrowth
+// touches only the resource planes, mutation only the weights.  The fork
+// joins before the step ends.
 const StepKernel kSplitStep[] = {
-    {K_LSTM, launch_lstm},           {K_MOVE_CLAIM, launch_move_claim},
-    {K_MOVE_APPLY, launch_move_apply}, {K_PHYSIO, launch_physio},
-    {K_BIRTH_CLAIM, launch_birth_claim}, {K_SCAN, launch_scan},
-    {K_SPAWN, launch_spawn},         {K_REGROW, launch_regrow}};
-const StepKernel kFusedStep[] = {{K_LSTM, launch_lstm},
-                                 {K_AGENTS_FUSED, launch_agents_fused},
-                                 {K_SPAWN, launch_spawn}};
+    {K_LSTM, launch_lstm, 0},           {K_MOVE_CLAIM, launch_move_claim, 0},
+    {K_MOVE_APPLY, launch_move_apply, 0}, {K_PHYSIO, launch_physio, 0},
+    {K_BIRTH_CLAIM, launch_birth_claim, 0}, {K_SCAN, launch_scan, 0},
+    {K_REGROW, launch_regrow, 1},       {K_SPAWN, launch_spawn, 0}};
+const StepKernel kFusedStep[] = {{K_LSTM, launch_lstm, 0},
+                                 {K_AGENTS_FUSED, launch_agents_fused, 0},
+                                 {K_REGROW, launch_regrow, 1},
+                                 {K_SPAWN, launch_spawn, 0}};
 
 int step_kernels(const BatchDev &bd, const StepKernel **list) {
   if (bd.fused) {
@@ -209,11 +213,30 @@ int step_kernels(const BatchDev &bd, const StepKernel **list) {
   return (int)(sizeof(kSplitStep) / sizeof(kSplitStep[0]));
 }
 
-// One step, kernel by kernel.
-void launch_step(const EcoBatch &b, cudaStream_t s, Profile *, int) {
+// One step, kernel by kernel, on stream s and the batch's side stream; with
+// `ev`, a pair of events around every kernel on the stream it runs on.
+void launch_step(const EcoBatch &b, cudaStream_t s, cudaEvent_t *ev) {
   const StepKernel *list;
   const int nk = step_kernels(b.bd, &list);
-  for (int k = 0; k < nk; ++k) list[k].fn(b.bd, s);
+  bool forked = false;
+  for (int k = 0; k < nk; ++k) {
+    cudaStream_t ks = s;
+    if (list[k].side) {
+      if (!forked) {
+        cudaEventRecord(b.fork, s);
+        cudaStreamWaitEvent(b.side, b.fork, 0);
+        forked = true;
+      }
+      ks = b.side;
+    }
+    if (ev) cudaEventRecordWithFlags(ev[2 * k], ks, cudaEventRecordExternal);
+    list[k].fn(b.bd, ks);
+    if (ev) cudaEventRecordWithFlags(ev[2 * k + 1], ks, cudaEventRecordExternal);
+  }
+  if (forked) {
+    cudaEventRecord(b.join, b.side);
+    cudaStreamWaitEvent(s, b.join, 0);
+  }
 }
 
 void destroy_graphs(EcoBatch &b) {
@@ -222,10 +245,18 @@ void destroy_graphs(EcoBatch &b) {
   b.g1 = b.gk = nullptr;
 }
 
+void release_batch_streams(EcoBatch &b) {
+  if (b.side) cudaStreamDestroy(b.side);
+  if (b.fork) cudaEventDestroy(b.fork);
+  if (b.join) cudaEventDestroy(b.join);
+  b.side = nullptr;
+  b.fork = b.join = nullptr;
+}
+
 int capture(EcoBatch &b, int steps, cudaGraphExec_t *out) {
   cudaGraph_t g = nullptr;
   ECO_CU(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
-  for (int i = 0; i < steps; ++i) launch_step(b, b.stream, nullptr, 0);
+  for (int i = 0; i < steps; ++i) launch_step(b, b.stream, nullptr);
   cudaError_t e = cudaStreamEndCapture(b.stream, &g);
   if (e != cudaSuccess) return cuda_err(e);
   e = cudaGraphInstantiate(out, g, 0);
@@ -237,6 +268,9 @@ int capture(EcoBatch &b, int steps, cudaGraphExec_t *out) {
 int batch_init(EcoBatch &b, EcoWorld *const *worlds, int n, void *table_dev) {
   b.worlds.assign(worlds, worlds + n);
   b.stream = worlds[0]->stream;
+  ECO_CU(cudaStreamCreateWithFlags(&b.side, cudaStreamNonBlocking));
+  ECO_CU(cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming));
+  ECO_CU(cudaEventCreateWithFlags(&b.join, cudaEventDisableTiming));
   const size_t tab_bytes = n * sizeof(WorldDev *) + 2 * (n + 1) * sizeof(int);
   if (table_dev) {
     b.table = table_dev;
@@ -279,18 +313,12 @@ int batch_init(EcoBatch &b, EcoWorld *const *worlds, int n, void *table_dev) {
 int capture_profiled(EcoBatch &b, Profile &pr) {
   const StepKernel *list;
   const int nk = step_kernels(b.bd, &list);
-  for (int k = 0; k <= nk; ++k) ECO_CU(cudaEventCreate(&pr.ev[k]));
-  pr.n_ev = nk + 1;
+  for (int k = 0; k < 2 * nk; ++k) ECO_CU(cudaEventCreate(&pr.ev[k]));
+  pr.n_ev = 2 * nk;
   cudaGraph_t g = nullptr;
   int rc = cuda_err(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
   if (rc == ECO_OK) {
-    for (int k = 0; k < nk; ++k) {
-      if (rc == ECO_OK)
-        rc = cuda_err(cudaEventRecordWithFlags(pr.ev[k], b.stream, cudaEventRecordExternal));
-      list[k].fn(b.bd, b.stream);
-    }
-    if (rc == ECO_OK)
-      rc = cuda_err(cudaEventRecordWithFlags(pr.ev[nk], b.stream, cudaEventRecordExternal));
+    launch_step(b, b.stream, pr.ev);
     const int rc_end = cuda_err(cudaStreamEndCapture(b.stream, &g));
     if (rc == ECO_OK) rc = rc_end;
   }
@@ -311,10 +339,10 @@ int profiled_step(EcoBatch &b, Profile &pr) {
   const StepKernel *list;
   const int nk = step_kernels(b.bd, &list);
   ECO_CU(cudaGraphLaunch(pr.exec, b.stream));
-  ECO_CU(cudaEventSynchronize(pr.ev[nk]));
+  ECO_CU(cudaStreamSynchronize(b.stream));
   for (int k = 0; k < nk; ++k) {
     float t = 0.f;
-    ECO_CU(cudaEventElapsedTime(&t, pr.ev[k], pr.ev[k + 1]));
+    ECO_CU(cudaEventElapsedTime(&t, pr.ev[2 * k], pr.ev[2 * k + 1]));
     pr.ms[list[k].id] += t;
     pr.launches[list[k].id] += 1;
   }
@@ -335,7 +363,7 @@ int batch_step(EcoBatch &b, int64_t n) {
         int rc = profiled_step(b, *prof);
         if (rc) return rc;
       } else {
-        launch_step(b, b.stream, nullptr, 0);
+        launch_step(b, b.stream, nullptr);
       }
     }
     return cuda_err(cudaGetLastError());
@@ -528,6 +556,7 @@ void eco_world_destroy(EcoWorld *w) {
   if (!w) return;
   cudaStreamSynchronize(w->stream);
   destroy_graphs(w->self);
+  release_batch_streams(w->self);
   profile_release(w->prof);
   if (w->owns_arena) cudaFree(w->arena);
   delete w;
@@ -547,7 +576,7 @@ int eco_world_step_forced(EcoWorld *w, const int32_t *actions, int actions_on_ho
                            actions_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
   static const int one = 1;
   ECO_CU(cudaMemcpyAsync(&w->hd.ctr->use_forced, &one, sizeof(int), cudaMemcpyHostToDevice, s));
-  launch_step(w->self, s, nullptr, 0);
+  launch_step(w->self, s, nullptr);
   ECO_CU(cudaGetLastError());
   ECO_CU(cudaMemsetAsync(&w->hd.ctr->use_forced, 0, sizeof(int), s));
   if (actions_on_host) ECO_CU(cudaStreamSynchronize(s));
@@ -789,6 +818,7 @@ void eco_batch_destroy(EcoBatch *b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   destroy_graphs(*b);
+  release_batch_streams(*b);
   if (b->owns_table) cudaFree(b->table);
   delete b;
 }

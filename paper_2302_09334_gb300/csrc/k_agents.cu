@@ -318,10 +318,10 @@ __device__ inline void cluster_prefix2(cg::cluster_group &cl, int *pub, int *out
 // Slots per thread of the cluster kernel (8 CTAs x 1024 threads).
 constexpr int CL_SPT = (FUSED_MAX_C + CLUSTER * SCAN_THREADS - 1) / (CLUSTER * SCAN_THREADS);
 
-// Every slot phase of a step for one world, and the regrowth of the next
-// step.  Each thread owns up to CL_SPT consecutive slots and keeps their
-// state in registers from phase to phase.  Phases: claims | moves, eating,
-// physiology, death | next regrowth and birth claims | compaction.  Moves and physiology share a phase: a winner's target was
+// Every slot phase of a step for one world.  Each thread owns up to CL_SPT
+// consecutive slots and keeps their state in registers from phase to phase.
+// Phases: claims | moves, eating, physiology, death | birth claims |
+// compaction.  Moves and physiology share a phase: a winner's target was
 // empty at the start of the phase and a dying agent clears its own final
 // cell, so their slot-map writes never meet.
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
@@ -425,14 +425,6 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
   __syncthreads();
   if (threadIdx.x == 0 && cta_deaths) atomicAdd(&wd.ctr->deaths_step, cta_deaths);
   cl.sync();
-  // ---- regrowth of the next step, from this step's plane after eating
-  //      (the other buffer of the pair); independent of the birth phases
-  {
-    uint32_t *res_next = (t & 1u) ? wd.res1 : wd.res0;
-    const int words = H * Wp;
-    for (int i = rank * SCAN_THREADS + threadIdx.x; i < words; i += CLUSTER * SCAN_THREADS)
-      regrow_word(wd, i / Wp, i % Wp, t + 1u, res, res_next);
-  }
   // ---- birth claims: first free N, S, E, W cell; lowest parent slot wins
 #pragma unroll
   for (int k = 0; k < CL_SPT; ++k) {

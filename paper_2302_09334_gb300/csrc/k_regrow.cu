@@ -1,7 +1,7 @@
-// k_regrow.cu -- step part a1: resource regrowth, App. B.1, Eq. (1), as a
-// grid-wide kernel (worlds above the fused capacity, and the first regrowth
-// after creating or loading a world; smaller worlds regrow inside the agents
-// cluster kernel of the previous step).
+// k_regrow.cu -- step part a1: resource regrowth, App. B.1, Eq. (1).  It
+// runs at the end of a step for the next one, concurrently with the
+// mutation kernel (they touch disjoint data), and once after creating or
+// loading a world.
 //
 // The resource field is a bit plane (one uint32 word = 32 cells of a row).
 // A CTA owns a tile of 8 rows x 4 words (8 x 128 cells) and stages the rows
