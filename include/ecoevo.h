@@ -210,9 +210,12 @@ void eco_batch_destroy(EcoBatch *batch);
  * consecutive events to the kernel in between (profiled stepping is
  * synchronous).  eco_world_profile_read returns the sums since enabling:
  * ms[k], launches[k] for k < ECO_NKERNELS (names: eco_kernel_name; a kernel
- * the world's step does not launch keeps 0 launches).  Worlds of capacity
- * <= 16384 run the slot phases (moves, physiology, birth claims,
- * compaction) as one kernel "agents_fused"; larger ones as five kernels. */
+ * the world's step does not launch keeps 0 launches).  A step runs
+ * "observe_lstm", then the slot phases (moves, physiology, birth claims,
+ * compaction) as one kernel "agents_fused" for worlds of capacity <= 16384
+ * or as five kernels otherwise, then "regrow_spawn": the regrowth of the
+ * next step's resource plane and the mutation of the births in one launch.
+ * "regrow" is the first regrowth after creating or loading a world. */
 #define ECO_NKERNELS 9
 int eco_world_profile(EcoWorld *world, int enable, int max_steps);
 int eco_world_profile_read(EcoWorld *world, double *ms, int64_t *launches);

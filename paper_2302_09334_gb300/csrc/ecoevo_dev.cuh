@@ -223,7 +223,7 @@ void launch_move_apply(const BatchDev &b, cudaStream_t s);
 void launch_physio(const BatchDev &b, cudaStream_t s);
 void launch_birth_claim(const BatchDev &b, cudaStream_t s);
 void launch_scan(const BatchDev &b, cudaStream_t s);
-void launch_spawn(const BatchDev &b, cudaStream_t s);
+void launch_tail(const BatchDev &b, cudaStream_t s);   // regrowth of t+1 + births of t
 void launch_agents_fused(const BatchDev &b, cudaStream_t s);
 void configure_lstm();   // once per device, before the first launch
 void launch_wait_selftest(int *status, unsigned long long limit_ns, cudaStream_t s);

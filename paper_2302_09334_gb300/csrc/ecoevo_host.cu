@@ -144,8 +144,6 @@ struct EcoBatch {
   bool owns_table = false;
   cudaGraphExec_t g1 = nullptr, gk = nullptr;
   Profile *prof = nullptr;  // the first world's profiler
-  cudaStream_t side = nullptr;        // forked stream of a step
-  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 struct EcoWorld {
@@ -186,23 +184,21 @@ int slot_blocks_of(const WorldDev &wd) { return (wd.C + SLOT_BLOCK - 1) / SLOT_B
 
 // Kernel ids for profiling (names: eco_kernel_name).
 enum { K_REGROW, K_LSTM, K_MOVE_CLAIM, K_MOVE_APPLY, K_PHYSIO, K_BIRTH_CLAIM, K_SCAN,
-       K_SPAWN, K_AGENTS_FUSED };
+       K_TAIL, K_AGENTS_FUSED };
 typedef void (*Launcher)(const BatchDev &, cudaStream_t);
-struct StepKernel { int id; Launcher fn; int side; };  // side: on the forked stream
+struct StepKernel { int id; Launcher fn; };
 // A step starts with its resource plane already regrown (by the previous
-// step, or at creation/loading) and ends by regrowing the plane of the next
-// step on a forked stream, concurrently with the mutation kernel: regrowth
-// touches only the resource planes, mutation only the weights.  The fork
-// joins before the step ends.
+// step, or at creation/loading) and ends with the tail kernel: the regrowth
+// of the next step's plane in the same launch as the mutation of this
+// step's births (they touch disjoint data).
 const StepKernel kSplitStep[] = {
-    {K_LSTM, launch_lstm, 0},           {K_MOVE_CLAIM, launch_move_claim, 0},
-    {K_MOVE_APPLY, launch_move_apply, 0}, {K_PHYSIO, launch_physio, 0},
-    {K_BIRTH_CLAIM, launch_birth_claim, 0}, {K_SCAN, launch_scan, 0},
-    {K_REGROW, launch_regrow, 1},       {K_SPAWN, launch_spawn, 0}};
-const StepKernel kFusedStep[] = {{K_LSTM, launch_lstm, 0},
-                                 {K_AGENTS_FUSED, launch_agents_fused, 0},
-                                 {K_REGROW, launch_regrow, 1},
-                                 {K_SPAWN, launch_spawn, 0}};
+    {K_LSTM, launch_lstm},           {K_MOVE_CLAIM, launch_move_claim},
+    {K_MOVE_APPLY, launch_move_apply}, {K_PHYSIO, launch_physio},
+    {K_BIRTH_CLAIM, launch_birth_claim}, {K_SCAN, launch_scan},
+    {K_TAIL, launch_tail}};
+const StepKernel kFusedStep[] = {{K_LSTM, launch_lstm},
+                                 {K_AGENTS_FUSED, launch_agents_fused},
+                                 {K_TAIL, launch_tail}};
 
 int step_kernels(const BatchDev &bd, const StepKernel **list) {
   if (bd.fused) {
@@ -213,29 +209,15 @@ int step_kernels(const BatchDev &bd, const StepKernel **list) {
   return (int)(sizeof(kSplitStep) / sizeof(kSplitStep[0]));
 }
 
-// One step, kernel by kernel, on stream s and the batch's side stream; with
-// `ev`, a pair of events around every kernel on the stream it runs on.
+// One step, kernel by kernel; with `ev`, a pair of events around every
+// kernel.
 void launch_step(const EcoBatch &b, cudaStream_t s, cudaEvent_t *ev) {
   const StepKernel *list;
   const int nk = step_kernels(b.bd, &list);
-  bool forked = false;
   for (int k = 0; k < nk; ++k) {
-    cudaStream_t ks = s;
-    if (list[k].side) {
-      if (!forked) {
-        cudaEventRecord(b.fork, s);
-        cudaStreamWaitEvent(b.side, b.fork, 0);
-        forked = true;
-      }
-      ks = b.side;
-    }
-    if (ev) cudaEventRecordWithFlags(ev[2 * k], ks, cudaEventRecordExternal);
-    list[k].fn(b.bd, ks);
-    if (ev) cudaEventRecordWithFlags(ev[2 * k + 1], ks, cudaEventRecordExternal);
-  }
-  if (forked) {
-    cudaEventRecord(b.join, b.side);
-    cudaStreamWaitEvent(s, b.join, 0);
+    if (ev) cudaEventRecordWithFlags(ev[2 * k], s, cudaEventRecordExternal);
+    list[k].fn(b.bd, s);
+    if (ev) cudaEventRecordWithFlags(ev[2 * k + 1], s, cudaEventRecordExternal);
   }
 }
 
@@ -243,14 +225,6 @@ void destroy_graphs(EcoBatch &b) {
   if (b.g1) cudaGraphExecDestroy(b.g1);
   if (b.gk) cudaGraphExecDestroy(b.gk);
   b.g1 = b.gk = nullptr;
-}
-
-void release_batch_streams(EcoBatch &b) {
-  if (b.side) cudaStreamDestroy(b.side);
-  if (b.fork) cudaEventDestroy(b.fork);
-  if (b.join) cudaEventDestroy(b.join);
-  b.side = nullptr;
-  b.fork = b.join = nullptr;
 }
 
 int capture(EcoBatch &b, int steps, cudaGraphExec_t *out) {
@@ -268,9 +242,6 @@ int capture(EcoBatch &b, int steps, cudaGraphExec_t *out) {
 int batch_init(EcoBatch &b, EcoWorld *const *worlds, int n, void *table_dev) {
   b.worlds.assign(worlds, worlds + n);
   b.stream = worlds[0]->stream;
-  ECO_CU(cudaStreamCreateWithFlags(&b.side, cudaStreamNonBlocking));
-  ECO_CU(cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming));
-  ECO_CU(cudaEventCreateWithFlags(&b.join, cudaEventDisableTiming));
   const size_t tab_bytes = n * sizeof(WorldDev *) + 2 * (n + 1) * sizeof(int);
   if (table_dev) {
     b.table = table_dev;
@@ -339,7 +310,7 @@ int profiled_step(EcoBatch &b, Profile &pr) {
   const StepKernel *list;
   const int nk = step_kernels(b.bd, &list);
   ECO_CU(cudaGraphLaunch(pr.exec, b.stream));
-  ECO_CU(cudaStreamSynchronize(b.stream));
+  ECO_CU(cudaEventSynchronize(pr.ev[2 * nk - 1]));
   for (int k = 0; k < nk; ++k) {
     float t = 0.f;
     ECO_CU(cudaEventElapsedTime(&t, pr.ev[2 * k], pr.ev[2 * k + 1]));
@@ -556,7 +527,6 @@ void eco_world_destroy(EcoWorld *w) {
   if (!w) return;
   cudaStreamSynchronize(w->stream);
   destroy_graphs(w->self);
-  release_batch_streams(w->self);
   profile_release(w->prof);
   if (w->owns_arena) cudaFree(w->arena);
   delete w;
@@ -818,7 +788,6 @@ void eco_batch_destroy(EcoBatch *b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   destroy_graphs(*b);
-  release_batch_streams(*b);
   if (b->owns_table) cudaFree(b->table);
   delete b;
 }
@@ -855,7 +824,7 @@ int eco_world_profile_read(EcoWorld *w, double *ms, int64_t *launches) {
 const char *eco_kernel_name(int k) {
   static const char *names[ECO_NKERNELS] = {
       "regrow", "observe_lstm", "move_claim", "move_apply", "physio",
-      "birth_claim", "scan", "spawn", "agents_fused"};
+      "birth_claim", "scan", "regrow_spawn", "agents_fused"};
   return (k >= 0 && k < ECO_NKERNELS) ? names[k] : "?";
 }
 

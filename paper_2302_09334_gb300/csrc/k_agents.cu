@@ -16,13 +16,15 @@
 //               alive list for the next step rebuilt, counters, t += 1
 //   agents_cluster  all of the above for worlds of capacity <= 16384, one
 //               thread-block cluster per world
-//   spawn       child weights = parent weights + sigma * N(0,1), a grid-
-//               stride pass over every float4 of every birth
+//   tail        child weights = parent weights + sigma * N(0,1) (a grid-
+//               stride pass over every float4 of every birth) in the same
+//               launch as the regrowth of the next step's resource plane
 #include <climits>
 
 #include <cooperative_groups.h>
 
 #include "ecoevo_dev.cuh"
+#include "regrow_tile.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -537,8 +539,8 @@ __device__ inline float4 mutate4(const WorldDev &wd, int vi, float4 base, uint32
 // issues the loads of SPAWN_UNROLL elements before any of their arithmetic.
 constexpr int SPAWN_UNROLL = 4;
 
-__global__ void __launch_bounds__(SPAWN_THREADS) k_spawn(const __grid_constant__ BatchDev b) {
-  __shared__ int pre[1025];
+// Mutation of every birth of the batch by CTAs cta .. of n_cta.
+__device__ inline void spawn_births(const BatchDev &b, int *pre, int cta, int n_cta) {
   if (threadIdx.x == 0) {
     int run = 0;
     for (int w = 0; w < b.n; ++w) {
@@ -549,8 +551,8 @@ __global__ void __launch_bounds__(SPAWN_THREADS) k_spawn(const __grid_constant__
   }
   __syncthreads();
   const long long total = (long long)pre[b.n] * NVEC;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; g0 < total;
+  const long long stride = (long long)n_cta * blockDim.x;
+  for (long long g0 = (long long)cta * blockDim.x + threadIdx.x; g0 < total;
        g0 += SPAWN_UNROLL * stride) {
     float4 in[SPAWN_UNROLL];
     float4 *dst[SPAWN_UNROLL];
@@ -586,6 +588,21 @@ __global__ void __launch_bounds__(SPAWN_THREADS) k_spawn(const __grid_constant__
   }
 }
 
+// The tail of a step: the regrowth of the next step's plane (the first
+// total_tiles CTAs) and the mutation of this step's births (the others), in
+// one launch -- they touch disjoint data (resource planes / weights).
+constexpr int SPAWN_CTAS_PER_SM = 4;
+static_assert(REGROW_THREADS == SPAWN_THREADS, "one block size for the tail kernel");
+
+__global__ void __launch_bounds__(SPAWN_THREADS) k_tail(const __grid_constant__ BatchDev b) {
+  __shared__ uint32_t tile[TILE_ROWS_MAX][TILE_COLS];
+  __shared__ int pre[1025];
+  if ((int)blockIdx.x < b.total_tiles)
+    regrow_tile(b, blockIdx.x, tile);
+  else
+    spawn_births(b, pre, blockIdx.x - b.total_tiles, gridDim.x - b.total_tiles);
+}
+
 // Initial weights of slots [0, n0): w_init_std * N_j of (TAG_INIT_W, 0, slot).
 __global__ void __launch_bounds__(SPAWN_THREADS) k_init_weights(const WorldDev *wdp, int n0) {
   const WorldDev &wd = *wdp;
@@ -606,7 +623,7 @@ void preload_agents() {
   cudaFuncGetAttributes(&a, k_physio);
   cudaFuncGetAttributes(&a, k_birth_claim);
   cudaFuncGetAttributes(&a, k_scan);
-  cudaFuncGetAttributes(&a, k_spawn);
+  cudaFuncGetAttributes(&a, k_tail);
   cudaFuncGetAttributes(&a, k_agents_cluster);
 }
 
@@ -628,8 +645,8 @@ void launch_scan(const BatchDev &b, cudaStream_t s) {
 void launch_agents_fused(const BatchDev &b, cudaStream_t s) {
   k_agents_cluster<<<b.n * CLUSTER, SCAN_THREADS, 0, s>>>(b);
 }
-void launch_spawn(const BatchDev &b, cudaStream_t s) {
-  k_spawn<<<4 * b.n_sms, SPAWN_THREADS, 0, s>>>(b);
+void launch_tail(const BatchDev &b, cudaStream_t s) {
+  k_tail<<<b.total_tiles + SPAWN_CTAS_PER_SM * b.n_sms, SPAWN_THREADS, 0, s>>>(b);
 }
 void launch_init_weights(const WorldDev *wd_dev, int n0, int n_sms, cudaStream_t s) {
   if (n0 > 0) k_init_weights<<<8 * n_sms, SPAWN_THREADS, 0, s>>>(wd_dev, n0);

@@ -27,7 +27,7 @@ def test_profiled_steps_equal_plain_steps(eco):
     b.step(12)
     prof = a.profile_read()
     assert prof["observe_lstm"][1] == 8 and prof["observe_lstm"][0] > 0
-    assert prof["spawn"][1] == 8 and prof["agents_fused"][1] == 8
+    assert prof["regrow_spawn"][1] == 8 and prof["agents_fused"][1] == 8
     a.step(3)
     prof2 = a.profile_read()
     assert prof2["observe_lstm"][1] == 11   # the cap restarts after each read
