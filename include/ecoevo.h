@@ -205,10 +205,11 @@ void eco_batch_destroy(EcoBatch *batch);
 
 /* Per-kernel timing with CUDA events on the world's stream.  While enabled,
  * each step (up to max_steps after each read) runs as a one-step CUDA graph
- * with an event-record node before every kernel and after the last; the
- * step call waits for the step to finish and adds the elapsed time between
- * consecutive events to the kernel in between (profiled stepping is
- * synchronous).  eco_world_profile_read returns the sums since enabling:
+ * with an event-record node before and after every kernel; the elapsed
+ * times of a step are added to their kernels when the next profiled step is
+ * launched (the events are reused, so that launch first waits for the
+ * previous one) or when they are read.  eco_world_profile_read waits for the
+ * stream and returns the sums since enabling:
  * ms[k], launches[k] for k < ECO_NKERNELS (names: eco_kernel_name; a kernel
  * the world's step does not launch keeps 0 launches).  A step runs
  * "observe_lstm", then the slot phases (moves, physiology, birth claims,

@@ -117,10 +117,14 @@ std::vector<uint32_t> threshold_table(const EcoParams *p) {
   return thr;
 }
 
+typedef void (*Launcher)(const BatchDev &, cudaStream_t);
+struct StepKernel { int id; Launcher fn; };
+
 // Per-kernel timing of graph-launched steps: the one-step graph is captured
-// with an event-record node before every kernel and after the last; after
-// each profiled launch the host waits for the last event and adds the
-// elapsed time between consecutive events to the kernel in between.
+// with an event-record node before and after every kernel.  A profiled
+// step launches the graph and returns; the times of a launch are added just
+// before the graph is launched again (its events are reused) or when they
+// are read.
 struct Profile {
   bool on = false;
   int max_steps = 0, used = 0;
@@ -129,6 +133,10 @@ struct Profile {
   cudaEvent_t ev[2 * ECO_NKERNELS] = {nullptr};
   int n_ev = 0;
   cudaGraphExec_t exec = nullptr;
+  const void *owner = nullptr;   // the batch the graph steps
+  const StepKernel *list = nullptr;
+  int nk = 0;
+  bool pending = false;      // a launch whose times are not yet added
 };
 
 }  // namespace
@@ -185,8 +193,6 @@ int slot_blocks_of(const WorldDev &wd) { return (wd.C + SLOT_BLOCK - 1) / SLOT_B
 // Kernel ids for profiling (names: eco_kernel_name).
 enum { K_REGROW, K_LSTM, K_MOVE_CLAIM, K_MOVE_APPLY, K_PHYSIO, K_BIRTH_CLAIM, K_SCAN,
        K_TAIL, K_AGENTS_FUSED };
-typedef void (*Launcher)(const BatchDev &, cudaStream_t);
-struct StepKernel { int id; Launcher fn; };
 // A step starts with its resource plane already regrown (by the previous
 // step, or at creation/loading) and ends with the tail kernel: the regrowth
 // of the next step's plane in the same launch as the mutation of this
@@ -286,6 +292,9 @@ int capture_profiled(EcoBatch &b, Profile &pr) {
   const int nk = step_kernels(b.bd, &list);
   for (int k = 0; k < 2 * nk; ++k) ECO_CU(cudaEventCreate(&pr.ev[k]));
   pr.n_ev = 2 * nk;
+  pr.owner = &b;
+  pr.list = list;
+  pr.nk = nk;
   cudaGraph_t g = nullptr;
   int rc = cuda_err(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
   if (rc == ECO_OK) {
@@ -303,20 +312,32 @@ void profile_release(Profile &pr) {
   pr.n_ev = 0;
   if (pr.exec) cudaGraphExecDestroy(pr.exec);
   pr.exec = nullptr;
+  pr.owner = nullptr;
+  pr.list = nullptr;
+  pr.nk = 0;
+  pr.pending = false;
 }
 
-// One profiled step: launch, wait, add the per-kernel times.
-int profiled_step(EcoBatch &b, Profile &pr) {
-  const StepKernel *list;
-  const int nk = step_kernels(b.bd, &list);
-  ECO_CU(cudaGraphLaunch(pr.exec, b.stream));
-  ECO_CU(cudaEventSynchronize(pr.ev[2 * nk - 1]));
-  for (int k = 0; k < nk; ++k) {
+// Add the per-kernel times of the pending profiled launch, if any.
+int profile_collect(Profile &pr) {
+  if (!pr.pending) return ECO_OK;
+  ECO_CU(cudaEventSynchronize(pr.ev[2 * pr.nk - 1]));
+  for (int k = 0; k < pr.nk; ++k) {
     float t = 0.f;
     ECO_CU(cudaEventElapsedTime(&t, pr.ev[2 * k], pr.ev[2 * k + 1]));
-    pr.ms[list[k].id] += t;
-    pr.launches[list[k].id] += 1;
+    pr.ms[pr.list[k].id] += t;
+    pr.launches[pr.list[k].id] += 1;
   }
+  pr.pending = false;
+  return ECO_OK;
+}
+
+// One profiled step: collect the previous launch's times, launch again.
+int profiled_step(EcoBatch &b, Profile &pr) {
+  int rc = profile_collect(pr);
+  if (rc) return rc;
+  ECO_CU(cudaGraphLaunch(pr.exec, b.stream));
+  pr.pending = true;
   pr.used += 1;
   return ECO_OK;
 }
@@ -325,6 +346,11 @@ int batch_step(EcoBatch &b, int64_t n) {
   if (n < 0) return ECO_EINVAL;
   Profile *prof = b.prof;
   if (prof && prof->on) {
+    if (prof->exec && prof->owner != &b) {  // profiled last as part of another batch
+      int rc = profile_collect(*prof);
+      if (rc) return rc;
+      profile_release(*prof);
+    }
     if (!prof->exec) {
       int rc = capture_profiled(b, *prof);
       if (rc) return rc;
@@ -797,6 +823,7 @@ int eco_world_profile(EcoWorld *w, int enable, int max_steps) {
   Profile &pr = w->prof;
   ECO_CU(cudaStreamSynchronize(w->stream));
   profile_release(pr);
+  pr.pending = false;
   pr.on = false;
   pr.used = 0;
   for (int k = 0; k < ECO_NKERNELS; ++k) {
@@ -813,6 +840,8 @@ int eco_world_profile_read(EcoWorld *w, double *ms, int64_t *launches) {
   if (!w || !ms || !launches) return ECO_EINVAL;
   Profile &pr = w->prof;
   ECO_CU(cudaStreamSynchronize(w->stream));
+  int rc = profile_collect(pr);
+  if (rc) return rc;
   pr.used = 0;
   for (int k = 0; k < ECO_NKERNELS; ++k) {
     ms[k] = pr.ms[k];
