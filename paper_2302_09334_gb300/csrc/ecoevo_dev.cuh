@@ -218,7 +218,6 @@ constexpr int FUSED_MAX_C = 16384;
 
 void launch_regrow(const BatchDev &b, cudaStream_t s);
 void launch_lstm(const BatchDev &b, cudaStream_t s);
-void launch_move_claim(const BatchDev &b, cudaStream_t s);
 void launch_move_apply(const BatchDev &b, cudaStream_t s);
 void launch_physio(const BatchDev &b, cudaStream_t s);
 void launch_birth_claim(const BatchDev &b, cudaStream_t s);

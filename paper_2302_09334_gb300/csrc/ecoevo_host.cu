@@ -194,11 +194,12 @@ int slot_blocks_of(const WorldDev &wd) { return (wd.C + SLOT_BLOCK - 1) / SLOT_B
 enum { K_REGROW, K_LSTM, K_MOVE_CLAIM, K_MOVE_APPLY, K_PHYSIO, K_BIRTH_CLAIM, K_SCAN,
        K_TAIL, K_AGENTS_FUSED };
 // A step starts with its resource plane already regrown (by the previous
-// step, or at creation/loading) and ends with the tail kernel: the regrowth
+// step, or at creation/loading); the observation+LSTM kernel also makes the
+// move claims; it ends with the tail kernel: the regrowth
 // of the next step's plane in the same launch as the mutation of this
 // step's births (they touch disjoint data).
 const StepKernel kSplitStep[] = {
-    {K_LSTM, launch_lstm},           {K_MOVE_CLAIM, launch_move_claim},
+    {K_LSTM, launch_lstm},
     {K_MOVE_APPLY, launch_move_apply}, {K_PHYSIO, launch_physio},
     {K_BIRTH_CLAIM, launch_birth_claim}, {K_SCAN, launch_scan},
     {K_TAIL, launch_tail}};

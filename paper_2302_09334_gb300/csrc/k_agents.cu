@@ -5,8 +5,9 @@
 // 256 slots, world found from a block prefix).  Conflicts are settled with
 // order-independent atomics only (atomicMin on claim cells, atomicAnd on
 // resource words), so results do not depend on thread scheduling:
-//   move_claim  target cell; a valid target (on the grid, not a wall, empty
-//               at the start of the phase) gets atomicMin(claim, slot)
+//   (claims)    made by the observation+LSTM kernel as soon as an agent's
+//               action is known: a valid target (on the grid, not a wall,
+//               empty at the start of the phase) gets atomicMin(claim, slot)
 //   move_apply  the lowest claimant moves and resets the claim cell
 //   physio      eat (atomicAnd clears the resource bit), energy update with
 //               exactly rounded float add/sub, death, reproduction counter
@@ -52,25 +53,8 @@ __constant__ int kDY[5] = {0, -1, 1, 0, 0};  // stay, N, S, E, W
 __constant__ int kDX[5] = {0, 0, 0, 1, -1};
 
 // ---------------------------------------------------------------- a4 ------
-__device__ inline void slot_move_claim(const WorldDev *wd, int s) {
-  wd->killed[s] = 0;
-  wd->target[s] = -1;
-  if (!wd->alive[s]) return;
-  const int a = wd->ctr->use_forced ? wd->forced[s] : wd->action[s];
-  if (a <= 0 || a >= NACT) return;
-  const int ty = wd->y[s] + kDY[a], tx = wd->x[s] + kDX[a];
-  if (ty < 0 || ty >= wd->H || tx < 0 || tx >= wd->W ||
-      bit_at(wd->wall, wd->Wp, ty, tx)) {
-    if (wd->wall_kills) wd->killed[s] = 1;
-    return;
-  }
-  const int cell = ty * wd->W + tx;
-  if (wd->slot_map[cell] != -1) return;
-  wd->target[s] = cell;
-  atomicMin(&wd->claim[cell], s);
-}
-
 __device__ inline void slot_move_apply(const WorldDev *wd, int s) {
+  if (!wd->alive[s]) return;
   const int cell = wd->target[s];
   if (cell < 0 || wd->claim[cell] != s) return;
   wd->claim[cell] = INT_MAX;  // only the winner resets; losers compare != s
@@ -261,11 +245,6 @@ __device__ void scan_world(const WorldDev &wd, int *sh) {
   if (threadIdx.x == 0) finish_step(wd, S, F, pop, t);
 }
 
-__global__ void __launch_bounds__(SLOT_BLOCK) k_move_claim(const __grid_constant__ BatchDev b) {
-  const WorldDev *wd;
-  const int s = slot_of_thread(b, wd);
-  if (s >= 0) slot_move_claim(wd, s);
-}
 __global__ void __launch_bounds__(SLOT_BLOCK) k_move_apply(const __grid_constant__ BatchDev b) {
   const WorldDev *wd;
   const int s = slot_of_thread(b, wd);
@@ -294,6 +273,71 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const __grid_constant__ B
 // exchanges per-CTA totals through distributed shared memory.
 constexpr int CLUSTER = 8;
 
+// Exclusive block scan of three counters over the CTA (<= 1024 threads):
+// e[i] = sum over lower threads, tot[i] = block total.
+__device__ inline void block_scan3(const int v[3], int e[3], int tot[3], int *sh /* [3*32+3] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc[3] = {v[0], v[1], v[2]};
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int x = __shfl_up_sync(0xFFFFFFFFu, inc[i], o);
+      if (lane >= o) inc[i] += x;
+    }
+  }
+  if (lane == 31)
+    for (int i = 0; i < 3; ++i) sh[32 * i + warp] = inc[i];
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int w0 = lane < nw ? sh[32 * i + lane] : 0;
+      int sc = w0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xFFFFFFFFu, sc, o);
+        if (lane >= o) sc += x;
+      }
+      if (lane < nw) sh[32 * i + lane] = sc - w0;
+      if (lane == 31) sh[96 + i] = sc;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    e[i] = sh[32 * i + warp] + inc[i] - v[i];
+    tot[i] = sh[96 + i];
+  }
+  __syncthreads();
+}
+
+// Exclusive prefix over the cluster's CTAs of three per-CTA totals:
+// out[0..2] = sum over lower ranks, out[3..5] = cluster totals.
+__device__ inline void cluster_prefix3(cg::cluster_group &cl, int *pub, int *out,
+                                       const int v[3]) {
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 3; ++i) pub[i] = v[i];
+  cl.sync();
+  if (threadIdx.x == 0) {
+    const int me = (int)cl.block_rank();
+    int base[3] = {0, 0, 0}, tot[3] = {0, 0, 0};
+    for (int r = 0; r < CLUSTER; ++r) {
+      const int *rp = cl.map_shared_rank(pub, r);
+      for (int i = 0; i < 3; ++i) {
+        if (r < me) base[i] += rp[i];
+        tot[i] += rp[i];
+      }
+    }
+    for (int i = 0; i < 3; ++i) {
+      out[i] = base[i];
+      out[3 + i] = tot[i];
+    }
+  }
+  __syncthreads();
+}
+
 // Exclusive prefix over the cluster's CTAs of two per-CTA totals.
 __device__ inline void cluster_prefix2(cg::cluster_group &cl, int *pub, int *out, int a,
                                        int b) {
@@ -320,16 +364,21 @@ __device__ inline void cluster_prefix2(cg::cluster_group &cl, int *pub, int *out
 // Slots per thread of the cluster kernel (8 CTAs x 1024 threads).
 constexpr int CL_SPT = (FUSED_MAX_C + CLUSTER * SCAN_THREADS - 1) / (CLUSTER * SCAN_THREADS);
 
-// Every slot phase of a step for one world.  Each thread owns up to CL_SPT
-// consecutive slots and keeps their state in registers from phase to phase.
-// Phases: claims | moves, eating, physiology, death | birth claims |
+// Every slot phase of a step for one world (the move claims are already
+// made by the observation+LSTM kernel).  Each thread owns up to CL_SPT
+// consecutive slots and keeps their state in registers from phase to
+// phase.  Phases: moves, eating, physiology, death | birth claims |
 // compaction.  Moves and physiology share a phase: a winner's target was
 // empty at the start of the phase and a dying agent clears its own final
-// cell, so their slot-map writes never meet.
+// cell, so their slot-map writes never meet.  The compaction is one scan of
+// three counts per slot range -- free slots, successful parents, survivors:
+// children fill the free slots of rank below the number of births in slot
+// order, so a slot's place in the next alive list is the survivors before
+// it plus min(free slots before it, births).
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
     k_agents_cluster(const __grid_constant__ BatchDev b) {
-  __shared__ int sh[66];
-  __shared__ int pub1[2], pub2[2], ex[4];
+  __shared__ int sh[3 * 32 + 3];
+  __shared__ int pub[3], ex[6];
   __shared__ int cta_deaths;
   cg::cluster_group cl = cg::this_cluster();
   const WorldDev &wd = *world_ptr(b, blockIdx.x / CLUSTER);
@@ -342,12 +391,11 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
   const int ns = min(c1, s0 + per) - s0;
   if (threadIdx.x == 0) cta_deaths = 0;
   const uint32_t t = (uint32_t)wd.ctr->t;
-  const int use_forced = wd.ctr->use_forced;
   uint32_t *res = (t & 1u) ? wd.res0 : wd.res1;  // plane after this step's regrowth
   float *h_next = (t & 1u) ? wd.h0 : wd.h1;
 
-  int al[CL_SPT], py[CL_SPT], px[CL_SPT], act[CL_SPT], tgt[CL_SPT], age[CL_SPT],
-      low[CL_SPT], rep[CL_SPT], bcell[CL_SPT];
+  int al[CL_SPT], py[CL_SPT], px[CL_SPT], tgt[CL_SPT], age[CL_SPT], low[CL_SPT],
+      rep[CL_SPT], bcell[CL_SPT];
   float en[CL_SPT];
   bool kil[CL_SPT];
 #pragma unroll
@@ -358,30 +406,15 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
       al[k] = wd.alive[s];
       py[k] = wd.y[s];
       px[k] = wd.x[s];
-      act[k] = use_forced ? wd.forced[s] : wd.action[s];
+      tgt[k] = wd.target[s];
+      kil[k] = wd.killed[s] != 0;
       en[k] = wd.energy[s];
       age[k] = wd.age[s];
       low[k] = wd.low_ctr[s];
       rep[k] = wd.repr_ctr[s];
     }
   }
-  // ---- claims: a valid target is on the grid, not a wall, empty now
-#pragma unroll
-  for (int k = 0; k < CL_SPT; ++k) {
-    tgt[k] = -1;
-    kil[k] = false;
-    if (!al[k] || act[k] <= 0 || act[k] >= NACT) continue;
-    const int ty = py[k] + kDY[act[k]], tx = px[k] + kDX[act[k]];
-    if (ty < 0 || ty >= H || tx < 0 || tx >= W || bit_at(wd.wall, Wp, ty, tx)) {
-      kil[k] = wd.wall_kills != 0;
-      continue;
-    }
-    const int cell = ty * W + tx;
-    if (wd.slot_map[cell] != -1) continue;
-    tgt[k] = cell;
-    atomicMin(&wd.claim[cell], s0 + k);
-  }
-  cl.sync();
+  __syncthreads();  // cta_deaths initialised
   // ---- moves (lowest claimant wins), eating, physiology, death
 #pragma unroll
   for (int k = 0; k < CL_SPT; ++k) {
@@ -444,55 +477,51 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
     }
   }
   cl.sync();
-  // ---- compaction: ranks follow slot order (contiguous slots per thread)
+  // ---- compaction (contiguous slots per thread, so ranks follow slot order)
   bool ok[CL_SPT];
-  int n_free = 0, n_succ = 0;
+  int cnt[3] = {0, 0, 0};  // free slots, successful parents, survivors
 #pragma unroll
   for (int k = 0; k < CL_SPT; ++k) {
     ok[k] = al[k] && bcell[k] >= 0 && wd.bclaim[bcell[k]] == s0 + k;
-    n_succ += ok[k];
-    n_free += (k < ns && !al[k]) ? 1 : 0;
+    cnt[0] += (k < ns && !al[k]) ? 1 : 0;
+    cnt[1] += ok[k];
+    cnt[2] += al[k];
   }
-  int free_off, succ_off, Fb, Sb;
-  block_scan2(n_free, n_succ, free_off, succ_off, Fb, Sb, sh);
-  cluster_prefix2(cl, pub1, ex, Fb, Sb);  // every claim cell read before any reset
-  free_off += ex[0];
-  succ_off += ex[1];
-  const int F = ex[2], S = ex[3];
+  int off[3], tot[3];
+  block_scan3(cnt, off, tot, sh);
+  cluster_prefix3(cl, pub, ex, tot);  // every claim cell read before any reset
+  int free_off = off[0] + ex[0], succ_off = off[1] + ex[1];
+  const int surv_off = off[2] + ex[2];
+  const int F = ex[3], S = ex[4], SURV = ex[5];
   const int births = min(S, F);
-  int free_rank[CL_SPT];
+  int alive_pos = surv_off + min(free_off, births);
+  int free_rank = free_off;
 #pragma unroll
   for (int k = 0; k < CL_SPT; ++k) {
-    free_rank[k] = INT_MAX;
     if (bcell[k] >= 0) wd.bclaim[bcell[k]] = INT_MAX;
     if (k < ns && !al[k]) {
-      free_rank[k] = free_off;
-      if (free_off < S) wd.free_list[free_off] = s0 + k;
-      ++free_off;
+      if (free_rank < S) wd.free_list[free_rank] = s0 + k;
+      ++free_rank;
     }
   }
   cl.sync();
+  free_rank = free_off;
 #pragma unroll
   for (int k = 0; k < CL_SPT; ++k) {
-    if (!ok[k]) continue;
-    const int kk = succ_off++;
-    if (kk < F) init_child(wd, s0 + k, bcell[k], kk, wd.free_list[kk], h_next);
+    if (k >= ns) continue;
+    const int s = s0 + k;
+    if (ok[k]) {
+      const int kk = succ_off++;
+      if (kk < F) init_child(wd, s, bcell[k], kk, wd.free_list[kk], h_next);
+    }
+    // the next alive list: survivors and the free slots that receive a child
+    if (al[k]) {
+      wd.alive_list[alive_pos++] = s;
+    } else if (free_rank++ < births) {
+      wd.alive_list[alive_pos++] = s;
+    }
   }
-  // alive list of the next step: survivors and the slots that received a child
-  int n_alive = 0;
-#pragma unroll
-  for (int k = 0; k < CL_SPT; ++k) {
-    if (free_rank[k] < births) al[k] = 1;
-    n_alive += (k < ns && al[k]) ? 1 : 0;
-  }
-  int alive_off, dummy, Ab, dummy2;
-  block_scan2(n_alive, 0, alive_off, dummy, Ab, dummy2, sh);
-  cluster_prefix2(cl, pub2, ex, Ab, 0);
-  alive_off += ex[0];
-#pragma unroll
-  for (int k = 0; k < CL_SPT; ++k)
-    if (k < ns && al[k]) wd.alive_list[alive_off++] = s0 + k;
-  if (rank == 0 && threadIdx.x == 0) finish_step(wd, S, F, ex[2], t);
+  if (rank == 0 && threadIdx.x == 0) finish_step(wd, S, F, SURV + births, t);
   cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
@@ -618,7 +647,6 @@ __global__ void __launch_bounds__(SPAWN_THREADS) k_init_weights(const WorldDev *
 
 void preload_agents() {
   cudaFuncAttributes a;
-  cudaFuncGetAttributes(&a, k_move_claim);
   cudaFuncGetAttributes(&a, k_move_apply);
   cudaFuncGetAttributes(&a, k_physio);
   cudaFuncGetAttributes(&a, k_birth_claim);
@@ -627,9 +655,6 @@ void preload_agents() {
   cudaFuncGetAttributes(&a, k_agents_cluster);
 }
 
-void launch_move_claim(const BatchDev &b, cudaStream_t s) {
-  k_move_claim<<<b.total_slot_blocks, SLOT_BLOCK, 0, s>>>(b);
-}
 void launch_move_apply(const BatchDev &b, cudaStream_t s) {
   k_move_apply<<<b.total_slot_blocks, SLOT_BLOCK, 0, s>>>(b);
 }

@@ -17,8 +17,9 @@
 //   * four compute warps, warp q on block q: lane l computes gate row l with
 //     128-bit shared loads (conflict-free: rows are 720 B apart), the gate
 //     nonlinearity, and lanes 0, 4, .., 28 update the cell of their hidden
-//     unit; warp 3 then takes the 32 new hidden values and computes the 5
-//     logits and the argmax (first maximum).
+//     unit; warp 3 then takes the 32 new hidden values, computes the 5
+//     logits and the argmax (first maximum), and makes the agent's move
+//     claim (step part a4), pipelined one agent behind.
 // Every hand-off is an mbarrier with a bounded wait; a wait that runs out
 // sets ST_TIMEOUT, every role leaves its loop, and the CTA waits (bounded)
 // for the copies it issued before returning.
@@ -45,7 +46,9 @@ struct VEntry {
   float hn[HID];      // new hidden state, filled by the compute warps
   float *c_row, *h_row, *logits_row;  // outputs of the agent
   int32_t *action;
-  int slot, pad[3];
+  const WorldDev *wd;
+  int slot, y, x;
+  int forced;         // action imposed on the move (use_forced), else -1
 };
 
 struct __align__(128) LstmSmem {
@@ -132,7 +135,7 @@ __device__ inline uint32_t row7(const uint32_t *row, int Wp, int W, int xs,
 // agent itself, off-grid cells read as wall, the last observation is the
 // agent's energy.
 __device__ inline void gather_input(const WorldDev &wd, int slot, int y, int x,
-                                    float energy, uint32_t t, VEntry &e,
+                                    float energy, uint32_t t, int forced, VEntry &e,
                                     uint32_t *masks, int lane) {
   const int H = wd.H, W = wd.W, Wp = wd.Wp;
   const uint32_t *res = (t & 1u) ? wd.res0 : wd.res1;
@@ -169,6 +172,10 @@ __device__ inline void gather_input(const WorldDev &wd, int slot, int y, int x,
   if (lane == 0) {
     e.v[147] = energy;
     e.slot = slot;
+    e.y = y;
+    e.x = x;
+    e.forced = forced;
+    e.wd = &wd;
     e.c_row = wd.c + (size_t)slot * HID;
     e.h_row = ((t & 1u) ? wd.h0 : wd.h1) + (size_t)slot * HID;
     e.logits_row = wd.logits + (size_t)slot * 8;
@@ -177,6 +184,51 @@ __device__ inline void gather_input(const WorldDev &wd, int slot, int y, int x,
   e.v[NOBS + lane] = hp;
   e.c[lane] = cp;
 }
+
+// Move claim of one agent (step part a4), made as soon as its action is
+// known: a target on the grid, not a wall and empty at the start of the
+// phase (the slot map does not change during this kernel) is claimed with
+// atomicMin; the lowest claimant moves in the next kernel.  The loads of an
+// agent's claim are issued when its action is known and used one agent
+// later, so their latency hides behind the next agent's work.
+struct MoveClaim {
+  const WorldDev *wd = nullptr;
+  int slot = -1, cell = -1, bit = 0, occ = 0;
+  uint32_t wall = 0;
+  bool moving = false, off_grid = false;
+
+  __device__ void issue(const WorldDev &w, int s, int y, int x, int a) {
+    wd = &w;
+    slot = s;
+    cell = -1;
+    moving = a >= 1 && a < NACT;
+    off_grid = false;
+    if (!moving) return;
+    const int ty = y + (a == 1 ? -1 : a == 2 ? 1 : 0);
+    const int tx = x + (a == 3 ? 1 : a == 4 ? -1 : 0);
+    if (ty < 0 || ty >= w.H || tx < 0 || tx >= w.W) {
+      off_grid = true;
+      return;
+    }
+    cell = ty * w.W + tx;
+    bit = tx & 31;
+    wall = w.wall[ty * w.Wp + (tx >> 5)];
+    occ = w.slot_map[cell];
+  }
+
+  __device__ void resolve() {
+    if (slot < 0) return;
+    const bool blocked = off_grid || (cell >= 0 && ((wall >> bit) & 1u));
+    int tgt = -1;
+    if (moving && !blocked && occ == -1) {
+      tgt = cell;
+      atomicMin(&wd->claim[cell], slot);
+    }
+    wd->target[slot] = tgt;
+    wd->killed[slot] = (moving && blocked && wd->wall_kills) ? 1 : 0;
+    slot = -1;
+  }
+};
 
 // World of global agent index a (prefix over worlds in shared memory).
 __device__ inline int world_of(const int *prefix, int n, int a) {
@@ -280,7 +332,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
   } else if (warp >= NCOMP) {
     // ------------------------------------------------ gather ---------------
     const int gw = warp - NCOMP;
-    int my_slot = 0, my_y = 0, my_x = 0;
+    int my_slot = 0, my_y = 0, my_x = 0, my_f = -1;
     float my_e = 0.f;
     uint32_t my_t = 0;
     const WorldDev *my_wd = nullptr;
@@ -297,6 +349,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
           my_x = my_wd->x[my_slot];
           my_e = my_wd->energy[my_slot];
           my_t = (uint32_t)my_wd->ctr->t;
+          my_f = my_wd->ctr->use_forced ? my_wd->forced[my_slot] : -1;
         }
       }
       const int src = m & 31;
@@ -305,6 +358,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
       const int x = __shfl_sync(FULL, my_x, src);
       const float e = __shfl_sync(FULL, my_e, src);
       const uint32_t t = __shfl_sync(FULL, my_t, src);
+      const int fa = __shfl_sync(FULL, my_f, src);
       const WorldDev *wd = reinterpret_cast<const WorldDev *>(
           __shfl_sync(FULL, reinterpret_cast<unsigned long long>(my_wd), src));
       const int ei = n % VRING, k = n / VRING;
@@ -315,7 +369,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
         sm.abort_flag = 1;
         break;
       }
-      gather_input(*wd, slot, y, x, e, t, sm.ring[ei], sm.masks[gw], lane);
+      gather_input(*wd, slot, y, x, e, t, fa, sm.ring[ei], sm.masks[gw], lane);
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.vfull[ei]);
       if (sm.abort_flag) break;
@@ -323,6 +377,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
   } else {
     // ------------------------------------------------ compute --------------
     const int q = warp;
+    MoveClaim pending;  // warp 3, lane 0: the previous agent's move claim
     for (int n = 0; n < n_agents; ++n) {
       if (sm.abort_flag) break;
       const int ei = n % VRING, kv = n / VRING;
@@ -394,7 +449,11 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
           if (lane == a) mine = lg[a];
         }
         if (lane < NACT) E.logits_row[lane] = mine;
-        if (lane == 0) *E.action = best;
+        if (lane == 0) {
+          *E.action = best;
+          pending.resolve();
+          pending.issue(*E.wd, E.slot, E.y, E.x, E.forced >= 0 ? E.forced : best);
+        }
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(&sm.empty[st]);
@@ -402,6 +461,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
         }
       }
     }
+    if (q == NCOMP - 1 && lane == 0) pending.resolve();
   }
 
   // Drain: wait (bounded) for every copy this CTA issued, so that no bulk
