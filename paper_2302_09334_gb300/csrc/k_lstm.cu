@@ -23,6 +23,8 @@
 // Every hand-off is an mbarrier with a bounded wait; a wait that runs out
 // sets ST_TIMEOUT, every role leaves its loop, and the CTA waits (bounded)
 // for the copies it issued before returning.
+#include <cstddef>
+
 #include "ecoevo_dev.cuh"
 
 namespace eco {
@@ -40,7 +42,8 @@ static_assert((STAGE_FLOATS * 4) % 16 == 0, "bulk copies are 16-B multiples");
 static_assert(3 * BLK_FLOATS + STAGE_FLOATS <= WSTRIDE, "last copy stays in the slot");
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
 
-struct VEntry {
+// 16-byte aligned: the compute warps read v with 128-bit loads.
+struct __align__(16) VEntry {
   float v[VLEN];      // [obs; h_prev]
   float c[HID];       // cell state before the step
   float hn[HID];      // new hidden state, filled by the compute warps
@@ -50,6 +53,8 @@ struct VEntry {
   int slot, y, x;
   int forced;         // action imposed on the move (use_forced), else -1
 };
+static_assert(sizeof(VEntry) % 16 == 0 && offsetof(VEntry, v) == 0,
+              "ring entries keep v 16-byte aligned");
 
 struct __align__(128) LstmSmem {
   float stage[LSTAGES][STAGE_FLOATS];
@@ -61,6 +66,8 @@ struct __align__(128) LstmSmem {
   int issued;
   volatile int abort_flag;
 };
+static_assert(offsetof(LstmSmem, ring) % 16 == 0 && (STAGE_FLOATS * 4) % 16 == 0,
+              "bulk-copy stages and ring entries are 16-byte aligned");
 
 __device__ inline uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
