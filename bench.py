@@ -167,7 +167,11 @@ def bench_ours(args, params, rank, world_size, dist):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    # the timed world steps by plain one-step CUDA graphs; its twin (same
+    # seed, hence the same states step by step) runs the profiled graphs
+    # whose event nodes give the per-kernel times
     world = World(params, seed=rank, device=local)
+    twin = World(params, seed=rank, device=local, stream=world.stream)
     stream = world.stream
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     flush_read = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -184,9 +188,10 @@ def bench_ours(args, params, rank, world_size, dist):
     for _ in range(args.warmup):
         flush_l2()
         world.step(1)
+        twin.step(1)
     world.sync()
 
-    world.profile(True, max_steps=args.steps)
+    twin.profile(True, max_steps=args.steps)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     pops = []
@@ -197,6 +202,8 @@ def bench_ours(args, params, rank, world_size, dist):
         for k in range(args.steps):
             pops.append(int(world.counters()[1]))
             flush_l2()
+            twin.step(1)
+            flush_l2()
             starts[k].record(stream)
             world.step(1)
             ends[k].record(stream)
@@ -206,8 +213,11 @@ def bench_ours(args, params, rank, world_size, dist):
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
-    prof = world.profile_read()
-    world.profile(False)
+    prof = twin.profile_read()
+    twin.profile(False)
+    if int(twin.counters()[1]) != int(world.counters()[1]):
+        raise RuntimeError("the profiled twin diverged from the timed world")
+    twin.close()
     agent_steps = sum(pops)
     cell_steps = params.H * params.W * args.steps
 
@@ -290,9 +300,9 @@ def bench_batched(args, local):
     batch.step(args.batched_warmup)
     batch.sync()
     pops0 = [int(w.counters()[1]) for w in worlds]
-    worlds[0].profile(True, max_steps=args.batched_steps)
     torch.cuda.synchronize()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # timed: plain one-step graphs
     pops = []
     total_ms = 0.0
     for _ in range(args.batched_steps):
@@ -302,11 +312,17 @@ def bench_batched(args, local):
         end.record(stream)
         end.synchronize()
         total_ms += start.elapsed_time(end)
+    # then as many profiled steps for the per-kernel times
+    worlds[0].profile(True, max_steps=args.batched_steps)
+    ppops = []
+    for _ in range(args.batched_steps):
+        ppops.append(sum(int(w.counters()[1]) for w in worlds))
+        batch.step(1)
     prof = worlds[0].profile_read()
     worlds[0].profile(False)
     lstm_ms, _ = prof["observe_lstm"]
     cells = sum(p.H * p.W for p, _ in specs)
-    bytes_lstm = sum(n * LSTM_BYTES_PER_AGENT for n in pops) + \
+    bytes_lstm = sum(n * LSTM_BYTES_PER_AGENT for n in ppops) + \
         args.batched_steps * sum(3 * p.H * p.W // 8 for p, _ in specs)
     peak, kind = load_peaks()
     achieved = bytes_lstm / (lstm_ms / 1e3) / 1e9 if lstm_ms > 0 else None

@@ -205,6 +205,32 @@ struct BatchDev {
 };
 
 #ifdef __CUDACC__
+// Programmatic dependent launch: a step kernel lets the next one be scheduled
+// as soon as it starts, and waits for the previous one to complete (and its
+// memory to be visible) before it reads anything.  Without the launch
+// attribute both are no-ops.
+__device__ inline void pdl_wait_and_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch a step kernel with the programmatic-stream-serialization attribute.
+template <typename Kernel>
+inline void launch_step_kernel(Kernel k, int grid, int block, size_t smem, cudaStream_t s,
+                               const BatchDev &b) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, b);
+}
+
 // Descriptor of world w.  Kernels take the batch as a __grid_constant__
 // parameter, so for a batch of one the descriptor is read from the launch's
 // constant bank instead of global memory.

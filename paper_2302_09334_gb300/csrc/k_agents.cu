@@ -169,11 +169,17 @@ __device__ inline void init_child(const WorldDev &wd, int s, int cell, int k, in
   wd.ate[child] = 0;
   wd.arrive[child] = 0u;
   wd.birth_cell[child] = -1;
-  for (int j = 0; j < HID; ++j) {
-    h_next[(size_t)child * HID + j] = 0.f;
-    wd.c[(size_t)child * HID + j] = 0.f;
+  float4 *hz = reinterpret_cast<float4 *>(h_next + (size_t)child * HID);
+  float4 *cz = reinterpret_cast<float4 *>(wd.c + (size_t)child * HID);
+  float4 *lz = reinterpret_cast<float4 *>(wd.logits + (size_t)child * 8);
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < HID / 4; ++j) {
+    hz[j] = zero;
+    cz[j] = zero;
   }
-  for (int a = 0; a < 8; ++a) wd.logits[(size_t)child * 8 + a] = 0.f;
+  lz[0] = zero;
+  lz[1] = zero;
 }
 
 // Counters at the end of a step: S successful parents, F free slots.
@@ -246,22 +252,26 @@ __device__ void scan_world(const WorldDev &wd, int *sh) {
 }
 
 __global__ void __launch_bounds__(SLOT_BLOCK) k_move_apply(const __grid_constant__ BatchDev b) {
+  pdl_wait_and_release();
   const WorldDev *wd;
   const int s = slot_of_thread(b, wd);
   if (s >= 0) slot_move_apply(wd, s);
 }
 __global__ void __launch_bounds__(SLOT_BLOCK) k_physio(const __grid_constant__ BatchDev b) {
+  pdl_wait_and_release();
   const WorldDev *wd;
   const int s = slot_of_thread(b, wd);
   if (s >= 0) slot_physio(wd, s);
 }
 __global__ void __launch_bounds__(SLOT_BLOCK) k_birth_claim(const __grid_constant__ BatchDev b) {
+  pdl_wait_and_release();
   const WorldDev *wd;
   const int s = slot_of_thread(b, wd);
   if (s >= 0) slot_birth_claim(wd, s);
 }
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const __grid_constant__ BatchDev b) {
   __shared__ int sh[66];
+  pdl_wait_and_release();
   scan_world(*world_ptr(b, blockIdx.x), sh);
 }
 
@@ -380,6 +390,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
   __shared__ int sh[3 * 32 + 3];
   __shared__ int pub[3], ex[6];
   __shared__ int cta_deaths;
+  pdl_wait_and_release();
   cg::cluster_group cl = cg::this_cluster();
   const WorldDev &wd = *world_ptr(b, blockIdx.x / CLUSTER);
   const int rank = (int)cl.block_rank();
@@ -626,6 +637,7 @@ static_assert(REGROW_THREADS == SPAWN_THREADS, "one block size for the tail kern
 __global__ void __launch_bounds__(SPAWN_THREADS) k_tail(const __grid_constant__ BatchDev b) {
   __shared__ uint32_t tile[TILE_ROWS_MAX][TILE_COLS];
   __shared__ int pre[1025];
+  pdl_wait_and_release();
   if ((int)blockIdx.x < b.total_tiles)
     regrow_tile(b, blockIdx.x, tile);
   else
@@ -656,22 +668,22 @@ void preload_agents() {
 }
 
 void launch_move_apply(const BatchDev &b, cudaStream_t s) {
-  k_move_apply<<<b.total_slot_blocks, SLOT_BLOCK, 0, s>>>(b);
+  launch_step_kernel(k_move_apply, b.total_slot_blocks, SLOT_BLOCK, 0, s, b);
 }
 void launch_physio(const BatchDev &b, cudaStream_t s) {
-  k_physio<<<b.total_slot_blocks, SLOT_BLOCK, 0, s>>>(b);
+  launch_step_kernel(k_physio, b.total_slot_blocks, SLOT_BLOCK, 0, s, b);
 }
 void launch_birth_claim(const BatchDev &b, cudaStream_t s) {
-  k_birth_claim<<<b.total_slot_blocks, SLOT_BLOCK, 0, s>>>(b);
+  launch_step_kernel(k_birth_claim, b.total_slot_blocks, SLOT_BLOCK, 0, s, b);
 }
 void launch_scan(const BatchDev &b, cudaStream_t s) {
-  k_scan<<<b.n, SCAN_THREADS, 0, s>>>(b);
+  launch_step_kernel(k_scan, b.n, SCAN_THREADS, 0, s, b);
 }
 void launch_agents_fused(const BatchDev &b, cudaStream_t s) {
-  k_agents_cluster<<<b.n * CLUSTER, SCAN_THREADS, 0, s>>>(b);
+  launch_step_kernel(k_agents_cluster, b.n * CLUSTER, SCAN_THREADS, 0, s, b);
 }
 void launch_tail(const BatchDev &b, cudaStream_t s) {
-  k_tail<<<b.total_tiles + SPAWN_CTAS_PER_SM * b.n_sms, SPAWN_THREADS, 0, s>>>(b);
+  launch_step_kernel(k_tail, b.total_tiles + SPAWN_CTAS_PER_SM * b.n_sms, SPAWN_THREADS, 0, s, b);
 }
 void launch_init_weights(const WorldDev *wd_dev, int n0, int n_sms, cudaStream_t s) {
   if (n0 > 0) k_init_weights<<<8 * n_sms, SPAWN_THREADS, 0, s>>>(wd_dev, n0);

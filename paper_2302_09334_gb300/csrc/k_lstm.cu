@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
   LstmSmem &sm = *reinterpret_cast<LstmSmem *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned FULL = 0xFFFFFFFFu;
+  pdl_wait_and_release();
 
   // agents per world (= alive-list length at the start of the step)
   if (warp == 0) {
@@ -514,7 +515,7 @@ void preload_lstm() {
 }
 
 void launch_lstm(const BatchDev &b, cudaStream_t s) {
-  k_lstm<<<b.n_sms, LTHREADS, sizeof(LstmSmem), s>>>(b);
+  launch_step_kernel(k_lstm, b.n_sms, LTHREADS, sizeof(LstmSmem), s, b);
 }
 
 }  // namespace eco
