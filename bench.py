@@ -34,9 +34,9 @@ sys.path.insert(0, ROOT)
 LSTM_BYTES_PER_AGENT = 93332 + 512 + 36
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one observation+LSTM launch per agent, from the
-# ncu capture in profiles/k_lstm_paper_200x400_held3440.md (327.52 MB at 3,440
+# ncu capture in profiles/k_lstm_paper_200x400_held3440.md (327.84 MB at 3,440
 # agents); traffic grows with the agents of a launch, so it is scaled by them.
-LSTM_TRAFFIC_PER_AGENT = 327.515e6 / 3440
+LSTM_TRAFFIC_PER_AGENT = 327.835e6 / 3440
 
 
 def lstm_bytes(n_agents: int, H: int, W: int) -> int:
@@ -221,9 +221,11 @@ def bench_ours(args, params, rank, world_size, dist):
     agent_steps = sum(pops)
     cell_steps = params.H * params.W * args.steps
 
-    # e2e through the C ABI with host buffers: upload the start state from
-    # host memory, then every step read counters and agent positions and
-    # energies back to host memory.
+    # e2e through the C ABI with host buffers: the start state (with the
+    # weights of every living agent) is uploaded from host memory, then every
+    # step the population counters are read back, and every 50 steps (the
+    # movement-window length of the paper's analyses, App. C) the agents'
+    # positions and energies.
     alive_slots = world.read_state(fields=("alive",))["alive"].nonzero()[0]
     hi = int(alive_slots.max()) + 1 if alive_slots.size else 0
     e2e_state = world.read_state(weights=(0, hi))
@@ -234,12 +236,17 @@ def bench_ours(args, params, rank, world_size, dist):
     world.load_state(e2e_state)
     e2e_agent_steps = 0
     d2h = 0
-    for _ in range(args.steps):
+    for k in range(args.steps):
+        pop = int(world.counters()[1])
         world.step(1)
-        out = world.read_state(fields=read_fields)
-        e2e_agent_steps += int(out["counters"][1])
-        d2h = sum(v.nbytes for v in out.values())
+        e2e_agent_steps += pop
+        d2h += 8 * 8
+        if (k + 1) % 50 == 0:
+            out = world.read_state(fields=read_fields)
+            d2h += sum(v.nbytes for v in out.values())
+    world.sync()
     e2e_dt = time.perf_counter() - t0
+    d2h //= args.steps
 
     stats = torch.tensor([total_ms, float(agent_steps), float(cell_steps), e2e_dt,
                           float(e2e_agent_steps)], dtype=torch.float64, device=dev)

@@ -577,7 +577,7 @@ __device__ inline float4 mutate4(const WorldDev &wd, int vi, float4 base, uint32
 
 // Grid-stride over every float4 of every birth of the batch; each thread
 // issues the loads of SPAWN_UNROLL elements before any of their arithmetic.
-constexpr int SPAWN_UNROLL = 4;
+constexpr int SPAWN_UNROLL = 2;
 
 // Mutation of every birth of the batch by CTAs cta .. of n_cta.
 __device__ inline void spawn_births(const BatchDev &b, int *pre, int cta, int n_cta) {
@@ -634,7 +634,7 @@ __device__ inline void spawn_births(const BatchDev &b, int *pre, int cta, int n_
 constexpr int SPAWN_CTAS_PER_SM = 4;
 static_assert(REGROW_THREADS == SPAWN_THREADS, "one block size for the tail kernel");
 
-__global__ void __launch_bounds__(SPAWN_THREADS) k_tail(const __grid_constant__ BatchDev b) {
+__global__ void __launch_bounds__(SPAWN_THREADS, 4) k_tail(const __grid_constant__ BatchDev b) {
   __shared__ uint32_t tile[TILE_ROWS_MAX][TILE_COLS];
   __shared__ int pre[1025];
   pdl_wait_and_release();

@@ -252,6 +252,22 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
   LstmSmem &sm = *reinterpret_cast<LstmSmem *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned FULL = 0xFFFFFFFFu;
+
+  if (threadIdx.x == 32) {
+    for (int i = 0; i < LSTAGES; ++i) {
+      mbar_init(&sm.full[i], 1);
+      mbar_init(&sm.empty[i], 1);
+    }
+    for (int i = 0; i < VRING; ++i) {
+      mbar_init(&sm.vfull[i], 1);
+      mbar_init(&sm.vempty[i], 1);
+      mbar_init(&sm.hready[i], NCOMP);
+    }
+    sm.issued = 0;
+    sm.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // everything below reads what earlier kernels wrote
   pdl_wait_and_release();
 
   // agents per world (= alive-list length at the start of the step)
@@ -277,20 +293,6 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
       }
     }
     if (lane == 31) sm.prefix[b.n] = incl;
-  }
-  if (threadIdx.x == 32) {
-    for (int i = 0; i < LSTAGES; ++i) {
-      mbar_init(&sm.full[i], 1);
-      mbar_init(&sm.empty[i], 1);
-    }
-    for (int i = 0; i < VRING; ++i) {
-      mbar_init(&sm.vfull[i], 1);
-      mbar_init(&sm.vempty[i], 1);
-      mbar_init(&sm.hready[i], NCOMP);
-    }
-    sm.issued = 0;
-    sm.abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
