@@ -175,6 +175,14 @@ int eco_world_read_state(EcoWorld *world, EcoState *out);
  * agent on a wall or off the grid, res set on a wall), ECO_ECUDA. */
 int eco_world_load_state(EcoWorld *world, const EcoState *in, int set_counters);
 
+/* Enqueue a copy of the world's counters (ECO_NCOUNTERS int64 in ECO_C_*
+ * order, as they stand after the work enqueued so far) into out_host.
+ * Asynchronous when out_host is page-locked host memory (for example from
+ * cudaHostAlloc or a pinned torch tensor); the values are valid once the
+ * world's stream has reached the copy (eco_world_sync).  Lets a step loop
+ * stream its results without waiting for every step. */
+int eco_world_counters_async(EcoWorld *world, int64_t *out_host);
+
 /* Wait for the world's stream; returns ECO_ETIMEOUT if a device wait ran
  * out, ECO_ECUDA on a CUDA error, else ECO_OK.  Synchronous. */
 int eco_world_sync(EcoWorld *world);

@@ -86,6 +86,7 @@ SIGNATURES = {
     "eco_world_read_state": (ctypes.c_int, [_P, ctypes.POINTER(CEcoState)]),
     "eco_world_load_state": (ctypes.c_int, [_P, ctypes.POINTER(CEcoState), ctypes.c_int]),
     "eco_world_sync": (ctypes.c_int, [_P]),
+    "eco_world_counters_async": (ctypes.c_int, [_P, _P]),
     "eco_world_selftest_timeout": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "eco_world_clear_status": (ctypes.c_int, [_P]),
     "eco_world_params": (_P, [_P]),

@@ -2,6 +2,7 @@
 // layout in one device arena, creation, stepping (CUDA graphs of whole
 // steps), state I/O, batches and per-kernel profiling.
 #include <algorithm>
+#include <cstddef>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -577,6 +578,16 @@ int eco_world_step_forced(EcoWorld *w, const int32_t *actions, int actions_on_ho
   ECO_CU(cudaGetLastError());
   ECO_CU(cudaMemsetAsync(&w->hd.ctr->use_forced, 0, sizeof(int), s));
   if (actions_on_host) ECO_CU(cudaStreamSynchronize(s));
+  return ECO_OK;
+}
+
+int eco_world_counters_async(EcoWorld *w, int64_t *out_host) {
+  if (!w || !out_host) return ECO_EINVAL;
+  static_assert(offsetof(Counters, t) == 0 && offsetof(Counters, dropped_last) ==
+                    (ECO_NCOUNTERS - 1) * sizeof(long long),
+                "the first ECO_NCOUNTERS fields of Counters are the ECO_C_* counters");
+  ECO_CU(cudaMemcpyAsync(out_host, w->hd.ctr, ECO_NCOUNTERS * sizeof(int64_t),
+                         cudaMemcpyDeviceToHost, w->stream));
   return ECO_OK;
 }
 

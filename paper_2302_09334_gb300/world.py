@@ -120,6 +120,13 @@ class World:
     def counters(self) -> np.ndarray:
         return self.read_state(fields=())["counters"]
 
+    def counters_async(self, out) -> None:
+        """Enqueue a copy of the counters into `out`, a page-locked int64
+        torch tensor of 8 elements on the host (valid after sync())."""
+        assert out.is_pinned() and out.numel() >= 8 and out.element_size() == 8
+        check(lib().eco_world_counters_async(self._h, ctypes.c_void_p(out.data_ptr())),
+              "eco_world_counters_async")
+
     def profile(self, enable: bool, max_steps: int = 1024) -> None:
         check(lib().eco_world_profile(self._h, 1 if enable else 0, int(max_steps)),
               "eco_world_profile")
