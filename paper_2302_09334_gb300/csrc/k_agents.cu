@@ -98,21 +98,33 @@ __device__ inline void slot_physio(const WorldDev *wd, int s) {
   }
 }
 
+// First free N, S, E, W neighbour of (y, x) after moves and deaths (on the
+// grid, not a wall, empty), or -1.  The four cells are read at once.
+__device__ inline int first_free_neighbour(const WorldDev &wd, int y, int x) {
+  int cell[4], occ[4];
+  bool ok[4];
+#pragma unroll
+  for (int a = 1; a < NACT; ++a) {
+    const int ny = y + kDY[a], nx = x + kDX[a];
+    ok[a - 1] = ny >= 0 && ny < wd.H && nx >= 0 && nx < wd.W;
+    cell[a - 1] = ok[a - 1] ? ny * wd.W + nx : 0;
+    occ[a - 1] = ok[a - 1] ? wd.slot_map[cell[a - 1]] : 0;
+    if (ok[a - 1]) ok[a - 1] = !bit_at(wd.wall, wd.Wp, ny, nx);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (ok[i] && occ[i] == -1) return cell[i];
+  return -1;
+}
+
 // ---------------------------------------------------------------- a6 ------
 __device__ inline void slot_birth_claim(const WorldDev *wd, int s) {
   wd->birth_cell[s] = -1;
   if (!wd->alive[s] || wd->repr_ctr[s] < wd->t_repr) return;
-  const int y = wd->y[s], x = wd->x[s];
-  for (int a = 1; a < NACT; ++a) {
-    const int ny = y + kDY[a], nx = x + kDX[a];
-    if (ny < 0 || ny >= wd->H || nx < 0 || nx >= wd->W) continue;
-    if (bit_at(wd->wall, wd->Wp, ny, nx)) continue;
-    const int cell = ny * wd->W + nx;
-    if (wd->slot_map[cell] != -1) continue;
-    wd->birth_cell[s] = cell;
-    atomicMin(&wd->bclaim[cell], s);
-    return;
-  }
+  const int cell = first_free_neighbour(*wd, wd->y[s], wd->x[s]);
+  if (cell < 0) return;
+  wd->birth_cell[s] = cell;
+  atomicMin(&wd->bclaim[cell], s);
 }
 
 // Exclusive block scan of two counters over SCAN_THREADS threads.
@@ -394,7 +406,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
   cg::cluster_group cl = cg::this_cluster();
   const WorldDev &wd = *world_ptr(b, blockIdx.x / CLUSTER);
   const int rank = (int)cl.block_rank();
-  const int C = wd.C, H = wd.H, W = wd.W, Wp = wd.Wp;
+  const int C = wd.C, W = wd.W, Wp = wd.Wp;
   const int per_cta = (C + CLUSTER - 1) / CLUSTER;
   const int c0 = min(C, rank * per_cta), c1 = min(C, c0 + per_cta);
   const int per = (c1 - c0 + SCAN_THREADS - 1) / SCAN_THREADS;
@@ -476,16 +488,8 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
   for (int k = 0; k < CL_SPT; ++k) {
     bcell[k] = -1;
     if (!al[k] || rep[k] < wd.t_repr) continue;
-    for (int a = 1; a < NACT; ++a) {
-      const int ny = py[k] + kDY[a], nx = px[k] + kDX[a];
-      if (ny < 0 || ny >= H || nx < 0 || nx >= W) continue;
-      if (bit_at(wd.wall, Wp, ny, nx)) continue;
-      const int cell = ny * W + nx;
-      if (wd.slot_map[cell] != -1) continue;
-      bcell[k] = cell;
-      atomicMin(&wd.bclaim[cell], s0 + k);
-      break;
-    }
+    bcell[k] = first_free_neighbour(wd, py[k], px[k]);
+    if (bcell[k] >= 0) atomicMin(&wd.bclaim[bcell[k]], s0 + k);
   }
   cl.sync();
   // ---- compaction (contiguous slots per thread, so ranks follow slot order)
