@@ -191,6 +191,11 @@ def bench_ours(args, params, rank, world_size, dist):
         twin.step(1)
     world.sync()
 
+    # host copy of the state the timed steps start from (input of the e2e leg)
+    alive_slots = world.read_state(fields=("alive",))["alive"].nonzero()[0]
+    hi = int(alive_slots.max()) + 1 if alive_slots.size else 0
+    e2e_state = world.read_state(weights=(0, hi))
+
     twin.profile(True, max_steps=args.steps)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -221,14 +226,12 @@ def bench_ours(args, params, rank, world_size, dist):
     agent_steps = sum(pops)
     cell_steps = params.H * params.W * args.steps
 
-    # e2e through the C ABI with host buffers: the start state (with the
-    # weights of every living agent) is uploaded from host memory, then every
-    # step's counters are streamed to page-locked host memory, and every 50
-    # steps (the movement-window length of the paper's analyses, App. C) the
-    # agents' positions and energies are read back.
-    alive_slots = world.read_state(fields=("alive",))["alive"].nonzero()[0]
-    hi = int(alive_slots.max()) + 1 if alive_slots.size else 0
-    e2e_state = world.read_state(weights=(0, hi))
+    # e2e through the C ABI with host buffers, over the same steps as the
+    # timed region: the state they start from (with the weights of every
+    # living agent) is uploaded from host memory, then every step's counters
+    # are streamed to page-locked host memory, and every 50 steps (the
+    # movement-window length of the paper's analyses, App. C) the agents'
+    # positions and energies are read back.
     read_fields = ("alive", "y", "x", "energy")
     h2d = sum(v.nbytes for k, v in e2e_state.items() if k not in ("slot_map",))
     counters_host = torch.empty((args.steps + 1, 8), dtype=torch.int64, pin_memory=True)

@@ -261,6 +261,10 @@ void launch_init_world(const WorldDev *wd_host, WorldDev *wd_dev, int n0,
                        const int32_t *place_y, const int32_t *place_x,
                        int border, uint32_t thr_init, int n_sms, cudaStream_t s);
 void launch_rebuild(const WorldDev *wd_host, int n_sms, cudaStream_t s);
+void launch_weights_to_physical(const float *logical, float *physical, int n, int n_sms,
+                                cudaStream_t s);
+void launch_weights_to_logical(const float *physical, float *logical, int n, int n_sms,
+                               cudaStream_t s);
 
 constexpr int SCAN_THREADS = 1024;
 constexpr int SLOT_BLOCK = 256;

@@ -18,6 +18,9 @@ using namespace eco;
 namespace {
 
 constexpr int STEPS_PER_GRAPH = 16;
+// Weights move between host (logical order) and device (physical order)
+// through a staging region of this many agents, permuted on the device.
+constexpr int STAGING_AGENTS = 64;
 
 // ---------------------------------------------------------------------------
 // Parameters and the arena layout.
@@ -42,7 +45,7 @@ struct Layout {
   size_t ctr, wdev, tab_worlds, tab_tiles, tab_blocks, thr, res0, res1, wall,
       slot_map, claim, bclaim, alive, killed, ate, flag, y, x, energy, repr_ctr,
       low_ctr, age, action, forced, target, birth_cell, arrive, h0, h1, c,
-      logits, alive_list, free_list, birth_parent, birth_child, weights, total;
+      logits, alive_list, free_list, birth_parent, birth_child, weights, staging, total;
 };
 
 Layout layout_of(const EcoParams *p) {
@@ -91,6 +94,7 @@ Layout layout_of(const EcoParams *p) {
   L.birth_parent = take(C1 * 4);
   L.birth_child = take(C1 * 4);
   L.weights = take(C1 * (size_t)WSTRIDE * 4);
+  L.staging = take((size_t)STAGING_AGENTS * WSTRIDE * 4);
   L.total = off;
   return L;
 }
@@ -694,18 +698,15 @@ int eco_world_read_state(EcoWorld *w, EcoState *out) {
       for (int a = 0; a < NACT; ++a) out->logits_host[s * NACT + a] = lg[s * 8 + a];
   }
   if (out->weights_host && out->weights_count > 0) {
-    const int chunk = 64;
-    std::vector<float> phys((size_t)chunk * WSTRIDE);
-    for (int s0 = 0; s0 < out->weights_count; s0 += chunk) {
-      const int n = std::min(chunk, out->weights_count - s0);
-      if ((rc = download(phys.data(), d.weights + (size_t)(out->weights_first + s0) * WSTRIDE,
-                         (size_t)n * WSTRIDE * 4)))
-        return rc;
-      for (int i = 0; i < n; ++i) {
-        float *dst = out->weights_host + (size_t)(s0 + i) * NPARAM;
-        const float *src = phys.data() + (size_t)i * WSTRIDE;
-        for (int j = 0; j < NPARAM; ++j) dst[j] = src[phys_of_logical(j)];
-      }
+    float *staging = (float *)(w->arena + w->L.staging);
+    for (int s0 = 0; s0 < out->weights_count; s0 += STAGING_AGENTS) {
+      const int n = std::min(STAGING_AGENTS, out->weights_count - s0);
+      launch_weights_to_logical(d.weights + (size_t)(out->weights_first + s0) * WSTRIDE,
+                                staging, n, w->n_sms, w->stream);
+      ECO_CU(cudaGetLastError());
+      ECO_CU(cudaMemcpy2DAsync(out->weights_host + (size_t)s0 * NPARAM, NPARAM * 4, staging,
+                               WSTRIDE * 4, NPARAM * 4, n, cudaMemcpyDeviceToHost, w->stream));
+      ECO_CU(cudaStreamSynchronize(w->stream));
     }
   }
   return ECO_OK;
@@ -758,19 +759,14 @@ int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
     if ((rc = upload(d.logits, lg.data(), lg.size() * 4))) return rc;
   }
   if (in->weights_host && in->weights_count > 0) {
-    const int chunk = 64;
-    std::vector<float> phys((size_t)chunk * WSTRIDE);
-    for (int s0 = 0; s0 < in->weights_count; s0 += chunk) {
-      const int n = std::min(chunk, in->weights_count - s0);
-      std::fill(phys.begin(), phys.end(), 0.f);
-      for (int i = 0; i < n; ++i) {
-        const float *src = in->weights_host + (size_t)(s0 + i) * NPARAM;
-        float *dst = phys.data() + (size_t)i * WSTRIDE;
-        for (int j = 0; j < NPARAM; ++j) dst[phys_of_logical(j)] = src[j];
-      }
-      if ((rc = upload(d.weights + (size_t)(in->weights_first + s0) * WSTRIDE, phys.data(),
-                       (size_t)n * WSTRIDE * 4)))
-        return rc;
+    float *staging = (float *)(w->arena + w->L.staging);
+    for (int s0 = 0; s0 < in->weights_count; s0 += STAGING_AGENTS) {
+      const int n = std::min(STAGING_AGENTS, in->weights_count - s0);
+      ECO_CU(cudaMemcpy2DAsync(staging, WSTRIDE * 4, in->weights_host + (size_t)s0 * NPARAM,
+                               NPARAM * 4, NPARAM * 4, n, cudaMemcpyHostToDevice, w->stream));
+      launch_weights_to_physical(staging, d.weights + (size_t)(in->weights_first + s0) * WSTRIDE,
+                                 n, w->n_sms, w->stream);
+      ECO_CU(cudaGetLastError());
     }
   }
   launch_rebuild(&w->hd, w->n_sms, w->stream);

@@ -136,6 +136,38 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_alive_list(WorldDev wd) {
   if (threadIdx.x == 0) wd.ctr->pop = sh[32];
 }
 
+// Weight rows (WSTRIDE floats apart) between the logical parameter order
+// (the host's) and the physical block order (the device's).
+__global__ void k_weights_to_physical(const float *logical, float *physical, int n) {
+  const long long total = (long long)n * WSTRIDE;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(g / WSTRIDE), p = (int)(g % WSTRIDE);
+    const int j = logical_of_phys(p);
+    physical[g] = j >= 0 ? logical[(size_t)a * WSTRIDE + j] : 0.f;
+  }
+}
+
+__global__ void k_weights_to_logical(const float *physical, float *logical, int n) {
+  const long long total = (long long)n * WSTRIDE;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(g / WSTRIDE), p = (int)(g % WSTRIDE);
+    const int j = logical_of_phys(p);
+    if (j >= 0) logical[(size_t)a * WSTRIDE + j] = physical[g];
+  }
+}
+
+void launch_weights_to_physical(const float *logical, float *physical, int n, int n_sms,
+                                cudaStream_t s) {
+  if (n > 0) k_weights_to_physical<<<4 * n_sms, 256, 0, s>>>(logical, physical, n);
+}
+
+void launch_weights_to_logical(const float *physical, float *logical, int n, int n_sms,
+                               cudaStream_t s) {
+  if (n > 0) k_weights_to_logical<<<4 * n_sms, 256, 0, s>>>(physical, logical, n);
+}
+
 void launch_init_world(const WorldDev *wd_host, WorldDev *wd_dev, int n0,
                        const int32_t *place_y, const int32_t *place_x,
                        int border, uint32_t thr_init, int n_sms, cudaStream_t s) {
