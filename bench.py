@@ -102,11 +102,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_oracle_sample(params, seed: int, budget_s: float, max_steps: int):
-    """Time the CPU oracle stepping the same world; returns (agent-steps/s,
+def _oracle_worker(args):
+    """One host process: the oracle stepping one world (its own seed) until
+    the step count or the time budget runs out.  Returns (agent-steps,
     steps, seconds)."""
+    params_dict, seed, budget_s, warmup, max_steps = args
+    sys.path.insert(0, ROOT)
     from oracle import pyoracle
-    ow = pyoracle.OracleWorld(params.asdict(), seed)
+    ow = pyoracle.OracleWorld(params_dict, seed)
+    for _ in range(warmup):
+        ow.step()
     agent_steps, steps = 0, 0
     t0 = time.perf_counter()
     while steps < max_steps and (time.perf_counter() - t0) < budget_s:
@@ -115,34 +120,44 @@ def run_oracle_sample(params, seed: int, budget_s: float, max_steps: int):
         steps += 1
     dt = time.perf_counter() - t0
     ow.close()
-    return agent_steps / dt, steps, dt
+    return agent_steps, steps, dt
+
+
+def run_oracle_pool(params, budget_s: float, warmup: int, max_steps: int, cores: int):
+    """The oracle on `cores` host processes, one independent world each
+    (seeds 0..cores-1), as they stand.  Processes are spawned (never forked
+    from a process that has used the GPU).  Returns (agent-steps/s, steps of
+    each world, seconds)."""
+    import multiprocessing as mp
+    from oracle import build as oracle_build
+    oracle_build.build()
+    jobs = [(params.asdict(), i, budget_s, warmup, max_steps) for i in range(cores)]
+    if cores == 1:
+        res = [_oracle_worker(jobs[0])]
+    else:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_worker, jobs)
+    agent_steps = sum(r[0] for r in res)
+    wall = max(r[2] for r in res)
+    return agent_steps / wall, [r[1] for r in res], wall
 
 
 def bench_reference(args, params, rank, world_size):
     if rank != 0:
         return
-    from oracle import build as oracle_build
-    oracle_build.build()
-    from oracle import pyoracle
-    ow = pyoracle.OracleWorld(params.asdict(), 0)
-    for _ in range(args.warmup):
-        ow.step()
-    agent_steps = 0
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        agent_steps += ow.population
-        ow.step()
-    dt = time.perf_counter() - t0
-    v = agent_steps / dt
+    cores = args.cpu_cores or os.cpu_count() or 1
+    v, steps, dt = run_oracle_pool(params, 1e9, args.warmup, args.steps, cores)
     line = {
         "impl": "reference", "metric": "agent-steps/s at 200x400", "value": v,
         "unit": "agent-steps/s", "n_gpus": world_size, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_of(args, params),
-        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "agent-steps/s",
-                         "sample": f"{args.workload} seed 0, steps {args.warmup + 1}.."
-                                   f"{args.warmup + args.steps}, single-threaded C oracle"},
+        "cpu_baseline": {"kind": "oracle", "cores": cores, "value": v, "unit": "agent-steps/s",
+                         "sample": f"{args.workload}, {cores} independent worlds (seeds "
+                                   f"0..{cores - 1}) on {cores} host processes, steps "
+                                   f"{args.warmup + 1}..{args.warmup + args.steps} each, "
+                                   "single-threaded C oracle"},
         "e2e": {"value": v, "unit": "agent-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -291,10 +306,13 @@ def bench_ours(args, params, rank, world_size, dist):
         line["batched"] = bench_batched(args, local)
         line["served"] = bench_served(args, local)
     if not args.no_cpu_baseline:
-        v, n, dt = run_oracle_sample(params, 0, args.cpu_budget, 100000)
-        line["cpu_baseline"] = {"value": v, "unit": "agent-steps/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{args.workload} seed 0, first {n} steps "
-                                          f"({dt:.1f} s, single-threaded C oracle)"}
+        cores = args.cpu_cores or os.cpu_count() or 1
+        v, steps, dt = run_oracle_pool(params, args.cpu_budget, 0, 100000, cores)
+        line["cpu_baseline"] = {
+            "value": v, "unit": "agent-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{args.workload}, {cores} independent worlds (seeds 0..{cores - 1}) on "
+                      f"{cores} host processes, first {min(steps)}-{max(steps)} steps each "
+                      f"({dt:.1f} s), single-threaded C oracle"}
     print(json.dumps(line), flush=True)
 
 
@@ -384,6 +402,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="paper_200x400")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-cores", type=int, default=0,
+                    help="host processes for the oracle (default: all cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--held", action="store_true",
                     help="no energy decay and no births: the population stays at n_agents0")
