@@ -172,6 +172,20 @@ def config_of(args, params):
             "parallelism": f"replicas{args.gpus}"}
 
 
+def reduce_over_ranks(stats, dist, n_times: int):
+    """Whole-job figures from one rank's 1-D tensor [times..., units...]:
+    the first n_times entries take the maximum over ranks (the job lasts as
+    long as its slowest rank), the others the sum (every rank steps its own
+    independent world).  Without a process group the rank's own values."""
+    if dist is None:
+        return [float(v) for v in stats]
+    mx = stats.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = stats.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return [float(mx[i]) if i < n_times else float(sm[i]) for i in range(stats.numel())]
+
+
 def bench_ours(args, params, rank, world_size, dist):
     import torch
     from paper_2302_09334_gb300 import build as lib_build
@@ -267,15 +281,10 @@ def bench_ours(args, params, rank, world_size, dist):
     e2e_agent_steps = int(counters_host[:args.steps, 1].sum())
     d2h //= args.steps
 
-    stats = torch.tensor([total_ms, float(agent_steps), float(cell_steps), e2e_dt,
+    stats = torch.tensor([total_ms, e2e_dt, float(agent_steps), float(cell_steps),
                           float(e2e_agent_steps)], dtype=torch.float64, device=dev)
-    if dist:
-        mx = stats.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = stats.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        total_ms, e2e_dt = float(mx[0]), float(mx[3])
-        agent_steps, cell_steps, e2e_agent_steps = float(sm[1]), float(sm[2]), float(sm[4])
+    total_ms, e2e_dt, agent_steps, cell_steps, e2e_agent_steps = \
+        reduce_over_ranks(stats, dist, n_times=2)
     if rank != 0:
         return
     value = agent_steps / (total_ms / 1e3)

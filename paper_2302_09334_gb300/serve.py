@@ -14,10 +14,22 @@ launches (every random draw is keyed by its own seed and step).
 Latency accounting: a request's chunk latency is the time between two
 consecutive chunk reports (the first from its admission); the queueing
 delay is admission time minus arrival time.
+
+Failures and cancellation, all handled on the host between chunks (no
+launch is ever interrupted):
+* a request whose arena alone exceeds the budget is rejected on arrival;
+* a world whose creation runs out of device memory goes back to the head of
+  the queue until a retirement frees memory, or is rejected when nothing is
+  live (no memory can come back);
+* a cancellation (Server.cancel, from any thread, or a trace entry's
+  cancel_after_steps) that arrives while a chunk runs takes effect at the end
+  of that chunk: the request retires with the steps it has completed, and its
+  state is that of a world stepped alone for that many steps.
 """
 from __future__ import annotations
 
 import ctypes
+import threading
 import time
 from collections import deque
 
@@ -29,12 +41,17 @@ from .world import Batch, World
 
 class Request:
     __slots__ = ("rid", "arrival", "params", "seed", "steps", "nbytes", "world", "done",
-                 "admitted", "last_report", "latencies", "agent_steps", "final")
+                 "admitted", "last_report", "latencies", "agent_steps", "final",
+                 "cancel_after_steps", "outcome")
 
-    def __init__(self, rid, arrival, params, seed, steps):
+    def __init__(self, rid, arrival, params, seed, steps, cancel_after_steps=None):
         self.rid, self.arrival, self.params, self.seed, self.steps = rid, arrival, params, seed, steps
         c = _lib.to_c_params(params)
-        self.nbytes = int(_lib.lib().eco_world_bytes(ctypes.byref(c))) + 256
+        nbytes = int(_lib.lib().eco_world_bytes(ctypes.byref(c)))
+        if nbytes == 0:
+            raise ValueError(f"request {rid}: invalid world parameters")
+        self.nbytes = nbytes + 256
+        self.cancel_after_steps = cancel_after_steps
         self.world = None
         self.done = 0
         self.admitted = None
@@ -42,55 +59,117 @@ class Request:
         self.latencies = []
         self.agent_steps = 0
         self.final = None
+        self.outcome = None   # "done" | "cancelled" | "rejected: <why>" | None (cut off)
+
+
+def _out_of_memory(e: BaseException) -> bool:
+    if isinstance(e, MemoryError) or type(e).__name__ == "OutOfMemoryError":
+        return True
+    return isinstance(e, _lib.EcoError) and e.code == _lib.ECO_ENOMEM
 
 
 class Server:
+    """world_factory(params, seed) and batch_factory(worlds) default to
+    World on this server's stream and Batch."""
+
     def __init__(self, budget_bytes: float = 120e9, chunk: int = 100, device: int = 0,
-                 keep_final: bool = False):
-        import torch
+                 keep_final: bool = False, world_factory=None, batch_factory=None):
         self.budget = float(budget_bytes)
         self.chunk = int(chunk)
         self.device = device
         self.keep_final = keep_final
-        self.stream = torch.cuda.Stream(device)
+        if world_factory is None:
+            import torch
+            self.stream = torch.cuda.Stream(device)
+            world_factory = lambda p, seed: World(p, seed, device=device, stream=self.stream)
+        self._new_world = world_factory
+        self._new_batch = batch_factory or Batch
         self.used = 0
         self.live: list[Request] = []
         self.finished: list[Request] = []
+        self.cancelled: list[Request] = []
+        self.rejected: list[Request] = []
         self._batch = None
         self._batch_members = ()
+        self._lock = threading.Lock()
+        self._cancel_ids = set()
+        self._wait_for_retire = False   # set by an out-of-memory admission
+
+    def cancel(self, rid: int) -> None:
+        """Ask for request rid to stop (safe from any thread).  A queued
+        request is dropped; a live one retires at the end of its chunk."""
+        with self._lock:
+            self._cancel_ids.add(rid)
+
+    def _take_cancels(self) -> set:
+        with self._lock:
+            ids, self._cancel_ids = self._cancel_ids, set()
+        return ids
 
     def _admit(self, req: Request, now: float) -> None:
-        req.world = World(req.params, req.seed, device=self.device, stream=self.stream)
+        req.world = self._new_world(req.params, req.seed)
         req.admitted = now
         req.last_report = now
         self.used += req.nbytes
         self.live.append(req)
 
-    def _retire(self, req: Request) -> None:
+    def _retire(self, req: Request, outcome: str) -> None:
         if self.keep_final:
             req.final = req.world.read_state()
         req.world.close()
         req.world = None
         self.used -= req.nbytes
-        self.finished.append(req)
+        self._wait_for_retire = False
+        req.outcome = outcome
+        (self.finished if outcome == "done" else self.cancelled).append(req)
+
+    def _reject(self, req: Request, why: str) -> None:
+        req.outcome = f"rejected: {why}"
+        self.rejected.append(req)
+
+    def _admit_queue(self, queue: deque, now: float) -> None:
+        """Admit from the head of the queue, in arrival order, while the
+        arenas fit in the budget and the device has the memory."""
+        while queue and not self._wait_for_retire:
+            req = queue[0]
+            if req.nbytes > self.budget:
+                queue.popleft()
+                self._reject(req, "arena larger than the memory budget")
+                continue
+            if self.used + req.nbytes > self.budget:
+                return
+            try:
+                self._admit(req, now)
+            except Exception as e:
+                if not _out_of_memory(e):
+                    raise
+                if self.live:
+                    self._wait_for_retire = True   # retry once memory is freed
+                    return
+                queue.popleft()
+                self._reject(req, "out of device memory with nothing live")
+                continue
+            queue.popleft()
 
     def _step_live(self, n: int) -> None:
         members = tuple(id(r) for r in self.live)
         if members != self._batch_members:
             if self._batch is not None:
                 self._batch.close()
-            self._batch = Batch([r.world for r in self.live])
+            self._batch = self._new_batch([r.world for r in self.live])
             self._batch_members = members
         self._batch.step(n)
         self._batch.sync()
 
     def run(self, trace, duration_s: float | None = None, max_wall_s: float | None = None):
         """Serve the requests of `trace` (dicts with arrival, params, seed,
-        steps; arrivals in seconds from the start).  Arrivals after
-        duration_s are ignored; the loop stops when every admitted request
-        is done, or at max_wall_s (requests still running are cut off)."""
+        steps, optionally cancel_after_steps; arrivals in seconds from the
+        start).  Arrivals after duration_s are ignored; the loop stops when
+        every request is done, cancelled or rejected, or at max_wall_s
+        (requests still running are cut off)."""
         pending = deque(sorted(
-            (Request(i, r["arrival"], r["params"], r["seed"], r["steps"])
+            (Request(i, r["arrival"], r["params"], r["seed"], r["steps"],
+                     r.get("cancel_after_steps"))
              for i, r in enumerate(trace)
              if duration_s is None or r["arrival"] < duration_s),
             key=lambda q: q.arrival))
@@ -104,8 +183,19 @@ class Server:
                 break
             while pending and pending[0].arrival <= now:
                 queue.append(pending.popleft())
-            while queue and self.used + queue[0].nbytes <= self.budget:
-                self._admit(queue.popleft(), time.perf_counter() - t0)
+            cancels = self._take_cancels()
+            if cancels:
+                for r in [q for q in queue if q.rid in cancels]:
+                    queue.remove(r)
+                    r.outcome = "cancelled"
+                    self.cancelled.append(r)
+                for r in [q for q in self.live if q.rid in cancels]:
+                    self.live.remove(r)
+                    self._retire(r, "cancelled")
+                # a cancel for a request not yet arrived waits for it
+                with self._lock:
+                    self._cancel_ids |= {q.rid for q in pending if q.rid in cancels}
+            self._admit_queue(queue, time.perf_counter() - t0)
             if not self.live:
                 if not pending and not queue:
                     break
@@ -125,14 +215,18 @@ class Server:
                     r.last_report = t_rep
                 if r.done == r.steps:
                     self.live.remove(r)
-                    self._retire(r)
+                    self._retire(r, "done")
+                elif r.cancel_after_steps is not None and r.done >= r.cancel_after_steps:
+                    self.live.remove(r)
+                    self._retire(r, "cancelled")
         self.wall = time.perf_counter() - t0
-        self.unfinished = list(self.live) + list(queue)
+        self.unfinished = list(self.live) + list(queue) + list(pending)
         self.chunks = chunks
         return self.report()
 
     def report(self) -> dict:
-        reqs = self.finished + [r for r in self.unfinished if r.world is not None]
+        reqs = self.finished + self.cancelled + [r for r in self.unfinished
+                                                 if r.world is not None]
         lat = np.array([x for r in reqs for x in r.latencies], np.float64)
         agent_steps = sum(r.agent_steps for r in reqs)
         delays = [r.admitted - r.arrival for r in reqs if r.admitted is not None]
@@ -141,8 +235,10 @@ class Server:
             "chunk_latency_p50_s": float(np.percentile(lat, 50)) if lat.size else None,
             "chunk_latency_p99_s": float(np.percentile(lat, 99)) if lat.size else None,
             "chunks_reported": int(lat.size),
-            "requests_admitted": len(reqs),
+            "requests_admitted": sum(1 for r in reqs if r.admitted is not None),
             "requests_completed": len(self.finished),
+            "requests_cancelled": len(self.cancelled),
+            "requests_rejected": len(self.rejected),
             "queue_delay_mean_s": float(np.mean(delays)) if delays else None,
             "wall_s": self.wall,
             "batch_launches": self.chunks,
@@ -154,6 +250,7 @@ class Server:
             self._batch = None
         for r in self.live:
             r.world.close()
+            r.world = None
         self.live.clear()
 
 

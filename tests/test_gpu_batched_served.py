@@ -71,3 +71,26 @@ def test_served_results_equal_alone(eco):
         for k in a:
             np.testing.assert_array_equal(a[k], r.final[k], err_msg=f"request {r.rid} {k}")
         alone.close()
+
+
+def test_served_cancel_mid_chunk_equals_alone(eco):
+    """A cancellation that arrives inside a chunk retires the request at the
+    end of that chunk; its state is a world stepped alone for the steps it
+    completed, and the requests that shared its launches are unaffected."""
+    from paper_2302_09334_gb300.serve import Server
+    trace = [{"arrival": 0.0, "params": EcoParams(H=20, W=40, n_agents0=60, capacity=240),
+              "seed": 7, "steps": 500, "cancel_after_steps": 130},
+             {"arrival": 0.0, "params": EcoParams(H=30, W=60, n_agents0=150, capacity=600),
+              "seed": 8, "steps": 300}]
+    srv = Server(budget_bytes=3 * 2**30, chunk=100, keep_final=True)
+    rep = srv.run(trace)
+    srv.close()
+    assert rep["requests_cancelled"] == 1 and rep["requests_completed"] == 1
+    for r in srv.cancelled + srv.finished:
+        assert r.done == (200 if r.rid == 0 else 300)
+        alone = eco.World(r.params, r.seed)
+        alone.step(r.done)
+        a = alone.read_state()
+        for k in a:
+            np.testing.assert_array_equal(a[k], r.final[k], err_msg=f"request {r.rid} {k}")
+        alone.close()
