@@ -234,6 +234,12 @@ struct OrWorld {
   double *h, *c, *logits;
   uint32_t *thr;
   int64_t counters[8];
+  /* analysis metrics, App. C: an identity for every agent (-1: empty slot),
+   * the identities and cells at the start of the current window, and the
+   * deaths and summed ages at death since then */
+  int64_t *agent_id, *snap_id;
+  int32_t *snap_cell;
+  int64_t next_id, snap_t, an_deaths, an_age_sum;
 };
 
 static const int DY[5] = {0, -1, 1, 0, 0}; /* stay, N, S, E, W */
@@ -276,6 +282,7 @@ void or_world_destroy(OrWorld *w) {
   free(w->move_action);
   free(w->energy); free(w->weights); free(w->h); free(w->c); free(w->logits);
   free(w->thr);
+  free(w->agent_id); free(w->snap_id); free(w->snap_cell);
   free(w);
 }
 
@@ -358,6 +365,25 @@ int or_initial_layout(const OrParams *p, uint64_t seed, uint8_t *res, uint8_t *w
   return 0;
 }
 
+/* A fresh identity for every living agent, and a new analysis window that
+ * starts at the current state. */
+static void take_snapshot(OrWorld *w) {
+  for (int s = 0; s < w->p.capacity; ++s) {
+    w->snap_id[s] = w->agent_id[s];
+    w->snap_cell[s] = w->alive[s] ? w->y[s] * w->p.W + w->x[s] : -1;
+  }
+  w->snap_t = w->counters[OR_C_T];
+  w->an_deaths = 0;
+  w->an_age_sum = 0;
+}
+
+static void new_identities(OrWorld *w) {
+  w->next_id = 0;
+  for (int s = 0; s < w->p.capacity; ++s)
+    w->agent_id[s] = w->alive[s] ? w->next_id++ : -1;
+  take_snapshot(w);
+}
+
 int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
   *out = NULL;
   if (!valid_params(p)) return -1;
@@ -384,7 +410,10 @@ int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
   w->c = calloc(C1 * OR_HID, sizeof(double));
   w->logits = calloc(C1 * OR_NACT, sizeof(double));
   w->thr = calloc((size_t)p->H * 4, sizeof(uint32_t));
-  if (!w->res || !w->wall || !w->res_tmp || !w->slot_map || !w->claim ||
+  w->agent_id = malloc(C1 * sizeof(int64_t));
+  w->snap_id = malloc(C1 * sizeof(int64_t));
+  w->snap_cell = malloc(C1 * sizeof(int32_t));
+  if (!w->agent_id || !w->snap_id || !w->snap_cell || !w->res || !w->wall || !w->res_tmp || !w->slot_map || !w->claim ||
       !w->alive || !w->ate || !w->killed || !w->wants || !w->y || !w->x ||
       !w->repr_ctr || !w->low_ctr || !w->age || !w->action || !w->target ||
       !w->cand || !w->birth_parent || !w->birth_child || !w->free_list || !w->move_action ||
@@ -419,6 +448,7 @@ int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
   }
   free(cells);
   w->counters[OR_C_POP] = p->n_agents0;
+  new_identities(w);
   *out = w;
   return 0;
 }
@@ -434,11 +464,12 @@ int or_world_sync(OrWorld *w) {
     int yy = w->y[s], xx = w->x[s];
     if (yy < 0 || yy >= H || xx < 0 || xx >= W) return -1;
     int cell = yy * W + xx;
-    if (w->wall[cell] || w->slot_map[cell] >= 0) return -1;
+    if (w->wall[cell] || w->slot_map[cell] >= 0 || w->age[s] < 0) return -1;
     w->slot_map[cell] = s;
     ++pop;
   }
   w->counters[OR_C_POP] = pop;
+  new_identities(w);
   return 0;
 }
 
@@ -539,6 +570,9 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
       w->alive[s] = 0;
       w->slot_map[w->y[s] * W + w->x[s]] = -1;
       ++deaths;
+      w->an_deaths += 1;
+      w->an_age_sum += w->age[s];   /* age at death, App. C */
+      w->agent_id[s] = -1;
       continue;
     }
     w->repr_ctr[s] = (w->energy[s] > p->e_repr) ? w->repr_ctr[s] + 1 : 0;
@@ -581,6 +615,7 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
     w->birth_child[k] = child;
     ++k;
     w->alive[child] = 1;
+    w->agent_id[child] = w->next_id++;
     w->y[child] = cell / W;
     w->x[child] = cell % W;
     w->slot_map[cell] = child;
@@ -610,5 +645,39 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
   w->counters[OR_C_BIRTHS_LAST] = k;
   w->counters[OR_C_DEATHS_LAST] = deaths;
   w->counters[OR_C_DROPPED_LAST] = dropped;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Metrics of the analyses, App. C.                                         */
+/* ------------------------------------------------------------------------ */
+int or_world_analysis(OrWorld *w, int64_t *out) {
+  const OrParams *p = &w->p;
+  const int W = p->W;
+  for (int i = 0; i < OR_NANALYSIS; ++i) out[i] = 0;
+  const int64_t t = w->counters[OR_C_T];
+  const int64_t len = t - w->snap_t;
+  out[OR_A_T] = t;
+  out[OR_A_WINDOW] = len;
+  /* population size: agents alive */
+  for (int s = 0; s < p->capacity; ++s) out[OR_A_POP] += w->alive[s];
+  /* amount of resources: the resource channel summed over the grid */
+  for (int i = 0; i < p->H * W; ++i) out[OR_A_RES] += w->res[i];
+  /* deaths of the window and their ages, for the life expectancy */
+  out[OR_A_DEATHS] = w->an_deaths;
+  out[OR_A_AGE_SUM] = w->an_age_sum;
+  /* movement: each agent alive over the whole window (the same identity at
+   * its start and now), Manhattan distance between its cells then and now,
+   * counted in 17 equal bins of the len+1 possible distances */
+  for (int s = 0; s < p->capacity; ++s) {
+    if (!w->alive[s] || w->agent_id[s] < 0 || w->agent_id[s] != w->snap_id[s]) continue;
+    const int y0 = w->snap_cell[s] / W, x0 = w->snap_cell[s] % W;
+    const int64_t d = llabs((long long)w->y[s] - y0) + llabs((long long)w->x[s] - x0);
+    int64_t bin = d * OR_MOVE_BINS / (len + 1);
+    if (bin > OR_MOVE_BINS - 1) bin = OR_MOVE_BINS - 1;
+    out[OR_A_MOVERS] += 1;
+    out[OR_A_BINS + bin] += 1;
+  }
+  take_snapshot(w);
   return 0;
 }

@@ -25,6 +25,8 @@
  *   or_lstm_step       pinned: torch.nn.LSTMCell (float64), bias-only closed form
  *   or_world_step      pinned: invariants, float32 energy closed forms,
  *                      brute force on <=4x4 worlds, slot-assignment rules
+ *   or_world_analysis  pinned: hand-counted walks and lifetimes, closed
+ *                      forms of the bin edges, age-based identity check
  */
 #ifndef ECOEVO_ORACLE_H
 #define ECOEVO_ORACLE_H
@@ -109,6 +111,20 @@ enum {
   OR_C_BIRTHS_LAST, OR_C_DEATHS_LAST, OR_C_DROPPED_LAST
 };
 
+/* Record of or_world_analysis (App. C metrics), OR_NANALYSIS int64. */
+#define OR_MOVE_BINS 17
+enum {
+  OR_A_T = 0,     /* steps done                                             */
+  OR_A_WINDOW,    /* L: steps since the previous analysis (or create/sync)  */
+  OR_A_POP,       /* agents alive                                           */
+  OR_A_RES,       /* cells holding a resource                               */
+  OR_A_DEATHS,    /* deaths during the window                               */
+  OR_A_AGE_SUM,   /* sum of their ages at death                             */
+  OR_A_MOVERS,    /* agents alive over the whole window                     */
+  OR_A_BINS,      /* OR_MOVE_BINS counts: displacement d in bin 17d/(L+1)   */
+  OR_NANALYSIS = OR_A_BINS + OR_MOVE_BINS
+};
+
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
                       uint32_t out[4]);
@@ -151,8 +167,14 @@ int or_world_step(OrWorld *w, const int32_t *forced);
 void *or_world_field(OrWorld *w, int field);
 /* Rebuild slot_map from alive/y/x and the threshold table from the params,
  * after a caller has written state into the fields.  Returns 0, or -1 if
- * two agents share a cell or an agent sits on a wall or off the grid. */
+ * two agents share a cell, an agent sits on a wall or off the grid, or an
+ * age is negative. */
 int or_world_sync(OrWorld *w);
+/* Metrics of the paper's analyses (App. C) for the window that ends now,
+ * then a new window starts: out[OR_NANALYSIS], see OR_A_*.  Life
+ * expectancy over a run of windows = sum of OR_A_AGE_SUM / sum of
+ * OR_A_DEATHS.  create and sync start a window with fresh identities. */
+int or_world_analysis(OrWorld *w, int64_t *out);
 
 #ifdef __cplusplus
 }

@@ -100,6 +100,7 @@ def lib():
         L.or_world_field.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.or_world_field.restype = ctypes.c_void_p
         L.or_world_sync.argtypes = [ctypes.c_void_p]
+        L.or_world_analysis.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         _lib = L
     return _lib
 
@@ -191,6 +192,18 @@ def initial_layout(params, seed):
     return res, wall, cells[:p.n_agents0]
 
 
+MOVE_BINS = 17
+NANALYSIS = 7 + MOVE_BINS
+ANALYSIS_KEYS = ("t", "window", "population", "resources", "deaths", "death_age_sum", "movers")
+
+
+def analysis_record(a) -> dict:
+    out = {k: int(a[i]) for i, k in enumerate(ANALYSIS_KEYS)}
+    out["move_bins"] = np.asarray(a[len(ANALYSIS_KEYS):len(ANALYSIS_KEYS) + MOVE_BINS],
+                                  np.int64).copy()
+    return out
+
+
 class OracleWorld:
     """One oracle world; the fields are numpy views into the C arrays."""
 
@@ -251,9 +264,17 @@ class OracleWorld:
             raise RuntimeError(f"or_world_step failed ({rc})")
 
     def sync(self):
-        """Rebuild slot_map/thresholds after fields were written directly."""
+        """Rebuild slot_map/thresholds after fields were written directly
+        (and start a new analysis window with fresh agent identities)."""
         if lib().or_world_sync(self._h) != 0:
             raise ValueError("inconsistent agent placement")
+
+    def analysis(self) -> dict:
+        """App. C metrics of the window that ends now (or_world_analysis);
+        a new window starts."""
+        out = np.zeros(NANALYSIS, np.int64)
+        lib().or_world_analysis(self._h, _ptr(out))
+        return analysis_record(out)
 
     def close(self):
         if self._h:
