@@ -172,6 +172,19 @@ def config_of(args, params):
             "parallelism": f"replicas{args.gpus}"}
 
 
+def analysis_summary(windows, life_expectancy):
+    """The e2e leg's 50-step analysis windows (App. C) in short: the last
+    window's population, resources and displacement bins, and the life
+    expectancy pooled over all windows."""
+    if not windows:
+        return None
+    last = windows[-1]
+    return {"windows": len(windows), "window_steps": last["window"], "t": last["t"],
+            "population": last["population"], "resources": last["resources"],
+            "movers": last["movers"], "move_bins": [int(v) for v in last["move_bins"]],
+            "life_expectancy": life_expectancy(windows)}
+
+
 def reduce_over_ranks(stats, dist, n_times: int):
     """Whole-job figures from one rank's 1-D tensor [times..., units...]:
     the first n_times entries take the maximum over ranks (the job lasts as
@@ -259,11 +272,13 @@ def bench_ours(args, params, rank, world_size, dist):
     # timed region: the state they start from (with the weights of every
     # living agent) is uploaded from host memory, then every step's counters
     # are streamed to page-locked host memory, and every 50 steps (the
-    # movement-window length of the paper's analyses, App. C) the agents'
-    # positions and energies are read back.
-    read_fields = ("alive", "y", "x", "energy")
+    # movement window of the paper's analyses, App. C) the window's analysis
+    # record (population, resources, deaths and ages, displacement bins).
+    from paper_2302_09334_gb300._lib import NANALYSIS
     h2d = sum(v.nbytes for k, v in e2e_state.items() if k not in ("slot_map",))
     counters_host = torch.empty((args.steps + 1, 8), dtype=torch.int64, pin_memory=True)
+    analysis_host = torch.empty((args.steps // 50 + 1, NANALYSIS), dtype=torch.int64,
+                                pin_memory=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     world.load_state(e2e_state)
@@ -274,12 +289,14 @@ def bench_ours(args, params, rank, world_size, dist):
         world.counters_async(counters_host[k + 1])
         d2h += 8 * 8
         if (k + 1) % 50 == 0:
-            out = world.read_state(fields=read_fields)
-            d2h += sum(v.nbytes for v in out.values())
+            world.analysis_async(analysis_host[(k + 1) // 50 - 1])
+            d2h += NANALYSIS * 8
     world.sync()
     e2e_dt = time.perf_counter() - t0
     e2e_agent_steps = int(counters_host[:args.steps, 1].sum())
     d2h //= args.steps
+    from paper_2302_09334_gb300.world import analysis_record, life_expectancy
+    windows = [analysis_record(r) for r in analysis_host[:args.steps // 50].numpy()]
 
     stats = torch.tensor([total_ms, e2e_dt, float(agent_steps), float(cell_steps),
                           float(e2e_agent_steps)], dtype=torch.float64, device=dev)
@@ -310,6 +327,7 @@ def bench_ours(args, params, rank, world_size, dist):
         "e2e": {"value": e2e_agent_steps / e2e_dt, "unit": "agent-steps/s",
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h},
         "clocks": clocks.summary(),
+        "analysis": analysis_summary(windows, life_expectancy),
     }
     if world_size == 1 and not args.no_many:
         line["batched"] = bench_batched(args, local)

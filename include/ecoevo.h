@@ -171,8 +171,10 @@ int eco_world_read_state(EcoWorld *world, EcoState *out);
  * the population and the free/alive lists are rebuilt from alive, y, x.
  * counters[ECO_C_T] and the cumulative counters are taken from `in` when
  * set_counters != 0.  h and c become the recurrent state for the next step.
- * Synchronous.  Errors: ECO_EINVAL, ECO_ESTATE (two agents on one cell, an
- * agent on a wall or off the grid, res set on a wall), ECO_ECUDA. */
+ * A new analysis window (eco_world_analysis_async) starts at the loaded
+ * state.  Synchronous.  Errors: ECO_EINVAL, ECO_ESTATE (two agents on one
+ * cell, an agent on a wall or off the grid, a negative age, res set on a
+ * wall), ECO_ECUDA. */
 int eco_world_load_state(EcoWorld *world, const EcoState *in, int set_counters);
 
 /* Enqueue a copy of the world's counters (ECO_NCOUNTERS int64 in ECO_C_*
@@ -182,6 +184,37 @@ int eco_world_load_state(EcoWorld *world, const EcoState *in, int set_counters);
  * world's stream has reached the copy (eco_world_sync).  Lets a step loop
  * stream its results without waiting for every step. */
 int eco_world_counters_async(EcoWorld *world, int64_t *out_host);
+
+/* Metrics of the paper's analyses (App. C), for the window of steps since
+ * the previous call (or since create / load_state, which start a window).
+ * Life expectancy over several windows = sum(death_age_sum) / sum(deaths);
+ * the paper uses 500-step windows for it and 50-step windows for movement.
+ * An agent's age at death is its age counter when it dies: after the
+ * step's increment when it dies of energy or age, unchanged when a wall
+ * kills it.  Movement: every agent alive over the whole window (present at
+ * its start and now) falls in bin floor(17 d / (L + 1)), d the Manhattan
+ * distance between its cells at the window start and now, L = window_steps
+ * (d <= L, so bins of three distances for L = 50). */
+#define ECO_MOVE_BINS 17
+typedef struct EcoAnalysis {
+  int64_t t;                 /* steps taken (ECO_C_T) at the call          */
+  int64_t window_steps;      /* L: steps in the window                     */
+  int64_t population;        /* living agents                              */
+  int64_t resources;         /* cells holding a resource                   */
+  int64_t deaths;            /* deaths during the window                   */
+  int64_t death_age_sum;     /* sum of their ages at death                 */
+  int64_t movers;            /* agents alive over the whole window         */
+  int64_t move_bins[ECO_MOVE_BINS];
+} EcoAnalysis;
+
+/* Enqueue the analysis of the window that ends now (three kernels on the
+ * world's stream, after the work enqueued so far) and a copy of the record
+ * into out_host; a new window starts.  Asynchronous when out_host is
+ * page-locked; valid once the stream has reached the copy (eco_world_sync).
+ * For a world stepped in a batch, call it when the batch's stream (the
+ * first world's) has reached the point of interest (eco_batch_sync), or
+ * share that stream.  Errors: ECO_EINVAL, ECO_ECUDA. */
+int eco_world_analysis_async(EcoWorld *world, EcoAnalysis *out_host);
 
 /* Wait for the world's stream; returns ECO_ETIMEOUT if a device wait ran
  * out, ECO_ECUDA on a CUDA error, else ECO_OK.  Synchronous. */

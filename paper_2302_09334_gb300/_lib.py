@@ -14,6 +14,10 @@ ECO_ABI_V1 = 0x45434F01
 ECO_OK, ECO_EINVAL, ECO_ENOMEM, ECO_ECUDA, ECO_ETIMEOUT, ECO_ESTATE = 0, -1, -2, -3, -4, -5
 NCOUNTERS = 8
 NKERNELS = 9
+MOVE_BINS = 17
+# EcoAnalysis: these int64 fields, then MOVE_BINS bin counts
+ANALYSIS_KEYS = ("t", "window", "population", "resources", "deaths", "death_age_sum", "movers")
+NANALYSIS = len(ANALYSIS_KEYS) + MOVE_BINS
 (C_T, C_POP, C_BIRTHS, C_DEATHS, C_DROPPED, C_BIRTHS_LAST, C_DEATHS_LAST,
  C_DROPPED_LAST) = range(8)
 
@@ -87,6 +91,7 @@ SIGNATURES = {
     "eco_world_load_state": (ctypes.c_int, [_P, ctypes.POINTER(CEcoState), ctypes.c_int]),
     "eco_world_sync": (ctypes.c_int, [_P]),
     "eco_world_counters_async": (ctypes.c_int, [_P, _P]),
+    "eco_world_analysis_async": (ctypes.c_int, [_P, _P]),
     "eco_world_selftest_timeout": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "eco_world_clear_status": (ctypes.c_int, [_P]),
     "eco_world_params": (_P, [_P]),

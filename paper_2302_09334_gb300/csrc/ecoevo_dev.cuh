@@ -81,7 +81,16 @@ struct Counters {            // mutable, updated by the kernels
   int use_forced;            // moves read `forced` instead of `action`
   int status;                // ST_* bits
   int pad[3];
+  // analysis window (App. C): the step it started at, and the deaths and
+  // summed ages at death since then
+  long long snap_t, an_deaths;
+  unsigned long long an_age_sum;
 };
+
+// Record of the analysis kernels, in the order of the C ABI's EcoAnalysis.
+constexpr int MOVE_BINS = 17;
+enum { A_T = 0, A_WINDOW, A_POP, A_RES, A_DEATHS, A_AGE_SUM, A_MOVERS, A_BINS,
+       ANALYSIS_WORDS = A_BINS + MOVE_BINS };
 
 struct WorldDev {            // read-only while kernels run
   int H, W, Wp, C;
@@ -109,6 +118,8 @@ struct WorldDev {            // read-only while kernels run
   int32_t *free_list, *birth_parent, *birth_child;  // [C]
   float *weights;            // [C][WSTRIDE], 256-B aligned
   Counters *ctr;
+  int32_t *snap_cell;        // [C] cell of each slot's agent at the window start, -1 none
+  unsigned long long *analysis;  // [ANALYSIS_WORDS] output of the analysis kernels
 };
 
 // ---------------------------------------------------------------------------
@@ -265,6 +276,9 @@ void launch_weights_to_physical(const float *logical, float *physical, int n, in
                                 cudaStream_t s);
 void launch_weights_to_logical(const float *physical, float *logical, int n, int n_sms,
                                cudaStream_t s);
+// analysis metrics of App. C (k_analysis.cu)
+void launch_analysis_reset(const WorldDev *wd_host, int n_sms, cudaStream_t s);
+void launch_analysis(const WorldDev *wd_host, int n_sms, cudaStream_t s);
 
 constexpr int SCAN_THREADS = 1024;
 constexpr int SLOT_BLOCK = 256;

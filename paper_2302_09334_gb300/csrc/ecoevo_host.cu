@@ -45,7 +45,8 @@ struct Layout {
   size_t ctr, wdev, tab_worlds, tab_tiles, tab_blocks, thr, res0, res1, wall,
       slot_map, claim, bclaim, alive, killed, ate, flag, y, x, energy, repr_ctr,
       low_ctr, age, action, forced, target, birth_cell, arrive, h0, h1, c,
-      logits, alive_list, free_list, birth_parent, birth_child, weights, staging, total;
+      logits, alive_list, free_list, birth_parent, birth_child, snap_cell, analysis,
+      weights, staging, total;
 };
 
 Layout layout_of(const EcoParams *p) {
@@ -93,6 +94,8 @@ Layout layout_of(const EcoParams *p) {
   L.free_list = take(C1 * 4);
   L.birth_parent = take(C1 * 4);
   L.birth_child = take(C1 * 4);
+  L.snap_cell = take(C1 * 4);
+  L.analysis = take(ANALYSIS_WORDS * 8);
   L.weights = take(C1 * (size_t)WSTRIDE * 4);
   L.staging = take((size_t)STAGING_AGENTS * WSTRIDE * 4);
   L.total = off;
@@ -448,6 +451,8 @@ static void fill_descriptor(EcoWorld *w) {
   d.birth_child = (int32_t *)(a + L.birth_child);
   d.weights = (float *)(a + L.weights);
   d.ctr = (Counters *)(a + L.ctr);
+  d.snap_cell = (int32_t *)(a + L.snap_cell);
+  d.analysis = (unsigned long long *)(a + L.analysis);
   w->dd = (WorldDev *)(a + L.wdev);
 }
 
@@ -592,6 +597,20 @@ int eco_world_counters_async(EcoWorld *w, int64_t *out_host) {
                 "the first ECO_NCOUNTERS fields of Counters are the ECO_C_* counters");
   ECO_CU(cudaMemcpyAsync(out_host, w->hd.ctr, ECO_NCOUNTERS * sizeof(int64_t),
                          cudaMemcpyDeviceToHost, w->stream));
+  return ECO_OK;
+}
+
+int eco_world_analysis_async(EcoWorld *w, EcoAnalysis *out_host) {
+  if (!w || !out_host) return ECO_EINVAL;
+  static_assert(sizeof(EcoAnalysis) == ANALYSIS_WORDS * sizeof(int64_t) &&
+                    offsetof(EcoAnalysis, movers) == A_MOVERS * sizeof(int64_t) &&
+                    offsetof(EcoAnalysis, move_bins) == A_BINS * sizeof(int64_t) &&
+                    ECO_MOVE_BINS == MOVE_BINS,
+                "EcoAnalysis mirrors the analysis kernels' record");
+  launch_analysis(&w->hd, w->n_sms, w->stream);
+  ECO_CU(cudaGetLastError());
+  ECO_CU(cudaMemcpyAsync(out_host, w->hd.analysis, sizeof(EcoAnalysis), cudaMemcpyDeviceToHost,
+                         w->stream));
   return ECO_OK;
 }
 

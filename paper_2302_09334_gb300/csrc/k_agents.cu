@@ -95,6 +95,7 @@ __device__ inline void slot_physio(const WorldDev *wd, int s) {
     wd->alive[s] = 0;
     wd->slot_map[y * wd->W + x] = -1;
     atomicAdd(&wd->ctr->deaths_step, 1);
+    atomicAdd(&wd->ctr->an_age_sum, (unsigned long long)wd->age[s]);  // age at death
   }
 }
 
@@ -204,6 +205,7 @@ __device__ inline void finish_step(const WorldDev &wd, int S, int F, int pop, ui
   c.births += births;
   c.dropped += S - births;
   c.deaths += c.deaths_step;
+  c.an_deaths += c.deaths_step;
   c.deaths_step = 0;
   c.n_births = births;
   c.births_t = t;
@@ -402,6 +404,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
   __shared__ int sh[3 * 32 + 3];
   __shared__ int pub[3], ex[6];
   __shared__ int cta_deaths;
+  __shared__ unsigned long long cta_age_sum;
   pdl_wait_and_release();
   cg::cluster_group cl = cg::this_cluster();
   const WorldDev &wd = *world_ptr(b, blockIdx.x / CLUSTER);
@@ -412,7 +415,10 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
   const int per = (c1 - c0 + SCAN_THREADS - 1) / SCAN_THREADS;
   const int s0 = min(c1, c0 + (int)threadIdx.x * per);
   const int ns = min(c1, s0 + per) - s0;
-  if (threadIdx.x == 0) cta_deaths = 0;
+  if (threadIdx.x == 0) {
+    cta_deaths = 0;
+    cta_age_sum = 0ull;
+  }
   const uint32_t t = (uint32_t)wd.ctr->t;
   uint32_t *res = (t & 1u) ? wd.res0 : wd.res1;  // plane after this step's regrowth
   float *h_next = (t & 1u) ? wd.h0 : wd.h1;
@@ -478,10 +484,14 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
       wd.alive[s] = 0;
       wd.slot_map[py[k] * W + px[k]] = -1;
       atomicAdd(&cta_deaths, 1);
+      atomicAdd(&cta_age_sum, (unsigned long long)age[k]);  // age at death
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0 && cta_deaths) atomicAdd(&wd.ctr->deaths_step, cta_deaths);
+  if (threadIdx.x == 0 && cta_deaths) {
+    atomicAdd(&wd.ctr->deaths_step, cta_deaths);
+    atomicAdd(&wd.ctr->an_age_sum, cta_age_sum);
+  }
   cl.sync();
   // ---- birth claims: first free N, S, E, W cell; lowest parent slot wins
 #pragma unroll

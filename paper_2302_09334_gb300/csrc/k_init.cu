@@ -80,7 +80,8 @@ __global__ void k_init_agents(WorldDev wd, int n0, const int32_t *py,
 }
 
 // Put every living agent on slot_map; a second agent on a cell, an agent on
-// a wall or off the grid, or a resource on a wall sets ST_STATE.
+// a wall or off the grid, a negative age, or a resource on a wall sets
+// ST_STATE.
 __global__ void k_place_agents(WorldDev wd) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < wd.C) {
@@ -89,7 +90,8 @@ __global__ void k_place_agents(WorldDev wd) {
     wd.target[s] = -1;
     if (wd.alive[s]) {
       const int y = wd.y[s], x = wd.x[s];
-      if (y < 0 || y >= wd.H || x < 0 || x >= wd.W || bit_at(wd.wall, wd.Wp, y, x)) {
+      if (y < 0 || y >= wd.H || x < 0 || x >= wd.W || bit_at(wd.wall, wd.Wp, y, x) ||
+          wd.age[s] < 0) {
         atomicOr(&wd.ctr->status, ST_STATE);
       } else if (atomicCAS(&wd.slot_map[y * wd.W + x], -1, s) != -1) {
         atomicOr(&wd.ctr->status, ST_STATE);
@@ -181,6 +183,7 @@ void launch_init_world(const WorldDev *wd_host, WorldDev *wd_dev, int n0,
   }
   k_alive_list<<<1, SCAN_THREADS, 0, s>>>(wd);
   launch_init_weights(wd_dev, n0, n_sms, s);
+  launch_analysis_reset(wd_host, n_sms, s);
 }
 
 void launch_rebuild(const WorldDev *wd_host, int n_sms, cudaStream_t s) {
@@ -189,6 +192,7 @@ void launch_rebuild(const WorldDev *wd_host, int n_sms, cudaStream_t s) {
   k_clear_cells<<<4 * n_sms, 256, 0, s>>>(wd);
   k_place_agents<<<(max(wd.C, nw) + 255) / 256, 256, 0, s>>>(wd);
   k_alive_list<<<1, SCAN_THREADS, 0, s>>>(wd);
+  launch_analysis_reset(wd_host, n_sms, s);
 }
 
 }  // namespace eco

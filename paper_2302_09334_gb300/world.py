@@ -33,6 +33,22 @@ def _ptr(a):
     return ctypes.c_void_p(a.ctypes.data) if a is not None else None
 
 
+def analysis_record(a) -> dict:
+    """EcoAnalysis as int64 values -> dict (move_bins: int64 array of 17)."""
+    a = np.asarray(a, np.int64)
+    out = {k: int(a[i]) for i, k in enumerate(_lib.ANALYSIS_KEYS)}
+    n = len(_lib.ANALYSIS_KEYS)
+    out["move_bins"] = a[n:n + _lib.MOVE_BINS].copy()
+    return out
+
+
+def life_expectancy(records) -> float | None:
+    """Mean age at death over consecutive analysis windows (App. C: the
+    paper pools 500 steps); None when nobody died."""
+    deaths = sum(r["deaths"] for r in records)
+    return sum(r["death_age_sum"] for r in records) / deaths if deaths else None
+
+
 class World:
     """One simulated world resident on a CUDA device."""
 
@@ -126,6 +142,21 @@ class World:
         assert out.is_pinned() and out.numel() >= 8 and out.element_size() == 8
         check(lib().eco_world_counters_async(self._h, ctypes.c_void_p(out.data_ptr())),
               "eco_world_counters_async")
+
+    def analysis_async(self, out) -> None:
+        """Enqueue the App. C metrics of the window that ends now into `out`,
+        a page-locked int64 torch tensor of at least 24 elements (valid after
+        sync(); decode with analysis_record).  A new window starts."""
+        assert out.is_pinned() and out.numel() >= _lib.NANALYSIS and out.element_size() == 8
+        check(lib().eco_world_analysis_async(self._h, ctypes.c_void_p(out.data_ptr())),
+              "eco_world_analysis_async")
+
+    def analysis(self) -> dict:
+        """Synchronous analysis_async, decoded."""
+        a = np.zeros(_lib.NANALYSIS, np.int64)
+        check(lib().eco_world_analysis_async(self._h, _ptr(a)), "eco_world_analysis_async")
+        self.sync()
+        return analysis_record(a)
 
     def profile(self, enable: bool, max_steps: int = 1024) -> None:
         check(lib().eco_world_profile(self._h, 1 if enable else 0, int(max_steps)),
