@@ -209,11 +209,20 @@ def bench_ours(args, params, rank, world_size, dist):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    # launch configuration: tuned on a world of the same shape (seed + 1000)
+    # so that the measured world starts from step 0
+    tuner = World(params, seed=1000 + rank, device=local)
+    tuned = tuner.autotune(trial_steps=8)
+    tuner.close()
+    del tuner
+    cfg = {k: tuned[k] for k in ("fused", "spawn_ctas_per_sm", "steps_per_graph")}
     # the timed world steps by plain one-step CUDA graphs; its twin (same
     # seed, hence the same states step by step) runs the profiled graphs
     # whose event nodes give the per-kernel times
     world = World(params, seed=rank, device=local)
     twin = World(params, seed=rank, device=local, stream=world.stream)
+    world.set_config(**cfg)
+    twin.set_config(**cfg)
     stream = world.stream
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     flush_read = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -276,7 +285,8 @@ def bench_ours(args, params, rank, world_size, dist):
     # record (population, resources, deaths and ages, displacement bins).
     from paper_2302_09334_gb300._lib import NANALYSIS
     h2d = sum(v.nbytes for k, v in e2e_state.items() if k not in ("slot_map",))
-    counters_host = torch.empty((args.steps + 1, 8), dtype=torch.int64, pin_memory=True)
+    from paper_2302_09334_gb300._lib import C_AGENT_STEPS, NCOUNTERS
+    counters_host = torch.empty((args.steps + 1, NCOUNTERS), dtype=torch.int64, pin_memory=True)
     analysis_host = torch.empty((args.steps // 50 + 1, NANALYSIS), dtype=torch.int64,
                                 pin_memory=True)
     torch.cuda.synchronize()
@@ -287,13 +297,14 @@ def bench_ours(args, params, rank, world_size, dist):
     for k in range(args.steps):
         world.step(1)
         world.counters_async(counters_host[k + 1])
-        d2h += 8 * 8
+        d2h += NCOUNTERS * 8
         if (k + 1) % 50 == 0:
             world.analysis_async(analysis_host[(k + 1) // 50 - 1])
             d2h += NANALYSIS * 8
     world.sync()
     e2e_dt = time.perf_counter() - t0
-    e2e_agent_steps = int(counters_host[:args.steps, 1].sum())
+    e2e_agent_steps = int(counters_host[args.steps, C_AGENT_STEPS] -
+                          counters_host[0, C_AGENT_STEPS])
     d2h //= args.steps
     from paper_2302_09334_gb300.world import analysis_record, life_expectancy
     windows = [analysis_record(r) for r in analysis_host[:args.steps // 50].numpy()]
@@ -324,6 +335,7 @@ def bench_ours(args, params, rank, world_size, dist):
                      "traffic": LSTM_TRAFFIC_PER_AGENT * (sum(pops) / max(len(pops), 1)),
                      "bytes_per_launch": bytes_lstm / max(lstm_n, 1)},
         "gpu_launches": kps * args.steps,
+        "launch_config": cfg,
         "e2e": {"value": e2e_agent_steps / e2e_dt, "unit": "agent-steps/s",
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h},
         "clocks": clocks.summary(),
@@ -345,48 +357,67 @@ def bench_ours(args, params, rank, world_size, dist):
 
 def bench_batched(args, local):
     """64 worlds of mixed sizes stepped together (one launch per kernel per
-    step).  ~12 GB of weights per step: inputs far larger than L2, no flush."""
+    step), run in CUDA-graph chunks whose length and launch shapes the tuner
+    picks on a twin batch (same shapes, other seeds).  The timed region is
+    one call of batched_steps steps; agent-steps come from the worlds'
+    cumulative counters.  ~12 GB of weights per step: inputs far larger than
+    L2, no flush."""
     import torch
+    from paper_2302_09334_gb300._lib import C_AGENT_STEPS
     from paper_2302_09334_gb300.params import batched_64
     from paper_2302_09334_gb300.world import Batch, World
     specs = batched_64()
     stream = torch.cuda.Stream(local)
+    # tuner: a twin batch of the same worlds with seeds 1000+
+    tw = [World(p, 1000 + s, device=local, stream=stream) for p, s in specs]
+    tb = Batch(tw)
+    tuned = tb.autotune(trial_steps=4)
+    tb.close()
+    for w in tw:
+        w.close()
+    del tw
+    torch.cuda.empty_cache()
     worlds = [World(p, s, device=local, stream=stream) for p, s in specs]
     batch = Batch(worlds)
+    batch.set_config(fused=tuned["fused"], spawn_ctas_per_sm=tuned["spawn_ctas_per_sm"],
+                     steps_per_graph=tuned["steps_per_graph"])
     batch.step(args.batched_warmup)
     batch.sync()
     pops0 = [int(w.counters()[1]) for w in worlds]
+    as0 = sum(int(w.counters()[C_AGENT_STEPS]) for w in worlds)
     torch.cuda.synchronize()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # timed: plain one-step graphs
-    pops = []
-    total_ms = 0.0
-    for _ in range(args.batched_steps):
-        pops.append(sum(int(w.counters()[1]) for w in worlds))
-        start.record(stream)
-        batch.step(1)
-        end.record(stream)
-        end.synchronize()
-        total_ms += start.elapsed_time(end)
+    start.record(stream)
+    batch.step(args.batched_steps)
+    end.record(stream)
+    end.synchronize()
+    total_ms = start.elapsed_time(end)
+    agent_steps = sum(int(w.counters()[C_AGENT_STEPS]) for w in worlds) - as0
     # then as many profiled steps for the per-kernel times
     worlds[0].profile(True, max_steps=args.batched_steps)
-    ppops = []
-    for _ in range(args.batched_steps):
-        ppops.append(sum(int(w.counters()[1]) for w in worlds))
-        batch.step(1)
+    as1 = sum(int(w.counters()[C_AGENT_STEPS]) for w in worlds)
+    batch.step(args.batched_steps)
+    batch.sync()
     prof = worlds[0].profile_read()
     worlds[0].profile(False)
+    prof_agent_steps = sum(int(w.counters()[C_AGENT_STEPS]) for w in worlds) - as1
     lstm_ms, _ = prof["observe_lstm"]
     cells = sum(p.H * p.W for p, _ in specs)
-    bytes_lstm = sum(n * LSTM_BYTES_PER_AGENT for n in ppops) + \
+    bytes_lstm = prof_agent_steps * LSTM_BYTES_PER_AGENT + \
         args.batched_steps * sum(3 * p.H * p.W // 8 for p, _ in specs)
     peak, kind = load_peaks()
     achieved = bytes_lstm / (lstm_ms / 1e3) / 1e9 if lstm_ms > 0 else None
     out = {"workload": "batched_64", "worlds": len(specs), "steps": args.batched_steps,
-           "warmup": args.batched_warmup, "value": sum(pops) / (total_ms / 1e3),
+           "warmup": args.batched_warmup, "value": agent_steps / (total_ms / 1e3),
            "unit": "agent-steps/s", "ms_per_step": total_ms / args.batched_steps,
            "cell_steps_per_s": cells * args.batched_steps / (total_ms / 1e3),
-           "mean_population": sum(pops) / len(pops), "initial_population": sum(pops0),
+           "mean_population": agent_steps / args.batched_steps,
+           "initial_population": sum(pops0),
+           "launch_config": {k: tuned[k] for k in ("fused", "spawn_ctas_per_sm",
+                                                   "steps_per_graph")},
+           "tuner": {"steps_taken": tuned["steps_taken"],
+                     "ms_per_step_initial": tuned["ms_per_step_initial"],
+                     "ms_per_step_best": tuned["ms_per_step_best"]},
            "kernel_ms_per_step": {k: v[0] / v[1] for k, v in prof.items() if v[1]},
            "roofline": {"kernel": "observe_lstm", "bound": "hbm", "achieved": achieved,
                         "peak": peak, "unit": "GB/s",
@@ -437,7 +468,7 @@ def main():
     ap.add_argument("--n-agents", type=int, default=None, help="override n_agents0")
     ap.add_argument("--no-many", action="store_true",
                     help="skip the batched (64 worlds) and served measurements")
-    ap.add_argument("--batched-steps", type=int, default=100)
+    ap.add_argument("--batched-steps", type=int, default=1000)
     ap.add_argument("--batched-warmup", type=int, default=10)
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     args = ap.parse_args()

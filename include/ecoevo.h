@@ -102,7 +102,8 @@ typedef struct EcoParams {
 #define ECO_C_BIRTHS_LAST 5  /* births of the last step           */
 #define ECO_C_DEATHS_LAST 6
 #define ECO_C_DROPPED_LAST 7
-#define ECO_NCOUNTERS 8
+#define ECO_C_AGENT_STEPS 8  /* sum over steps of the agents alive at the step's start */
+#define ECO_NCOUNTERS 9
 
 /* Host-side view of a world's state.  Every pointer is caller-owned host
  * memory and may be NULL to skip that field.  Grid fields are unpacked
@@ -243,6 +244,51 @@ int eco_batch_create(EcoWorld *const *worlds, int n_worlds, EcoBatch **out);
 int eco_batch_step(EcoBatch *batch, int64_t n_steps);
 int eco_batch_sync(EcoBatch *batch);
 void eco_batch_destroy(EcoBatch *batch);
+
+/* Launch configuration of a batch (or of a world stepped alone).  None of
+ * these choices changes any result, only how a step's work is cut into
+ * launches and CTAs:
+ *   fused              1: the slot phases of a step (moves, physiology,
+ *                      death, birth claims, slot compaction) run as one
+ *                      8-CTA cluster per world; 0: as four grid-wide
+ *                      kernels.  1 is allowed only when every world's
+ *                      capacity is at most 16384 (the default then).
+ *   spawn_ctas_per_sm  CTAs per SM that write the children's mutated weights
+ *                      (1..32, default 4).
+ *   steps_per_graph    steps captured in one CUDA graph for eco_*_step
+ *                      (1..1024, default 16).
+ * set_config waits for the stream when the configuration changes.  Errors:
+ * ECO_EINVAL (a value out of range, fused with a capacity above 16384). */
+int eco_batch_set_config(EcoBatch *batch, int fused, int spawn_ctas_per_sm,
+                         int steps_per_graph);
+int eco_batch_get_config(const EcoBatch *batch, int *fused, int *spawn_ctas_per_sm,
+                         int *steps_per_graph);
+
+/* Result of the tuner. */
+typedef struct EcoTuneResult {
+  int32_t fused, spawn_ctas_per_sm, steps_per_graph, reserved;
+  int64_t steps_taken;          /* steps every world advanced while tuning  */
+  double ms_per_step_initial;   /* one trial in the configuration it started from */
+  double ms_per_step_best;      /* median trial of the configuration it left */
+} EcoTuneResult;
+
+/* Choose the launch configuration for this batch's worlds by timing real
+ * steps of the batch: one knob after the other (fused, then
+ * spawn_ctas_per_sm, then steps_per_graph), every candidate value three
+ * times round-robin, trial_steps steps per trial (the graph-length trials
+ * use trial_steps rounded up to a multiple of 16), keeping the candidate
+ * with the lowest median time per step.  The worlds advance by
+ * out->steps_taken steps, exactly as eco_batch_step would have taken them.
+ * Synchronous.  Errors: ECO_EINVAL (trial_steps outside 1..100000, profiling
+ * on), ECO_ECUDA. */
+int eco_batch_autotune(EcoBatch *batch, int trial_steps, EcoTuneResult *out);
+
+/* The same for a world stepped alone (eco_world_step). */
+int eco_world_set_config(EcoWorld *world, int fused, int spawn_ctas_per_sm,
+                         int steps_per_graph);
+int eco_world_get_config(const EcoWorld *world, int *fused, int *spawn_ctas_per_sm,
+                         int *steps_per_graph);
+int eco_world_autotune(EcoWorld *world, int trial_steps, EcoTuneResult *out);
 
 /* Per-kernel timing with CUDA events on the world's stream.  While enabled,
  * each step (up to max_steps after each read) runs as a one-step CUDA graph

@@ -233,7 +233,7 @@ struct OrWorld {
   float *energy, *weights;
   double *h, *c, *logits;
   uint32_t *thr;
-  int64_t counters[8];
+  int64_t counters[OR_NCOUNTERS];
   /* analysis metrics, App. C: an identity for every agent (-1: empty slot),
    * the identities and cells at the start of the current window, and the
    * deaths and summed ages at death since then */
@@ -484,6 +484,8 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
   const OrParams *p = &w->p;
   const int H = p->H, W = p->W, C = p->capacity;
   const uint32_t t = (uint32_t)w->counters[OR_C_T];
+  /* agent-steps: every agent alive at the start of the step takes one */
+  w->counters[OR_C_AGENT_STEPS] += w->counters[OR_C_POP];
 
   /* 1. regrowth from the grid as it stood at the start of the step */
   or_regrow(p, w->seed, t, w->thr, w->res, w->wall, w->res_tmp);

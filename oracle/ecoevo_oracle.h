@@ -98,7 +98,7 @@ enum {
   OR_F_LOGITS,       /* double [C*5]                                         */
   OR_F_ATE,          /* uint8  [C]  ate during the last step                 */
   OR_F_WEIGHTS,      /* float  [C*23333] logical parameter vectors           */
-  OR_F_COUNTERS,     /* int64  [8]  see OR_C_*                               */
+  OR_F_COUNTERS,     /* int64  [OR_NCOUNTERS]  see OR_C_*                    */
   OR_F_THR,          /* uint32 [H*4] growth thresholds                       */
   OR_F_BIRTH_PARENT, /* int32  [C]  parents of the last step's births        */
   OR_F_BIRTH_CHILD,  /* int32  [C]  child slots of the last step's births    */
@@ -108,7 +108,9 @@ enum {
 };
 enum {
   OR_C_T = 0, OR_C_POP, OR_C_BIRTHS, OR_C_DEATHS, OR_C_DROPPED,
-  OR_C_BIRTHS_LAST, OR_C_DEATHS_LAST, OR_C_DROPPED_LAST
+  OR_C_BIRTHS_LAST, OR_C_DEATHS_LAST, OR_C_DROPPED_LAST,
+  OR_C_AGENT_STEPS,  /* sum over steps of the agents alive at the step's start */
+  OR_NCOUNTERS
 };
 
 /* Record of or_world_analysis (App. C metrics), OR_NANALYSIS int64. */

@@ -20,7 +20,8 @@ TAG_REGROW, TAG_PLACE, TAG_RES_INIT, TAG_INIT_W, TAG_MUT = 1, 2, 3, 4, 5
  F_AGE, F_H, F_C, F_ACTION, F_LOGITS, F_ATE, F_WEIGHTS, F_COUNTERS, F_THR,
  F_BIRTH_PARENT, F_BIRTH_CHILD, F_MOVE_ACTION) = range(21)
 (C_T, C_POP, C_BIRTHS, C_DEATHS, C_DROPPED, C_BIRTHS_LAST, C_DEATHS_LAST,
- C_DROPPED_LAST) = range(8)
+ C_DROPPED_LAST, C_AGENT_STEPS) = range(9)
+NCOUNTERS = 9
 
 
 class OrParams(ctypes.Structure):
@@ -233,7 +234,7 @@ class OracleWorld:
         self.logits = f(F_LOGITS, np.float64, (C, NACT))
         self.ate = f(F_ATE, np.uint8, (C,))
         self.weights = f(F_WEIGHTS, np.float32, (C, NPARAM))
-        self.counters = f(F_COUNTERS, np.int64, (8,))
+        self.counters = f(F_COUNTERS, np.int64, (NCOUNTERS,))
         self.thr = f(F_THR, np.uint32, (H, 4))
         self.birth_parent = f(F_BIRTH_PARENT, np.int32, (C,))
         self.birth_child = f(F_BIRTH_CHILD, np.int32, (C,))

@@ -12,14 +12,14 @@ from .params import EcoParams
 
 ECO_ABI_V1 = 0x45434F01
 ECO_OK, ECO_EINVAL, ECO_ENOMEM, ECO_ECUDA, ECO_ETIMEOUT, ECO_ESTATE = 0, -1, -2, -3, -4, -5
-NCOUNTERS = 8
+NCOUNTERS = 9
 NKERNELS = 9
 MOVE_BINS = 17
 # EcoAnalysis: these int64 fields, then MOVE_BINS bin counts
 ANALYSIS_KEYS = ("t", "window", "population", "resources", "deaths", "death_age_sum", "movers")
 NANALYSIS = len(ANALYSIS_KEYS) + MOVE_BINS
 (C_T, C_POP, C_BIRTHS, C_DEATHS, C_DROPPED, C_BIRTHS_LAST, C_DEATHS_LAST,
- C_DROPPED_LAST) = range(8)
+ C_DROPPED_LAST, C_AGENT_STEPS) = range(9)
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libecoevo.so")
 
@@ -80,6 +80,15 @@ class CEcoState(ctypes.Structure):
 
 
 # name -> (restype, argtypes)
+class CEcoTuneResult(ctypes.Structure):
+    _fields_ = [("fused", ctypes.c_int32), ("spawn_ctas_per_sm", ctypes.c_int32),
+                ("steps_per_graph", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("steps_taken", ctypes.c_int64), ("ms_per_step_initial", ctypes.c_double),
+                ("ms_per_step_best", ctypes.c_double)]
+
+
+_I = ctypes.POINTER(ctypes.c_int)
+
 SIGNATURES = {
     "eco_world_bytes": (ctypes.c_size_t, [ctypes.POINTER(CEcoParams)]),
     "eco_world_create": (ctypes.c_int, [ctypes.POINTER(CEcoParams), ctypes.c_uint64, _P,
@@ -100,6 +109,12 @@ SIGNATURES = {
     "eco_batch_step": (ctypes.c_int, [_P, ctypes.c_int64]),
     "eco_batch_sync": (ctypes.c_int, [_P]),
     "eco_batch_destroy": (None, [_P]),
+    "eco_batch_set_config": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "eco_batch_get_config": (ctypes.c_int, [_P, _I, _I, _I]),
+    "eco_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(CEcoTuneResult)]),
+    "eco_world_set_config": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "eco_world_get_config": (ctypes.c_int, [_P, _I, _I, _I]),
+    "eco_world_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(CEcoTuneResult)]),
     "eco_world_profile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "eco_world_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_int64)]),

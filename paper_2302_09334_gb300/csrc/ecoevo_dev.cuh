@@ -74,7 +74,7 @@ constexpr int ST_STATE = 2;
 // ---------------------------------------------------------------------------
 struct Counters {            // mutable, updated by the kernels
   long long t, pop, births, deaths, dropped, births_last, deaths_last,
-      dropped_last;
+      dropped_last, agent_steps;
   int deaths_step;           // atomically accumulated during a step
   int n_births;              // births of the step, read by the spawn kernel
   unsigned births_t;         // step index the births belong to
@@ -212,7 +212,8 @@ struct BatchDev {
   int total_tiles, total_slot_blocks;
   int max_capacity;
   int n_sms;
-  int fused;                 // every world has capacity <= FUSED_MAX_C
+  int fused;                 // slot phases in one cluster kernel (capacity <= FUSED_MAX_C)
+  int spawn_ctas;            // CTAs of the tail kernel that mutate births
 };
 
 #ifdef __CUDACC__

@@ -17,7 +17,8 @@ using namespace eco;
 
 namespace {
 
-constexpr int STEPS_PER_GRAPH = 16;
+constexpr int STEPS_PER_GRAPH = 16;     // default chunk graph length
+constexpr int DEFAULT_SPAWN_PER_SM = 4;  // default mutation CTAs of the tail kernel per SM
 // Weights move between host (logical order) and device (physical order)
 // through a staging region of this many agents, permuted on the device.
 constexpr int STAGING_AGENTS = 64;
@@ -159,6 +160,7 @@ struct EcoBatch {
   void *table = nullptr;  // device: worlds[], tile prefix, block prefix
   bool owns_table = false;
   cudaGraphExec_t g1 = nullptr, gk = nullptr;
+  int steps_per_graph = STEPS_PER_GRAPH;  // steps in the chunk graph gk
   Profile *prof = nullptr;  // the first world's profiler
 };
 
@@ -291,6 +293,7 @@ int batch_init(EcoBatch &b, EcoWorld *const *worlds, int n, void *table_dev) {
   b.bd.max_capacity = maxc;
   b.bd.n_sms = worlds[0]->n_sms;
   b.bd.fused = maxc <= FUSED_MAX_C ? 1 : 0;
+  b.bd.spawn_ctas = DEFAULT_SPAWN_PER_SM * b.bd.n_sms;
   b.prof = &worlds[0]->prof;
   return ECO_OK;
 }
@@ -374,16 +377,127 @@ int batch_step(EcoBatch &b, int64_t n) {
     }
     return cuda_err(cudaGetLastError());
   }
-  if (n >= STEPS_PER_GRAPH && !b.gk) {
-    int rc = capture(b, STEPS_PER_GRAPH, &b.gk);
+  const int k = b.steps_per_graph;
+  if (k > 1 && n >= k && !b.gk) {
+    int rc = capture(b, k, &b.gk);
     if (rc) return rc;
   }
-  if (n % STEPS_PER_GRAPH && !b.g1) {
+  const int64_t chunks = k > 1 ? n / k : 0, singles = n - chunks * k;
+  if (singles && !b.g1) {
     int rc = capture(b, 1, &b.g1);
     if (rc) return rc;
   }
-  for (int64_t i = 0; i < n / STEPS_PER_GRAPH; ++i) ECO_CU(cudaGraphLaunch(b.gk, b.stream));
-  for (int64_t i = 0; i < n % STEPS_PER_GRAPH; ++i) ECO_CU(cudaGraphLaunch(b.g1, b.stream));
+  for (int64_t i = 0; i < chunks; ++i) ECO_CU(cudaGraphLaunch(b.gk, b.stream));
+  for (int64_t i = 0; i < singles; ++i) ECO_CU(cudaGraphLaunch(b.g1, b.stream));
+  return ECO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch configuration and its tuner.  Every choice here leaves the results
+// unchanged (the same kernels compute the same values; only how the work is
+// split into launches and CTAs differs), so the tuner times real steps of the
+// batch it tunes.
+// ---------------------------------------------------------------------------
+int set_config(EcoBatch &b, int fused, int spawn_per_sm, int steps_per_graph) {
+  if (fused != 0 && fused != 1) return ECO_EINVAL;
+  if (fused && b.bd.max_capacity > FUSED_MAX_C) return ECO_EINVAL;
+  if (spawn_per_sm < 1 || spawn_per_sm > 32) return ECO_EINVAL;
+  if (steps_per_graph < 1 || steps_per_graph > 1024) return ECO_EINVAL;
+  const int spawn = spawn_per_sm * b.bd.n_sms;
+  if (fused == b.bd.fused && spawn == b.bd.spawn_ctas && steps_per_graph == b.steps_per_graph)
+    return ECO_OK;
+  ECO_CU(cudaStreamSynchronize(b.stream));
+  destroy_graphs(b);
+  if (b.prof && b.prof->owner == &b) {  // its profiled graph holds the old launches
+    int rc = profile_collect(*b.prof);
+    if (rc) return rc;
+    profile_release(*b.prof);
+  }
+  b.bd.fused = fused;
+  b.bd.spawn_ctas = spawn;
+  b.steps_per_graph = steps_per_graph;
+  return ECO_OK;
+}
+
+// Milliseconds per step of `steps` steps under the batch's current config.
+int time_steps(EcoBatch &b, int64_t steps, cudaEvent_t e0, cudaEvent_t e1, double *ms) {
+  ECO_CU(cudaEventRecord(e0, b.stream));
+  int rc = batch_step(b, steps);
+  if (rc) return rc;
+  ECO_CU(cudaEventRecord(e1, b.stream));
+  ECO_CU(cudaEventSynchronize(e1));
+  float t = 0.f;
+  ECO_CU(cudaEventElapsedTime(&t, e0, e1));
+  *ms = (double)t / (double)steps;
+  return ECO_OK;
+}
+
+// One coordinate of the search: every candidate value of one knob, timed
+// round-robin (so that a population that drifts during the search affects
+// all of them alike); the median of each candidate's trials decides.
+template <class Apply>
+int tune_knob(EcoBatch &b, const std::vector<int> &cand, int64_t trial, int rounds, Apply apply,
+              cudaEvent_t e0, cudaEvent_t e1, int64_t *steps, int *best, double *best_ms) {
+  std::vector<std::vector<double>> t(cand.size());
+  for (int r = 0; r < rounds; ++r) {
+    for (size_t i = 0; i < cand.size(); ++i) {
+      int rc = apply(cand[i]);
+      if (rc) return rc;
+      double ms = 0.0;
+      if ((rc = time_steps(b, trial, e0, e1, &ms))) return rc;
+      *steps += trial;
+      t[i].push_back(ms);
+    }
+  }
+  *best_ms = 1e300;
+  for (size_t i = 0; i < cand.size(); ++i) {
+    std::sort(t[i].begin(), t[i].end());
+    const double med = t[i][t[i].size() / 2];
+    if (med < *best_ms) {
+      *best_ms = med;
+      *best = cand[i];
+    }
+  }
+  return apply(*best);
+}
+
+int autotune(EcoBatch &b, int trial_steps, EcoTuneResult *out) {
+  if (trial_steps < 1 || trial_steps > 100000) return ECO_EINVAL;
+  if (b.prof && b.prof->on) return ECO_EINVAL;  // would time the profiled graph
+  *out = EcoTuneResult{};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ECO_CU(cudaEventCreate(&e0));
+  int rc = cuda_err(cudaEventCreate(&e1));
+  const int rounds = 3;
+  int64_t steps = 0;
+  int fused = b.bd.fused, spawn = b.bd.spawn_ctas / b.bd.n_sms, k = b.steps_per_graph;
+  double ms = 0.0;
+  if (!rc) rc = set_config(b, fused, spawn, k);
+  if (!rc) rc = time_steps(b, trial_steps, e0, e1, &out->ms_per_step_initial);
+  if (!rc) steps += trial_steps;
+  if (!rc && b.bd.max_capacity <= FUSED_MAX_C) {
+    rc = tune_knob(b, {1, 0}, trial_steps, rounds,
+                   [&](int v) { return set_config(b, v, spawn, k); }, e0, e1, &steps, &fused, &ms);
+  }
+  if (!rc) {
+    rc = tune_knob(b, {1, 2, 4, 8}, trial_steps, rounds,
+                   [&](int v) { return set_config(b, fused, v, k); }, e0, e1, &steps, &spawn, &ms);
+  }
+  if (!rc) {
+    // chunk lengths are compared over the same number of steps, a multiple
+    // of every candidate
+    const int64_t chunk_trial = ((trial_steps + 15) / 16) * 16;
+    rc = tune_knob(b, {1, 4, 16}, chunk_trial, rounds,
+                   [&](int v) { return set_config(b, fused, spawn, v); }, e0, e1, &steps, &k, &ms);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc) return rc;
+  out->fused = fused;
+  out->spawn_ctas_per_sm = spawn;
+  out->steps_per_graph = k;
+  out->steps_taken = steps;
+  out->ms_per_step_best = ms;
   return ECO_OK;
 }
 
@@ -592,7 +706,7 @@ int eco_world_step_forced(EcoWorld *w, const int32_t *actions, int actions_on_ho
 
 int eco_world_counters_async(EcoWorld *w, int64_t *out_host) {
   if (!w || !out_host) return ECO_EINVAL;
-  static_assert(offsetof(Counters, t) == 0 && offsetof(Counters, dropped_last) ==
+  static_assert(offsetof(Counters, t) == 0 && offsetof(Counters, agent_steps) ==
                     (ECO_NCOUNTERS - 1) * sizeof(long long),
                 "the first ECO_NCOUNTERS fields of Counters are the ECO_C_* counters");
   ECO_CU(cudaMemcpyAsync(out_host, w->hd.ctr, ECO_NCOUNTERS * sizeof(int64_t),
@@ -650,6 +764,7 @@ static void counters_to_array(const Counters &c, int64_t *out) {
   out[ECO_C_BIRTHS_LAST] = c.births_last;
   out[ECO_C_DEATHS_LAST] = c.deaths_last;
   out[ECO_C_DROPPED_LAST] = c.dropped_last;
+  out[ECO_C_AGENT_STEPS] = c.agent_steps;
 }
 
 static int download(void *dst, const void *src, size_t bytes) {
@@ -752,6 +867,7 @@ int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
     c.births_last = in->counters[ECO_C_BIRTHS_LAST];
     c.deaths_last = in->counters[ECO_C_DEATHS_LAST];
     c.dropped_last = in->counters[ECO_C_DROPPED_LAST];
+    c.agent_steps = in->counters[ECO_C_AGENT_STEPS];
     if (c.t < 0 || c.t > 0xFFFFFFFFll) return ECO_EINVAL;
   }
   c.deaths_step = 0;
@@ -823,6 +939,41 @@ int eco_batch_create(EcoWorld *const *worlds, int n, EcoBatch **out) {
 int eco_batch_step(EcoBatch *b, int64_t n_steps) {
   if (!b) return ECO_EINVAL;
   return batch_step(*b, n_steps);
+}
+
+int eco_batch_set_config(EcoBatch *b, int fused, int spawn_ctas_per_sm, int steps_per_graph) {
+  if (!b) return ECO_EINVAL;
+  return set_config(*b, fused, spawn_ctas_per_sm, steps_per_graph);
+}
+
+int eco_batch_get_config(const EcoBatch *b, int *fused, int *spawn_ctas_per_sm,
+                         int *steps_per_graph) {
+  if (!b || !fused || !spawn_ctas_per_sm || !steps_per_graph) return ECO_EINVAL;
+  *fused = b->bd.fused;
+  *spawn_ctas_per_sm = b->bd.spawn_ctas / b->bd.n_sms;
+  *steps_per_graph = b->steps_per_graph;
+  return ECO_OK;
+}
+
+int eco_batch_autotune(EcoBatch *b, int trial_steps, EcoTuneResult *out) {
+  if (!b || !out) return ECO_EINVAL;
+  return autotune(*b, trial_steps, out);
+}
+
+int eco_world_set_config(EcoWorld *w, int fused, int spawn_ctas_per_sm, int steps_per_graph) {
+  if (!w) return ECO_EINVAL;
+  return set_config(w->self, fused, spawn_ctas_per_sm, steps_per_graph);
+}
+
+int eco_world_get_config(const EcoWorld *w, int *fused, int *spawn_ctas_per_sm,
+                         int *steps_per_graph) {
+  if (!w) return ECO_EINVAL;
+  return eco_batch_get_config(&w->self, fused, spawn_ctas_per_sm, steps_per_graph);
+}
+
+int eco_world_autotune(EcoWorld *w, int trial_steps, EcoTuneResult *out) {
+  if (!w || !out) return ECO_EINVAL;
+  return autotune(w->self, trial_steps, out);
 }
 
 int eco_batch_sync(EcoBatch *b) {

@@ -209,6 +209,7 @@ __device__ inline void finish_step(const WorldDev &wd, int S, int F, int pop, ui
   c.deaths_step = 0;
   c.n_births = births;
   c.births_t = t;
+  c.agent_steps += c.pop;  // the agents alive at the start of this step
   c.pop = pop;
   c.t = (long long)t + 1;
 }
@@ -697,7 +698,8 @@ void launch_agents_fused(const BatchDev &b, cudaStream_t s) {
   launch_step_kernel(k_agents_cluster, b.n * CLUSTER, SCAN_THREADS, 0, s, b);
 }
 void launch_tail(const BatchDev &b, cudaStream_t s) {
-  launch_step_kernel(k_tail, b.total_tiles + SPAWN_CTAS_PER_SM * b.n_sms, SPAWN_THREADS, 0, s, b);
+  const int spawn = b.spawn_ctas > 0 ? b.spawn_ctas : SPAWN_CTAS_PER_SM * b.n_sms;
+  launch_step_kernel(k_tail, b.total_tiles + spawn, SPAWN_THREADS, 0, s, b);
 }
 void launch_init_weights(const WorldDev *wd_dev, int n0, int n_sms, cudaStream_t s) {
   if (n0 > 0) k_init_weights<<<8 * n_sms, SPAWN_THREADS, 0, s>>>(wd_dev, n0);

@@ -49,8 +49,38 @@ def life_expectancy(records) -> float | None:
     return sum(r["death_age_sum"] for r in records) / deaths if deaths else None
 
 
-class World:
+class _Configurable:
+    """Launch configuration (results do not depend on it) and its tuner."""
+    _prefix = ""
+
+    def _fn(self, name):
+        return getattr(lib(), f"eco_{self._prefix}_{name}")
+
+    def get_config(self) -> dict:
+        f, sp, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(self._fn("get_config")(self._h, ctypes.byref(f), ctypes.byref(sp), ctypes.byref(k)),
+              f"eco_{self._prefix}_get_config")
+        return {"fused": f.value, "spawn_ctas_per_sm": sp.value, "steps_per_graph": k.value}
+
+    def set_config(self, fused=None, spawn_ctas_per_sm=None, steps_per_graph=None) -> None:
+        c = self.get_config()
+        c.update({k: v for k, v in (("fused", fused), ("spawn_ctas_per_sm", spawn_ctas_per_sm),
+                                     ("steps_per_graph", steps_per_graph)) if v is not None})
+        check(self._fn("set_config")(self._h, int(c["fused"]), int(c["spawn_ctas_per_sm"]),
+                                     int(c["steps_per_graph"])), f"eco_{self._prefix}_set_config")
+
+    def autotune(self, trial_steps: int = 16) -> dict:
+        """Time real steps under each candidate configuration and keep the
+        fastest; the worlds advance by the returned steps_taken."""
+        r = _lib.CEcoTuneResult()
+        check(self._fn("autotune")(self._h, int(trial_steps), ctypes.byref(r)),
+              f"eco_{self._prefix}_autotune")
+        return {k: getattr(r, k) for k, _ in r._fields_ if k != "reserved"}
+
+
+class World(_Configurable):
     """One simulated world resident on a CUDA device."""
+    _prefix = "world"
 
     def __init__(self, params: EcoParams, seed: int = 0, device=None, stream=None):
         import torch
@@ -138,8 +168,9 @@ class World:
 
     def counters_async(self, out) -> None:
         """Enqueue a copy of the counters into `out`, a page-locked int64
-        torch tensor of 8 elements on the host (valid after sync())."""
-        assert out.is_pinned() and out.numel() >= 8 and out.element_size() == 8
+        torch tensor of NCOUNTERS (9) elements on the host (valid after
+        sync())."""
+        assert out.is_pinned() and out.numel() >= _lib.NCOUNTERS and out.element_size() == 8
         check(lib().eco_world_counters_async(self._h, ctypes.c_void_p(out.data_ptr())),
               "eco_world_counters_async")
 
@@ -181,8 +212,9 @@ class World:
             pass
 
 
-class Batch:
+class Batch(_Configurable):
     """Independent worlds stepped together, one launch per kernel per step."""
+    _prefix = "batch"
 
     def __init__(self, worlds):
         self.worlds = list(worlds)

@@ -50,7 +50,7 @@ def random_state(p, seed: int, n_agents: int | None = None, wall_p: float = 0.03
     h = np.where(alive[:, None] == 1, rng.uniform(-0.9, 0.9, (C, 32)), 0).astype(np.float32)
     c = np.where(alive[:, None] == 1, rng.uniform(-2, 2, (C, 32)), 0).astype(np.float32)
     weights = (rng.standard_normal((C, NPARAM)) * w_std).astype(np.float32)
-    counters = np.zeros(8, np.int64)
+    counters = np.zeros(9, np.int64)
     counters[0] = t
     return dict(res=res, wall=wall, alive=alive, y=y, x=x, energy=energy,
                 repr_ctr=repr_ctr, low_ctr=low_ctr, age=age, h=h, c=c,

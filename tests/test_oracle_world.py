@@ -258,11 +258,14 @@ def test_free_run_invariants(oracle):
     w = oracle.OracleWorld(p.asdict(), 0)
     pop = w.population
     births_seen = 0
+    agent_steps = 0
     for step in range(300):
         e_before = w.energy.copy()
         alive_before = w.alive.copy()
+        agent_steps += int(alive_before.sum())     # agents that act in this step
         w.step()
         c = w.counters
+        assert c[oracle.C_AGENT_STEPS] == agent_steps
         assert w.population == pop + c[oracle.C_BIRTHS_LAST] - c[oracle.C_DEATHS_LAST]
         pop = w.population
         births_seen += int(c[oracle.C_BIRTHS_LAST])
