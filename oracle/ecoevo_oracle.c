@@ -220,6 +220,129 @@ int or_lstm_step(const float *w, const double *obs, double *h, double *c,
 }
 
 /* ------------------------------------------------------------------------ */
+/* The paper's controller, App. B.5.                                        */
+/* ------------------------------------------------------------------------ */
+int or_param_count(int controller) {
+  if (controller == OR_CTRL_LSTM32) return OR_NPARAM;
+  if (controller == OR_CTRL_PAPER) return OR_PC_NPARAM;
+  return -1;
+}
+
+/* Sensorimotor ability with the paper's 15x15 view: resource, other agent
+ * (the agent's own cell reads 0) and wall channels; cells off the grid read
+ * as wall. */
+void or_pc_observe(const OrParams *p, const uint8_t *res, const uint8_t *wall,
+                   const int32_t *slot_map, int32_t y, int32_t x, double *obs) {
+  const int half = OR_PC_VIEW / 2;
+  for (int dy = -half; dy <= half; ++dy) {
+    for (int dx = -half; dx <= half; ++dx) {
+      double *o = obs + ((dy + half) * OR_PC_VIEW + (dx + half)) * 3;
+      int yy = y + dy, xx = x + dx;
+      if (yy < 0 || yy >= p->H || xx < 0 || xx >= p->W) {
+        o[0] = 0.0; o[1] = 0.0; o[2] = 1.0;
+        continue;
+      }
+      int cell = yy * p->W + xx;
+      o[0] = res[cell] ? 1.0 : 0.0;
+      o[1] = (slot_map[cell] >= 0 && !(dy == 0 && dx == 0)) ? 1.0 : 0.0;
+      o[2] = wall[cell] ? 1.0 : 0.0;
+    }
+  }
+}
+
+/* 3x3 convolution, stride 2, zero padding of one cell on each side ("same"
+ * for these sizes): in [n][n][ci], out [m][m][co], weights [co][3][3][ci]. */
+static void conv3x3_s2(const double *in, int n, int ci, const float *wt, const float *b,
+                       int co, double *out, int m) {
+  for (int oy = 0; oy < m; ++oy)
+    for (int ox = 0; ox < m; ++ox)
+      for (int f = 0; f < co; ++f) {
+        double acc = (double)b[f];
+        for (int ky = 0; ky < 3; ++ky)
+          for (int kx = 0; kx < 3; ++kx) {
+            int iy = 2 * oy + ky - 1, ix = 2 * ox + kx - 1;
+            if (iy < 0 || iy >= n || ix < 0 || ix >= n) continue;
+            for (int c = 0; c < ci; ++c)
+              acc += (double)wt[((f * 3 + ky) * 3 + kx) * ci + c] * in[(iy * n + ix) * ci + c];
+          }
+        out[(oy * m + ox) * co + f] = acc;
+      }
+}
+
+/* 2x2 average pool, stride 1, no padding: [n][n][c] -> [n-1][n-1][c]. */
+static void avgpool2_s1(const double *in, int n, int c, double *out) {
+  for (int y = 0; y + 1 < n; ++y)
+    for (int x = 0; x + 1 < n; ++x)
+      for (int k = 0; k < c; ++k)
+        out[(y * (n - 1) + x) * c + k] =
+            0.25 * (in[(y * n + x) * c + k] + in[(y * n + x + 1) * c + k] +
+                    in[((y + 1) * n + x) * c + k] + in[((y + 1) * n + x + 1) * c + k]);
+}
+
+void or_pc_forward(const float *w, const double *obs, int prev_action, int ate,
+                   double *h, double *c, double *logits) {
+  double a1[8 * 8 * 4], p1[7 * 7 * 4], a2[4 * 4 * 8], emb[OR_PC_EMB + OR_PC_HID];
+  conv3x3_s2(obs, OR_PC_VIEW, 3, w + OR_PC_W1, w + OR_PC_B1, 4, a1, 8);
+  avgpool2_s1(a1, 8, 4, p1);
+  conv3x3_s2(p1, 7, 4, w + OR_PC_W2, w + OR_PC_B2, 8, a2, 4);
+  avgpool2_s1(a2, 4, 8, emb);                      /* emb[0..71] */
+  for (int a = 0; a < OR_NACT; ++a) emb[72 + a] = (a == prev_action) ? 1.0 : 0.0;
+  emb[77] = ate ? 1.0 : 0.0;
+  /* LSTM, 4 units, gates i, f, g, o */
+  double z[4 * OR_PC_HID];
+  for (int r = 0; r < 4 * OR_PC_HID; ++r) {
+    double acc = (double)w[OR_PC_BL + r];
+    for (int k = 0; k < OR_PC_EMB; ++k) acc += (double)w[OR_PC_WI + r * OR_PC_EMB + k] * emb[k];
+    for (int j = 0; j < OR_PC_HID; ++j) acc += (double)w[OR_PC_WH + r * OR_PC_HID + j] * h[j];
+    z[r] = acc;
+  }
+  for (int j = 0; j < OR_PC_HID; ++j) {
+    double gi = sigmoid(z[0 * OR_PC_HID + j]);
+    double gf = sigmoid(z[1 * OR_PC_HID + j]);
+    double gg = tanh(z[2 * OR_PC_HID + j]);
+    double go = sigmoid(z[3 * OR_PC_HID + j]);
+    c[j] = gf * c[j] + gi * gg;
+    h[j] = go * tanh(c[j]);
+  }
+  /* [embedding, h'] -> dense 8, tanh -> dense 5 */
+  for (int j = 0; j < OR_PC_HID; ++j) emb[OR_PC_EMB + j] = h[j];
+  double d[8];
+  for (int i = 0; i < 8; ++i) {
+    double acc = (double)w[OR_PC_DB1 + i];
+    for (int k = 0; k < OR_PC_EMB + OR_PC_HID; ++k)
+      acc += (double)w[OR_PC_D1 + i * (OR_PC_EMB + OR_PC_HID) + k] * emb[k];
+    d[i] = tanh(acc);
+  }
+  for (int a = 0; a < OR_NACT; ++a) {
+    double acc = (double)w[OR_PC_DB2 + a];
+    for (int i = 0; i < 8; ++i) acc += (double)w[OR_PC_D2 + a * 8 + i] * d[i];
+    logits[a] = acc;
+  }
+}
+
+double or_action_uniform(uint64_t seed, uint32_t t, uint32_t slot) {
+  uint32_t word = philox_word(seed, slot, t, OR_TAG_ACT, 0u, 0);
+  return (double)(word >> 8) * (1.0 / 16777216.0);
+}
+
+int or_pc_sample(const double *logits, double u) {
+  double m = logits[0];
+  for (int a = 1; a < OR_NACT; ++a) if (logits[a] > m) m = logits[a];
+  double e[OR_NACT], sum = 0.0;
+  for (int a = 0; a < OR_NACT; ++a) {
+    e[a] = exp(OR_PC_INV_TEMP * (logits[a] - m));
+    sum += e[a];
+  }
+  int action = 0;
+  double cdf = 0.0;
+  for (int k = 0; k < OR_NACT - 1; ++k) {
+    cdf += e[k] / sum;
+    if (cdf <= u) action = k + 1;
+  }
+  return action;
+}
+
+/* ------------------------------------------------------------------------ */
 /* The world.                                                               */
 /* ------------------------------------------------------------------------ */
 struct OrWorld {
@@ -229,7 +352,7 @@ struct OrWorld {
   int32_t *slot_map;
   uint8_t *alive, *ate, *killed, *wants;
   int32_t *y, *x, *repr_ctr, *low_ctr, *age, *action, *target, *cand;
-  int32_t *claim, *birth_parent, *birth_child, *free_list, *move_action;
+  int32_t *claim, *birth_parent, *birth_child, *free_list, *move_action, *prev_act;
   float *energy, *weights;
   double *h, *c, *logits;
   uint32_t *thr;
@@ -268,6 +391,7 @@ void *or_world_field(OrWorld *w, int f) {
     case OR_F_BIRTH_PARENT: return w->birth_parent;
     case OR_F_BIRTH_CHILD: return w->birth_child;
     case OR_F_MOVE_ACTION: return w->move_action;
+    case OR_F_PREV_ACTION: return w->prev_act;
     default: return NULL;
   }
 }
@@ -279,7 +403,7 @@ void or_world_destroy(OrWorld *w) {
   free(w->y); free(w->x); free(w->repr_ctr); free(w->low_ctr); free(w->age);
   free(w->action); free(w->target); free(w->cand); free(w->claim);
   free(w->birth_parent); free(w->birth_child); free(w->free_list);
-  free(w->move_action);
+  free(w->move_action); free(w->prev_act);
   free(w->energy); free(w->weights); free(w->h); free(w->c); free(w->logits);
   free(w->thr);
   free(w->agent_id); free(w->snap_id); free(w->snap_cell);
@@ -292,6 +416,7 @@ static int valid_params(const OrParams *p) {
   if (p->nbr_radius < 1 || p->nbr_radius > 3) return 0;
   if (p->nbr_shape != 0 && p->nbr_shape != 1) return 0;
   if (p->lat_mode != 0 && p->lat_mode != 1) return 0;
+  if (or_param_count(p->controller) < 0) return 0;
   return 1;
 }
 
@@ -305,15 +430,20 @@ static int cmp_u64(const void *a, const void *b) {
  * the four normals 4q..4q+3, as or_normal defines them. */
 void or_fill_normals(uint64_t seed, uint32_t tag, uint32_t t, uint32_t id,
                      float scale, const float *base, float *out) {
+  or_fill_normals_n(seed, tag, t, id, scale, base, out, OR_NPARAM);
+}
+
+void or_fill_normals_n(uint64_t seed, uint32_t tag, uint32_t t, uint32_t id,
+                       float scale, const float *base, float *out, int n) {
   uint32_t key[2];
   key_of(seed, key);
-  for (uint32_t q = 0; 4 * q < OR_NPARAM; ++q) {
+  for (uint32_t q = 0; 4 * q < (uint32_t)n; ++q) {
     uint32_t ctr[4] = {q, t, tag, id}, r[4];
     or_philox4x32_10(ctr, key, r);
     double z[4];
     or_box_muller(r[0], r[1], &z[0], &z[1]);
     or_box_muller(r[2], r[3], &z[2], &z[3]);
-    for (uint32_t i = 0; i < 4 && 4 * q + i < OR_NPARAM; ++i) {
+    for (uint32_t i = 0; i < 4 && 4 * q + i < (uint32_t)n; ++i) {
       uint32_t j = 4 * q + i;
       double b = base ? (double)base[j] : 0.0;
       out[j] = (float)(b + (double)scale * z[i]);
@@ -404,6 +534,7 @@ int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
   w->birth_parent = calloc(C1, 4); w->birth_child = calloc(C1, 4);
   w->free_list = calloc(C1, 4);
   w->move_action = calloc(C1, 4);
+  w->prev_act = calloc(C1, 4);
   w->energy = calloc(C1, sizeof(float));
   w->weights = calloc(C1 * OR_NPARAM, sizeof(float));
   w->h = calloc(C1 * OR_HID, sizeof(double));
@@ -417,6 +548,7 @@ int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
       !w->alive || !w->ate || !w->killed || !w->wants || !w->y || !w->x ||
       !w->repr_ctr || !w->low_ctr || !w->age || !w->action || !w->target ||
       !w->cand || !w->birth_parent || !w->birth_child || !w->free_list || !w->move_action ||
+      !w->prev_act ||
       !w->energy || !w->weights || !w->h || !w->c || !w->logits || !w->thr) {
     or_world_destroy(w);
     return -2;
@@ -443,8 +575,8 @@ int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
     w->slot_map[cell] = s;
     w->energy[s] = p->e0;
     /* weights drawn once at the start of the simulation, App. B.2 */
-    or_fill_normals(seed, OR_TAG_INIT_W, 0u, (uint32_t)s, p->w_init_std, NULL,
-                    w->weights + (size_t)s * OR_NPARAM);
+    or_fill_normals_n(seed, OR_TAG_INIT_W, 0u, (uint32_t)s, p->w_init_std, NULL,
+                      w->weights + (size_t)s * OR_NPARAM, or_param_count(p->controller));
   }
   free(cells);
   w->counters[OR_C_POP] = p->n_agents0;
@@ -494,12 +626,25 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
   /* 2-3. observation (new resources, start-of-step occupancy) and one
    * controller step per living agent */
   for (int s = 0; s < C; ++s) {
+    const int ate_last = w->ate[s];   /* the paper controller's input */
     w->ate[s] = 0;
     w->killed[s] = 0;
     w->wants[s] = 0;
     w->target[s] = -1;
     w->cand[s] = -1;
     if (!w->alive[s]) continue;
+    if (p->controller == OR_CTRL_PAPER) {
+      /* App. B.5: CNN embedding, LSTM(4), dense layers, then an action
+       * sampled from the softmax at temperature 1/50 */
+      double obs[OR_PC_NOBS];
+      or_pc_observe(p, w->res, w->wall, w->slot_map, w->y[s], w->x[s], obs);
+      or_pc_forward(w->weights + (size_t)s * OR_NPARAM, obs, w->prev_act[s], ate_last,
+                    w->h + (size_t)s * OR_HID, w->c + (size_t)s * OR_HID,
+                    w->logits + (size_t)s * OR_NACT);
+      w->action[s] = or_pc_sample(w->logits + (size_t)s * OR_NACT,
+                                  or_action_uniform(w->seed, t, (uint32_t)s));
+      continue;
+    }
     double obs[OR_NOBS];
     or_observe(p, w->res, w->wall, w->slot_map, w->y[s], w->x[s], w->energy[s],
                obs);
@@ -518,6 +663,7 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
     if (!w->alive[s]) continue;
     int a = forced ? forced[s] : w->action[s];
     w->move_action[s] = a;
+    w->prev_act[s] = (a >= 0 && a < OR_NACT) ? a : 0;
     if (a <= 0 || a >= OR_NACT) continue;
     int ty = w->y[s] + DY[a], tx = w->x[s] + DX[a];
     if (!in_grid(p, ty, tx) || w->wall[ty * W + tx]) {
@@ -626,6 +772,7 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
     w->low_ctr[child] = 0;
     w->age[child] = 0;
     w->action[child] = 0;
+    w->prev_act[child] = 0;
     w->ate[child] = 0;
     for (int j = 0; j < OR_HID; ++j) {
       w->h[(size_t)child * OR_HID + j] = 0.0;
@@ -633,9 +780,9 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
     }
     for (int a = 0; a < OR_NACT; ++a) w->logits[(size_t)child * OR_NACT + a] = 0.0;
     /* asexual reproduction: parent weights plus N(0, sigma) noise, App. B.3 */
-    or_fill_normals(w->seed, OR_TAG_MUT, t, (uint32_t)parent, p->mut_std,
-                 w->weights + (size_t)parent * OR_NPARAM,
-                 w->weights + (size_t)child * OR_NPARAM);
+    or_fill_normals_n(w->seed, OR_TAG_MUT, t, (uint32_t)parent, p->mut_std,
+                      w->weights + (size_t)parent * OR_NPARAM,
+                      w->weights + (size_t)child * OR_NPARAM, or_param_count(p->controller));
     w->repr_ctr[parent] = 0;
   }
 

@@ -57,6 +57,38 @@ extern "C" {
 #define OR_TAG_RES_INIT 3u
 #define OR_TAG_INIT_W 4u
 #define OR_TAG_MUT 5u
+#define OR_TAG_ACT 6u            /* action sampling of the paper controller */
+
+/* Controllers (OrParams.controller). */
+#define OR_CTRL_LSTM32 0         /* LSTM(32) on the 7x7 view + energy, argmax   */
+#define OR_CTRL_PAPER 1          /* CNN -> LSTM(4) -> dense(8) -> dense(5),
+                                    softmax at temperature 1/50, sampled (App. B.5) */
+
+/* Paper controller (App. B.5).  Input: the 15x15 view with 3 channels
+ * (resource, other agent, wall), row-major [y][x][channel]; off-grid cells
+ * read as wall.  conv1 3x3 stride 2 "same" (pad 1) -> 8x8x4; average pool
+ * 2x2 stride 1 -> 7x7x4; conv2 3x3 stride 2 "same" (pad 1) -> 4x4x8;
+ * average pool -> 3x3x8, flattened [y][x][channel] (72); embedding = those
+ * 72, the previous action one-hot (5), the ate-last-step bit (1) = 78;
+ * LSTM with 4 units; [embedding, h'] (82) -> dense 8 + tanh -> dense 5.
+ * Logical parameter vector (2445 floats): */
+#define OR_PC_VIEW 15
+#define OR_PC_NOBS (15 * 15 * 3)   /* 675 */
+#define OR_PC_HID 4
+#define OR_PC_EMB 78
+#define OR_PC_W1 0                 /* conv1 [4 out][3 ky][3 kx][3 in]          */
+#define OR_PC_B1 108               /* [4]                                      */
+#define OR_PC_W2 112               /* conv2 [8 out][3][3][4 in]                */
+#define OR_PC_B2 400               /* [8]                                      */
+#define OR_PC_WI 408               /* LSTM input kernel [16][78], row = gate*4 + unit, gates i,f,g,o */
+#define OR_PC_WH 1656              /* LSTM recurrent kernel [16][4]            */
+#define OR_PC_BL 1720              /* LSTM bias [16]                           */
+#define OR_PC_D1 1736              /* dense [8][82]                            */
+#define OR_PC_DB1 2392             /* [8]                                      */
+#define OR_PC_D2 2400              /* dense [5][8]                             */
+#define OR_PC_DB2 2440             /* [5]                                      */
+#define OR_PC_NPARAM 2445
+#define OR_PC_INV_TEMP 50.0        /* softmax temperature 1/50                 */
 
 typedef struct OrParams {
   int32_t H, W, capacity, n_agents0;
@@ -76,6 +108,7 @@ typedef struct OrParams {
   int32_t t_death, max_age;
   int32_t wall_kills;       /* 1: an agent moving into a wall dies         */
   float w_init_std, mut_std;
+  int32_t controller;       /* OR_CTRL_*                                   */
 } OrParams;
 
 typedef struct OrWorld OrWorld;
@@ -104,6 +137,9 @@ enum {
   OR_F_BIRTH_CHILD,  /* int32  [C]  child slots of the last step's births    */
   OR_F_MOVE_ACTION,  /* int32  [C]  action each agent alive at the start of the
                                     last step moved with (0 for the others)  */
+  OR_F_PREV_ACTION,  /* int32  [C]  action the agent moved with in its last
+                                    step (0 for newborns): a paper-controller
+                                    input                                    */
   OR_NFIELDS
 };
 enum {
@@ -141,6 +177,24 @@ double or_normal(uint64_t seed, uint32_t tag, uint32_t t, uint32_t id,
  * OR_TAG_INIT_W, t = 0, id = slot, base NULL). */
 void or_fill_normals(uint64_t seed, uint32_t tag, uint32_t t, uint32_t id,
                      float scale, const float *base, float *out);
+/* The same for the first n parameters only. */
+void or_fill_normals_n(uint64_t seed, uint32_t tag, uint32_t t, uint32_t id,
+                       float scale, const float *base, float *out, int n);
+/* Parameters per agent of a controller (23333 or 2445), -1 if unknown. */
+int or_param_count(int controller);
+/* Paper controller (App. B.5): the 15x15x3 view of the agent at (y, x). */
+void or_pc_observe(const OrParams *p, const uint8_t *res, const uint8_t *wall,
+                   const int32_t *slot_map, int32_t y, int32_t x,
+                   double *obs /* [675] */);
+/* One forward step: h, c [4] updated in place, logits [5] written. */
+void or_pc_forward(const float *w /* [2445] */, const double *obs, int prev_action,
+                   int ate, double *h, double *c, double *logits);
+/* Uniform of the action draw of slot s at step t: word 0 of the Philox
+ * block {s, t, OR_TAG_ACT, 0}, u = (word >> 8) 2^-24. */
+double or_action_uniform(uint64_t seed, uint32_t t, uint32_t slot);
+/* Sampled action: probabilities softmax(50 logits); the action is the
+ * number of k in 0..3 whose cumulative probability is <= u. */
+int or_pc_sample(const double *logits, double u);
 /* Growth thresholds thr[y*4+cls] = floor(p * 2^32), App. B.1 Eq. (1). */
 int or_threshold_table(const OrParams *p, uint32_t *thr);
 /* One synchronous regrowth pass, App. B.1 Eq. (1). */

@@ -14,11 +14,16 @@ from . import build as _build
 NOBS, HID, NACT = 148, 32, 5
 NPARAM = 23333
 OFF_B, OFF_WO, OFF_BO = 23040, 23168, 23328
-TAG_REGROW, TAG_PLACE, TAG_RES_INIT, TAG_INIT_W, TAG_MUT = 1, 2, 3, 4, 5
+TAG_REGROW, TAG_PLACE, TAG_RES_INIT, TAG_INIT_W, TAG_MUT, TAG_ACT = 1, 2, 3, 4, 5, 6
+CTRL_LSTM32, CTRL_PAPER = 0, 1
+PC_VIEW, PC_NOBS, PC_HID, PC_EMB, PC_NPARAM = 15, 675, 4, 78, 2445
+# logical parameter offsets of the paper controller (see the oracle header)
+PC_OFF = {"W1": 0, "B1": 108, "W2": 112, "B2": 400, "WI": 408, "WH": 1656, "BL": 1720,
+          "D1": 1736, "DB1": 2392, "D2": 2400, "DB2": 2440}
 
 (F_RES, F_WALL, F_SLOT_MAP, F_ALIVE, F_Y, F_X, F_ENERGY, F_REPR_CTR, F_LOW_CTR,
  F_AGE, F_H, F_C, F_ACTION, F_LOGITS, F_ATE, F_WEIGHTS, F_COUNTERS, F_THR,
- F_BIRTH_PARENT, F_BIRTH_CHILD, F_MOVE_ACTION) = range(21)
+ F_BIRTH_PARENT, F_BIRTH_CHILD, F_MOVE_ACTION, F_PREV_ACTION) = range(22)
 (C_T, C_POP, C_BIRTHS, C_DEATHS, C_DROPPED, C_BIRTHS_LAST, C_DEATHS_LAST,
  C_DROPPED_LAST, C_AGENT_STEPS) = range(9)
 NCOUNTERS = 9
@@ -44,6 +49,7 @@ class OrParams(ctypes.Structure):
         ("max_age", ctypes.c_int32),
         ("wall_kills", ctypes.c_int32),
         ("w_init_std", ctypes.c_float), ("mut_std", ctypes.c_float),
+        ("controller", ctypes.c_int32),
     ]
 
 
@@ -53,6 +59,8 @@ def make_params(values) -> OrParams:
     p = OrParams()
     for name, ctype in OrParams._fields_:
         v = get(name)
+        if v is None and name == "controller":
+            v = 0
         if name == "class_edges":
             p.class_edges = (ctypes.c_int32 * 3)(*[int(e) for e in v])
         elif name == "p_class":
@@ -102,6 +110,20 @@ def lib():
         L.or_world_field.restype = ctypes.c_void_p
         L.or_world_sync.argtypes = [ctypes.c_void_p]
         L.or_world_analysis.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.or_fill_normals_n.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_uint32, ctypes.c_float, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int]
+        L.or_param_count.argtypes = [ctypes.c_int]
+        L.or_param_count.restype = ctypes.c_int
+        L.or_pc_observe.argtypes = [ctypes.POINTER(OrParams), ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_void_p]
+        L.or_pc_forward.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.or_action_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
+        L.or_action_uniform.restype = ctypes.c_double
+        L.or_pc_sample.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        L.or_pc_sample.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -181,6 +203,52 @@ def lstm_step(w, obs, h, c):
     return a, h2, c2, logits
 
 
+def param_count(controller: int) -> int:
+    return int(lib().or_param_count(int(controller)))
+
+
+def fill_normals_n(seed, tag, t, ident, scale, n, base=None) -> np.ndarray:
+    """The first n values of fill_normals."""
+    out = np.zeros(n, np.float32)
+    b = None if base is None else np.ascontiguousarray(base, np.float32)
+    lib().or_fill_normals_n(int(seed), tag, t, ident, float(scale),
+                            None if b is None else _ptr(b), _ptr(out), int(n))
+    return out
+
+
+def pc_observe(params, res, wall, slot_map, y, x) -> np.ndarray:
+    """The paper controller's 15x15x3 view, shape (15, 15, 3)."""
+    p = make_params(params)
+    res = np.ascontiguousarray(res, np.uint8)
+    wall = np.ascontiguousarray(wall, np.uint8)
+    slot_map = np.ascontiguousarray(slot_map, np.int32)
+    out = np.zeros(PC_NOBS, np.float64)
+    lib().or_pc_observe(ctypes.byref(p), _ptr(res), _ptr(wall), _ptr(slot_map),
+                        int(y), int(x), _ptr(out))
+    return out.reshape(PC_VIEW, PC_VIEW, 3)
+
+
+def pc_forward(w, obs, prev_action, ate, h, c):
+    """Returns (h', c', logits) of the paper controller (inputs untouched)."""
+    w = np.ascontiguousarray(np.asarray(w, np.float32)[:PC_NPARAM])
+    obs = np.ascontiguousarray(obs, np.float64).reshape(-1)
+    h2 = np.array(h, np.float64)[:PC_HID].copy()
+    c2 = np.array(c, np.float64)[:PC_HID].copy()
+    logits = np.zeros(NACT, np.float64)
+    lib().or_pc_forward(_ptr(w), _ptr(obs), int(prev_action), int(ate), _ptr(h2), _ptr(c2),
+                        _ptr(logits))
+    return h2, c2, logits
+
+
+def action_uniform(seed, t, slot) -> float:
+    return float(lib().or_action_uniform(int(seed), int(t), int(slot)))
+
+
+def pc_sample(logits, u) -> int:
+    lg = np.ascontiguousarray(logits, np.float64)
+    return int(lib().or_pc_sample(_ptr(lg), float(u)))
+
+
 def initial_layout(params, seed):
     """(res [H,W] u8, wall [H,W] u8, cells [n_agents0] int32) of a new world."""
     p = make_params(params)
@@ -239,6 +307,7 @@ class OracleWorld:
         self.birth_parent = f(F_BIRTH_PARENT, np.int32, (C,))
         self.birth_child = f(F_BIRTH_CHILD, np.int32, (C,))
         self.move_action = f(F_MOVE_ACTION, np.int32, (C,))
+        self.prev_action = f(F_PREV_ACTION, np.int32, (C,))
 
     def _field(self, fid, dtype, shape):
         addr = lib().or_world_field(self._h, fid)

@@ -42,6 +42,8 @@ class EcoParams:
     wall_kills: int = 0
     w_init_std: float = 0.1
     mut_std: float = 0.02
+    controller: int = 0           # 0: LSTM(32) on the 7x7 view + energy, argmax;
+                                  # 1: the paper's CNN -> LSTM(4) -> dense, sampled (App. B.5)
 
     def replace(self, **kw) -> "EcoParams":
         return dataclasses.replace(self, **kw)
@@ -65,6 +67,22 @@ def large_1000x2000() -> EcoParams:
     return EcoParams(H=1000, W=2000, capacity=131072, n_agents0=20000)
 
 
+def paper_natural() -> EcoParams:
+    """The paper's natural environment (App. B.4, B.5): 200x400 grid, 330
+    agents at the start, at most 1000, the CNN+LSTM(4) controller with its
+    15x15 view and sampled actions, von Neumann regrowth (p = 0.002 when
+    exactly one of the 4 direct neighbours holds a resource) scaled by the
+    climate (200^x + 1)/201 plus 5e-5, ~16,000 initial resources, E0 = Emax
+    = 3, decay 0.025, gain 1, reproduction after 140 steps above 0, death
+    after 200 steps at or below 0 or past age 650, walls that kill."""
+    return EcoParams(H=200, W=400, capacity=1000, n_agents0=330, res_init_p=0.2,
+                     nbr_shape=1, nbr_radius=1, class_edges=(1, 2, 5),
+                     p_class=(0.0, 0.002, 0.0, 0.0), lat_mode=1, lat_alpha=200.0,
+                     p_spont=5e-5, e0=3.0, e_max=3.0, e_decay=0.025, e_gain=1.0,
+                     e_repr=0.0, t_repr=140, e_death=0.0, t_death=200, max_age=650,
+                     wall_kills=1, controller=1)
+
+
 def held(p: EcoParams) -> EcoParams:
     """Held population: no energy decay and no reproduction, so the agent
     count stays at n_agents0 (roofline microbenchmark)."""
@@ -75,6 +93,7 @@ PRESETS = {
     "small_20x40": small_20x40,
     "paper_200x400": paper_200x400,
     "large_1000x2000": large_1000x2000,
+    "paper_natural": paper_natural,
 }
 
 
