@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define ECO_ABI_V1 0x45434F01u
+#define ECO_ABI_V2 0x45434F02u
 
 /* Error codes. */
 #define ECO_OK 0
@@ -44,11 +44,25 @@ extern "C" {
 #define ECO_ETIMEOUT -4  /* a bounded device wait ran out                  */
 #define ECO_ESTATE -5    /* loaded state is inconsistent (shared cell ...) */
 
-/* Fixed controller shape (7x7 view, 3 channels + energy, hidden 32). */
+/* Controllers (EcoParams.controller).
+ *   ECO_CTRL_LSTM32  LSTM with 32 units on the 7x7 view (resource, other
+ *                    agent, wall) + energy, 5 logits, action = first argmax
+ *                    (App. B.2 form, the 200x400 workloads' controller).
+ *   ECO_CTRL_PAPER   the paper's own controller (App. B.5): 15x15 view,
+ *                    conv 3x3/2 (4) + average pool 2x2/1, conv 3x3/2 (8) +
+ *                    pool, embedding [72 features, previous action one-hot,
+ *                    ate-last-step bit], LSTM with 4 units, dense 8 + tanh on
+ *                    [embedding, h], dense 5; the action is sampled from the
+ *                    softmax at temperature 1/50 with the uniform
+ *                    (word0 >> 8) 2^-24 of the Philox block {slot, t, 6, 0}:
+ *                    the number of k < 4 whose cumulative probability is <= u. */
+#define ECO_CTRL_LSTM32 0
+#define ECO_CTRL_PAPER 1
 #define ECO_NOBS 148
-#define ECO_HIDDEN 32
+#define ECO_HIDDEN 32        /* h and c have 32 floats per slot (4 used by ECO_CTRL_PAPER) */
 #define ECO_NACT 5
-#define ECO_NPARAM 23333 /* logical parameter vector of one agent */
+#define ECO_NPARAM 23333     /* parameters per agent, ECO_CTRL_LSTM32 */
+#define ECO_PC_NPARAM 2445   /* parameters per agent, ECO_CTRL_PAPER   */
 
 /* World parameters; all plain data.  Field meanings:
  *   H, W            grid rows (latitude axis, row 0 = top) and columns
@@ -72,9 +86,10 @@ extern "C" {
  *                   (App. B.1); 0: the move is blocked
  *   w_init_std      std of the initial weights; mut_std: std sigma of the
  *                   mutation noise N(0, sigma)                  App. B.3
+ *   controller      ECO_CTRL_LSTM32 or ECO_CTRL_PAPER           App. B.2, B.5
  * Sizes: 3 <= H, W <= 16384 with H*W <= 2^26; capacity <= 2^24. */
 typedef struct EcoParams {
-  uint32_t abi_version; /* must be ECO_ABI_V1 */
+  uint32_t abi_version; /* must be ECO_ABI_V2 */
   int32_t H, W, capacity, n_agents0;
   int32_t border_walls;
   double res_init_p;
@@ -91,6 +106,7 @@ typedef struct EcoParams {
   int32_t t_death, max_age;
   int32_t wall_kills;
   float w_init_std, mut_std;
+  int32_t controller;
 } EcoParams;
 
 /* Counters (int64), indices into EcoState.counters. */
@@ -109,13 +125,24 @@ typedef struct EcoParams {
  * memory and may be NULL to skip that field.  Grid fields are unpacked
  * uint8 [H*W] row-major; per-slot fields have `capacity` entries; h, c are
  * [capacity*32]; logits [capacity*5]; weights are logical parameter
- * vectors [weights_count * 23333] for slots weights_first ..
- * weights_first + weights_count - 1, laid out as
+ * vectors [weights_count * P] for slots weights_first ..
+ * weights_first + weights_count - 1.  ECO_CTRL_LSTM32, P = 23333:
  *   W[r][k]  r < 128 gate rows (i, f, g, o blocks of 32), k < 180
  *            (148 observation inputs, then 32 hidden inputs)   [0, 23040)
  *   b[r]                                                    [23040, 23168)
  *   Wo[a][j] a < 5, j < 32                                  [23168, 23328)
- *   bo[a]                                                   [23328, 23333) */
+ *   bo[a]                                                   [23328, 23333)
+ * ECO_CTRL_PAPER, P = 2445:
+ *   conv1 [4 out][3 ky][3 kx][3 in]     [0, 108)     bias [108, 112)
+ *   conv2 [8 out][3][3][4 in]           [112, 400)   bias [400, 408)
+ *   LSTM input kernel [16][78]          [408, 1656)  (row = gate*4 + unit,
+ *   LSTM recurrent kernel [16][4]       [1656, 1720)  gates i, f, g, o)
+ *   LSTM bias [16]                      [1720, 1736)
+ *   dense [8][82]                       [1736, 2392) bias [2392, 2400)
+ *   dense [5][8]                        [2400, 2440) bias [2440, 2445)
+ * prev_action: the action each agent moved with in its last step (0 for
+ * newborns); ate: 1 if it ate in its last step.  Both are inputs of
+ * ECO_CTRL_PAPER. */
 typedef struct EcoState {
   int64_t counters[ECO_NCOUNTERS];
   uint8_t *res_host, *wall_host;
@@ -129,6 +156,8 @@ typedef struct EcoState {
   float *logits_host;
   float *weights_host;
   int32_t weights_first, weights_count;
+  int32_t *prev_action_host;
+  uint8_t *ate_host;
 } EcoState;
 
 typedef struct EcoWorld EcoWorld;
@@ -238,8 +267,8 @@ void *eco_world_stream(const EcoWorld *world);
 
 /* Batch of independent worlds stepped together: every kernel of a step is
  * launched once for all of them (work lists over worlds and agents).  The
- * worlds must live on the current device; the batch uses the first
- * world's stream.  The worlds must outlive the batch. */
+ * worlds must live on the current device and share one controller; the
+ * batch uses the first world's stream.  The worlds must outlive the batch. */
 int eco_batch_create(EcoWorld *const *worlds, int n_worlds, EcoBatch **out);
 int eco_batch_step(EcoBatch *batch, int64_t n_steps);
 int eco_batch_sync(EcoBatch *batch);
@@ -299,12 +328,12 @@ int eco_world_autotune(EcoWorld *world, int trial_steps, EcoTuneResult *out);
  * stream and returns the sums since enabling:
  * ms[k], launches[k] for k < ECO_NKERNELS (names: eco_kernel_name; a kernel
  * the world's step does not launch keeps 0 launches).  A step runs
- * "observe_lstm", then the slot phases (moves, physiology, birth claims,
+ * "observe_lstm" (ECO_CTRL_PAPER: "observe_paper"), then the slot phases (moves, physiology, birth claims,
  * compaction) as one kernel "agents_fused" for worlds of capacity <= 16384
  * or as five kernels otherwise, then "regrow_spawn": the regrowth of the
  * next step's resource plane and the mutation of the births in one launch.
  * "regrow" is the first regrowth after creating or loading a world. */
-#define ECO_NKERNELS 9
+#define ECO_NKERNELS 10
 int eco_world_profile(EcoWorld *world, int enable, int max_steps);
 int eco_world_profile_read(EcoWorld *world, double *ms, int64_t *launches);
 const char *eco_kernel_name(int k);

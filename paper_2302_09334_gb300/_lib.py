@@ -10,10 +10,12 @@ import os
 
 from .params import EcoParams
 
-ECO_ABI_V1 = 0x45434F01
+ECO_ABI_V2 = 0x45434F02
+CTRL_LSTM32, CTRL_PAPER = 0, 1
+NPARAM_OF = {CTRL_LSTM32: 23333, CTRL_PAPER: 2445}
 ECO_OK, ECO_EINVAL, ECO_ENOMEM, ECO_ECUDA, ECO_ETIMEOUT, ECO_ESTATE = 0, -1, -2, -3, -4, -5
 NCOUNTERS = 9
-NKERNELS = 9
+NKERNELS = 10
 MOVE_BINS = 17
 # EcoAnalysis: these int64 fields, then MOVE_BINS bin counts
 ANALYSIS_KEYS = ("t", "window", "population", "resources", "deaths", "death_age_sum", "movers")
@@ -45,12 +47,13 @@ class CEcoParams(ctypes.Structure):
         ("max_age", ctypes.c_int32),
         ("wall_kills", ctypes.c_int32),
         ("w_init_std", ctypes.c_float), ("mut_std", ctypes.c_float),
+        ("controller", ctypes.c_int32),
     ]
 
 
 def to_c_params(p: EcoParams) -> CEcoParams:
     c = CEcoParams()
-    c.abi_version = ECO_ABI_V1
+    c.abi_version = ECO_ABI_V2
     for name, ctype in CEcoParams._fields_[1:]:
         v = getattr(p, name)
         if name == "class_edges":
@@ -76,6 +79,7 @@ class CEcoState(ctypes.Structure):
         ("h_host", _P), ("c_host", _P), ("action_host", _P), ("logits_host", _P),
         ("weights_host", _P),
         ("weights_first", ctypes.c_int32), ("weights_count", ctypes.c_int32),
+        ("prev_action_host", _P), ("ate_host", _P),
     ]
 
 

@@ -21,7 +21,7 @@ LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(LIBDIR, "libecoevo.so")
 SOURCES = ["k_regrow.cu", "k_lstm.cu", "k_agents.cu", "k_init.cu", "ecoevo_host.cu",
-           "k_moves_noalloc.cu", "k_analysis.cu"]
+           "k_moves_noalloc.cu", "k_analysis.cu", "k_paper.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

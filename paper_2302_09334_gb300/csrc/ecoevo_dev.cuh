@@ -63,7 +63,16 @@ __host__ __device__ inline int logical_of_phys(int p) {
 
 // Philox stream tags (third counter word).
 constexpr uint32_t TAG_REGROW = 1u, TAG_PLACE = 2u, TAG_RES_INIT = 3u,
-                   TAG_INIT_W = 4u, TAG_MUT = 5u;
+                   TAG_INIT_W = 4u, TAG_MUT = 5u, TAG_ACT = 6u;
+
+// The paper's controller (App. B.5): parameters in logical order, one row
+// of PC_WSTRIDE floats per slot (16-byte multiple, padding zero).
+constexpr int PC_NPARAM = 2445;
+constexpr int PC_WSTRIDE = 2448;
+constexpr int PC_OFF_W1 = 0, PC_OFF_B1 = 108, PC_OFF_W2 = 112, PC_OFF_B2 = 400,
+              PC_OFF_WI = 408, PC_OFF_WH = 1656, PC_OFF_BL = 1720, PC_OFF_D1 = 1736,
+              PC_OFF_DB1 = 2392, PC_OFF_D2 = 2400, PC_OFF_DB2 = 2440;
+constexpr int PC_HID = 4, PC_EMB = 78, PC_VIEW = 15;
 
 // Status bits written by kernels.
 constexpr int ST_TIMEOUT = 1;
@@ -94,6 +103,8 @@ enum { A_T = 0, A_WINDOW, A_POP, A_RES, A_DEATHS, A_AGE_SUM, A_MOVERS, A_BINS,
 
 struct WorldDev {            // read-only while kernels run
   int H, W, Wp, C;
+  int controller;            // ECO_CTRL_*
+  int wstride, nparam;       // weight row stride (floats) and parameters per agent
   int nbr_shape, nbr_radius;
   int class_edges[3];
   int t_repr, t_death, max_age, wall_kills;
@@ -119,6 +130,7 @@ struct WorldDev {            // read-only while kernels run
   float *weights;            // [C][WSTRIDE], 256-B aligned
   Counters *ctr;
   int32_t *snap_cell;        // [C] cell of each slot's agent at the window start, -1 none
+  int32_t *prev_act;         // [C] action moved with in the last step (paper controller input)
   unsigned long long *analysis;  // [ANALYSIS_WORDS] output of the analysis kernels
 };
 
@@ -214,6 +226,7 @@ struct BatchDev {
   int n_sms;
   int fused;                 // slot phases in one cluster kernel (capacity <= FUSED_MAX_C)
   int spawn_ctas;            // CTAs of the tail kernel that mutate births
+  int controller, wstride;   // shared by every world of the batch
 };
 
 #ifdef __CUDACC__
@@ -256,6 +269,8 @@ constexpr int FUSED_MAX_C = 16384;
 
 void launch_regrow(const BatchDev &b, cudaStream_t s);
 void launch_lstm(const BatchDev &b, cudaStream_t s);
+void launch_paper_ctrl(const BatchDev &b, cudaStream_t s);   // k_paper.cu
+void preload_paper();
 void launch_move_apply(const BatchDev &b, cudaStream_t s);
 void launch_physio(const BatchDev &b, cudaStream_t s);
 void launch_birth_claim(const BatchDev &b, cudaStream_t s);
@@ -273,10 +288,12 @@ void launch_init_world(const WorldDev *wd_host, WorldDev *wd_dev, int n0,
                        const int32_t *place_y, const int32_t *place_x,
                        int border, uint32_t thr_init, int n_sms, cudaStream_t s);
 void launch_rebuild(const WorldDev *wd_host, int n_sms, cudaStream_t s);
-void launch_weights_to_physical(const float *logical, float *physical, int n, int n_sms,
-                                cudaStream_t s);
-void launch_weights_to_logical(const float *physical, float *logical, int n, int n_sms,
-                               cudaStream_t s);
+// Rows of `wstride` floats; ECO_CTRL_LSTM32 rows are permuted, ECO_CTRL_PAPER
+// rows are in logical order already (copied, padding zeroed).
+void launch_weights_to_physical(const float *logical, float *physical, int n, int controller,
+                                int n_sms, cudaStream_t s);
+void launch_weights_to_logical(const float *physical, float *logical, int n, int controller,
+                               int n_sms, cudaStream_t s);
 // analysis metrics of App. C (k_analysis.cu)
 void launch_analysis_reset(const WorldDev *wd_host, int n_sms, cudaStream_t s);
 void launch_analysis(const WorldDev *wd_host, int n_sms, cudaStream_t s);

@@ -27,7 +27,8 @@ constexpr int STAGING_AGENTS = 64;
 // Parameters and the arena layout.
 // ---------------------------------------------------------------------------
 bool params_ok(const EcoParams *p) {
-  if (!p || p->abi_version != ECO_ABI_V1) return false;
+  if (!p || p->abi_version != ECO_ABI_V2) return false;
+  if (p->controller != ECO_CTRL_LSTM32 && p->controller != ECO_CTRL_PAPER) return false;
   if (p->H < 1 || p->W < 1 || p->H > 16384 || p->W > 16384) return false;
   if ((long long)p->H * p->W > (1ll << 26)) return false;
   if (p->capacity < 0 || p->capacity > (1 << 24)) return false;
@@ -42,12 +43,16 @@ bool params_ok(const EcoParams *p) {
   return true;
 }
 
+// Weight row stride (floats) and parameters per agent of a controller.
+int wstride_of(int controller) { return controller == ECO_CTRL_PAPER ? PC_WSTRIDE : WSTRIDE; }
+int nparam_of(int controller) { return controller == ECO_CTRL_PAPER ? PC_NPARAM : NPARAM; }
+
 struct Layout {
   size_t ctr, wdev, tab_worlds, tab_tiles, tab_blocks, thr, res0, res1, wall,
       slot_map, claim, bclaim, alive, killed, ate, flag, y, x, energy, repr_ctr,
       low_ctr, age, action, forced, target, birth_cell, arrive, h0, h1, c,
       logits, alive_list, free_list, birth_parent, birth_child, snap_cell, analysis,
-      weights, staging, total;
+      prev_act, weights, staging, total;
 };
 
 Layout layout_of(const EcoParams *p) {
@@ -97,7 +102,8 @@ Layout layout_of(const EcoParams *p) {
   L.birth_child = take(C1 * 4);
   L.snap_cell = take(C1 * 4);
   L.analysis = take(ANALYSIS_WORDS * 8);
-  L.weights = take(C1 * (size_t)WSTRIDE * 4);
+  L.prev_act = take(C1 * 4);
+  L.weights = take(C1 * (size_t)wstride_of(p->controller) * 4);
   L.staging = take((size_t)STAGING_AGENTS * WSTRIDE * 4);
   L.total = off;
   return L;
@@ -202,10 +208,10 @@ int slot_blocks_of(const WorldDev &wd) { return (wd.C + SLOT_BLOCK - 1) / SLOT_B
 
 // Kernel ids for profiling (names: eco_kernel_name).
 enum { K_REGROW, K_LSTM, K_MOVE_CLAIM, K_MOVE_APPLY, K_PHYSIO, K_BIRTH_CLAIM, K_SCAN,
-       K_TAIL, K_AGENTS_FUSED };
+       K_TAIL, K_AGENTS_FUSED, K_PAPER };
 // A step starts with its resource plane already regrown (by the previous
-// step, or at creation/loading); the observation+LSTM kernel also makes the
-// move claims; it ends with the tail kernel: the regrowth
+// step, or at creation/loading); the observation+controller kernel also
+// makes the move claims; it ends with the tail kernel: the regrowth
 // of the next step's plane in the same launch as the mutation of this
 // step's births (they touch disjoint data).
 const StepKernel kSplitStep[] = {
@@ -216,13 +222,23 @@ const StepKernel kSplitStep[] = {
 const StepKernel kFusedStep[] = {{K_LSTM, launch_lstm},
                                  {K_AGENTS_FUSED, launch_agents_fused},
                                  {K_TAIL, launch_tail}};
+// the same with the paper's controller
+const StepKernel kSplitStepPaper[] = {
+    {K_PAPER, launch_paper_ctrl},
+    {K_MOVE_APPLY, launch_move_apply}, {K_PHYSIO, launch_physio},
+    {K_BIRTH_CLAIM, launch_birth_claim}, {K_SCAN, launch_scan},
+    {K_TAIL, launch_tail}};
+const StepKernel kFusedStepPaper[] = {{K_PAPER, launch_paper_ctrl},
+                                      {K_AGENTS_FUSED, launch_agents_fused},
+                                      {K_TAIL, launch_tail}};
 
 int step_kernels(const BatchDev &bd, const StepKernel **list) {
+  const bool paper = bd.controller == ECO_CTRL_PAPER;
   if (bd.fused) {
-    *list = kFusedStep;
+    *list = paper ? kFusedStepPaper : kFusedStep;
     return (int)(sizeof(kFusedStep) / sizeof(kFusedStep[0]));
   }
-  *list = kSplitStep;
+  *list = paper ? kSplitStepPaper : kSplitStep;
   return (int)(sizeof(kSplitStep) / sizeof(kSplitStep[0]));
 }
 
@@ -294,6 +310,8 @@ int batch_init(EcoBatch &b, EcoWorld *const *worlds, int n, void *table_dev) {
   b.bd.n_sms = worlds[0]->n_sms;
   b.bd.fused = maxc <= FUSED_MAX_C ? 1 : 0;
   b.bd.spawn_ctas = DEFAULT_SPAWN_PER_SM * b.bd.n_sms;
+  b.bd.controller = worlds[0]->hd.controller;
+  b.bd.wstride = worlds[0]->hd.wstride;
   b.prof = &worlds[0]->prof;
   return ECO_OK;
 }
@@ -524,6 +542,9 @@ static void fill_descriptor(EcoWorld *w) {
   char *a = w->arena;
   WorldDev &d = w->hd;
   d.H = p.H; d.W = p.W; d.Wp = (p.W + 31) / 32; d.C = p.capacity;
+  d.controller = p.controller;
+  d.wstride = wstride_of(p.controller);
+  d.nparam = nparam_of(p.controller);
   d.nbr_shape = p.nbr_shape; d.nbr_radius = p.nbr_radius;
   for (int i = 0; i < 3; ++i) d.class_edges[i] = p.class_edges[i];
   d.t_repr = p.t_repr; d.t_death = p.t_death; d.max_age = p.max_age;
@@ -566,6 +587,7 @@ static void fill_descriptor(EcoWorld *w) {
   d.weights = (float *)(a + L.weights);
   d.ctr = (Counters *)(a + L.ctr);
   d.snap_cell = (int32_t *)(a + L.snap_cell);
+  d.prev_act = (int32_t *)(a + L.prev_act);
   d.analysis = (unsigned long long *)(a + L.analysis);
   w->dd = (WorldDev *)(a + L.wdev);
 }
@@ -627,6 +649,7 @@ int eco_world_create(const EcoParams *params, uint64_t seed, void *arena,
     configure_lstm();
     preload_regrow();
     preload_lstm();
+    preload_paper();
     preload_agents();
     if (arena) {
       w->arena = (char *)arena;
@@ -825,6 +848,8 @@ int eco_world_read_state(EcoWorld *w, EcoState *out) {
   if ((rc = download(out->h_host, odd ? d.h1 : d.h0, C * HID * 4))) return rc;
   if ((rc = download(out->c_host, d.c, C * HID * 4))) return rc;
   if ((rc = download(out->action_host, d.action, C * 4))) return rc;
+  if ((rc = download(out->prev_action_host, d.prev_act, C * 4))) return rc;
+  if ((rc = download(out->ate_host, d.ate, C))) return rc;
   if (out->logits_host && C) {
     std::vector<float> lg(C * 8);
     if ((rc = download(lg.data(), d.logits, lg.size() * 4))) return rc;
@@ -833,13 +858,14 @@ int eco_world_read_state(EcoWorld *w, EcoState *out) {
   }
   if (out->weights_host && out->weights_count > 0) {
     float *staging = (float *)(w->arena + w->L.staging);
+    const size_t ws = d.wstride, np = d.nparam;
     for (int s0 = 0; s0 < out->weights_count; s0 += STAGING_AGENTS) {
       const int n = std::min(STAGING_AGENTS, out->weights_count - s0);
-      launch_weights_to_logical(d.weights + (size_t)(out->weights_first + s0) * WSTRIDE,
-                                staging, n, w->n_sms, w->stream);
+      launch_weights_to_logical(d.weights + (size_t)(out->weights_first + s0) * ws, staging, n,
+                                d.controller, w->n_sms, w->stream);
       ECO_CU(cudaGetLastError());
-      ECO_CU(cudaMemcpy2DAsync(out->weights_host + (size_t)s0 * NPARAM, NPARAM * 4, staging,
-                               WSTRIDE * 4, NPARAM * 4, n, cudaMemcpyDeviceToHost, w->stream));
+      ECO_CU(cudaMemcpy2DAsync(out->weights_host + (size_t)s0 * np, np * 4, staging, ws * 4,
+                               np * 4, n, cudaMemcpyDeviceToHost, w->stream));
       ECO_CU(cudaStreamSynchronize(w->stream));
     }
   }
@@ -887,6 +913,8 @@ int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
   if ((rc = upload(odd ? d.h1 : d.h0, in->h_host, C * HID * 4))) return rc;
   if ((rc = upload(d.c, in->c_host, C * HID * 4))) return rc;
   if ((rc = upload(d.action, in->action_host, C * 4))) return rc;
+  if ((rc = upload(d.prev_act, in->prev_action_host, C * 4))) return rc;
+  if ((rc = upload(d.ate, in->ate_host, C))) return rc;
   if (in->logits_host && C) {
     std::vector<float> lg(C * 8, 0.f);
     for (size_t s = 0; s < C; ++s)
@@ -895,12 +923,13 @@ int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
   }
   if (in->weights_host && in->weights_count > 0) {
     float *staging = (float *)(w->arena + w->L.staging);
+    const size_t ws = d.wstride, np = d.nparam;
     for (int s0 = 0; s0 < in->weights_count; s0 += STAGING_AGENTS) {
       const int n = std::min(STAGING_AGENTS, in->weights_count - s0);
-      ECO_CU(cudaMemcpy2DAsync(staging, WSTRIDE * 4, in->weights_host + (size_t)s0 * NPARAM,
-                               NPARAM * 4, NPARAM * 4, n, cudaMemcpyHostToDevice, w->stream));
-      launch_weights_to_physical(staging, d.weights + (size_t)(in->weights_first + s0) * WSTRIDE,
-                                 n, w->n_sms, w->stream);
+      ECO_CU(cudaMemcpy2DAsync(staging, ws * 4, in->weights_host + (size_t)s0 * np, np * 4,
+                               np * 4, n, cudaMemcpyHostToDevice, w->stream));
+      launch_weights_to_physical(staging, d.weights + (size_t)(in->weights_first + s0) * ws, n,
+                                 d.controller, w->n_sms, w->stream);
       ECO_CU(cudaGetLastError());
     }
   }
@@ -923,7 +952,9 @@ int eco_batch_create(EcoWorld *const *worlds, int n, EcoBatch **out) {
   *out = nullptr;
   if (!worlds || n < 1 || n > 1024) return ECO_EINVAL;
   for (int i = 0; i < n; ++i)
-    if (!worlds[i] || worlds[i]->device != worlds[0]->device) return ECO_EINVAL;
+    if (!worlds[i] || worlds[i]->device != worlds[0]->device ||
+        worlds[i]->p.controller != worlds[0]->p.controller)
+      return ECO_EINVAL;
   EcoBatch *b = new (std::nothrow) EcoBatch;
   if (!b) return ECO_ENOMEM;
   int rc = batch_init(*b, worlds, n, nullptr);
@@ -1031,7 +1062,7 @@ int eco_world_profile_read(EcoWorld *w, double *ms, int64_t *launches) {
 const char *eco_kernel_name(int k) {
   static const char *names[ECO_NKERNELS] = {
       "regrow", "observe_lstm", "move_claim", "move_apply", "physio",
-      "birth_claim", "scan", "regrow_spawn", "agents_fused"};
+      "birth_claim", "scan", "regrow_spawn", "agents_fused", "observe_paper"};
   return (k >= 0 && k < ECO_NKERNELS) ? names[k] : "?";
 }
 

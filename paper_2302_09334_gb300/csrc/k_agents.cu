@@ -179,6 +179,7 @@ __device__ inline void init_child(const WorldDev &wd, int s, int cell, int k, in
   wd.low_ctr[child] = 0;
   wd.age[child] = 0;
   wd.action[child] = 0;
+  wd.prev_act[child] = 0;
   wd.ate[child] = 0;
   wd.arrive[child] = 0u;
   wd.birth_cell[child] = -1;
@@ -459,14 +460,15 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
       wd.y[s] = py[k];
       wd.x[s] = px[k];
     }
-    bool dead;
+    bool dead, ate = false;
     if (kil[k]) {
       dead = true;
     } else {
       const uint32_t bit = 1u << (px[k] & 31);
       const uint32_t old = atomicAnd(&res[py[k] * Wp + (px[k] >> 5)], ~bit);
+      ate = (old & bit) != 0u;
       float e = en[k];
-      if (old & bit) e = __fadd_rn(e, wd.e_gain);
+      if (ate) e = __fadd_rn(e, wd.e_gain);
       e = __fsub_rn(e, wd.e_decay);
       e = fminf(e, wd.e_max);
       wd.energy[s] = e;
@@ -480,6 +482,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
         wd.repr_ctr[s] = rep[k];
       }
     }
+    wd.ate[s] = ate ? 1 : 0;  // an input of the paper's controller next step
     if (dead) {
       al[k] = 0;
       wd.alive[s] = 0;
@@ -557,24 +560,28 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
 // indices starting at a multiple of 4, so one Philox draw serves it; the
 // bias rows of a block are permuted and take one draw per element.
 constexpr int SPAWN_THREADS = 256;
-constexpr int NVEC = WSTRIDE / 4;  // 5840 float4 per agent
+constexpr int NVEC = WSTRIDE / 4;  // 5840 float4 per agent (LSTM(32) controller)
 
 // Float4 number vi of an agent's physical weights after adding scale * N_j
-// (stream tag, t, id) to `base`.
+// (stream tag, t, id) to `base`.  The paper controller's rows are in
+// logical order, so every float4 is four consecutive parameters.
 __device__ inline float4 mutate4(const WorldDev &wd, int vi, float4 base, uint32_t tag,
                                  uint32_t t, uint32_t id, float scale) {
   const int p = vi * 4;
   float out[4] = {base.x, base.y, base.z, base.w};
+  const bool paper = wd.controller == ECO_CTRL_PAPER;
   const int o = p % BLK_FLOATS;
-  const bool bias_vec = p < TAIL && o >= BLK_ROWS * NIN;
+  const bool bias_vec = !paper && p < TAIL && o >= BLK_ROWS * NIN;
   if (!bias_vec) {
-    const int j = logical_of_phys(p);  // multiple of 4, or -1 for padding
+    // multiple of 4, or -1 for padding
+    const int j = paper ? (p < PC_NPARAM ? p : -1) : logical_of_phys(p);
+    const int np = paper ? PC_NPARAM : NPARAM;
     if (j >= 0) {
       float z[4];
       normals4(wd.key0, wd.key1, (uint32_t)j >> 2, t, tag, id, z);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        out[i] = (j + i < NPARAM) ? __fadd_rn(out[i], __fmul_rn(scale, z[i])) : 0.f;
+        out[i] = (j + i < np) ? __fadd_rn(out[i], __fmul_rn(scale, z[i])) : 0.f;
     } else {
       out[0] = out[1] = out[2] = out[3] = 0.f;
     }
@@ -605,7 +612,8 @@ __device__ inline void spawn_births(const BatchDev &b, int *pre, int cta, int n_
     pre[b.n] = run;
   }
   __syncthreads();
-  const long long total = (long long)pre[b.n] * NVEC;
+  const int nvec = b.wstride / 4;
+  const long long total = (long long)pre[b.n] * nvec;
   const long long stride = (long long)n_cta * blockDim.x;
   for (long long g0 = (long long)cta * blockDim.x + threadIdx.x; g0 < total;
        g0 += SPAWN_UNROLL * stride) {
@@ -618,8 +626,8 @@ __device__ inline void spawn_births(const BatchDev &b, int *pre, int cta, int n_
       const long long g = g0 + u * stride;
       dst[u] = nullptr;
       if (g >= total) continue;
-      const int bi = (int)(g / NVEC);
-      vi[u] = (int)(g % NVEC);
+      const int bi = (int)(g / nvec);
+      vi[u] = (int)(g % nvec);
       int lo = 0, hi = b.n - 1;
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -630,8 +638,8 @@ __device__ inline void spawn_births(const BatchDev &b, int *pre, int cta, int n_
       par[u] = wd.birth_parent[k];
       const int child = wd.birth_child[k];
       wdu[u] = &wd;
-      in[u] = reinterpret_cast<const float4 *>(wd.weights + (size_t)par[u] * WSTRIDE)[vi[u]];
-      dst[u] = reinterpret_cast<float4 *>(wd.weights + (size_t)child * WSTRIDE) + vi[u];
+      in[u] = reinterpret_cast<const float4 *>(wd.weights + (size_t)par[u] * b.wstride)[vi[u]];
+      dst[u] = reinterpret_cast<float4 *>(wd.weights + (size_t)child * b.wstride) + vi[u];
     }
 #pragma unroll
     for (int u = 0; u < SPAWN_UNROLL; ++u) {
@@ -662,11 +670,12 @@ __global__ void __launch_bounds__(SPAWN_THREADS, 4) k_tail(const __grid_constant
 // Initial weights of slots [0, n0): w_init_std * N_j of (TAG_INIT_W, 0, slot).
 __global__ void __launch_bounds__(SPAWN_THREADS) k_init_weights(const WorldDev *wdp, int n0) {
   const WorldDev &wd = *wdp;
-  const long long total = (long long)n0 * NVEC;
+  const int nvec = wd.wstride / 4;
+  const long long total = (long long)n0 * nvec;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(g / NVEC), vi = (int)(g % NVEC);
-    reinterpret_cast<float4 *>(wd.weights + (size_t)s * WSTRIDE)[vi] =
+    const int s = (int)(g / nvec), vi = (int)(g % nvec);
+    reinterpret_cast<float4 *>(wd.weights + (size_t)s * wd.wstride)[vi] =
         mutate4(wd, vi, make_float4(0.f, 0.f, 0.f, 0.f), TAG_INIT_W, 0u, (uint32_t)s,
                 wd.w_init_std);
   }

@@ -65,6 +65,7 @@ __global__ void k_init_agents(WorldDev wd, int n0, const int32_t *py,
   wd.low_ctr[s] = 0;
   wd.age[s] = 0;
   wd.action[s] = 0;
+  wd.prev_act[s] = 0;
   wd.forced[s] = 0;
   wd.killed[s] = 0;
   wd.ate[s] = 0;
@@ -138,36 +139,52 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_alive_list(WorldDev wd) {
   if (threadIdx.x == 0) wd.ctr->pop = sh[32];
 }
 
-// Weight rows (WSTRIDE floats apart) between the logical parameter order
-// (the host's) and the physical block order (the device's).
-__global__ void k_weights_to_physical(const float *logical, float *physical, int n) {
-  const long long total = (long long)n * WSTRIDE;
+// Weight rows (`stride` floats apart) between the logical parameter order
+// (the host's) and the physical order (the device's): the block permutation
+// of the LSTM(32) controller, the identity for the paper's controller.
+__device__ inline int logical_of(int controller, int p) {
+  if (controller == ECO_CTRL_PAPER) return p < PC_NPARAM ? p : -1;
+  return logical_of_phys(p);
+}
+
+__global__ void k_weights_to_physical(const float *logical, float *physical, int n,
+                                      int controller, int stride) {
+  const long long total = (long long)n * stride;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
-    const int a = (int)(g / WSTRIDE), p = (int)(g % WSTRIDE);
-    const int j = logical_of_phys(p);
-    physical[g] = j >= 0 ? logical[(size_t)a * WSTRIDE + j] : 0.f;
+    const int a = (int)(g / stride), p = (int)(g % stride);
+    const int j = logical_of(controller, p);
+    physical[g] = j >= 0 ? logical[(size_t)a * stride + j] : 0.f;
   }
 }
 
-__global__ void k_weights_to_logical(const float *physical, float *logical, int n) {
-  const long long total = (long long)n * WSTRIDE;
+__global__ void k_weights_to_logical(const float *physical, float *logical, int n,
+                                     int controller, int stride) {
+  const long long total = (long long)n * stride;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
-    const int a = (int)(g / WSTRIDE), p = (int)(g % WSTRIDE);
-    const int j = logical_of_phys(p);
-    if (j >= 0) logical[(size_t)a * WSTRIDE + j] = physical[g];
+    const int a = (int)(g / stride), p = (int)(g % stride);
+    const int j = logical_of(controller, p);
+    if (j >= 0) logical[(size_t)a * stride + j] = physical[g];
   }
 }
 
-void launch_weights_to_physical(const float *logical, float *physical, int n, int n_sms,
-                                cudaStream_t s) {
-  if (n > 0) k_weights_to_physical<<<4 * n_sms, 256, 0, s>>>(logical, physical, n);
+static int stride_of(int controller) {
+  return controller == ECO_CTRL_PAPER ? PC_WSTRIDE : WSTRIDE;
 }
 
-void launch_weights_to_logical(const float *physical, float *logical, int n, int n_sms,
-                               cudaStream_t s) {
-  if (n > 0) k_weights_to_logical<<<4 * n_sms, 256, 0, s>>>(physical, logical, n);
+void launch_weights_to_physical(const float *logical, float *physical, int n, int controller,
+                                int n_sms, cudaStream_t s) {
+  if (n > 0)
+    k_weights_to_physical<<<4 * n_sms, 256, 0, s>>>(logical, physical, n, controller,
+                                                    stride_of(controller));
+}
+
+void launch_weights_to_logical(const float *physical, float *logical, int n, int controller,
+                               int n_sms, cudaStream_t s) {
+  if (n > 0)
+    k_weights_to_logical<<<4 * n_sms, 256, 0, s>>>(physical, logical, n, controller,
+                                                   stride_of(controller));
 }
 
 void launch_init_world(const WorldDev *wd_host, WorldDev *wd_dev, int n0,

@@ -25,6 +25,7 @@ _SLOT = {
     "energy": (np.float32, 1), "repr_ctr": (np.int32, 1), "low_ctr": (np.int32, 1),
     "age": (np.int32, 1), "h": (np.float32, HID), "c": (np.float32, HID),
     "action": (np.int32, 1), "logits": (np.float32, NACT),
+    "prev_action": (np.int32, 1), "ate": (np.uint8, 1),
 }
 ALL_FIELDS = tuple(_GRID) + tuple(_SLOT)
 
@@ -86,6 +87,7 @@ class World(_Configurable):
         import torch
         self.p = params
         self.seed = int(seed)
+        self.nparam = _lib.NPARAM_OF[int(getattr(params, "controller", 0))]
         self._c = to_c_params(params)
         L = lib()
         nbytes = L.eco_world_bytes(ctypes.byref(self._c))
@@ -136,7 +138,7 @@ class World(_Configurable):
             setattr(st, f + "_host", out[f].ctypes.data)
         if weights is not None:
             first, count = weights
-            out["weights"] = np.zeros((count, NPARAM), np.float32)
+            out["weights"] = np.zeros((count, self.nparam), np.float32)
             st.weights_host = out["weights"].ctypes.data
             st.weights_first, st.weights_count = int(first), int(count)
         check(lib().eco_world_read_state(self._h, ctypes.byref(st)), "eco_world_read_state")
@@ -153,7 +155,7 @@ class World(_Configurable):
             keep.append(a)
             setattr(st, f + "_host", a.ctypes.data)
         if "weights" in state:
-            wts = np.ascontiguousarray(state["weights"], np.float32).reshape(-1, NPARAM)
+            wts = np.ascontiguousarray(state["weights"], np.float32).reshape(-1, self.nparam)
             keep.append(wts)
             st.weights_host = wts.ctypes.data
             st.weights_first, st.weights_count = int(weights_first), wts.shape[0]
