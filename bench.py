@@ -344,6 +344,7 @@ def bench_ours(args, params, rank, world_size, dist):
     if world_size == 1 and not args.no_many:
         line["batched"] = bench_batched(args, local)
         line["served"] = bench_served(args, local)
+        line["paper_preset"] = bench_paper_preset(args, local)
     if not args.no_cpu_baseline:
         cores = args.cpu_cores or os.cpu_count() or 1
         v, steps, dt = run_oracle_pool(params, args.cpu_budget, 0, 100000, cores)
@@ -430,6 +431,57 @@ def bench_batched(args, local):
     return out
 
 
+def bench_paper_preset(args, local):
+    """The paper's own natural environment (App. B.4, B.5): 200x400 grid, 330
+    agents at the start (at most 1000), the CNN+LSTM(4) controller with
+    sampled actions.  The world (~10 MB of weights) stays in L2 over a long
+    run, as it would over the paper's 10^6 steps, so it is not flushed; the
+    timed region is one call of paper_steps steps (CUDA-graph chunks of the
+    tuned length).  The paper reports 10^6 steps in about 20 minutes on an
+    unnamed GPU (App. B.4): about 833 steps/s."""
+    import torch
+    from paper_2302_09334_gb300._lib import C_AGENT_STEPS
+    from paper_2302_09334_gb300.params import paper_natural
+    from paper_2302_09334_gb300.world import World
+    p = paper_natural()
+    stream = torch.cuda.Stream(local)
+    tuner = World(p, 1000, device=local, stream=stream)
+    tuned = tuner.autotune(trial_steps=16)
+    tuner.close()
+    cfg = {k: tuned[k] for k in ("fused", "spawn_ctas_per_sm", "steps_per_graph")}
+    w = World(p, 0, device=local, stream=stream)
+    w.set_config(**cfg)
+    w.step(args.paper_warmup)
+    w.sync()
+    c0 = w.counters()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    w.step(args.paper_steps)
+    end.record(stream)
+    end.synchronize()
+    ms = start.elapsed_time(end)
+    c1 = w.counters()
+    agent_steps = int(c1[C_AGENT_STEPS] - c0[C_AGENT_STEPS])
+    w.profile(True, max_steps=200)
+    w.step(200)
+    prof = w.profile_read()
+    w.profile(False)
+    w.close()
+    steps_per_s = args.paper_steps / (ms / 1e3)
+    return {"workload": "paper_natural", "steps": args.paper_steps,
+            "warmup": args.paper_warmup, "steps_per_s": steps_per_s,
+            "agent_steps_per_s": agent_steps / (ms / 1e3), "ms_per_step": ms / args.paper_steps,
+            "mean_population": agent_steps / args.paper_steps,
+            "population_end": int(c1[1]), "births": int(c1[2] - c0[2]),
+            "deaths": int(c1[3] - c0[3]),
+            "launch_config": cfg,
+            "kernel_ms_per_step": {k: v[0] / v[1] for k, v in prof.items() if v[1]},
+            "minutes_per_1e6_steps": 1e6 / steps_per_s / 60.0,
+            "paper_context": "10^6 steps in about 20 min on an unnamed GPU, JAX (App. B.4): "
+                             "about 833 steps/s",
+            "l2": "not flushed: the world (about 10 MB of weights) stays L2-resident over a run"}
+
+
 def bench_served(args, local):
     """Serving: Poisson request arrivals (20/s), admission by a 120 GB
     device-memory budget, continuous batching in chunks of 100 steps; the
@@ -471,6 +523,8 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=1000)
     ap.add_argument("--batched-warmup", type=int, default=10)
     ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--paper-steps", type=int, default=20000)
+    ap.add_argument("--paper-warmup", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

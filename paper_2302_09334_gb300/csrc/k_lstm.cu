@@ -407,8 +407,10 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
         if (lane < NACT) E.logits_row[lane] = mine;
         if (lane == 0) {
           *E.action = best;
+          const int moved = E.forced >= 0 ? E.forced : best;
+          E.wd->prev_act[E.slot] = (moved >= 0 && moved < NACT) ? moved : 0;
           pending.resolve();
-          pending.issue(*E.wd, E.slot, E.y, E.x, E.forced >= 0 ? E.forced : best);
+          pending.issue(*E.wd, E.slot, E.y, E.x, moved);
         }
         __syncwarp();
         if (lane == 0) {

@@ -15,7 +15,12 @@ Tolerances (derived from the arithmetic; see the design notes):
     adds its own rounding, the initial draw one more):
     |gpu - oracle| <= (g + 1) 1e-6 (|oracle| + |parent| + sigma);
   * actions: equal, except where the oracle's top-two logit margin is below
-    1e-5 * max(1, max|logit|) (flagged, not counted as a mismatch).
+    1e-5 * max(1, max|logit|) (flagged, not counted as a mismatch);
+  * sampled actions (the paper's controller): equal, except where the
+    agent's uniform lies within 2e-3 * max(1, max|logit|) of a cumulative
+    probability of the oracle's softmax at temperature 1/50 (the logit
+    tolerance, scaled by 50 for the two logits of a difference, bounds the
+    error of every cumulative probability by 1e-3 * max(1, max|logit|)).
 """
 from __future__ import annotations
 
@@ -23,6 +28,7 @@ import numpy as np
 
 RNN_TOL = 1e-5
 W_TOL = 1e-6
+SAMPLE_TOL = 2e-3
 
 
 def rnn_close(gpu, ref, what):
@@ -67,7 +73,7 @@ def compare(gs: dict, ow, where: str, check_rnn: bool = True) -> dict:
     np.testing.assert_array_equal(gs["alive"], ow.alive, err_msg=f"{where}: alive")
     np.testing.assert_array_equal(gs["slot_map"], ow.slot_map, err_msg=f"{where}: slot_map")
     live = ow.alive.astype(bool)
-    for f in ("y", "x", "repr_ctr", "low_ctr", "age"):
+    for f in ("y", "x", "repr_ctr", "low_ctr", "age", "prev_action", "ate"):
         np.testing.assert_array_equal(gs[f][live], getattr(ow, f)[live], err_msg=f"{where}: {f}")
     np.testing.assert_array_equal(gs["energy"][live].view(np.uint32),
                                   ow.energy[live].view(np.uint32), err_msg=f"{where}: energy")
@@ -91,6 +97,31 @@ def compare_actions(g_action, g_logits, ow, acted, where: str) -> int:
     return int((diff & flagged).sum())
 
 
+def near_sample_boundary(logits, u):
+    """Oracle logits [n, 5], uniforms [n] -> bool [n]: u within the sampling
+    tolerance of a cumulative probability of softmax(50 logits)."""
+    lg = np.asarray(logits, np.float64)
+    z = np.exp(50.0 * (lg - lg.max(axis=1, keepdims=True)))
+    cdf = np.cumsum(z / z.sum(axis=1, keepdims=True), axis=1)[:, :4]
+    tol = SAMPLE_TOL * np.maximum(1.0, np.abs(lg).max(axis=1))
+    return (np.abs(cdf - np.asarray(u)[:, None]) < tol[:, None]).any(axis=1)
+
+
+def compare_sampled_actions(g_action, g_logits, ow, acted, t, where: str) -> int:
+    """The paper controller's logits and sampled actions of the agents that
+    acted at step t; returns the number of flagged differences."""
+    from oracle import pyoracle
+    idx = np.flatnonzero(acted)
+    if idx.size == 0:
+        return 0
+    rnn_close(g_logits[idx], ow.logits[idx], f"{where}: logits")
+    u = np.array([pyoracle.action_uniform(ow.seed, t, int(s)) for s in idx])
+    diff = g_action[idx] != ow.action[idx]
+    flagged = near_sample_boundary(ow.logits[idx], u)
+    assert not (diff & ~flagged).any(), f"{where}: sampled actions differ at {idx[diff & ~flagged]}"
+    return int((diff & flagged).sum())
+
+
 def check_births(gw, ow, nb, sigma, where, gen):
     """Weights of this step's children (see the tolerance rules above);
     gen[slot] is the generation of the agent in the slot (updated here)."""
@@ -101,10 +132,11 @@ def check_births(gw, ow, nb, sigma, where, gen):
     for par, ch in zip(parents, children):
         wp = gw.read_state(fields=(), weights=(int(par), 1))["weights"][0]
         wc = gw.read_state(fields=(), weights=(int(ch), 1))["weights"][0]
-        expected = pyoracle.fill_normals(ow.seed, pyoracle.TAG_MUT, t, int(par), sigma, wp)
+        n = wp.shape[0]
+        expected = pyoracle.fill_normals_n(ow.seed, pyoracle.TAG_MUT, t, int(par), sigma, n, wp)
         weights_close(wc, expected, sigma, f"{where} child {ch} (mutation)")
         gen[ch] = gen[par] + 1
-        weights_drift_close(wc, ow.weights[ch], ow.weights[par], sigma, gen[ch],
+        weights_drift_close(wc, ow.weights[ch, :n], ow.weights[par, :n], sigma, gen[ch],
                             f"{where} child {ch} (generation {gen[ch]})")
 
 
@@ -162,7 +194,13 @@ def run_forced(gw, ow, steps: int, where: str, weight_std: float,
         ow_action_saved = ow.action.copy()
         try:
             ow.action[:] = ow.move_action
-            flagged += compare_actions(gs["action"], gs["logits"], ow, acted & ~reborn, label)
+            if getattr(ow.p, "controller", 0) == 1:
+                flagged += compare_sampled_actions(gs["action"], gs["logits"], ow,
+                                                   acted & ~reborn, int(ow.counters[0]) - 1,
+                                                   label)
+            else:
+                flagged += compare_actions(gs["action"], gs["logits"], ow, acted & ~reborn,
+                                           label)
         finally:
             ow.action[:] = ow_action_saved
         if nb:
