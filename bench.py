@@ -34,14 +34,22 @@ sys.path.insert(0, ROOT)
 LSTM_BYTES_PER_AGENT = 93332 + 512 + 36
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one observation+LSTM launch per agent, from the
-# ncu capture in profiles/k_lstm_paper_200x400_held3440.md (327.84 MB at 3,440
-# agents); traffic grows with the agents of a launch, so it is scaled by them.
-LSTM_TRAFFIC_PER_AGENT = 327.835e6 / 3440
+# ncu capture in profiles/k_lstm_paper_200x400_held3440.md; traffic grows with
+# the agents of a launch, so it is scaled by them.  None until the counters
+# are taken again for the current kernel.
+LSTM_TRAFFIC_PER_AGENT = None
 
 
-def lstm_bytes(n_agents: int, H: int, W: int) -> int:
+# the same for the paper's controller: 2,445 FP32 parameters, h and c of 4
+# units read and written, position, previous action (read + written), ate,
+# logits and action
+PAPER_BYTES_PER_AGENT = 2445 * 4 + 32 + 8 + 8 + 1 + 20 + 4
+
+
+def lstm_bytes(n_agents: int, H: int, W: int, controller: int = 0) -> int:
     # + the three observation channels of the grid, one bit per cell
-    return n_agents * LSTM_BYTES_PER_AGENT + 3 * H * W // 8
+    per = PAPER_BYTES_PER_AGENT if controller == 1 else LSTM_BYTES_PER_AGENT
+    return n_agents * per + 3 * H * W // 8
 
 
 def load_peaks():
@@ -211,11 +219,16 @@ def bench_ours(args, params, rank, world_size, dist):
     dev = torch.device("cuda", local)
     # launch configuration: tuned on a world of the same shape (seed + 1000)
     # so that the measured world starts from step 0
-    tuner = World(params, seed=1000 + rank, device=local)
-    tuned = tuner.autotune(trial_steps=8)
-    tuner.close()
-    del tuner
-    cfg = {k: tuned[k] for k in ("fused", "spawn_ctas_per_sm", "steps_per_graph")}
+    if args.no_tune:
+        probe = World(params, seed=1000 + rank, device=local)
+        cfg = probe.get_config()
+        probe.close()
+    else:
+        tuner = World(params, seed=1000 + rank, device=local)
+        tuned = tuner.autotune(trial_steps=8)
+        tuner.close()
+        del tuner
+        cfg = {k: tuned[k] for k in ("fused", "spawn_ctas_per_sm", "steps_per_graph")}
     # the timed world steps by plain one-step CUDA graphs; its twin (same
     # seed, hence the same states step by step) runs the profiled graphs
     # whose event nodes give the per-kernel times
@@ -316,9 +329,10 @@ def bench_ours(args, params, rank, world_size, dist):
     if rank != 0:
         return
     value = agent_steps / (total_ms / 1e3)
-    lstm_ms, lstm_n = prof["observe_lstm"]
+    ctrl_kernel = "observe_paper" if params.controller == 1 else "observe_lstm"
+    lstm_ms, lstm_n = prof[ctrl_kernel]
     peak, peak_kind = load_peaks()
-    bytes_lstm = sum(lstm_bytes(n, params.H, params.W) for n in pops)
+    bytes_lstm = sum(lstm_bytes(n, params.H, params.W, params.controller) for n in pops)
     achieved = bytes_lstm / (lstm_ms / 1e3) / 1e9 if lstm_ms > 0 else None
     line = {
         "metric": "agent-steps/s at 200x400", "value": value, "unit": "agent-steps/s",
@@ -329,10 +343,11 @@ def bench_ours(args, params, rank, world_size, dist):
         "cell_steps_per_s": cell_steps / (total_ms / 1e3),
         "mean_population": agent_steps / max(args.steps * world_size, 1),
         "kernel_ms_per_step": {k: v[0] / v[1] for k, v in prof.items() if v[1]},
-        "roofline": {"kernel": "observe_lstm", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": ctrl_kernel, "bound": "hbm", "achieved": achieved,
                      "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
-                     "traffic": LSTM_TRAFFIC_PER_AGENT * (sum(pops) / max(len(pops), 1)),
+                     "traffic": (LSTM_TRAFFIC_PER_AGENT * (sum(pops) / max(len(pops), 1))
+                                 if params.controller == 0 and LSTM_TRAFFIC_PER_AGENT else None),
                      "bytes_per_launch": bytes_lstm / max(lstm_n, 1)},
         "gpu_launches": kps * args.steps,
         "launch_config": cfg,
@@ -523,6 +538,8 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=1000)
     ap.add_argument("--batched-warmup", type=int, default=10)
     ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="default launch configuration (no tuner world before the timed one)")
     ap.add_argument("--paper-steps", type=int, default=20000)
     ap.add_argument("--paper-warmup", type=int, default=100)
     args = ap.parse_args()
