@@ -353,6 +353,11 @@ struct OrWorld {
   uint8_t *alive, *ate, *killed, *wants;
   int32_t *y, *x, *repr_ctr, *low_ctr, *age, *action, *target, *cand;
   int32_t *claim, *birth_parent, *birth_child, *free_list, *move_action, *prev_act;
+  /* lab-environment greediness (App. C): per slot, bit 0 = a resource was in
+   * view during the current window, bit 1 = ate during it; windows with a
+   * resource in view (T_r) and with a consumption (C_r) */
+  uint8_t *lab_flags;
+  int32_t *lab_t, *lab_c;
   float *energy, *weights;
   double *h, *c, *logits;
   uint32_t *thr;
@@ -392,6 +397,9 @@ void *or_world_field(OrWorld *w, int f) {
     case OR_F_BIRTH_CHILD: return w->birth_child;
     case OR_F_MOVE_ACTION: return w->move_action;
     case OR_F_PREV_ACTION: return w->prev_act;
+    case OR_F_LAB_FLAGS: return w->lab_flags;
+    case OR_F_LAB_T: return w->lab_t;
+    case OR_F_LAB_C: return w->lab_c;
     default: return NULL;
   }
 }
@@ -404,6 +412,7 @@ void or_world_destroy(OrWorld *w) {
   free(w->action); free(w->target); free(w->cand); free(w->claim);
   free(w->birth_parent); free(w->birth_child); free(w->free_list);
   free(w->move_action); free(w->prev_act);
+  free(w->lab_flags); free(w->lab_t); free(w->lab_c);
   free(w->energy); free(w->weights); free(w->h); free(w->c); free(w->logits);
   free(w->thr);
   free(w->agent_id); free(w->snap_id); free(w->snap_cell);
@@ -535,6 +544,9 @@ int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
   w->free_list = calloc(C1, 4);
   w->move_action = calloc(C1, 4);
   w->prev_act = calloc(C1, 4);
+  w->lab_flags = calloc(C1, 1);
+  w->lab_t = calloc(C1, 4);
+  w->lab_c = calloc(C1, 4);
   w->energy = calloc(C1, sizeof(float));
   w->weights = calloc(C1 * OR_NPARAM, sizeof(float));
   w->h = calloc(C1 * OR_HID, sizeof(double));
@@ -548,7 +560,7 @@ int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
       !w->alive || !w->ate || !w->killed || !w->wants || !w->y || !w->x ||
       !w->repr_ctr || !w->low_ctr || !w->age || !w->action || !w->target ||
       !w->cand || !w->birth_parent || !w->birth_child || !w->free_list || !w->move_action ||
-      !w->prev_act ||
+      !w->prev_act || !w->lab_flags || !w->lab_t || !w->lab_c ||
       !w->energy || !w->weights || !w->h || !w->c || !w->logits || !w->thr) {
     or_world_destroy(w);
     return -2;
@@ -602,6 +614,11 @@ int or_world_sync(OrWorld *w) {
   }
   w->counters[OR_C_POP] = pop;
   new_identities(w);
+  for (int s = 0; s < p->capacity; ++s) {
+    w->lab_flags[s] = 0;
+    w->lab_t[s] = 0;
+    w->lab_c[s] = 0;
+  }
   return 0;
 }
 
@@ -638,6 +655,8 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
        * sampled from the softmax at temperature 1/50 */
       double obs[OR_PC_NOBS];
       or_pc_observe(p, w->res, w->wall, w->slot_map, w->y[s], w->x[s], obs);
+      for (int k = 0; k < OR_PC_VIEW * OR_PC_VIEW; ++k)
+        if (obs[3 * k] != 0.0) w->lab_flags[s] |= 1;   /* a resource in view */
       or_pc_forward(w->weights + (size_t)s * OR_NPARAM, obs, w->prev_act[s], ate_last,
                     w->h + (size_t)s * OR_HID, w->c + (size_t)s * OR_HID,
                     w->logits + (size_t)s * OR_NACT);
@@ -648,6 +667,8 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
     double obs[OR_NOBS];
     or_observe(p, w->res, w->wall, w->slot_map, w->y[s], w->x[s], w->energy[s],
                obs);
+    for (int k = 0; k < OR_VIEW * OR_VIEW; ++k)
+      if (obs[k] != 0.0) w->lab_flags[s] |= 1;     /* a resource in view */
     w->action[s] = or_lstm_step(w->weights + (size_t)s * OR_NPARAM, obs,
                                 w->h + (size_t)s * OR_HID,
                                 w->c + (size_t)s * OR_HID,
@@ -691,6 +712,7 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
     if (w->res[cell]) {
       w->res[cell] = 0;
       w->ate[s] = 1;
+      w->lab_flags[s] |= 2;
     }
   }
 
@@ -773,6 +795,9 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
     w->age[child] = 0;
     w->action[child] = 0;
     w->prev_act[child] = 0;
+    w->lab_flags[child] = 0;
+    w->lab_t[child] = 0;
+    w->lab_c[child] = 0;
     w->ate[child] = 0;
     for (int j = 0; j < OR_HID; ++j) {
       w->h[(size_t)child * OR_HID + j] = 0.0;
@@ -829,4 +854,17 @@ int or_world_analysis(OrWorld *w, int64_t *out) {
   }
   take_snapshot(w);
   return 0;
+}
+
+/* Greediness of the lab environments (App. C): a window ends now; every
+ * living agent counts it in T_r if a resource was in its view at some step
+ * of the window and in C_r if it ate during it. */
+void or_world_lab_window(OrWorld *w) {
+  for (int s = 0; s < w->p.capacity; ++s) {
+    if (w->alive[s]) {
+      w->lab_t[s] += w->lab_flags[s] & 1;
+      w->lab_c[s] += (w->lab_flags[s] >> 1) & 1;
+    }
+    w->lab_flags[s] = 0;
+  }
 }

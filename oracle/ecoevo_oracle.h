@@ -140,6 +140,10 @@ enum {
   OR_F_PREV_ACTION,  /* int32  [C]  action the agent moved with in its last
                                     step (0 for newborns): a paper-controller
                                     input                                    */
+  OR_F_LAB_FLAGS,    /* uint8  [C]  current window: bit 0 resource in view,
+                                    bit 1 ate                                */
+  OR_F_LAB_T,        /* int32  [C]  windows with a resource in view (T_r)    */
+  OR_F_LAB_C,        /* int32  [C]  windows with a consumption (C_r)         */
   OR_NFIELDS
 };
 enum {
@@ -231,6 +235,10 @@ int or_world_sync(OrWorld *w);
  * expectancy over a run of windows = sum of OR_A_AGE_SUM / sum of
  * OR_A_DEATHS.  create and sync start a window with fresh identities. */
 int or_world_analysis(OrWorld *w, int64_t *out);
+/* Lab-environment greediness G = C_r / T_r (App. C): ends the current
+ * window (the paper's are 20 steps): every living agent adds 1 to T_r if a
+ * resource was in its view during the window and 1 to C_r if it ate. */
+void or_world_lab_window(OrWorld *w);
 
 #ifdef __cplusplus
 }

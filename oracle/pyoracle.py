@@ -23,7 +23,8 @@ PC_OFF = {"W1": 0, "B1": 108, "W2": 112, "B2": 400, "WI": 408, "WH": 1656, "BL":
 
 (F_RES, F_WALL, F_SLOT_MAP, F_ALIVE, F_Y, F_X, F_ENERGY, F_REPR_CTR, F_LOW_CTR,
  F_AGE, F_H, F_C, F_ACTION, F_LOGITS, F_ATE, F_WEIGHTS, F_COUNTERS, F_THR,
- F_BIRTH_PARENT, F_BIRTH_CHILD, F_MOVE_ACTION, F_PREV_ACTION) = range(22)
+ F_BIRTH_PARENT, F_BIRTH_CHILD, F_MOVE_ACTION, F_PREV_ACTION, F_LAB_FLAGS, F_LAB_T,
+ F_LAB_C) = range(25)
 (C_T, C_POP, C_BIRTHS, C_DEATHS, C_DROPPED, C_BIRTHS_LAST, C_DEATHS_LAST,
  C_DROPPED_LAST, C_AGENT_STEPS) = range(9)
 NCOUNTERS = 9
@@ -110,6 +111,7 @@ def lib():
         L.or_world_field.restype = ctypes.c_void_p
         L.or_world_sync.argtypes = [ctypes.c_void_p]
         L.or_world_analysis.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.or_world_lab_window.argtypes = [ctypes.c_void_p]
         L.or_fill_normals_n.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                         ctypes.c_uint32, ctypes.c_float, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int]
@@ -308,6 +310,9 @@ class OracleWorld:
         self.birth_child = f(F_BIRTH_CHILD, np.int32, (C,))
         self.move_action = f(F_MOVE_ACTION, np.int32, (C,))
         self.prev_action = f(F_PREV_ACTION, np.int32, (C,))
+        self.lab_flags = f(F_LAB_FLAGS, np.uint8, (C,))
+        self.lab_t = f(F_LAB_T, np.int32, (C,))
+        self.lab_c = f(F_LAB_C, np.int32, (C,))
 
     def _field(self, fid, dtype, shape):
         addr = lib().or_world_field(self._h, fid)
@@ -338,6 +343,10 @@ class OracleWorld:
         (and start a new analysis window with fresh agent identities)."""
         if lib().or_world_sync(self._h) != 0:
             raise ValueError("inconsistent agent placement")
+
+    def lab_window(self) -> None:
+        """End a greediness window (or_world_lab_window)."""
+        lib().or_world_lab_window(self._h)
 
     def analysis(self) -> dict:
         """App. C metrics of the window that ends now (or_world_analysis);

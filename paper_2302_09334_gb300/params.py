@@ -83,6 +83,18 @@ def paper_natural() -> EcoParams:
                      wall_kills=1, controller=1)
 
 
+def lab(p: EcoParams, res_init_p: float, reproduction: bool = False,
+        capacity: int = 1) -> EcoParams:
+    """Lab environment of the paper's greediness study (App. C): the world
+    of `p` with one agent, resource regrowth switched off, initial resources
+    Bernoulli(res_init_p), and reproduction off unless asked for (then up
+    to `capacity` agents).  Load the evolved agent into slot 0 with
+    World.load_state; greediness comes from World.lab_window/lab_read."""
+    return p.replace(n_agents0=1, capacity=max(1, capacity), res_init_p=res_init_p,
+                     p_class=(0.0, 0.0, 0.0, 0.0), p_spont=0.0,
+                     t_repr=p.t_repr if reproduction else INT32_MAX)
+
+
 def held(p: EcoParams) -> EcoParams:
     """Held population: no energy decay and no reproduction, so the agent
     count stays at n_agents0 (roofline microbenchmark)."""
