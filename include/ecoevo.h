@@ -246,6 +246,18 @@ typedef struct EcoAnalysis {
  * share that stream.  Errors: ECO_EINVAL, ECO_ECUDA. */
 int eco_world_analysis_async(EcoWorld *world, EcoAnalysis *out_host);
 
+/* Greediness in the lab environments (App. C): G = C_r / T_r, where T_r
+ * counts the windows (the paper's are 20 steps) in which a resource was in
+ * the agent's field of view at the observation of some step (7x7 or 15x15
+ * by controller) and C_r the windows in which it ate.  eco_world_lab_window
+ * ends the current window (asynchronous, on the world's stream): every
+ * living agent adds its two window flags to its T_r, C_r.  A newborn starts
+ * at zero; create and load_state zero every slot.  eco_world_lab_read
+ * copies T_r, C_r of every slot (int32 [capacity] each, caller-owned host
+ * memory) after waiting for the stream.  Errors: ECO_EINVAL, ECO_ECUDA. */
+int eco_world_lab_window(EcoWorld *world);
+int eco_world_lab_read(EcoWorld *world, int32_t *seen_windows_host, int32_t *meal_windows_host);
+
 /* Wait for the world's stream; returns ECO_ETIMEOUT if a device wait ran
  * out, ECO_ECUDA on a CUDA error, else ECO_OK.  Synchronous. */
 int eco_world_sync(EcoWorld *world);

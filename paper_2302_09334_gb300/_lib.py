@@ -105,6 +105,8 @@ SIGNATURES = {
     "eco_world_sync": (ctypes.c_int, [_P]),
     "eco_world_counters_async": (ctypes.c_int, [_P, _P]),
     "eco_world_analysis_async": (ctypes.c_int, [_P, _P]),
+    "eco_world_lab_window": (ctypes.c_int, [_P]),
+    "eco_world_lab_read": (ctypes.c_int, [_P, _P, _P]),
     "eco_world_selftest_timeout": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "eco_world_clear_status": (ctypes.c_int, [_P]),
     "eco_world_params": (_P, [_P]),

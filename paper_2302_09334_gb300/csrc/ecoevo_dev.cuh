@@ -131,6 +131,8 @@ struct WorldDev {            // read-only while kernels run
   Counters *ctr;
   int32_t *snap_cell;        // [C] cell of each slot's agent at the window start, -1 none
   int32_t *prev_act;         // [C] action moved with in the last step (paper controller input)
+  uint8_t *lab_flags;        // [C] greediness window: bit 0 resource in view, bit 1 ate
+  int32_t *lab_t, *lab_c;    // [C] windows with a resource in view / with a meal
   unsigned long long *analysis;  // [ANALYSIS_WORDS] output of the analysis kernels
 };
 
@@ -297,6 +299,7 @@ void launch_weights_to_logical(const float *physical, float *logical, int n, int
 // analysis metrics of App. C (k_analysis.cu)
 void launch_analysis_reset(const WorldDev *wd_host, int n_sms, cudaStream_t s);
 void launch_analysis(const WorldDev *wd_host, int n_sms, cudaStream_t s);
+void launch_lab_window(const WorldDev *wd_host, int n_sms, cudaStream_t s);
 
 constexpr int SCAN_THREADS = 1024;
 constexpr int SLOT_BLOCK = 256;

@@ -52,7 +52,7 @@ struct Layout {
       slot_map, claim, bclaim, alive, killed, ate, flag, y, x, energy, repr_ctr,
       low_ctr, age, action, forced, target, birth_cell, arrive, h0, h1, c,
       logits, alive_list, free_list, birth_parent, birth_child, snap_cell, analysis,
-      prev_act, weights, staging, total;
+      prev_act, lab_flags, lab_t, lab_c, weights, staging, total;
 };
 
 Layout layout_of(const EcoParams *p) {
@@ -103,6 +103,9 @@ Layout layout_of(const EcoParams *p) {
   L.snap_cell = take(C1 * 4);
   L.analysis = take(ANALYSIS_WORDS * 8);
   L.prev_act = take(C1 * 4);
+  L.lab_flags = take(C1);
+  L.lab_t = take(C1 * 4);
+  L.lab_c = take(C1 * 4);
   L.weights = take(C1 * (size_t)wstride_of(p->controller) * 4);
   L.staging = take((size_t)STAGING_AGENTS * WSTRIDE * 4);
   L.total = off;
@@ -588,6 +591,9 @@ static void fill_descriptor(EcoWorld *w) {
   d.ctr = (Counters *)(a + L.ctr);
   d.snap_cell = (int32_t *)(a + L.snap_cell);
   d.prev_act = (int32_t *)(a + L.prev_act);
+  d.lab_flags = (uint8_t *)(a + L.lab_flags);
+  d.lab_t = (int32_t *)(a + L.lab_t);
+  d.lab_c = (int32_t *)(a + L.lab_c);
   d.analysis = (unsigned long long *)(a + L.analysis);
   w->dd = (WorldDev *)(a + L.wdev);
 }
@@ -748,6 +754,24 @@ int eco_world_analysis_async(EcoWorld *w, EcoAnalysis *out_host) {
   ECO_CU(cudaGetLastError());
   ECO_CU(cudaMemcpyAsync(out_host, w->hd.analysis, sizeof(EcoAnalysis), cudaMemcpyDeviceToHost,
                          w->stream));
+  return ECO_OK;
+}
+
+int eco_world_lab_window(EcoWorld *w) {
+  if (!w) return ECO_EINVAL;
+  launch_lab_window(&w->hd, w->n_sms, w->stream);
+  ECO_CU(cudaGetLastError());
+  return ECO_OK;
+}
+
+int eco_world_lab_read(EcoWorld *w, int32_t *seen_windows_host, int32_t *meal_windows_host) {
+  if (!w || !seen_windows_host || !meal_windows_host) return ECO_EINVAL;
+  ECO_CU(cudaStreamSynchronize(w->stream));
+  const size_t bytes = (size_t)w->p.capacity * 4;
+  if (bytes) {
+    ECO_CU(cudaMemcpy(seen_windows_host, w->hd.lab_t, bytes, cudaMemcpyDeviceToHost));
+    ECO_CU(cudaMemcpy(meal_windows_host, w->hd.lab_c, bytes, cudaMemcpyDeviceToHost));
+  }
   return ECO_OK;
 }
 
@@ -933,6 +957,10 @@ int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
       ECO_CU(cudaGetLastError());
     }
   }
+  // greediness counters start over with a loaded state
+  ECO_CU(cudaMemsetAsync(d.lab_flags, 0, C ? C : 1, w->stream));
+  ECO_CU(cudaMemsetAsync(d.lab_t, 0, (C ? C : 1) * 4, w->stream));
+  ECO_CU(cudaMemsetAsync(d.lab_c, 0, (C ? C : 1) * 4, w->stream));
   launch_rebuild(&w->hd, w->n_sms, w->stream);
   launch_regrow(w->self.bd, w->stream);  // the plane the next step observes
   ECO_CU(cudaGetLastError());

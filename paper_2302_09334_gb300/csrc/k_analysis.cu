@@ -106,6 +106,19 @@ __global__ void k_analysis_finish(WorldDev wd) {
   c.an_age_sum = 0ull;
 }
 
+// Lab-environment greediness (App. C): a window ends; every living agent
+// adds 1 to T_r if a resource was in its view during it, 1 to C_r if it ate.
+__global__ void k_lab_window(WorldDev wd) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < wd.C; s += gridDim.x * blockDim.x) {
+    const uint32_t f = wd.lab_flags[s];
+    if (wd.alive[s]) {
+      wd.lab_t[s] += (int)(f & 1u);
+      wd.lab_c[s] += (int)((f >> 1) & 1u);
+    }
+    wd.lab_flags[s] = 0;
+  }
+}
+
 static int analysis_grid(const WorldDev &wd, int n_sms) {
   const int work = max(wd.C, wd.H * wd.Wp);
   const int need = (work + ANALYSIS_THREADS - 1) / ANALYSIS_THREADS;
@@ -114,6 +127,11 @@ static int analysis_grid(const WorldDev &wd, int n_sms) {
 
 void launch_analysis_reset(const WorldDev *wd_host, int n_sms, cudaStream_t s) {
   k_analysis_reset<<<analysis_grid(*wd_host, n_sms), ANALYSIS_THREADS, 0, s>>>(*wd_host);
+}
+
+void launch_lab_window(const WorldDev *wd_host, int n_sms, cudaStream_t s) {
+  if (wd_host->C > 0)
+    k_lab_window<<<analysis_grid(*wd_host, n_sms), ANALYSIS_THREADS, 0, s>>>(*wd_host);
 }
 
 void launch_analysis(const WorldDev *wd_host, int n_sms, cudaStream_t s) {

@@ -178,6 +178,11 @@ __device__ inline void gather_input(const WorldDev &wd, int slot, int y, int x,
     e.v[98 + k] = (float)((masks[7 + r] >> cc) & 1u);
   }
   if (lane == 0) {
+    // greediness window: a resource in view
+    uint32_t any = 0u;
+#pragma unroll
+    for (int r = 0; r < 7; ++r) any |= masks[r];
+    if (any) wd.lab_flags[slot] |= 1u;
     e.v[147] = energy;
     e.slot = slot;
     e.y = y;

@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
     // the 15x15x3 view
     const uint32_t *res = (t & 1u) ? wd.res0 : wd.res1;
     const int half = PC_VIEW / 2;
+    bool res_seen = false;
     for (int k = lane; k < PC_VIEW * PC_VIEW; k += 32) {
       const int yy = y + k / PC_VIEW - half, xx = x + k % PC_VIEW - half;
       float r = 0.f, ag = 0.f, wl = 1.f;
@@ -153,7 +154,10 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
       S.obs[3 * k] = r;
       S.obs[3 * k + 1] = ag;
       S.obs[3 * k + 2] = wl;
+      res_seen |= r != 0.f;
     }
+    // greediness window: a resource in view
+    if (__any_sync(FULL, res_seen) && lane == 0) wd.lab_flags[s] |= 1u;
     const int prev = wd.prev_act[s];
     const int ate = wd.ate[s];
     const float *h_prev = ((t & 1u) ? wd.h1 : wd.h0) + (size_t)s * HID;

@@ -43,6 +43,14 @@ def analysis_record(a) -> dict:
     return out
 
 
+def greediness(seen_windows, meal_windows):
+    """G = C_r / T_r per agent (App. C); NaN where T_r = 0."""
+    T = np.asarray(seen_windows, np.float64)
+    C = np.asarray(meal_windows, np.float64)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(T > 0, C / np.maximum(T, 1), np.nan)
+
+
 def life_expectancy(records) -> float | None:
     """Mean age at death over consecutive analysis windows (App. C: the
     paper pools 500 steps); None when nobody died."""
@@ -183,6 +191,17 @@ class World(_Configurable):
         assert out.is_pinned() and out.numel() >= _lib.NANALYSIS and out.element_size() == 8
         check(lib().eco_world_analysis_async(self._h, ctypes.c_void_p(out.data_ptr())),
               "eco_world_analysis_async")
+
+    def lab_window(self) -> None:
+        """End a greediness window (App. C; the paper's are 20 steps)."""
+        check(lib().eco_world_lab_window(self._h), "eco_world_lab_window")
+
+    def lab_read(self):
+        """(T_r, C_r) per slot: windows with a resource in view, with a meal."""
+        T = np.zeros(self.p.capacity, np.int32)
+        C = np.zeros(self.p.capacity, np.int32)
+        check(lib().eco_world_lab_read(self._h, _ptr(T), _ptr(C)), "eco_world_lab_read")
+        return T, C
 
     def analysis(self) -> dict:
         """Synchronous analysis_async, decoded."""
