@@ -317,8 +317,10 @@ typedef struct EcoTuneResult {
  * steps of the batch: one knob after the other (fused, then
  * spawn_ctas_per_sm, then steps_per_graph), every candidate value three
  * times round-robin, trial_steps steps per trial (the graph-length trials
- * use trial_steps rounded up to a multiple of 16), keeping the candidate
- * with the lowest median time per step.  The worlds advance by
+ * use trial_steps rounded up to a multiple of 16); a knob moves to the
+ * candidate with the lowest median time per step only if that median is
+ * more than 3% below the current value's.  Candidates: fused {1, 0},
+ * spawn_ctas_per_sm {2, 4, 8}, steps_per_graph {1, 4, 16}.  The worlds advance by
  * out->steps_taken steps, exactly as eco_batch_step would have taken them.
  * Synchronous.  Errors: ECO_EINVAL (trial_steps outside 1..100000, profiling
  * on), ECO_ECUDA. */

@@ -455,7 +455,11 @@ int time_steps(EcoBatch &b, int64_t steps, cudaEvent_t e0, cudaEvent_t e1, doubl
 
 // One coordinate of the search: every candidate value of one knob, timed
 // round-robin (so that a population that drifts during the search affects
-// all of them alike); the median of each candidate's trials decides.
+// all of them alike); the median of each candidate's trials decides, and a
+// candidate replaces the current value (*best on entry, one of `cand`) only
+// if it is faster by more than SWITCH_MARGIN: trials of a few steps are
+// noisy, and births (which some knobs act on) come in bursts.
+constexpr double SWITCH_MARGIN = 0.03;
 template <class Apply>
 int tune_knob(EcoBatch &b, const std::vector<int> &cand, int64_t trial, int rounds, Apply apply,
               cudaEvent_t e0, cudaEvent_t e1, int64_t *steps, int *best, double *best_ms) {
@@ -470,15 +474,27 @@ int tune_knob(EcoBatch &b, const std::vector<int> &cand, int64_t trial, int roun
       t[i].push_back(ms);
     }
   }
-  *best_ms = 1e300;
+  std::vector<double> med(cand.size());
+  double cur_ms = -1.0;
   for (size_t i = 0; i < cand.size(); ++i) {
     std::sort(t[i].begin(), t[i].end());
-    const double med = t[i][t[i].size() / 2];
-    if (med < *best_ms) {
-      *best_ms = med;
-      *best = cand[i];
+    med[i] = t[i][t[i].size() / 2];
+    if (cand[i] == *best) cur_ms = med[i];
+  }
+  int choice = *best;
+  double choice_ms = cur_ms;
+  for (size_t i = 0; i < cand.size(); ++i) {
+    // the current value is not a candidate: the fastest candidate wins
+    const bool better = cur_ms < 0.0 ? (choice_ms < 0.0 || med[i] < choice_ms)
+                                     : (med[i] < (1.0 - SWITCH_MARGIN) * cur_ms &&
+                                        med[i] < choice_ms);
+    if (better) {
+      choice = cand[i];
+      choice_ms = med[i];
     }
   }
+  *best = choice;
+  *best_ms = choice_ms;
   return apply(*best);
 }
 
@@ -501,7 +517,7 @@ int autotune(EcoBatch &b, int trial_steps, EcoTuneResult *out) {
                    [&](int v) { return set_config(b, v, spawn, k); }, e0, e1, &steps, &fused, &ms);
   }
   if (!rc) {
-    rc = tune_knob(b, {1, 2, 4, 8}, trial_steps, rounds,
+    rc = tune_knob(b, {2, 4, 8}, trial_steps, rounds,
                    [&](int v) { return set_config(b, fused, v, k); }, e0, e1, &steps, &spawn, &ms);
   }
   if (!rc) {

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2302_09334_gb300.params import EcoParams, paper_natural
-from tests.parity import compare, run_forced
+from tests.parity import compare, run_forced, weights_close
 
 pytestmark = pytest.mark.gpu
 
@@ -33,7 +33,7 @@ def test_initial_state(eco, oracle):
     st = gw.read_state(weights=(0, SMALL.n_agents0))
     compare(st, ow, "init")
     assert st["weights"].shape == (SMALL.n_agents0, 2445)
-    np.testing.assert_array_equal(st["weights"][7], ow.weights[7, :2445])
+    weights_close(st["weights"][7], ow.weights[7, :2445], SMALL.w_init_std, "initial weights")
     assert not st["prev_action"].any() and not st["ate"].any()
     gw.close()
 
