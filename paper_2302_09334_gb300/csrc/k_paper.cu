@@ -139,22 +139,36 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
     float4 *dst = reinterpret_cast<float4 *>(S.w);
     for (int i = lane; i < PC_WSTRIDE / 4; i += 32) cp_async16(dst + i, src + i);
 
-    // the 15x15x3 view
+    // the 15x15x3 view: every lane issues the loads of its (up to 8) cells
+    // before it uses any of them
     const uint32_t *res = (t & 1u) ? wd.res0 : wd.res1;
     const int half = PC_VIEW / 2;
-    bool res_seen = false;
-    for (int k = lane; k < PC_VIEW * PC_VIEW; k += 32) {
+    constexpr int CELLS = PC_VIEW * PC_VIEW, PER_LANE = (CELLS + 31) / 32;
+    uint32_t rw[PER_LANE], ww[PER_LANE];
+    int occ[PER_LANE];
+#pragma unroll
+    for (int i = 0; i < PER_LANE; ++i) {
+      const int k = lane + 32 * i;
       const int yy = y + k / PC_VIEW - half, xx = x + k % PC_VIEW - half;
-      float r = 0.f, ag = 0.f, wl = 1.f;
-      if (yy >= 0 && yy < wd.H && xx >= 0 && xx < wd.W) {
-        r = (float)bit_at(res, wd.Wp, yy, xx);
-        wl = (float)bit_at(wd.wall, wd.Wp, yy, xx);
-        ag = (k != half * PC_VIEW + half && wd.slot_map[yy * wd.W + xx] >= 0) ? 1.f : 0.f;
+      rw[i] = 0u;
+      ww[i] = 1u;   // off the grid: wall
+      occ[i] = -1;
+      if (k < CELLS && yy >= 0 && yy < wd.H && xx >= 0 && xx < wd.W) {
+        rw[i] = res[yy * wd.Wp + (xx >> 5)] >> (xx & 31);
+        ww[i] = wd.wall[yy * wd.Wp + (xx >> 5)] >> (xx & 31);
+        occ[i] = (k != half * PC_VIEW + half) ? wd.slot_map[yy * wd.W + xx] : -1;
       }
-      S.obs[3 * k] = r;
-      S.obs[3 * k + 1] = ag;
-      S.obs[3 * k + 2] = wl;
-      res_seen |= r != 0.f;
+    }
+    bool res_seen = false;
+#pragma unroll
+    for (int i = 0; i < PER_LANE; ++i) {
+      const int k = lane + 32 * i;
+      if (k < CELLS) {
+        S.obs[3 * k] = (float)(rw[i] & 1u);
+        S.obs[3 * k + 1] = occ[i] >= 0 ? 1.f : 0.f;
+        S.obs[3 * k + 2] = (float)(ww[i] & 1u);
+        res_seen |= (rw[i] & 1u) != 0u;
+      }
     }
     // greediness window: a resource in view
     if (__any_sync(FULL, res_seen) && lane == 0) wd.lab_flags[s] |= 1u;
