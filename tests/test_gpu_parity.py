@@ -149,3 +149,31 @@ def test_held_population_stays_constant(eco):
     w.step(100)
     c = w.counters()
     assert c[1] == p.n_agents0 and c[2] == 0 and c[3] == 0
+
+
+def test_checkpoint_resume_is_exact(eco):
+    """n steps straight == k steps, save, load into a fresh world of the same
+    seed, n - k steps (every field, every weight, bit for bit)."""
+    p = small_20x40().replace(capacity=400, max_age=150)
+    a = eco.World(p, seed=31)
+    a.step(300)
+    b = eco.World(p, seed=31)
+    b.step(120)
+    saved = b.read_state(weights=(0, p.capacity))
+    b.close()
+    c = eco.World(p, seed=31)
+    c.step(7)                     # whatever it held before is replaced
+    c.load_state(saved)
+    c.step(180)
+    sa = a.read_state(weights=(0, p.capacity))
+    sc = c.read_state(weights=(0, p.capacity))
+    live = sa["alive"].astype(bool)
+    for k in sa:
+        if k in ("h", "c", "logits", "weights", "action", "prev_action", "ate", "y", "x",
+                 "energy", "repr_ctr", "low_ctr", "age"):
+            np.testing.assert_array_equal(sa[k][live], sc[k][live], err_msg=k)
+        else:
+            np.testing.assert_array_equal(sa[k], sc[k], err_msg=k)
+    assert int(sa["counters"][0]) == 300 and sa["counters"][2] > 0
+    a.close()
+    c.close()
