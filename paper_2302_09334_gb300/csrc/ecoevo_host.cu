@@ -11,9 +11,24 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ecoevo_dev.cuh"
 
 using namespace eco;
+
+namespace {
+
+// NVTX range over one call of the C ABI (a chunk of steps, a state copy, an
+// analysis): visible to profilers that record NVTX, free otherwise.
+struct Trace {
+  explicit Trace(const char *name) { nvtxRangePushA(name); }
+  ~Trace() { nvtxRangePop(); }
+  Trace(const Trace &) = delete;
+  Trace &operator=(const Trace &) = delete;
+};
+
+}  // namespace
 
 namespace {
 
@@ -729,11 +744,13 @@ void eco_world_destroy(EcoWorld *w) {
 }
 
 int eco_world_step(EcoWorld *w, int64_t n_steps) {
+  Trace trace("eco_world_step");
   if (!w) return ECO_EINVAL;
   return batch_step(w->self, n_steps);
 }
 
 int eco_world_step_forced(EcoWorld *w, const int32_t *actions, int actions_on_host) {
+  Trace trace("eco_world_step_forced");
   if (!w || (!actions && w->p.capacity > 0)) return ECO_EINVAL;
   cudaStream_t s = w->stream;
   const size_t bytes = (size_t)w->p.capacity * 4;
@@ -760,6 +777,7 @@ int eco_world_counters_async(EcoWorld *w, int64_t *out_host) {
 }
 
 int eco_world_analysis_async(EcoWorld *w, EcoAnalysis *out_host) {
+  Trace trace("eco_world_analysis_async");
   if (!w || !out_host) return ECO_EINVAL;
   static_assert(sizeof(EcoAnalysis) == ANALYSIS_WORDS * sizeof(int64_t) &&
                     offsetof(EcoAnalysis, movers) == A_MOVERS * sizeof(int64_t) &&
@@ -861,6 +879,7 @@ static int write_plane(uint32_t *plane, const EcoParams &p, const uint8_t *in) {
 }
 
 int eco_world_read_state(EcoWorld *w, EcoState *out) {
+  Trace trace("eco_world_read_state");
   if (!w || !out) return ECO_EINVAL;
   const EcoParams &p = w->p;
   const WorldDev &d = w->hd;
@@ -913,6 +932,7 @@ int eco_world_read_state(EcoWorld *w, EcoState *out) {
 }
 
 int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
+  Trace trace("eco_world_load_state");
   if (!w || !in) return ECO_EINVAL;
   const EcoParams &p = w->p;
   const WorldDev &d = w->hd;
@@ -1012,6 +1032,7 @@ int eco_batch_create(EcoWorld *const *worlds, int n, EcoBatch **out) {
 }
 
 int eco_batch_step(EcoBatch *b, int64_t n_steps) {
+  Trace trace("eco_batch_step");
   if (!b) return ECO_EINVAL;
   return batch_step(*b, n_steps);
 }
@@ -1031,6 +1052,7 @@ int eco_batch_get_config(const EcoBatch *b, int *fused, int *spawn_ctas_per_sm,
 }
 
 int eco_batch_autotune(EcoBatch *b, int trial_steps, EcoTuneResult *out) {
+  Trace trace("eco_batch_autotune");
   if (!b || !out) return ECO_EINVAL;
   return autotune(*b, trial_steps, out);
 }
@@ -1047,6 +1069,7 @@ int eco_world_get_config(const EcoWorld *w, int *fused, int *spawn_ctas_per_sm,
 }
 
 int eco_world_autotune(EcoWorld *w, int trial_steps, EcoTuneResult *out) {
+  Trace trace("eco_world_autotune");
   if (!w || !out) return ECO_EINVAL;
   return autotune(w->self, trial_steps, out);
 }
