@@ -23,6 +23,10 @@
  *     host threads.
  *   - Device-side waits are bounded: a wait that runs out sets a status bit
  *     that eco_world_sync / eco_batch_sync return as ECO_ETIMEOUT.
+ *   - The checked build of this library (libecoevo_checked.so) range-checks
+ *     every index it reads from device memory before using it; a failed
+ *     check skips the access and eco_world_sync / eco_batch_sync return
+ *     ECO_EBOUNDS.  The regular build has no such checks.
  */
 #ifndef ECOEVO_H
 #define ECOEVO_H
@@ -43,6 +47,7 @@ extern "C" {
 #define ECO_ECUDA -3     /* a CUDA runtime call failed                     */
 #define ECO_ETIMEOUT -4  /* a bounded device wait ran out                  */
 #define ECO_ESTATE -5    /* loaded state is inconsistent (shared cell ...) */
+#define ECO_EBOUNDS -6   /* a device index was out of range (checked build)  */
 
 /* Controllers (EcoParams.controller).
  *   ECO_CTRL_LSTM32  LSTM with 32 units on the 7x7 view (resource, other

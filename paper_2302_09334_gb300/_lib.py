@@ -13,7 +13,8 @@ from .params import EcoParams
 ECO_ABI_V2 = 0x45434F02
 CTRL_LSTM32, CTRL_PAPER = 0, 1
 NPARAM_OF = {CTRL_LSTM32: 23333, CTRL_PAPER: 2445}
-ECO_OK, ECO_EINVAL, ECO_ENOMEM, ECO_ECUDA, ECO_ETIMEOUT, ECO_ESTATE = 0, -1, -2, -3, -4, -5
+ECO_OK, ECO_EINVAL, ECO_ENOMEM, ECO_ECUDA, ECO_ETIMEOUT, ECO_ESTATE, ECO_EBOUNDS = \
+    0, -1, -2, -3, -4, -5, -6
 NCOUNTERS = 9
 NKERNELS = 10
 MOVE_BINS = 17
@@ -23,7 +24,10 @@ NANALYSIS = len(ANALYSIS_KEYS) + MOVE_BINS
 (C_T, C_POP, C_BIRTHS, C_DEATHS, C_DROPPED, C_BIRTHS_LAST, C_DEATHS_LAST,
  C_DROPPED_LAST, C_AGENT_STEPS) = range(9)
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libecoevo.so")
+# ECO_CHECKED=1 in the environment selects the range-checked build
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib",
+                        "libecoevo_checked.so" if os.environ.get("ECO_CHECKED") == "1"
+                        else "libecoevo.so")
 
 
 class CEcoParams(ctypes.Structure):

@@ -77,6 +77,36 @@ constexpr int PC_HID = 4, PC_EMB = 78, PC_VIEW = 15;
 // Status bits written by kernels.
 constexpr int ST_TIMEOUT = 1;
 constexpr int ST_STATE = 2;
+constexpr int ST_BOUNDS = 4;
+
+// Range check of an index read from device memory.  In the checked build
+// (ECO_CHECKED) a failed check sets ST_BOUNDS in the world's status word and
+// the caller skips the access; otherwise the check compiles away.
+#ifdef ECO_CHECKED
+#define ECO_IN_RANGE(wd, cond) \
+  ((cond) ? true : (atomicOr(&(wd).ctr->status, ST_BOUNDS), false))
+#else
+#define ECO_IN_RANGE(wd, cond) true
+#endif
+
+#ifdef __CUDACC__
+struct WorldDev;
+// Index i of an array of n entries, read from device memory: in the checked
+// build an index out of range is reported and replaced by 0, where a kernel
+// cannot skip the work item (a pipeline slot that must be filled).
+template <class WD>
+__device__ inline int checked_index(const WD &wd, int i, int n) {
+#ifdef ECO_CHECKED
+  if (i >= 0 && i < n) return i;
+  atomicOr(&wd.ctr->status, ST_BOUNDS);
+  return 0;
+#else
+  (void)wd;
+  (void)n;
+  return i;
+#endif
+}
+#endif
 
 // ---------------------------------------------------------------------------
 // Per-world device structures.

@@ -816,6 +816,7 @@ int eco_world_sync(EcoWorld *w) {
   int rc = read_status(w, &st);
   if (rc) return rc;
   if (st & ST_TIMEOUT) return ECO_ETIMEOUT;
+  if (st & ST_BOUNDS) return ECO_EBOUNDS;
   return ECO_OK;
 }
 
@@ -1082,6 +1083,7 @@ int eco_batch_sync(EcoBatch *b) {
     int rc = read_status(w, &st);
     if (rc) return rc;
     if (st & ST_TIMEOUT) return ECO_ETIMEOUT;
+    if (st & ST_BOUNDS) return ECO_EBOUNDS;
   }
   return ECO_OK;
 }
@@ -1147,6 +1149,7 @@ const char *eco_strerror(int code) {
     case ECO_ECUDA: return "CUDA error";
     case ECO_ETIMEOUT: return "device wait timed out";
     case ECO_ESTATE: return "inconsistent state";
+    case ECO_EBOUNDS: return "device index out of range";
     default: return "unknown error";
   }
 }

@@ -56,7 +56,10 @@ __constant__ int kDX[5] = {0, 0, 0, 1, -1};
 __device__ inline void slot_move_apply(const WorldDev *wd, int s) {
   if (!wd->alive[s]) return;
   const int cell = wd->target[s];
-  if (cell < 0 || wd->claim[cell] != s) return;
+  if (cell < 0 || !ECO_IN_RANGE(*wd, cell < wd->H * wd->W) || wd->claim[cell] != s) return;
+  if (!ECO_IN_RANGE(*wd, wd->y[s] >= 0 && wd->y[s] < wd->H && wd->x[s] >= 0 &&
+                         wd->x[s] < wd->W))
+    return;
   wd->claim[cell] = INT_MAX;  // only the winner resets; losers compare != s
   wd->slot_map[wd->y[s] * wd->W + wd->x[s]] = -1;
   wd->slot_map[cell] = s;
@@ -231,7 +234,8 @@ __device__ void scan_world(const WorldDev &wd, int *sh) {
   int n_free = 0, n_succ = 0;
   for (int s = s0; s < s1; ++s) {
     const int cell = wd.birth_cell[s];
-    const bool ok = wd.alive[s] && cell >= 0 && wd.bclaim[cell] == s;
+    const bool ok = wd.alive[s] && cell >= 0 && ECO_IN_RANGE(wd, cell < wd.H * wd.W) &&
+                    wd.bclaim[cell] == s;
     wd.flag[s] = ok ? 1 : 0;
     n_succ += ok;
     n_free += wd.alive[s] ? 0 : 1;
@@ -242,7 +246,7 @@ __device__ void scan_world(const WorldDev &wd, int *sh) {
   // 2. reset the claim cells; list the free slots the births will take
   for (int s = s0; s < s1; ++s) {
     const int cell = wd.birth_cell[s];
-    if (cell >= 0) wd.bclaim[cell] = INT_MAX;
+    if (cell >= 0 && cell < wd.H * wd.W) wd.bclaim[cell] = INT_MAX;
     if (!wd.alive[s]) {
       if (free_off < S) wd.free_list[free_off] = s;
       ++free_off;
@@ -256,7 +260,9 @@ __device__ void scan_world(const WorldDev &wd, int *sh) {
     if (!wd.flag[s]) continue;
     const int k = succ_off++;
     if (k >= F) continue;
-    init_child(wd, s, wd.birth_cell[s], k, wd.free_list[k], h_next);
+    const int child = wd.free_list[k];
+    if (!ECO_IN_RANGE(wd, child >= 0 && child < wd.C)) continue;
+    init_child(wd, s, wd.birth_cell[s], k, child, h_next);
   }
   __syncthreads();
 
@@ -455,7 +461,11 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
   for (int k = 0; k < CL_SPT; ++k) {
     if (!al[k]) continue;
     const int s = s0 + k;
-    if (tgt[k] >= 0 && wd.claim[tgt[k]] == s) {
+    if (!ECO_IN_RANGE(wd, py[k] >= 0 && py[k] < wd.H && px[k] >= 0 && px[k] < W)) {
+      al[k] = 0;
+      continue;
+    }
+    if (tgt[k] >= 0 && ECO_IN_RANGE(wd, tgt[k] < wd.H * W) && wd.claim[tgt[k]] == s) {
       wd.claim[tgt[k]] = INT_MAX;  // only the winner resets its cell
       wd.slot_map[py[k] * W + px[k]] = -1;
       wd.slot_map[tgt[k]] = s;
@@ -546,7 +556,11 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
     const int s = s0 + k;
     if (ok[k]) {
       const int kk = succ_off++;
-      if (kk < F) init_child(wd, s, bcell[k], kk, wd.free_list[kk], h_next);
+      if (kk < F) {
+        const int child = wd.free_list[kk];
+        if (ECO_IN_RANGE(wd, child >= 0 && child < wd.C))
+          init_child(wd, s, bcell[k], kk, child, h_next);
+      }
     }
     // the next alive list: survivors and the free slots that receive a child
     if (al[k]) {
@@ -612,7 +626,10 @@ __device__ inline void spawn_births(const BatchDev &b, int *pre, int cta, int n_
     int run = 0;
     for (int w = 0; w < b.n; ++w) {
       pre[w] = run;
-      run += world_ptr(b, w)->ctr->n_births;
+      const WorldDev &wdw = *world_ptr(b, w);
+      int nb = wdw.ctr->n_births;
+      if (!ECO_IN_RANGE(wdw, nb >= 0 && nb <= wdw.C)) nb = 0;
+      run += nb;
     }
     pre[b.n] = run;
   }
@@ -642,6 +659,8 @@ __device__ inline void spawn_births(const BatchDev &b, int *pre, int cta, int n_
       const int k = bi - pre[lo];
       par[u] = wd.birth_parent[k];
       const int child = wd.birth_child[k];
+      if (!ECO_IN_RANGE(wd, par[u] >= 0 && par[u] < wd.C && child >= 0 && child < wd.C))
+        continue;
       wdu[u] = &wd;
       in[u] = reinterpret_cast<const float4 *>(wd.weights + (size_t)par[u] * b.wstride)[vi[u]];
       dst[u] = reinterpret_cast<float4 *>(wd.weights + (size_t)child * b.wstride) + vi[u];

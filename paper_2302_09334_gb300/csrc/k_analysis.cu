@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(ANALYSIS_THREADS) k_analysis(WorldDev wd) {
       cell = y * W + x;
       ++pop;
       const int start = wd.snap_cell[s];
-      if ((long long)wd.age[s] >= L && start >= 0) {
+      if ((long long)wd.age[s] >= L && start >= 0 &&
+          ECO_IN_RANGE(wd, start < wd.H * wd.W)) {
         const long long d = (long long)abs(y - start / W) + abs(x - start % W);
         const long long bin = min((long long)(MOVE_BINS - 1), d * MOVE_BINS / (L + 1));
         atomicAdd(&bins[bin], 1ull);

@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
         if (a < a_end) {
           const int w = world_of(sm.prefix, b.n, a);
           const WorldDev *wd = world_ptr(b, w);
-          my_slot = wd->alive_list[a - sm.prefix[w]];
+          my_slot = checked_index(*wd, wd->alive_list[a - sm.prefix[w]], wd->C);
           my_w = wd->weights;
         }
       }
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
         if (a < a_end) {
           const int w = world_of(sm.prefix, b.n, a);
           my_wd = world_ptr(b, w);
-          my_slot = my_wd->alive_list[a - sm.prefix[w]];
+          my_slot = checked_index(*my_wd, my_wd->alive_list[a - sm.prefix[w]], my_wd->C);
           my_y = my_wd->y[my_slot];
           my_x = my_wd->x[my_slot];
           my_e = my_wd->energy[my_slot];

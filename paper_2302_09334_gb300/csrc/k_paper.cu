@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
   for (int a = blockIdx.x * PC_WARPS + warp; a < A; a += gridDim.x * PC_WARPS) {
     const int wi = world_of(sm.prefix, b.n, a);
     const WorldDev &wd = *world_ptr(b, wi);
-    const int s = wd.alive_list[a - sm.prefix[wi]];
+    const int s = checked_index(wd, wd.alive_list[a - sm.prefix[wi]], wd.C);
     const uint32_t t = (uint32_t)wd.ctr->t;
     const int y = wd.y[s], x = wd.x[s];
 
