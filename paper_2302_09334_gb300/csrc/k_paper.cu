@@ -1,16 +1,18 @@
 // k_paper.cu -- observation, controller and move claim of the paper's own
-// agent (App. B.5) for worlds with controller ECO_CTRL_PAPER.  One warp per
-// agent, agents of the batch in world-major alive-list order:
-//   * the agent's 2445 parameters (9,792 B row) are copied to the warp's
-//     shared memory with 16-byte cp.async while the lanes build the 15x15x3
+// agent (App. B.5) for worlds with controller ECO_CTRL_PAPER.  One CTA of
+// 128 threads per agent (grid-stride over the batch's agents in
+// world-major alive-list order), so that an agent's work is spread wide
+// (the paper's few hundred agents make this kernel latency-bound):
+//   * the agent's 2445 parameters (9,792 B row) are copied to shared memory
+//     with 16-byte cp.async while the threads build the 15x15x3
 //     view (resource plane after this step's regrowth, start-of-step
 //     occupancy without the agent itself, off-grid cells read as wall);
 //   * conv 3x3 stride 2 with one cell of zero padding (15 -> 8, 4 maps),
 //     2x2 average pool stride 1 (-> 7), conv 3x3 stride 2 (-> 4, 8 maps),
 //     pool (-> 3): 72 features in [y][x][map] order, then the previous
 //     action one-hot and the ate-last-step bit (78 inputs);
-//   * LSTM with 4 units (two lanes per gate row), dense 8 + tanh on
-//     [embedding, h'], dense 5;
+//   * LSTM with 4 units (eight threads per gate row), dense 8 + tanh on
+//     [embedding, h'] (sixteen threads per row), dense 5;
 //   * softmax at temperature 1/50 and the sampled action: the number of
 //     k < 4 whose cumulative probability is <= u, u = (w0 >> 8) 2^-24 of
 //     the Philox block {slot, t, TAG_ACT, 0};
@@ -24,23 +26,20 @@
 
 namespace eco {
 
-constexpr int PC_WARPS = 4;
-constexpr int PC_THREADS = PC_WARPS * 32;
-constexpr int PC_CTAS_PER_SM = 3;
+constexpr int PC_THREADS = 128;        // one CTA per agent
+constexpr int PC_CTAS_PER_SM = 8;
 
-struct __align__(16) PcWarp {
-  float w[PC_WSTRIDE];                 // the agent's parameters
+struct __align__(16) PcSmem {
+  float w[PC_WSTRIDE];                   // the agent's parameters
   float obs[PC_VIEW * PC_VIEW * 3 + 1];  // [y][x][channel]
-  float a1[8 * 8 * 4];                 // conv1
-  float p1[7 * 7 * 4];                 // pool1
-  float a2[4 * 4 * 8];                 // conv2
-  float emb[PC_EMB + PC_HID + 2];      // pool2 (72), one-hot (5), ate (1), h' (4)
-  float d[8];                          // dense 1 after tanh
-};
-
-struct PcSmem {
-  PcWarp warp[PC_WARPS];
-  int prefix[1025];                    // agents before world w of the batch
+  float a1[8 * 8 * 4];                   // conv1
+  float p1[7 * 7 * 4];                   // pool1
+  float a2[4 * 4 * 8];                   // conv2
+  float emb[PC_EMB + PC_HID + 2];        // pool2 (72), one-hot (5), ate (1), h' (4)
+  float hc[2 * PC_HID];                  // h and c before the step
+  float z[4 * PC_HID];                   // LSTM gate pre-activations
+  float d[8];                            // dense 1 after tanh
+  int prefix[1025];                      // agents before world w of the batch
 };
 
 __device__ inline void cp_async16(void *smem, const void *gmem) {
@@ -57,8 +56,8 @@ __device__ inline float sigmoidf_(float z) { return 1.f / (1.f + expf(-z)); }
 // out [m][m][CO], weights [CO][3][3][CI]; output o = (oy*m + ox)*CO + f.
 template <int CI, int CO>
 __device__ inline void conv3x3_s2(const float *in, int n, const float *wt, const float *bias,
-                                  float *out, int m, int lane) {
-  for (int o = lane; o < m * m * CO; o += 32) {
+                                  float *out, int m, int tid) {
+  for (int o = tid; o < m * m * CO; o += PC_THREADS) {
     const int f = o % CO, pos = o / CO, oy = pos / m, ox = pos % m;
     float acc = bias[f];
 #pragma unroll
@@ -81,9 +80,9 @@ __device__ inline void conv3x3_s2(const float *in, int n, const float *wt, const
 
 // 2x2 average pool, stride 1: [n][n][C] -> [n-1][n-1][C].
 template <int C>
-__device__ inline void avgpool2(const float *in, int n, float *out, int lane) {
+__device__ inline void avgpool2(const float *in, int n, float *out, int tid) {
   const int m = n - 1;
-  for (int o = lane; o < m * m * C; o += 32) {
+  for (int o = tid; o < m * m * C; o += PC_THREADS) {
     const int c = o % C, pos = o / C, y = pos / m, x = pos % m;
     const float s = ((in[(y * n + x) * C + c] + in[(y * n + x + 1) * C + c]) +
                      in[((y + 1) * n + x) * C + c]) + in[((y + 1) * n + x + 1) * C + c];
@@ -94,8 +93,8 @@ __device__ inline void avgpool2(const float *in, int n, float *out, int lane) {
 __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
     k_paper(const __grid_constant__ BatchDev b) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  PcSmem &sm = *reinterpret_cast<PcSmem *>(smem_raw);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  PcSmem &S = *reinterpret_cast<PcSmem *>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned FULL = 0xFFFFFFFFu;
   pdl_wait_and_release();
 
@@ -117,38 +116,37 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
     for (int i = 0; i < per; ++i) {
       const int w = lane * per + i;
       if (w < b.n) {
-        sm.prefix[w] = run;
+        S.prefix[w] = run;
         run += (int)world_ptr(b, w)->ctr->pop;
       }
     }
-    if (lane == 31) sm.prefix[b.n] = incl;
+    if (lane == 31) S.prefix[b.n] = incl;
   }
   __syncthreads();
 
-  PcWarp &S = sm.warp[warp];
-  const int A = sm.prefix[b.n];
-  for (int a = blockIdx.x * PC_WARPS + warp; a < A; a += gridDim.x * PC_WARPS) {
-    const int wi = world_of(sm.prefix, b.n, a);
+  const int A = S.prefix[b.n];
+  for (int a = blockIdx.x; a < A; a += gridDim.x) {
+    const int wi = world_of(S.prefix, b.n, a);
     const WorldDev &wd = *world_ptr(b, wi);
-    const int s = checked_index(wd, wd.alive_list[a - sm.prefix[wi]], wd.C);
+    const int s = checked_index(wd, wd.alive_list[a - S.prefix[wi]], wd.C);
     const uint32_t t = (uint32_t)wd.ctr->t;
     const int y = wd.y[s], x = wd.x[s];
 
     // parameters -> shared memory, asynchronously
     const float4 *src = reinterpret_cast<const float4 *>(wd.weights + (size_t)s * PC_WSTRIDE);
     float4 *dst = reinterpret_cast<float4 *>(S.w);
-    for (int i = lane; i < PC_WSTRIDE / 4; i += 32) cp_async16(dst + i, src + i);
+    for (int i = tid; i < PC_WSTRIDE / 4; i += PC_THREADS) cp_async16(dst + i, src + i);
 
-    // the 15x15x3 view: every lane issues the loads of its (up to 8) cells
-    // before it uses any of them
+    // the 15x15x3 view: each thread loads its (up to 2) cells, then stores
     const uint32_t *res = (t & 1u) ? wd.res0 : wd.res1;
     const int half = PC_VIEW / 2;
-    constexpr int CELLS = PC_VIEW * PC_VIEW, PER_LANE = (CELLS + 31) / 32;
-    uint32_t rw[PER_LANE], ww[PER_LANE];
-    int occ[PER_LANE];
+    constexpr int CELLS = PC_VIEW * PC_VIEW;
+    constexpr int PER = (CELLS + PC_THREADS - 1) / PC_THREADS;
+    uint32_t rw[PER], ww[PER];
+    int occ[PER];
 #pragma unroll
-    for (int i = 0; i < PER_LANE; ++i) {
-      const int k = lane + 32 * i;
+    for (int i = 0; i < PER; ++i) {
+      const int k = tid + PC_THREADS * i;
       const int yy = y + k / PC_VIEW - half, xx = x + k % PC_VIEW - half;
       rw[i] = 0u;
       ww[i] = 1u;   // off the grid: wall
@@ -159,120 +157,123 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
         occ[i] = (k != half * PC_VIEW + half) ? wd.slot_map[yy * wd.W + xx] : -1;
       }
     }
-    bool res_seen = false;
+    int res_seen = 0;
 #pragma unroll
-    for (int i = 0; i < PER_LANE; ++i) {
-      const int k = lane + 32 * i;
+    for (int i = 0; i < PER; ++i) {
+      const int k = tid + PC_THREADS * i;
       if (k < CELLS) {
         S.obs[3 * k] = (float)(rw[i] & 1u);
         S.obs[3 * k + 1] = occ[i] >= 0 ? 1.f : 0.f;
         S.obs[3 * k + 2] = (float)(ww[i] & 1u);
-        res_seen |= (rw[i] & 1u) != 0u;
+        res_seen |= (int)(rw[i] & 1u);
       }
     }
-    // greediness window: a resource in view
-    if (__any_sync(FULL, res_seen) && lane == 0) wd.lab_flags[s] |= 1u;
     const int prev = wd.prev_act[s];
     const int ate = wd.ate[s];
     const float *h_prev = ((t & 1u) ? wd.h1 : wd.h0) + (size_t)s * HID;
     float *h_next = ((t & 1u) ? wd.h0 : wd.h1) + (size_t)s * HID;
-    const float h_old = lane < PC_HID ? h_prev[lane] : 0.f;
-    const float c_old = lane < PC_HID ? wd.c[(size_t)s * HID + lane] : 0.f;
+    if (tid < PC_HID) {
+      S.hc[tid] = h_prev[tid];
+      S.hc[PC_HID + tid] = wd.c[(size_t)s * HID + tid];
+    }
     cp_async_wait_all();
-    __syncwarp();
+    // greediness window: a resource in view (the barrier also publishes
+    // the view, the parameters and h, c)
+    if (__syncthreads_or(res_seen) && tid == 0) wd.lab_flags[s] |= 1u;
 
     // embedding
-    conv3x3_s2<3, 4>(S.obs, PC_VIEW, S.w + PC_OFF_W1, S.w + PC_OFF_B1, S.a1, 8, lane);
-    __syncwarp();
-    avgpool2<4>(S.a1, 8, S.p1, lane);
-    __syncwarp();
-    conv3x3_s2<4, 8>(S.p1, 7, S.w + PC_OFF_W2, S.w + PC_OFF_B2, S.a2, 4, lane);
-    __syncwarp();
-    avgpool2<8>(S.a2, 4, S.emb, lane);
-    if (lane < NACT) S.emb[72 + lane] = (lane == prev) ? 1.f : 0.f;
-    if (lane == NACT) S.emb[77] = ate ? 1.f : 0.f;
-    __syncwarp();
+    conv3x3_s2<3, 4>(S.obs, PC_VIEW, S.w + PC_OFF_W1, S.w + PC_OFF_B1, S.a1, 8, tid);
+    __syncthreads();
+    avgpool2<4>(S.a1, 8, S.p1, tid);
+    __syncthreads();
+    conv3x3_s2<4, 8>(S.p1, 7, S.w + PC_OFF_W2, S.w + PC_OFF_B2, S.a2, 4, tid);
+    __syncthreads();
+    avgpool2<8>(S.a2, 4, S.emb, tid);
+    if (tid >= 72 && tid < 72 + NACT) S.emb[tid] = (tid - 72 == prev) ? 1.f : 0.f;
+    if (tid == 77) S.emb[77] = ate ? 1.f : 0.f;
+    __syncthreads();
 
-    // LSTM gate rows: row r = lane % 16, inputs split between the two halves
-    const int r = lane & 15, hf = lane >> 4;
-    float z = 0.f;
+    // LSTM gate rows: row r = tid / 8, eight threads per row
     {
+      const int r = tid >> 3, q = tid & 7;
       const float *wi_row = S.w + PC_OFF_WI + r * PC_EMB;
-      const int k0 = hf ? PC_EMB / 2 : 0, k1 = hf ? PC_EMB : PC_EMB / 2;
-      for (int k = k0; k < k1; ++k) z = fmaf(wi_row[k], S.emb[k], z);
+      float z = 0.f;
+      for (int k = q; k < PC_EMB; k += 8) z = fmaf(wi_row[k], S.emb[k], z);
+      if (q < PC_HID) z = fmaf(S.w[PC_OFF_WH + r * PC_HID + q], S.hc[q], z);
+      z += __shfl_xor_sync(FULL, z, 1);
+      z += __shfl_xor_sync(FULL, z, 2);
+      z += __shfl_xor_sync(FULL, z, 4);
+      if (q == 0) S.z[r] = z + S.w[PC_OFF_BL + r];
     }
-#pragma unroll
-    for (int j = 0; j < PC_HID; ++j) {
-      const float hj = __shfl_sync(FULL, h_old, j);
-      if (hf) z = fmaf(S.w[PC_OFF_WH + r * PC_HID + j], hj, z);
+    __syncthreads();
+    // cell update of unit j (gates i, f, g, o)
+    if (tid < PC_HID) {
+      const float c_new =
+          sigmoidf_(S.z[PC_HID + tid]) * S.hc[PC_HID + tid] +
+          sigmoidf_(S.z[tid]) * tanhf(S.z[2 * PC_HID + tid]);
+      const float h_new = sigmoidf_(S.z[3 * PC_HID + tid]) * tanhf(c_new);
+      wd.c[(size_t)s * HID + tid] = c_new;
+      h_next[tid] = h_new;
+      S.emb[PC_EMB + tid] = h_new;
     }
-    if (hf) z += S.w[PC_OFF_BL + r];
-    z += __shfl_xor_sync(FULL, z, 16);
-    // cell update of unit j = lane (lanes 0..3): gates i, f, g, o
-    const int j = lane & 3;
-    const float zi = __shfl_sync(FULL, z, j), zf = __shfl_sync(FULL, z, 4 + j);
-    const float zg = __shfl_sync(FULL, z, 8 + j), zo = __shfl_sync(FULL, z, 12 + j);
-    if (lane < PC_HID) {
-      const float c_new = sigmoidf_(zf) * c_old + sigmoidf_(zi) * tanhf(zg);
-      const float h_new = sigmoidf_(zo) * tanhf(c_new);
-      wd.c[(size_t)s * HID + lane] = c_new;
-      h_next[lane] = h_new;
-      S.emb[PC_EMB + lane] = h_new;
-    }
-    __syncwarp();
+    __syncthreads();
 
-    // dense 8 + tanh on [embedding, h']: four lanes per row
+    // dense 8 + tanh on [embedding, h']: sixteen threads per row
     {
-      const int i = lane >> 2, q = lane & 3;
+      const int i = tid >> 4, q = tid & 15;
       const float *row = S.w + PC_OFF_D1 + i * (PC_EMB + PC_HID);
       float acc = 0.f;
-      for (int k = q; k < PC_EMB + PC_HID; k += 4) acc = fmaf(row[k], S.emb[k], acc);
+      for (int k = q; k < PC_EMB + PC_HID; k += 16) acc = fmaf(row[k], S.emb[k], acc);
       acc += __shfl_xor_sync(FULL, acc, 1);
       acc += __shfl_xor_sync(FULL, acc, 2);
+      acc += __shfl_xor_sync(FULL, acc, 4);
+      acc += __shfl_xor_sync(FULL, acc, 8);
       if (q == 0) S.d[i] = tanhf(acc + S.w[PC_OFF_DB1 + i]);
     }
-    __syncwarp();
-    // dense 5
-    float logit = 0.f;
-    if (lane < NACT) {
-      float acc = S.w[PC_OFF_DB2 + lane];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) acc = fmaf(S.w[PC_OFF_D2 + lane * 8 + i], S.d[i], acc);
-      logit = acc;
-      wd.logits[(size_t)s * 8 + lane] = logit;
-    }
-    float lg[NACT];
-#pragma unroll
-    for (int k = 0; k < NACT; ++k) lg[k] = __shfl_sync(FULL, logit, k);
+    __syncthreads();
 
-    if (lane == 0) {
-      // softmax at temperature 1/50 and the sampled action
-      float m = lg[0];
+    if (warp == 0) {
+      // dense 5
+      float logit = 0.f;
+      if (lane < NACT) {
+        float acc = S.w[PC_OFF_DB2 + lane];
 #pragma unroll
-      for (int k = 1; k < NACT; ++k) m = fmaxf(m, lg[k]);
-      float e[NACT], sum = 0.f;
-#pragma unroll
-      for (int k = 0; k < NACT; ++k) {
-        e[k] = expf(50.f * (lg[k] - m));
-        sum += e[k];
+        for (int i = 0; i < 8; ++i) acc = fmaf(S.w[PC_OFF_D2 + lane * 8 + i], S.d[i], acc);
+        logit = acc;
+        wd.logits[(size_t)s * 8 + lane] = logit;
       }
-      const U4 rnd = philox4x32_10(U4{(uint32_t)s, t, TAG_ACT, 0u}, wd.key0, wd.key1);
-      const float u = (float)(rnd.x >> 8) * (1.f / 16777216.f);
-      int act = 0;
-      float cdf = 0.f;
+      float lg[NACT];
 #pragma unroll
-      for (int k = 0; k < NACT - 1; ++k) {
-        cdf += e[k] / sum;
-        if (cdf <= u) act = k + 1;
+      for (int k = 0; k < NACT; ++k) lg[k] = __shfl_sync(FULL, logit, k);
+      if (lane == 0) {
+        // softmax at temperature 1/50 and the sampled action
+        float m = lg[0];
+#pragma unroll
+        for (int k = 1; k < NACT; ++k) m = fmaxf(m, lg[k]);
+        float e[NACT], sum = 0.f;
+#pragma unroll
+        for (int k = 0; k < NACT; ++k) {
+          e[k] = expf(50.f * (lg[k] - m));
+          sum += e[k];
+        }
+        const U4 rnd = philox4x32_10(U4{(uint32_t)s, t, TAG_ACT, 0u}, wd.key0, wd.key1);
+        const float u = (float)(rnd.x >> 8) * (1.f / 16777216.f);
+        int act = 0;
+        float cdf = 0.f;
+#pragma unroll
+        for (int k = 0; k < NACT - 1; ++k) {
+          cdf += e[k] / sum;
+          if (cdf <= u) act = k + 1;
+        }
+        wd.action[s] = act;
+        const int moved = wd.ctr->use_forced ? wd.forced[s] : act;
+        wd.prev_act[s] = (moved >= 0 && moved < NACT) ? moved : 0;
+        MoveClaim mc;
+        mc.issue(wd, s, y, x, moved);
+        mc.resolve();
       }
-      wd.action[s] = act;
-      const int moved = wd.ctr->use_forced ? wd.forced[s] : act;
-      wd.prev_act[s] = (moved >= 0 && moved < NACT) ? moved : 0;
-      MoveClaim mc;
-      mc.issue(wd, s, y, x, moved);
-      mc.resolve();
     }
-    __syncwarp();
+    __syncthreads();   // the shared buffers are reused by the next agent
   }
 }
 
