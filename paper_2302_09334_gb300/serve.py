@@ -15,6 +15,10 @@ Latency accounting: a request's chunk latency is the time between two
 consecutive chunk reports (the first from its admission); the queueing
 delay is admission time minus arrival time.
 
+With `log` (a text file), every chunk appends one JSON record: its time,
+steps, live and queued requests, agent-steps, seconds, agent-steps/s and the
+device memory in use.
+
 Failures and cancellation, all handled on the host between chunks (no
 launch is ever interrupted):
 * a request whose arena alone exceeds the budget is rejected on arrival;
@@ -29,6 +33,7 @@ launch is ever interrupted):
 from __future__ import annotations
 
 import ctypes
+import json
 import threading
 import time
 from collections import deque
@@ -73,7 +78,8 @@ class Server:
     World on this server's stream and Batch."""
 
     def __init__(self, budget_bytes: float = 120e9, chunk: int = 100, device: int = 0,
-                 keep_final: bool = False, world_factory=None, batch_factory=None):
+                 keep_final: bool = False, world_factory=None, batch_factory=None,
+                 log=None):
         self.budget = float(budget_bytes)
         self.chunk = int(chunk)
         self.device = device
@@ -94,6 +100,7 @@ class Server:
         self._lock = threading.Lock()
         self._cancel_ids = set()
         self._wait_for_retire = False   # set by an out-of-memory admission
+        self.log = log                  # text file: one JSON record per chunk
 
     def cancel(self, rid: int) -> None:
         """Ask for request rid to stop (safe from any thread).  A queued
@@ -204,9 +211,18 @@ class Server:
                 continue
             n = min(self.chunk, min(r.steps - r.done for r in self.live))
             pops = [int(r.world.counters()[1]) for r in self.live]
+            t_chunk = time.perf_counter()
             self._step_live(n)
             chunks += 1
             t_rep = time.perf_counter() - t0
+            if self.log is not None:
+                dt = time.perf_counter() - t_chunk
+                self.log.write(json.dumps({
+                    "t_s": round(t_rep, 6), "chunk": chunks, "steps": n,
+                    "live": len(self.live), "queued": len(queue),
+                    "agent_steps": sum(pops) * n, "seconds": round(dt, 6),
+                    "agent_steps_per_s": sum(pops) * n / dt if dt > 0 else None,
+                    "used_gb": round(self.used / 1e9, 3)}) + "\n")
             for r, pop in zip(list(self.live), pops):
                 r.done += n
                 r.agent_steps += pop * n  # population at the chunk start

@@ -165,3 +165,16 @@ def test_cancel_from_another_thread_mid_chunk():
     assert by_rid[1].done == 200            # ran to the end of its chunk
     assert by_rid[2].admitted is None and by_rid[2].world is None
     assert len(FakeWorld.created) == 2 and all(w.closed for w in FakeWorld.created)
+
+
+def test_chunk_log_is_jsonl():
+    import io
+    import json
+    buf = io.StringIO()
+    srv = _server(10 * _size(64), log=buf)
+    srv.run([_req(0.0, 64, 250, seed=0), _req(0.0, 64, 120, seed=1)])
+    recs = [json.loads(ln) for ln in buf.getvalue().splitlines()]
+    # chunks end where a request finishes: 100, 20 (request 1 done), 100, 30
+    assert [r["steps"] for r in recs] == [100, 20, 100, 30]
+    assert [r["live"] for r in recs] == [2, 2, 1, 1]
+    assert all(r["agent_steps"] == 64 * r["steps"] * r["live"] for r in recs)
