@@ -12,8 +12,10 @@ Tolerances (derived from the arithmetic; see the design notes):
     |gpu - expected| <= 1e-6 * (|expected| + sigma); and the drift against
     the oracle's child after several generations, relative to the operands
     of the mutation and scaled by the child's generation g (each mutation
-    adds its own rounding, the initial draw one more):
-    |gpu - oracle| <= (g + 1) 1e-6 (|oracle| + |parent| + sigma);
+    adds its own rounding, the initial draw one more, on the scale of the
+    initial weights' std sigma0):
+    |gpu - oracle| <= 1e-6 (g (|oracle| + |parent| + sigma)
+                            + |oracle| + |parent| + sigma0);
   * actions: equal, except where the oracle's top-two logit margin is below
     1e-5 * max(1, max|logit|) (flagged, not counted as a mismatch);
   * sampled actions (the paper's controller): equal, except where the
@@ -49,11 +51,13 @@ def weights_close(gpu, ref, std, what):
                            f"{(np.abs(gpu - ref) / (np.abs(ref) + std)).max():.3g}")
 
 
-def weights_drift_close(gpu, ref, parent, std, generation, what):
+def weights_drift_close(gpu, ref, parent, std, generation, what, init_std=None):
     gpu = np.asarray(gpu, np.float64)
     ref = np.asarray(ref, np.float64)
-    # the initial draw counts as one more rounding step
-    bound = (generation + 1) * W_TOL * (np.abs(ref) + np.abs(np.asarray(parent, np.float64)) + std)
+    mag = np.abs(ref) + np.abs(np.asarray(parent, np.float64))
+    # each mutation adds its rounding; the initial draw one more, on the
+    # scale of the initial weights
+    bound = W_TOL * (generation * (mag + std) + mag + (std if init_std is None else init_std))
     bad = np.abs(gpu - ref) > bound
     assert not bad.any(), f"{what}: {int(bad.sum())} weights drifted"
 
@@ -137,7 +141,8 @@ def check_births(gw, ow, nb, sigma, where, gen):
         weights_close(wc, expected, sigma, f"{where} child {ch} (mutation)")
         gen[ch] = gen[par] + 1
         weights_drift_close(wc, ow.weights[ch, :n], ow.weights[par, :n], sigma, gen[ch],
-                            f"{where} child {ch} (generation {gen[ch]})")
+                            f"{where} child {ch} (generation {gen[ch]})",
+                            init_std=float(ow.p.w_init_std))
 
 
 def _diagnose(prev, gs, ow, forced, where):
