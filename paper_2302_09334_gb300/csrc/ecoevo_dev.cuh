@@ -161,7 +161,8 @@ struct WorldDev {            // read-only while kernels run
   Counters *ctr;
   int32_t *snap_cell;        // [C] cell of each slot's agent at the window start, -1 none
   int32_t *prev_act;         // [C] action moved with in the last step (paper controller input)
-  uint8_t *lab_flags;        // [C] greediness window: bit 0 resource in view, bit 1 ate
+  uint8_t *lab_seen, *lab_ate;  // [C] greediness window: a resource in view / a meal
+                             // (plain stores, no read-modify-write, in the hot kernels)
   int32_t *lab_t, *lab_c;    // [C] windows with a resource in view / with a meal
   unsigned long long *analysis;  // [ANALYSIS_WORDS] output of the analysis kernels
 };

@@ -67,7 +67,7 @@ struct Layout {
       slot_map, claim, bclaim, alive, killed, ate, flag, y, x, energy, repr_ctr,
       low_ctr, age, action, forced, target, birth_cell, arrive, h0, h1, c,
       logits, alive_list, free_list, birth_parent, birth_child, snap_cell, analysis,
-      prev_act, lab_flags, lab_t, lab_c, weights, staging, total;
+      prev_act, lab_seen, lab_ate, lab_t, lab_c, weights, staging, total;
 };
 
 Layout layout_of(const EcoParams *p) {
@@ -118,7 +118,8 @@ Layout layout_of(const EcoParams *p) {
   L.snap_cell = take(C1 * 4);
   L.analysis = take(ANALYSIS_WORDS * 8);
   L.prev_act = take(C1 * 4);
-  L.lab_flags = take(C1);
+  L.lab_seen = take(C1);
+  L.lab_ate = take(C1);
   L.lab_t = take(C1 * 4);
   L.lab_c = take(C1 * 4);
   L.weights = take(C1 * (size_t)wstride_of(p->controller) * 4);
@@ -622,7 +623,8 @@ static void fill_descriptor(EcoWorld *w) {
   d.ctr = (Counters *)(a + L.ctr);
   d.snap_cell = (int32_t *)(a + L.snap_cell);
   d.prev_act = (int32_t *)(a + L.prev_act);
-  d.lab_flags = (uint8_t *)(a + L.lab_flags);
+  d.lab_seen = (uint8_t *)(a + L.lab_seen);
+  d.lab_ate = (uint8_t *)(a + L.lab_ate);
   d.lab_t = (int32_t *)(a + L.lab_t);
   d.lab_c = (int32_t *)(a + L.lab_c);
   d.analysis = (unsigned long long *)(a + L.analysis);
@@ -995,7 +997,8 @@ int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
     }
   }
   // greediness counters start over with a loaded state
-  ECO_CU(cudaMemsetAsync(d.lab_flags, 0, C ? C : 1, w->stream));
+  ECO_CU(cudaMemsetAsync(d.lab_seen, 0, C ? C : 1, w->stream));
+  ECO_CU(cudaMemsetAsync(d.lab_ate, 0, C ? C : 1, w->stream));
   ECO_CU(cudaMemsetAsync(d.lab_t, 0, (C ? C : 1) * 4, w->stream));
   ECO_CU(cudaMemsetAsync(d.lab_c, 0, (C ? C : 1) * 4, w->stream));
   launch_rebuild(&w->hd, w->n_sms, w->stream);

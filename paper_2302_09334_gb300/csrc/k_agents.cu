@@ -82,7 +82,7 @@ __device__ inline void slot_physio(const WorldDev *wd, int s) {
     const uint32_t old = atomicAnd(&res[y * wd->Wp + (x >> 5)], ~bit);
     const bool ate = (old & bit) != 0u;
     wd->ate[s] = ate ? 1 : 0;
-    if (ate) wd->lab_flags[s] |= 2u;
+    if (ate) wd->lab_ate[s] = 1;
     float e = wd->energy[s];
     if (ate) e = __fadd_rn(e, wd->e_gain);
     e = __fsub_rn(e, wd->e_decay);
@@ -185,7 +185,8 @@ __device__ inline void init_child(const WorldDev &wd, int s, int cell, int k, in
   wd.action[child] = 0;
   wd.prev_act[child] = 0;
   wd.ate[child] = 0;
-  wd.lab_flags[child] = 0;
+  wd.lab_seen[child] = 0;
+  wd.lab_ate[child] = 0;
   wd.lab_t[child] = 0;
   wd.lab_c[child] = 0;
   wd.arrive[child] = 0u;
@@ -497,7 +498,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
       }
     }
     wd.ate[s] = ate ? 1 : 0;  // an input of the paper's controller next step
-    if (ate) wd.lab_flags[s] |= 2u;
+    if (ate) wd.lab_ate[s] = 1;
     if (dead) {
       al[k] = 0;
       wd.alive[s] = 0;

@@ -111,12 +111,12 @@ __global__ void k_analysis_finish(WorldDev wd) {
 // adds 1 to T_r if a resource was in its view during it, 1 to C_r if it ate.
 __global__ void k_lab_window(WorldDev wd) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < wd.C; s += gridDim.x * blockDim.x) {
-    const uint32_t f = wd.lab_flags[s];
     if (wd.alive[s]) {
-      wd.lab_t[s] += (int)(f & 1u);
-      wd.lab_c[s] += (int)((f >> 1) & 1u);
+      wd.lab_t[s] += wd.lab_seen[s] ? 1 : 0;
+      wd.lab_c[s] += wd.lab_ate[s] ? 1 : 0;
     }
-    wd.lab_flags[s] = 0;
+    wd.lab_seen[s] = 0;
+    wd.lab_ate[s] = 0;
   }
 }
 

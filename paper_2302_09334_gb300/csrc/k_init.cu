@@ -66,7 +66,8 @@ __global__ void k_init_agents(WorldDev wd, int n0, const int32_t *py,
   wd.age[s] = 0;
   wd.action[s] = 0;
   wd.prev_act[s] = 0;
-  wd.lab_flags[s] = 0;
+  wd.lab_seen[s] = 0;
+  wd.lab_ate[s] = 0;
   wd.lab_t[s] = 0;
   wd.lab_c[s] = 0;
   wd.forced[s] = 0;

@@ -182,7 +182,7 @@ __device__ inline void gather_input(const WorldDev &wd, int slot, int y, int x,
     uint32_t any = 0u;
 #pragma unroll
     for (int r = 0; r < 7; ++r) any |= masks[r];
-    if (any) wd.lab_flags[slot] |= 1u;
+    if (any) wd.lab_seen[slot] = 1;
     e.v[147] = energy;
     e.slot = slot;
     e.y = y;

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
     cp_async_wait_all();
     // greediness window: a resource in view (the barrier also publishes
     // the view, the parameters and h, c)
-    if (__syncthreads_or(res_seen) && tid == 0) wd.lab_flags[s] |= 1u;
+    if (__syncthreads_or(res_seen) && tid == 0) wd.lab_seen[s] = 1;
 
     // embedding
     conv3x3_s2<3, 4>(S.obs, PC_VIEW, S.w + PC_OFF_W1, S.w + PC_OFF_B1, S.a1, 8, tid);
