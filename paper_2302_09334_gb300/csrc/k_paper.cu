@@ -40,6 +40,7 @@ struct __align__(16) PcSmem {
   float z[4 * PC_HID];                   // LSTM gate pre-activations
   float d[8];                            // dense 1 after tanh
   int prefix[1025];                      // agents before world w of the batch
+  int first_slot;                        // one world: slot of this CTA's first agent
 };
 
 __device__ inline void cp_async16(void *smem, const void *gmem) {
@@ -98,8 +99,18 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
   const unsigned FULL = 0xFFFFFFFFu;
   pdl_wait_and_release();
 
-  // agents per world (= alive-list length at the start of the step)
-  if (warp == 0) {
+  // agents per world (= alive-list length at the start of the step); with
+  // one world, the population and this CTA's first slot are loaded together
+  if (warp == 0 && b.n == 1) {
+    if (lane == 0) {
+      const WorldDev &w0 = *world_ptr(b, 0);
+      const int pop = (int)w0.ctr->pop;
+      const int first = (int)blockIdx.x < w0.C ? w0.alive_list[blockIdx.x] : 0;
+      S.prefix[0] = 0;
+      S.prefix[1] = pop;
+      S.first_slot = first;
+    }
+  } else if (warp == 0) {
     const int per = (b.n + 31) / 32;
     int local = 0;
     for (int i = 0; i < per; ++i) {
@@ -128,7 +139,9 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
   for (int a = blockIdx.x; a < A; a += gridDim.x) {
     const int wi = world_of(S.prefix, b.n, a);
     const WorldDev &wd = *world_ptr(b, wi);
-    const int s = checked_index(wd, wd.alive_list[a - S.prefix[wi]], wd.C);
+    const int s = checked_index(
+        wd, (b.n == 1 && a == (int)blockIdx.x) ? S.first_slot : wd.alive_list[a - S.prefix[wi]],
+        wd.C);
     const uint32_t t = (uint32_t)wd.ctr->t;
     const int y = wd.y[s], x = wd.x[s];
 
@@ -268,9 +281,23 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
         wd.action[s] = act;
         const int moved = wd.ctr->use_forced ? wd.forced[s] : act;
         wd.prev_act[s] = (moved >= 0 && moved < NACT) ? moved : 0;
-        MoveClaim mc;
-        mc.issue(wd, s, y, x, moved);
-        mc.resolve();
+        // move claim (step part a4) from the view in shared memory: the
+        // target's wall channel (walls and off-grid cells) and agent channel
+        // (start-of-step occupancy) are the cell's state for the claim
+        int tgt = -1, kill = 0;
+        if (moved >= 1 && moved < NACT) {
+          const int dy = moved == 1 ? -1 : moved == 2 ? 1 : 0;
+          const int dx = moved == 3 ? 1 : moved == 4 ? -1 : 0;
+          const int k = (half + dy) * PC_VIEW + (half + dx);
+          if (S.obs[3 * k + 2] != 0.f) {
+            kill = wd.wall_kills ? 1 : 0;
+          } else if (S.obs[3 * k + 1] == 0.f) {
+            tgt = (y + dy) * wd.W + (x + dx);
+            atomicMin(&wd.claim[tgt], s);
+          }
+        }
+        wd.target[s] = tgt;
+        wd.killed[s] = kill;
       }
     }
     __syncthreads();   // the shared buffers are reused by the next agent
