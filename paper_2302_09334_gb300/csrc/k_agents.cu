@@ -621,51 +621,7 @@ __device__ inline float4 mutate4(const WorldDev &wd, int vi, float4 base, uint32
 // issues the loads of SPAWN_UNROLL elements before any of their arithmetic.
 constexpr int SPAWN_UNROLL = 2;
 
-// Mutation of every birth of the batch by CTAs cta .. of n_cta; NV float4
-// per weight row (a compile-time constant per controller, so that the
-// index arithmetic is multiplications, not 64-bit divisions).
-template <int NV>
-__device__ inline void spawn_births_nv(const BatchDev &b, const int *pre, int cta, int n_cta) {
-  const long long total = (long long)pre[b.n] * NV;
-  const long long stride = (long long)n_cta * blockDim.x;
-  for (long long g0 = (long long)cta * blockDim.x + threadIdx.x; g0 < total;
-       g0 += SPAWN_UNROLL * stride) {
-    float4 in[SPAWN_UNROLL];
-    float4 *dst[SPAWN_UNROLL];
-    const WorldDev *wdu[SPAWN_UNROLL];
-    int vi[SPAWN_UNROLL], par[SPAWN_UNROLL];
-#pragma unroll
-    for (int u = 0; u < SPAWN_UNROLL; ++u) {
-      const long long g = g0 + u * stride;
-      dst[u] = nullptr;
-      if (g >= total) continue;
-      const int bi = (int)(g / NV);
-      vi[u] = (int)(g - (long long)bi * NV);
-      int lo = 0, hi = b.n - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (pre[mid] <= bi) lo = mid; else hi = mid - 1;
-      }
-      const WorldDev &wd = *world_ptr(b, lo);
-      const int k = bi - pre[lo];
-      par[u] = wd.birth_parent[k];
-      const int child = wd.birth_child[k];
-      if (!ECO_IN_RANGE(wd, par[u] >= 0 && par[u] < wd.C && child >= 0 && child < wd.C))
-        continue;
-      wdu[u] = &wd;
-      in[u] = reinterpret_cast<const float4 *>(wd.weights + (size_t)par[u] * (NV * 4))[vi[u]];
-      dst[u] = reinterpret_cast<float4 *>(wd.weights + (size_t)child * (NV * 4)) + vi[u];
-    }
-#pragma unroll
-    for (int u = 0; u < SPAWN_UNROLL; ++u) {
-      if (!dst[u]) continue;
-      const WorldDev &wd = *wdu[u];
-      *dst[u] = mutate4(wd, vi[u], in[u], TAG_MUT, wd.ctr->births_t, (uint32_t)par[u],
-                        wd.mut_std);
-    }
-  }
-}
-
+// Mutation of every birth of the batch by CTAs cta .. of n_cta.
 __device__ inline void spawn_births(const BatchDev &b, int *pre, int cta, int n_cta) {
   if (threadIdx.x == 0) {
     int run = 0;
@@ -679,10 +635,45 @@ __device__ inline void spawn_births(const BatchDev &b, int *pre, int cta, int n_
     pre[b.n] = run;
   }
   __syncthreads();
-  if (b.controller == ECO_CTRL_PAPER)
-    spawn_births_nv<PC_WSTRIDE / 4>(b, pre, cta, n_cta);
-  else
-    spawn_births_nv<NVEC>(b, pre, cta, n_cta);
+  const int nvec = b.wstride / 4;
+  const long long total = (long long)pre[b.n] * nvec;
+  const long long stride = (long long)n_cta * blockDim.x;
+  for (long long g0 = (long long)cta * blockDim.x + threadIdx.x; g0 < total;
+       g0 += SPAWN_UNROLL * stride) {
+    float4 in[SPAWN_UNROLL];
+    float4 *dst[SPAWN_UNROLL];
+    const WorldDev *wdu[SPAWN_UNROLL];
+    int vi[SPAWN_UNROLL], par[SPAWN_UNROLL];
+#pragma unroll
+    for (int u = 0; u < SPAWN_UNROLL; ++u) {
+      const long long g = g0 + u * stride;
+      dst[u] = nullptr;
+      if (g >= total) continue;
+      const int bi = (int)(g / nvec);
+      vi[u] = (int)(g % nvec);
+      int lo = 0, hi = b.n - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= bi) lo = mid; else hi = mid - 1;
+      }
+      const WorldDev &wd = *world_ptr(b, lo);
+      const int k = bi - pre[lo];
+      par[u] = wd.birth_parent[k];
+      const int child = wd.birth_child[k];
+      if (!ECO_IN_RANGE(wd, par[u] >= 0 && par[u] < wd.C && child >= 0 && child < wd.C))
+        continue;
+      wdu[u] = &wd;
+      in[u] = reinterpret_cast<const float4 *>(wd.weights + (size_t)par[u] * b.wstride)[vi[u]];
+      dst[u] = reinterpret_cast<float4 *>(wd.weights + (size_t)child * b.wstride) + vi[u];
+    }
+#pragma unroll
+    for (int u = 0; u < SPAWN_UNROLL; ++u) {
+      if (!dst[u]) continue;
+      const WorldDev &wd = *wdu[u];
+      *dst[u] = mutate4(wd, vi[u], in[u], TAG_MUT, wd.ctr->births_t, (uint32_t)par[u],
+                        wd.mut_std);
+    }
+  }
 }
 
 // The tail of a step: the regrowth of the next step's plane (the first
