@@ -271,6 +271,10 @@ __device__ inline void pdl_wait_and_release() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
+__device__ inline void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ inline void pdl_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // Launch a step kernel with the programmatic-stream-serialization attribute.
 template <typename Kernel>

@@ -218,8 +218,14 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
     sm.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // everything below reads what earlier kernels wrote
-  pdl_wait_and_release();
+  // The kernel before this one in a step is the tail (this step's
+  // regrowth, the mutation of the last step's births); the one before that
+  // (the slot phases) has completed by the time this kernel starts, since
+  // every tail CTA waits for it before it lets this kernel launch.  So the
+  // populations, alive lists and ages, and the weights of every agent not
+  // born in the last step, are read before waiting for the tail (through
+  // L2, ld.cg); the resource plane and the newborns' weights only after.
+  pdl_release();
 
   // agents per world (= alive-list length at the start of the step)
   if (warp == 0) {
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
     int local = 0;
     for (int i = 0; i < per; ++i) {
       const int w = lane * per + i;
-      if (w < b.n) local += (int)world_ptr(b, w)->ctr->pop;
+      if (w < b.n) local += (int)__ldcg(&world_ptr(b, w)->ctr->pop);
     }
     int incl = local;
 #pragma unroll
@@ -240,7 +246,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
       const int w = lane * per + i;
       if (w < b.n) {
         sm.prefix[w] = run;
-        run += (int)world_ptr(b, w)->ctr->pop;
+        run += (int)__ldcg(&world_ptr(b, w)->ctr->pop);
       }
     }
     if (lane == 31) sm.prefix[b.n] = incl;
@@ -255,22 +261,28 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
 
   if (warp == W_PROD) {
     // ------------------------------------------------ producer -------------
-    int my_slot = 0;
+    int my_slot = 0, my_new = 0;
     const float *my_w = nullptr;
     int issued = 0;
+    bool waited = false;
     for (int n = 0; n < n_agents; ++n) {
       if ((n & 31) == 0) {
         const int a = a_begin + n + lane;
         if (a < a_end) {
           const int w = world_of(sm.prefix, b.n, a);
           const WorldDev *wd = world_ptr(b, w);
-          my_slot = checked_index(*wd, wd->alive_list[a - sm.prefix[w]], wd->C);
+          my_slot = checked_index(*wd, __ldcg(&wd->alive_list[a - sm.prefix[w]]), wd->C);
+          my_new = __ldcg(&wd->age[my_slot]) == 0;  // born in the last step (or never stepped)
           my_w = wd->weights;
         }
       }
       const int slot = __shfl_sync(FULL, my_slot, n & 31);
       const float *wts = reinterpret_cast<const float *>(
           __shfl_sync(FULL, reinterpret_cast<unsigned long long>(my_w), n & 31));
+      if (!waited && __shfl_sync(FULL, my_new, n & 31)) {
+        pdl_wait();   // its weights are written by the tail kernel
+        waited = true;
+      }
       if (lane == 0) {
         for (int q = 0; q < NBLK; ++q) {
           const int u = NBLK * n + q, st = u % LSTAGES, k = u / LSTAGES;
@@ -292,6 +304,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
     if (lane == 0) sm.issued = issued;
   } else if (warp >= NCOMP) {
     // ------------------------------------------------ gather ---------------
+    pdl_wait();   // the resource plane of this step is the tail kernel's
     const int gw = warp - NCOMP;
     int my_slot = 0, my_y = 0, my_x = 0, my_f = -1;
     float my_e = 0.f;

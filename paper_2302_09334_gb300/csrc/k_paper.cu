@@ -97,15 +97,20 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
   PcSmem &S = *reinterpret_cast<PcSmem *>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned FULL = 0xFFFFFFFFu;
-  pdl_wait_and_release();
+  // As in the LSTM kernel: the slot phases have completed when this kernel
+  // starts (the tail kernel before it waits for them before releasing it),
+  // so populations, alive lists, positions, ages and the parameters of the
+  // agents not born in the last step are read (through L2) before waiting
+  // for the tail; the resource plane and newborns' parameters after.
+  pdl_release();
 
   // agents per world (= alive-list length at the start of the step); with
   // one world, the population and this CTA's first slot are loaded together
   if (warp == 0 && b.n == 1) {
     if (lane == 0) {
       const WorldDev &w0 = *world_ptr(b, 0);
-      const int pop = (int)w0.ctr->pop;
-      const int first = (int)blockIdx.x < w0.C ? w0.alive_list[blockIdx.x] : 0;
+      const int pop = (int)__ldcg(&w0.ctr->pop);
+      const int first = (int)blockIdx.x < w0.C ? __ldcg(&w0.alive_list[blockIdx.x]) : 0;
       S.prefix[0] = 0;
       S.prefix[1] = pop;
       S.first_slot = first;
@@ -115,7 +120,7 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
     int local = 0;
     for (int i = 0; i < per; ++i) {
       const int w = lane * per + i;
-      if (w < b.n) local += (int)world_ptr(b, w)->ctr->pop;
+      if (w < b.n) local += (int)__ldcg(&world_ptr(b, w)->ctr->pop);
     }
     int incl = local;
 #pragma unroll
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
       const int w = lane * per + i;
       if (w < b.n) {
         S.prefix[w] = run;
-        run += (int)world_ptr(b, w)->ctr->pop;
+        run += (int)__ldcg(&world_ptr(b, w)->ctr->pop);
       }
     }
     if (lane == 31) S.prefix[b.n] = incl;
@@ -140,15 +145,20 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
     const int wi = world_of(S.prefix, b.n, a);
     const WorldDev &wd = *world_ptr(b, wi);
     const int s = checked_index(
-        wd, (b.n == 1 && a == (int)blockIdx.x) ? S.first_slot : wd.alive_list[a - S.prefix[wi]],
+        wd,
+        (b.n == 1 && a == (int)blockIdx.x) ? S.first_slot
+                                           : __ldcg(&wd.alive_list[a - S.prefix[wi]]),
         wd.C);
-    const uint32_t t = (uint32_t)wd.ctr->t;
-    const int y = wd.y[s], x = wd.x[s];
+    const uint32_t t = (uint32_t)__ldcg(&wd.ctr->t);
+    const int y = __ldcg(&wd.y[s]), x = __ldcg(&wd.x[s]);
+    // a newborn's parameters are written by the tail kernel
+    if (__ldcg(&wd.age[s]) == 0) pdl_wait();
 
     // parameters -> shared memory, asynchronously
     const float4 *src = reinterpret_cast<const float4 *>(wd.weights + (size_t)s * PC_WSTRIDE);
     float4 *dst = reinterpret_cast<float4 *>(S.w);
     for (int i = tid; i < PC_WSTRIDE / 4; i += PC_THREADS) cp_async16(dst + i, src + i);
+    pdl_wait();   // the resource plane of this step is the tail kernel's
 
     // the 15x15x3 view: each thread loads its (up to 2) cells, then stores
     const uint32_t *res = (t & 1u) ? wd.res0 : wd.res1;
