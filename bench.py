@@ -35,9 +35,9 @@ LSTM_BYTES_PER_AGENT = 93332 + 512 + 36
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one observation+LSTM launch per agent, from the
 # ncu capture in profiles/k_lstm_paper_200x400_held3440.md; traffic grows with
-# the agents of a launch, so it is scaled by them (327.57 MB at 3,440 agents,
+# the agents of a launch, so it is scaled by them (327.55 MB at 3,440 agents,
 # mean of the two captured launches).
-LSTM_TRAFFIC_PER_AGENT = 327.57e6 / 3440
+LSTM_TRAFFIC_PER_AGENT = 327.55e6 / 3440
 
 
 # the same for the paper's controller: 2,445 FP32 parameters, h and c of 4
