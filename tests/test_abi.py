@@ -88,3 +88,32 @@ def test_create_rejects_bad_arguments_without_gpu(L):
     assert L.eco_world_create(ctypes.byref(c), 0, ctypes.c_void_p(0x1000), 16,
                               ctypes.c_void_p(1), ctypes.byref(h)) == _lib.ECO_ENOMEM
     assert L.eco_batch_create(None, 0, ctypes.byref(h)) == _lib.ECO_EINVAL
+
+
+def test_new_entry_points_validate_arguments_without_gpu(L):
+    # every entry point checks its handle and pointers before any CUDA call
+    null = None
+    p = ctypes.c_void_p(0)
+    assert L.eco_world_analysis_async(null, null) == _lib.ECO_EINVAL
+    assert L.eco_world_lab_window(null) == _lib.ECO_EINVAL
+    assert L.eco_world_lab_read(null, null, null) == _lib.ECO_EINVAL
+    assert L.eco_world_counters_async(null, null) == _lib.ECO_EINVAL
+    r = _lib.CEcoTuneResult()
+    assert L.eco_batch_autotune(null, 4, ctypes.byref(r)) == _lib.ECO_EINVAL
+    assert L.eco_world_autotune(null, 4, ctypes.byref(r)) == _lib.ECO_EINVAL
+    assert L.eco_batch_set_config(null, 1, 4, 16) == _lib.ECO_EINVAL
+    assert L.eco_world_set_config(null, 1, 4, 16) == _lib.ECO_EINVAL
+    f = ctypes.c_int()
+    assert L.eco_world_get_config(null, ctypes.byref(f), ctypes.byref(f),
+                                  ctypes.byref(f)) == _lib.ECO_EINVAL
+    assert L.eco_strerror(_lib.ECO_EBOUNDS) == b"device index out of range"
+    # the paper controller's parameters are accepted, an unknown controller is not
+    c = _lib.to_c_params(P.paper_natural())
+    assert L.eco_world_bytes(ctypes.byref(c)) > 0
+    c.controller = 2
+    assert L.eco_world_bytes(ctypes.byref(c)) == 0
+    # the paper controller's arena is an order of magnitude smaller (9.8 KB rows)
+    lstm = _lib.to_c_params(P.paper_natural().replace(controller=0))
+    paper = _lib.to_c_params(P.paper_natural())
+    assert L.eco_world_bytes(ctypes.byref(lstm)) > 5 * L.eco_world_bytes(ctypes.byref(paper))
+    assert p.value is None
