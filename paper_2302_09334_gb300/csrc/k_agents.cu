@@ -418,7 +418,6 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
   __shared__ int pub[3], ex[6];
   __shared__ int cta_deaths;
   __shared__ unsigned long long cta_age_sum;
-  pdl_wait_and_release();
   cg::cluster_group cl = cg::this_cluster();
   const WorldDev &wd = *world_ptr(b, blockIdx.x / CLUSTER);
   const int rank = (int)cl.block_rank();
@@ -432,7 +431,12 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
     cta_deaths = 0;
     cta_age_sum = 0ull;
   }
-  const uint32_t t = (uint32_t)wd.ctr->t;
+  // The slot state below was last written by the previous step's slot
+  // phases, which have completed when this kernel starts (the kernels in
+  // between waited for them before releasing theirs), so it is read, through
+  // L2, before waiting for the observation+controller kernel; its outputs
+  // (targets, kills, claims) after.
+  const uint32_t t = (uint32_t)__ldcg(&wd.ctr->t);
   uint32_t *res = (t & 1u) ? wd.res0 : wd.res1;  // plane after this step's regrowth
   float *h_next = (t & 1u) ? wd.h0 : wd.h1;
 
@@ -445,15 +449,22 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
     al[k] = 0;
     if (k < ns) {
       const int s = s0 + k;
-      al[k] = wd.alive[s];
-      py[k] = wd.y[s];
-      px[k] = wd.x[s];
+      al[k] = __ldcg(&wd.alive[s]);
+      py[k] = __ldcg(&wd.y[s]);
+      px[k] = __ldcg(&wd.x[s]);
+      en[k] = __ldcg(&wd.energy[s]);
+      age[k] = __ldcg(&wd.age[s]);
+      low[k] = __ldcg(&wd.low_ctr[s]);
+      rep[k] = __ldcg(&wd.repr_ctr[s]);
+    }
+  }
+  pdl_wait_and_release();
+#pragma unroll
+  for (int k = 0; k < CL_SPT; ++k) {
+    if (k < ns) {
+      const int s = s0 + k;
       tgt[k] = wd.target[s];
       kil[k] = wd.killed[s] != 0;
-      en[k] = wd.energy[s];
-      age[k] = wd.age[s];
-      low[k] = wd.low_ctr[s];
-      rep[k] = wd.repr_ctr[s];
     }
   }
   __syncthreads();  // cta_deaths initialised
