@@ -28,7 +28,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# algorithmic bytes of the observation + LSTM kernel per agent (see DESIGN.md):
+# algorithmic bytes of the observation + LSTM kernel per agent:
 # 93,332 B of weights (4 blocks + read-out), h and c read and written
 # (4 x 128 B), position, energy, action and logits (36 B)
 LSTM_BYTES_PER_AGENT = 93332 + 512 + 36
