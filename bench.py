@@ -33,10 +33,10 @@ sys.path.insert(0, ROOT)
 # (4 x 128 B), position, energy, action and logits (36 B)
 LSTM_BYTES_PER_AGENT = 93332 + 512 + 36
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) of one observation+LSTM launch per agent, from the
-# ncu capture in profiles/k_lstm_paper_200x400_held3440.md; traffic grows with
-# the agents of a launch, so it is scaled by them (327.55 MB at 3,440 agents,
-# mean of the two captured launches).
+# DRAM bytes (read + write) of one observation+LSTM launch per agent, from an
+# ncu capture of this kernel on the 200x400 world with 3,440 agents held
+# (327.55 MB, mean of two launches); traffic grows with the agents of a
+# launch, so it is scaled by them.
 LSTM_TRAFFIC_PER_AGENT = 327.55e6 / 3440
 
 
