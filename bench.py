@@ -375,6 +375,7 @@ def bench_ours(args, params, rank, world_size, dist):
         line["batched"] = bench_batched(args, local)
         line["served"] = bench_served(args, local)
         line["paper_preset"] = bench_paper_preset(args, local)
+        line["large"] = bench_large(args, local)
     if not args.no_cpu_baseline:
         cores = args.cpu_cores or os.cpu_count() or 1
         v, steps, dt = run_oracle_pool(params, args.cpu_budget, 0, 100000, cores)
@@ -512,6 +513,56 @@ def bench_paper_preset(args, local):
             "l2": "not flushed: the world (about 10 MB of weights) stays L2-resident over a run"}
 
 
+def bench_large(args, local):
+    """The 1000x2000 world (20,000 agents at the start, capacity 131,072,
+    12.2 GB of weight rows; slot phases on the grid-wide kernels): one world
+    whose weights per step (1.9 GB and growing) are far larger than L2, so no
+    flush.  Plain steps timed one call at a time, then as many profiled
+    steps of a twin (same seed) for the per-kernel times."""
+    import torch
+    from paper_2302_09334_gb300._lib import C_AGENT_STEPS
+    from paper_2302_09334_gb300.params import large_1000x2000
+    from paper_2302_09334_gb300.world import World
+    p = large_1000x2000()
+    stream = torch.cuda.Stream(local)
+    w = World(p, 0, device=local, stream=stream)
+    twin = World(p, 0, device=local, stream=stream)
+    w.step(args.large_warmup)
+    twin.step(args.large_warmup)
+    w.sync()
+    a0 = int(w.counters()[C_AGENT_STEPS])
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    w.step(args.large_steps)
+    end.record(stream)
+    end.synchronize()
+    ms = start.elapsed_time(end)
+    agent_steps = int(w.counters()[C_AGENT_STEPS]) - a0
+    twin.profile(True, max_steps=args.large_steps)
+    t0 = int(twin.counters()[C_AGENT_STEPS])
+    twin.step(args.large_steps)
+    prof = twin.profile_read()
+    twin.profile(False)
+    prof_agent_steps = int(twin.counters()[C_AGENT_STEPS]) - t0
+    w.close()
+    twin.close()
+    torch.cuda.empty_cache()
+    lstm_ms, _ = prof["observe_lstm"]
+    bytes_lstm = prof_agent_steps * LSTM_BYTES_PER_AGENT + args.large_steps * 3 * p.H * p.W // 8
+    peak, kind = load_peaks()
+    achieved = bytes_lstm / (lstm_ms / 1e3) / 1e9 if lstm_ms > 0 else None
+    return {"workload": "large_1000x2000", "steps": args.large_steps,
+            "warmup": args.large_warmup, "value": agent_steps / (ms / 1e3),
+            "unit": "agent-steps/s", "ms_per_step": ms / args.large_steps,
+            "cell_steps_per_s": p.H * p.W * args.large_steps / (ms / 1e3),
+            "mean_population": agent_steps / args.large_steps,
+            "kernel_ms_per_step": {k: v[0] / v[1] for k, v in prof.items() if v[1]},
+            "roofline": {"kernel": "observe_lstm", "bound": "hbm", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if achieved else None},
+            "l2": "inputs larger than L2 (about 1.9 GB of weights per step), not flushed"}
+
+
 def bench_served(args, local):
     """Serving: Poisson request arrivals (20/s), admission by a 120 GB
     device-memory budget, continuous batching in chunks of 100 steps; the
@@ -555,6 +606,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--no-tune", action="store_true",
                     help="default launch configuration (no tuner world before the timed one)")
+    ap.add_argument("--large-steps", type=int, default=100)
+    ap.add_argument("--large-warmup", type=int, default=10)
     ap.add_argument("--paper-steps", type=int, default=20000)
     ap.add_argument("--paper-warmup", type=int, default=100)
     args = ap.parse_args()
