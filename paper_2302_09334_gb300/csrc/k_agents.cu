@@ -477,22 +477,33 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
       al[k] = 0;
       continue;
     }
-    if (tgt[k] >= 0 && ECO_IN_RANGE(wd, tgt[k] < wd.H * W) && wd.claim[tgt[k]] == s) {
+    // The claim and the resource words of both possible final cells are
+    // loaded together.  Only this agent can clear its final cell's bit (one
+    // agent per cell: a target was empty at the start of the phase and has
+    // one winner), so the bit read here is the one it eats, and the clear
+    // needs no returned value.
+    const bool cand = tgt[k] >= 0 && ECO_IN_RANGE(wd, tgt[k] < wd.H * W);
+    const int claimant = cand ? wd.claim[tgt[k]] : -1;
+    const int ty = cand ? tgt[k] / W : 0, tx = cand ? tgt[k] % W : 0;
+    uint32_t word = __ldcg(&res[py[k] * Wp + (px[k] >> 5)]);
+    const uint32_t word_there = cand ? __ldcg(&res[ty * Wp + (tx >> 5)]) : 0u;
+    if (cand && claimant == s) {
       wd.claim[tgt[k]] = INT_MAX;  // only the winner resets its cell
       wd.slot_map[py[k] * W + px[k]] = -1;
       wd.slot_map[tgt[k]] = s;
-      py[k] = tgt[k] / W;
-      px[k] = tgt[k] % W;
+      py[k] = ty;
+      px[k] = tx;
       wd.y[s] = py[k];
       wd.x[s] = px[k];
+      word = word_there;
     }
     bool dead, ate = false;
     if (kil[k]) {
       dead = true;
     } else {
       const uint32_t bit = 1u << (px[k] & 31);
-      const uint32_t old = atomicAnd(&res[py[k] * Wp + (px[k] >> 5)], ~bit);
-      ate = (old & bit) != 0u;
+      ate = (word & bit) != 0u;
+      if (ate) atomicAnd(&res[py[k] * Wp + (px[k] >> 5)], ~bit);
       float e = en[k];
       if (ate) e = __fadd_rn(e, wd.e_gain);
       e = __fsub_rn(e, wd.e_decay);
