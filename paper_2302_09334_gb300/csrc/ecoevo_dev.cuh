@@ -164,6 +164,8 @@ struct WorldDev {            // read-only while kernels run
   uint8_t *lab_seen, *lab_ate;  // [C] greediness window: a resource in view / a meal
                              // (plain stores, no read-modify-write, in the hot kernels)
   int32_t *lab_t, *lab_c;    // [C] windows with a resource in view / with a meal
+  int32_t *scan_blocks;      // [(ceil(C/SLOT_BLOCK) + 1) * 4] per-block counts of the
+                             // split compaction (free, successful parents, survivors)
   unsigned long long *analysis;  // [ANALYSIS_WORDS] output of the analysis kernels
 };
 
@@ -311,7 +313,11 @@ void preload_paper();
 void launch_move_apply(const BatchDev &b, cudaStream_t s);
 void launch_physio(const BatchDev &b, cudaStream_t s);
 void launch_birth_claim(const BatchDev &b, cudaStream_t s);
-void launch_scan(const BatchDev &b, cudaStream_t s);
+// the split compaction, for worlds of any capacity: four kernels
+void launch_scan_count(const BatchDev &b, cudaStream_t s);
+void launch_scan_prefix(const BatchDev &b, cudaStream_t s);
+void launch_scan_lists(const BatchDev &b, cudaStream_t s);
+void launch_scan_children(const BatchDev &b, cudaStream_t s);
 void launch_tail(const BatchDev &b, cudaStream_t s);   // regrowth of t+1 + births of t
 void launch_agents_fused(const BatchDev &b, cudaStream_t s);
 void configure_lstm();   // once per device, before the first launch

@@ -67,7 +67,7 @@ struct Layout {
       slot_map, claim, bclaim, alive, killed, ate, flag, y, x, energy, repr_ctr,
       low_ctr, age, action, forced, target, birth_cell, arrive, h0, h1, c,
       logits, alive_list, free_list, birth_parent, birth_child, snap_cell, analysis,
-      prev_act, lab_seen, lab_ate, lab_t, lab_c, weights, staging, total;
+      prev_act, lab_seen, lab_ate, lab_t, lab_c, scan_blocks, weights, staging, total;
 };
 
 Layout layout_of(const EcoParams *p) {
@@ -122,6 +122,7 @@ Layout layout_of(const EcoParams *p) {
   L.lab_ate = take(C1);
   L.lab_t = take(C1 * 4);
   L.lab_c = take(C1 * 4);
+  L.scan_blocks = take(((C1 + SLOT_BLOCK - 1) / SLOT_BLOCK + 1) * 4 * 4);
   L.weights = take(C1 * (size_t)wstride_of(p->controller) * 4);
   L.staging = take((size_t)STAGING_AGENTS * WSTRIDE * 4);
   L.total = off;
@@ -233,10 +234,12 @@ enum { K_REGROW, K_LSTM, K_MOVE_CLAIM, K_MOVE_APPLY, K_PHYSIO, K_BIRTH_CLAIM, K_
 // makes the move claims; it ends with the tail kernel: the regrowth
 // of the next step's plane in the same launch as the mutation of this
 // step's births (they touch disjoint data).
+// (the four kernels of the split compaction are timed together as "scan")
 const StepKernel kSplitStep[] = {
     {K_LSTM, launch_lstm},
     {K_MOVE_APPLY, launch_move_apply}, {K_PHYSIO, launch_physio},
-    {K_BIRTH_CLAIM, launch_birth_claim}, {K_SCAN, launch_scan},
+    {K_BIRTH_CLAIM, launch_birth_claim}, {K_SCAN, launch_scan_count},
+    {K_SCAN, launch_scan_prefix}, {K_SCAN, launch_scan_lists}, {K_SCAN, launch_scan_children},
     {K_TAIL, launch_tail}};
 const StepKernel kFusedStep[] = {{K_LSTM, launch_lstm},
                                  {K_AGENTS_FUSED, launch_agents_fused},
@@ -245,11 +248,15 @@ const StepKernel kFusedStep[] = {{K_LSTM, launch_lstm},
 const StepKernel kSplitStepPaper[] = {
     {K_PAPER, launch_paper_ctrl},
     {K_MOVE_APPLY, launch_move_apply}, {K_PHYSIO, launch_physio},
-    {K_BIRTH_CLAIM, launch_birth_claim}, {K_SCAN, launch_scan},
+    {K_BIRTH_CLAIM, launch_birth_claim}, {K_SCAN, launch_scan_count},
+    {K_SCAN, launch_scan_prefix}, {K_SCAN, launch_scan_lists}, {K_SCAN, launch_scan_children},
     {K_TAIL, launch_tail}};
 const StepKernel kFusedStepPaper[] = {{K_PAPER, launch_paper_ctrl},
                                       {K_AGENTS_FUSED, launch_agents_fused},
                                       {K_TAIL, launch_tail}};
+
+static_assert(sizeof(kSplitStep) / sizeof(kSplitStep[0]) <= ECO_NKERNELS,
+              "the profiler keeps two events per kernel of a step, for up to ECO_NKERNELS");
 
 int step_kernels(const BatchDev &bd, const StepKernel **list) {
   const bool paper = bd.controller == ECO_CTRL_PAPER;
@@ -627,6 +634,7 @@ static void fill_descriptor(EcoWorld *w) {
   d.lab_ate = (uint8_t *)(a + L.lab_ate);
   d.lab_t = (int32_t *)(a + L.lab_t);
   d.lab_c = (int32_t *)(a + L.lab_c);
+  d.scan_blocks = (int32_t *)(a + L.scan_blocks);
   d.analysis = (unsigned long long *)(a + L.analysis);
   w->dd = (WorldDev *)(a + L.wdev);
 }

@@ -132,40 +132,6 @@ __device__ inline void slot_birth_claim(const WorldDev *wd, int s) {
   atomicMin(&wd->bclaim[cell], s);
 }
 
-// Exclusive block scan of two counters over SCAN_THREADS threads.
-__device__ inline void block_scan2(int a, int b, int &ea, int &eb, int &ta,
-                                   int &tb, int *sh /* [2*32] */) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int ia = a, ib = b;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int xa = __shfl_up_sync(0xFFFFFFFFu, ia, o);
-    const int xb = __shfl_up_sync(0xFFFFFFFFu, ib, o);
-    if (lane >= o) { ia += xa; ib += xb; }
-  }
-  if (lane == 31) { sh[warp] = ia; sh[32 + warp] = ib; }
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = blockDim.x >> 5;
-    int va = lane < nw ? sh[lane] : 0, vb = lane < nw ? sh[32 + lane] : 0;
-    int sa = va, sb = vb;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int xa = __shfl_up_sync(0xFFFFFFFFu, sa, o);
-      const int xb = __shfl_up_sync(0xFFFFFFFFu, sb, o);
-      if (lane >= o) { sa += xa; sb += xb; }
-    }
-    if (lane < nw) { sh[lane] = sa - va; sh[32 + lane] = sb - vb; }
-    if (lane == 31) { sh[64] = sa; sh[65] = sb; }
-  }
-  __syncthreads();
-  ea = sh[warp] + ia - a;
-  eb = sh[32 + warp] + ib - b;
-  ta = sh[64];
-  tb = sh[65];
-  __syncthreads();
-}
-
 // Birth k of the step: parent s, child in free slot `child` on the parent's
 // claimed cell; the child starts with e0, zero counters and zero recurrent
 // state, the parent's reproduction counter restarts.
@@ -223,60 +189,6 @@ __device__ inline void finish_step(const WorldDev &wd, int S, int F, int pop, ui
   c.t = (long long)t + 1;
 }
 
-// Births and the next alive list of one world, by one CTA of SCAN_THREADS.
-__device__ void scan_world(const WorldDev &wd, int *sh) {
-  const int C = wd.C;
-  const int per = (C + SCAN_THREADS - 1) / SCAN_THREADS;
-  const int s0 = min(C, (int)threadIdx.x * per), s1 = min(C, s0 + per);
-  const uint32_t t = (uint32_t)wd.ctr->t;
-  float *h_next = (t & 1u) ? wd.h0 : wd.h1;
-
-  // 1. successful parents: lowest claimant of their birth cell
-  int n_free = 0, n_succ = 0;
-  for (int s = s0; s < s1; ++s) {
-    const int cell = wd.birth_cell[s];
-    const bool ok = wd.alive[s] && cell >= 0 && ECO_IN_RANGE(wd, cell < wd.H * wd.W) &&
-                    wd.bclaim[cell] == s;
-    wd.flag[s] = ok ? 1 : 0;
-    n_succ += ok;
-    n_free += wd.alive[s] ? 0 : 1;
-  }
-  int free_off, succ_off, F, S;
-  block_scan2(n_free, n_succ, free_off, succ_off, F, S, sh);
-
-  // 2. reset the claim cells; list the free slots the births will take
-  for (int s = s0; s < s1; ++s) {
-    const int cell = wd.birth_cell[s];
-    if (cell >= 0 && cell < wd.H * wd.W) wd.bclaim[cell] = INT_MAX;
-    if (!wd.alive[s]) {
-      if (free_off < S) wd.free_list[free_off] = s;
-      ++free_off;
-    }
-  }
-  __syncthreads();
-
-  // 3. birth k (ascending parent) takes free slot k; past the free list the
-  //    birth is dropped and the parent keeps its counter
-  for (int s = s0; s < s1; ++s) {
-    if (!wd.flag[s]) continue;
-    const int k = succ_off++;
-    if (k >= F) continue;
-    const int child = wd.free_list[k];
-    if (!ECO_IN_RANGE(wd, child >= 0 && child < wd.C)) continue;
-    init_child(wd, s, wd.birth_cell[s], k, child, h_next);
-  }
-  __syncthreads();
-
-  // 4. alive list of the next step (ascending slots)
-  int n_alive = 0;
-  for (int s = s0; s < s1; ++s) n_alive += wd.alive[s];
-  int alive_off, dummy, pop, dummy2;
-  block_scan2(n_alive, 0, alive_off, dummy, pop, dummy2, sh);
-  for (int s = s0; s < s1; ++s)
-    if (wd.alive[s]) wd.alive_list[alive_off++] = s;
-
-  if (threadIdx.x == 0) finish_step(wd, S, F, pop, t);
-}
 
 __global__ void __launch_bounds__(SLOT_BLOCK) k_move_apply(const __grid_constant__ BatchDev b) {
   pdl_wait_and_release();
@@ -295,11 +207,6 @@ __global__ void __launch_bounds__(SLOT_BLOCK) k_birth_claim(const __grid_constan
   const WorldDev *wd;
   const int s = slot_of_thread(b, wd);
   if (s >= 0) slot_birth_claim(wd, s);
-}
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan(const __grid_constant__ BatchDev b) {
-  __shared__ int sh[66];
-  pdl_wait_and_release();
-  scan_world(*world_ptr(b, blockIdx.x), sh);
 }
 
 // Worlds of capacity <= FUSED_MAX_C: every slot phase of a step (moves,
@@ -596,6 +503,127 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
   cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
+// ---------------------------------------------------------------------------
+// Split compaction (worlds of any capacity): the same ranks as the cluster
+// kernel's, over blocks of SLOT_BLOCK slots in four kernels --
+//   count     per block: free slots, successful parents, survivors
+//   prefix    per world, one CTA: exclusive prefixes of the block counts,
+//             totals, and the step's counters
+//   lists     per block: claim resets, the free slots the births take, the
+//             next alive list (survivors before + min(free before, births))
+//   children  per block: birth k (ascending parent) takes free slot k
+// scan_blocks[4*blk + i] holds block blk's count i, then its prefix;
+// scan_blocks[4*nb + i] the world's total i.
+// ---------------------------------------------------------------------------
+__device__ inline int slot_blocks(const WorldDev &wd) { return (wd.C + SLOT_BLOCK - 1) / SLOT_BLOCK; }
+
+__global__ void __launch_bounds__(SLOT_BLOCK) k_scan_count(const __grid_constant__ BatchDev b) {
+  __shared__ int sh[3 * 32 + 3];
+  pdl_wait_and_release();
+  const WorldDev *wdp;
+  const int s = slot_of_thread(b, wdp);
+  const WorldDev &wd = *wdp;
+  int v[3] = {0, 0, 0};
+  if (s >= 0) {
+    const int a = wd.alive[s];
+    const int cell = wd.birth_cell[s];
+    const bool ok = a && cell >= 0 && ECO_IN_RANGE(wd, cell < wd.H * wd.W) &&
+                    wd.bclaim[cell] == s;
+    wd.flag[s] = ok ? 1 : 0;
+    v[0] = a ? 0 : 1;
+    v[1] = ok ? 1 : 0;
+    v[2] = a ? 1 : 0;
+  }
+  int e[3], tot[3];
+  block_scan3(v, e, tot, sh);
+  if (threadIdx.x == 0) {   // the block's first slot exists
+    const int blk = s / SLOT_BLOCK;
+    for (int i = 0; i < 3; ++i) wd.scan_blocks[4 * blk + i] = tot[i];
+  }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_prefix(const __grid_constant__ BatchDev b) {
+  __shared__ int sh[3 * 32 + 3];
+  pdl_wait_and_release();
+  const WorldDev &wd = *world_ptr(b, blockIdx.x);
+  const int nb = slot_blocks(wd);
+  const int per = (nb + SCAN_THREADS - 1) / SCAN_THREADS;
+  const int b0 = min(nb, (int)threadIdx.x * per), b1 = min(nb, b0 + per);
+  int v[3] = {0, 0, 0};
+  for (int k = b0; k < b1; ++k)
+    for (int i = 0; i < 3; ++i) v[i] += wd.scan_blocks[4 * k + i];
+  int e[3], tot[3];
+  block_scan3(v, e, tot, sh);
+  for (int k = b0; k < b1; ++k)
+    for (int i = 0; i < 3; ++i) {
+      const int c = wd.scan_blocks[4 * k + i];
+      wd.scan_blocks[4 * k + i] = e[i];
+      e[i] += c;
+    }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 3; ++i) wd.scan_blocks[4 * nb + i] = tot[i];
+    const int F = tot[0], S = tot[1], SURV = tot[2];
+    // counters of the step; the later kernels read births_t, never t
+    finish_step(wd, S, F, SURV + min(S, F), (uint32_t)wd.ctr->t);
+  }
+}
+
+__global__ void __launch_bounds__(SLOT_BLOCK) k_scan_lists(const __grid_constant__ BatchDev b) {
+  __shared__ int sh[3 * 32 + 3];
+  pdl_wait_and_release();
+  const WorldDev *wdp;
+  const int s = slot_of_thread(b, wdp);
+  const WorldDev &wd = *wdp;
+  const int nb = slot_blocks(wd);
+  int v[3] = {0, 0, 0};
+  int a = 0;
+  if (s >= 0) {
+    a = wd.alive[s];
+    v[0] = a ? 0 : 1;
+    v[1] = wd.flag[s];
+    v[2] = a ? 1 : 0;
+  }
+  int e[3], tot[3];
+  block_scan3(v, e, tot, sh);
+  if (s < 0) return;
+  const int blk = s / SLOT_BLOCK;
+  const int F = wd.scan_blocks[4 * nb], S = wd.scan_blocks[4 * nb + 1];
+  const int births = min(S, F);
+  const int free_before = wd.scan_blocks[4 * blk] + e[0];
+  const int surv_before = wd.scan_blocks[4 * blk + 2] + e[2];
+  const int cell = wd.birth_cell[s];
+  if (cell >= 0 && cell < wd.H * wd.W) wd.bclaim[cell] = INT_MAX;
+  const int pos = surv_before + min(free_before, births);
+  if (a) {
+    wd.alive_list[pos] = s;
+  } else {
+    if (free_before < S) wd.free_list[free_before] = s;
+    if (free_before < births) wd.alive_list[pos] = s;   // receives a child
+  }
+}
+
+__global__ void __launch_bounds__(SLOT_BLOCK) k_scan_children(const __grid_constant__ BatchDev b) {
+  __shared__ int sh[3 * 32 + 3];
+  pdl_wait_and_release();
+  const WorldDev *wdp;
+  const int s = slot_of_thread(b, wdp);
+  const WorldDev &wd = *wdp;
+  const int nb = slot_blocks(wd);
+  int v[3] = {0, 0, 0};
+  if (s >= 0) v[1] = wd.flag[s];
+  int e[3], tot[3];
+  block_scan3(v, e, tot, sh);
+  if (s < 0 || !v[1]) return;
+  const int blk = s / SLOT_BLOCK;
+  const int F = wd.scan_blocks[4 * nb];
+  const int k = wd.scan_blocks[4 * blk + 1] + e[1];
+  if (k >= F) return;   // dropped: the parent keeps its counter
+  const int child = wd.free_list[k];
+  if (!ECO_IN_RANGE(wd, child >= 0 && child < wd.C)) return;
+  const uint32_t t = wd.ctr->births_t;   // the step's index (finish_step ran)
+  init_child(wd, s, wd.birth_cell[s], k, child, (t & 1u) ? wd.h0 : wd.h1);
+}
+
 // Child weights, physical layout: W[child][p] = W[parent][p] + sigma * N_j
 // with N_j normal j = logical index of p of the stream (TAG_MUT, t, parent).
 // A float4 of a weight row or of the read-out holds four consecutive logical
@@ -733,7 +761,10 @@ void preload_agents() {
   cudaFuncGetAttributes(&a, k_move_apply);
   cudaFuncGetAttributes(&a, k_physio);
   cudaFuncGetAttributes(&a, k_birth_claim);
-  cudaFuncGetAttributes(&a, k_scan);
+  cudaFuncGetAttributes(&a, k_scan_count);
+  cudaFuncGetAttributes(&a, k_scan_prefix);
+  cudaFuncGetAttributes(&a, k_scan_lists);
+  cudaFuncGetAttributes(&a, k_scan_children);
   cudaFuncGetAttributes(&a, k_tail);
   cudaFuncGetAttributes(&a, k_agents_cluster);
 }
@@ -747,8 +778,17 @@ void launch_physio(const BatchDev &b, cudaStream_t s) {
 void launch_birth_claim(const BatchDev &b, cudaStream_t s) {
   launch_step_kernel(k_birth_claim, b.total_slot_blocks, SLOT_BLOCK, 0, s, b);
 }
-void launch_scan(const BatchDev &b, cudaStream_t s) {
-  launch_step_kernel(k_scan, b.n, SCAN_THREADS, 0, s, b);
+void launch_scan_count(const BatchDev &b, cudaStream_t s) {
+  launch_step_kernel(k_scan_count, b.total_slot_blocks, SLOT_BLOCK, 0, s, b);
+}
+void launch_scan_prefix(const BatchDev &b, cudaStream_t s) {
+  launch_step_kernel(k_scan_prefix, b.n, SCAN_THREADS, 0, s, b);
+}
+void launch_scan_lists(const BatchDev &b, cudaStream_t s) {
+  launch_step_kernel(k_scan_lists, b.total_slot_blocks, SLOT_BLOCK, 0, s, b);
+}
+void launch_scan_children(const BatchDev &b, cudaStream_t s) {
+  launch_step_kernel(k_scan_children, b.total_slot_blocks, SLOT_BLOCK, 0, s, b);
 }
 void launch_agents_fused(const BatchDev &b, cudaStream_t s) {
   launch_step_kernel(k_agents_cluster, b.n * CLUSTER, SCAN_THREADS, 0, s, b);
