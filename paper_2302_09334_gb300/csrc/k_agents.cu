@@ -282,31 +282,10 @@ __device__ inline void cluster_prefix3(cg::cluster_group &cl, int *pub, int *out
   __syncthreads();
 }
 
-// Exclusive prefix over the cluster's CTAs of two per-CTA totals.
-__device__ inline void cluster_prefix2(cg::cluster_group &cl, int *pub, int *out, int a,
-                                       int b) {
-  if (threadIdx.x == 0) {
-    pub[0] = a;
-    pub[1] = b;
-  }
-  cl.sync();
-  if (threadIdx.x == 0) {
-    const int me = (int)cl.block_rank();
-    int ba = 0, bb = 0, ta = 0, tb = 0;
-    for (int r = 0; r < CLUSTER; ++r) {
-      const int *rp = cl.map_shared_rank(pub, r);
-      const int ra = rp[0], rb = rp[1];
-      if (r < me) { ba += ra; bb += rb; }
-      ta += ra;
-      tb += rb;
-    }
-    out[0] = ba; out[1] = bb; out[2] = ta; out[3] = tb;
-  }
-  __syncthreads();
-}
-
-// Slots per thread of the cluster kernel (8 CTAs x 1024 threads).
+// Slots per thread of the fused kernel (8 CTAs x 1024 threads per world), and
+// the largest capacity one CTA covers with as many slots per thread.
 constexpr int CL_SPT = (FUSED_MAX_C + CLUSTER * SCAN_THREADS - 1) / (CLUSTER * SCAN_THREADS);
+constexpr int SINGLE_MAX_C = CL_SPT * SCAN_THREADS;
 
 // Every slot phase of a step for one world (the move claims are already
 // made by the observation+LSTM kernel).  Each thread owns up to CL_SPT
@@ -319,17 +298,29 @@ constexpr int CL_SPT = (FUSED_MAX_C + CLUSTER * SCAN_THREADS - 1) / (CLUSTER * S
 // children fill the free slots of rank below the number of births in slot
 // order, so a slot's place in the next alive list is the survivors before
 // it plus min(free slots before it, births).
-__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
-    k_agents_cluster(const __grid_constant__ BatchDev b) {
+//
+// NCTA = CLUSTER: one 8-CTA cluster per world, phases separated by the
+// cluster barrier, per-CTA totals exchanged through distributed shared
+// memory.  NCTA = 1 (every capacity <= SINGLE_MAX_C): one CTA per world, the
+// same phases separated by CTA barriers.
+template <int NCTA>
+__device__ __forceinline__ void phase_sync() {
+  if constexpr (NCTA == 1)
+    __syncthreads();
+  else
+    cg::this_cluster().sync();
+}
+
+template <int NCTA>
+__device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
   __shared__ int sh[3 * 32 + 3];
   __shared__ int pub[3], ex[6];
   __shared__ int cta_deaths;
   __shared__ unsigned long long cta_age_sum;
-  cg::cluster_group cl = cg::this_cluster();
-  const WorldDev &wd = *world_ptr(b, blockIdx.x / CLUSTER);
-  const int rank = (int)cl.block_rank();
+  const WorldDev &wd = *world_ptr(b, blockIdx.x / NCTA);
+  const int rank = NCTA == 1 ? 0 : (int)cg::this_cluster().block_rank();
   const int C = wd.C, W = wd.W, Wp = wd.Wp;
-  const int per_cta = (C + CLUSTER - 1) / CLUSTER;
+  const int per_cta = (C + NCTA - 1) / NCTA;
   const int c0 = min(C, rank * per_cta), c1 = min(C, c0 + per_cta);
   const int per = (c1 - c0 + SCAN_THREADS - 1) / SCAN_THREADS;
   const int s0 = min(c1, c0 + (int)threadIdx.x * per);
@@ -441,7 +432,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
     atomicAdd(&wd.ctr->deaths_step, cta_deaths);
     atomicAdd(&wd.ctr->an_age_sum, cta_age_sum);
   }
-  cl.sync();
+  phase_sync<NCTA>();
   // ---- birth claims: first free N, S, E, W cell; lowest parent slot wins
 #pragma unroll
   for (int k = 0; k < CL_SPT; ++k) {
@@ -450,7 +441,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
     bcell[k] = first_free_neighbour(wd, py[k], px[k]);
     if (bcell[k] >= 0) atomicMin(&wd.bclaim[bcell[k]], s0 + k);
   }
-  cl.sync();
+  phase_sync<NCTA>();
   // ---- compaction (contiguous slots per thread, so ranks follow slot order)
   bool ok[CL_SPT];
   int cnt[3] = {0, 0, 0};  // free slots, successful parents, survivors
@@ -463,7 +454,17 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
   }
   int off[3], tot[3];
   block_scan3(cnt, off, tot, sh);
-  cluster_prefix3(cl, pub, ex, tot);  // every claim cell read before any reset
+  if constexpr (NCTA == 1) {
+    if (threadIdx.x == 0)
+      for (int i = 0; i < 3; ++i) {
+        ex[i] = 0;
+        ex[3 + i] = tot[i];
+      }
+    __syncthreads();   // every claim cell read before any reset
+  } else {
+    cg::cluster_group cl = cg::this_cluster();
+    cluster_prefix3(cl, pub, ex, tot);  // every claim cell read before any reset
+  }
   int free_off = off[0] + ex[0], succ_off = off[1] + ex[1];
   const int surv_off = off[2] + ex[2];
   const int F = ex[3], S = ex[4], SURV = ex[5];
@@ -478,7 +479,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
       ++free_rank;
     }
   }
-  cl.sync();
+  phase_sync<NCTA>();
   free_rank = free_off;
 #pragma unroll
   for (int k = 0; k < CL_SPT; ++k) {
@@ -500,7 +501,16 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
     }
   }
   if (rank == 0 && threadIdx.x == 0) finish_step(wd, S, F, SURV + births, t);
-  cl.sync();  // no CTA leaves while another may still read its shared memory
+  phase_sync<NCTA>();  // no CTA leaves while another may still read its shared memory
+}
+
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
+    k_agents_cluster(const __grid_constant__ BatchDev b) {
+  agents_fused_body<CLUSTER>(b);
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_agents_single(const __grid_constant__ BatchDev b) {
+  agents_fused_body<1>(b);
 }
 
 // ---------------------------------------------------------------------------
@@ -630,7 +640,6 @@ __global__ void __launch_bounds__(SLOT_BLOCK) k_scan_children(const __grid_const
 // indices starting at a multiple of 4, so one Philox draw serves it; the
 // bias rows of a block are permuted and take one draw per element.
 constexpr int SPAWN_THREADS = 256;
-constexpr int NVEC = WSTRIDE / 4;  // 5840 float4 per agent (LSTM(32) controller)
 
 // Float4 number vi of an agent's physical weights after adding scale * N_j
 // (stream tag, t, id) to `base`.  The paper controller's rows are in
@@ -767,6 +776,7 @@ void preload_agents() {
   cudaFuncGetAttributes(&a, k_scan_children);
   cudaFuncGetAttributes(&a, k_tail);
   cudaFuncGetAttributes(&a, k_agents_cluster);
+  cudaFuncGetAttributes(&a, k_agents_single);
 }
 
 void launch_move_apply(const BatchDev &b, cudaStream_t s) {
@@ -791,7 +801,10 @@ void launch_scan_children(const BatchDev &b, cudaStream_t s) {
   launch_step_kernel(k_scan_children, b.total_slot_blocks, SLOT_BLOCK, 0, s, b);
 }
 void launch_agents_fused(const BatchDev &b, cudaStream_t s) {
-  launch_step_kernel(k_agents_cluster, b.n * CLUSTER, SCAN_THREADS, 0, s, b);
+  if (b.max_capacity <= SINGLE_MAX_C)
+    launch_step_kernel(k_agents_single, b.n, SCAN_THREADS, 0, s, b);
+  else
+    launch_step_kernel(k_agents_cluster, b.n * CLUSTER, SCAN_THREADS, 0, s, b);
 }
 void launch_tail(const BatchDev &b, cudaStream_t s) {
   const int spawn = b.spawn_ctas > 0 ? b.spawn_ctas : SPAWN_CTAS_PER_SM * b.n_sms;
