@@ -27,6 +27,15 @@
  *                      brute force on <=4x4 worlds, slot-assignment rules
  *   or_world_analysis  pinned: hand-counted walks and lifetimes, closed
  *                      forms of the bin edges, age-based identity check
+ *   or_pc_observe      pinned: numpy padded-slice reconstruction (15x15)
+ *   or_pc_forward      pinned: torch conv2d/avg_pool2d/LSTMCell/linear
+ *                      (float64); the layer sizes give the paper's 2445
+ *                      parameters
+ *   or_pc_sample       pinned: closed forms (uniform, one-hot, ties),
+ *                      frequencies against softmax(50 logits)
+ *   or_action_uniform  pinned: numpy Philox reconstruction
+ *   or_world_lab_window pinned: hand-counted walks past placed resources,
+ *                      free-run recount from the views and meals
  */
 #ifndef ECOEVO_ORACLE_H
 #define ECOEVO_ORACLE_H
