@@ -501,7 +501,9 @@ __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
     }
   }
   if (rank == 0 && threadIdx.x == 0) finish_step(wd, S, F, SURV + births, t);
-  phase_sync<NCTA>();  // no CTA leaves while another may still read its shared memory
+  // no closing barrier: the last reads of another CTA's shared memory (the
+  // per-CTA totals of the compaction) precede the barrier before the
+  // children, so a CTA may leave as soon as it is done
 }
 
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
