@@ -307,32 +307,43 @@ def bench_ours(args, params, rank, world_size, dist):
 
     # e2e through the C ABI with host buffers, over the same steps as the
     # timed region: the state they start from (with the weights of every
-    # living agent) is uploaded from host memory, then every step's counters
-    # are streamed to page-locked host memory, and every 50 steps (the
-    # movement window of the paper's analyses, App. C) the window's analysis
-    # record (population, resources, deaths and ages, displacement bins).
-    from paper_2302_09334_gb300._lib import NANALYSIS
+    # living agent) is uploaded from host memory; the steps run as a user
+    # runs them (world.step over 50-step windows, in the world's graph
+    # chunks), and every step's counters reach page-locked host memory
+    # through the counter log, written by the kernel that ends the step;
+    # after every 50 steps (the movement window of the paper's analyses,
+    # App. C) the window's analysis record (population, resources, deaths
+    # and ages, displacement bins) is copied back too.
+    import numpy as np
+    from paper_2302_09334_gb300._lib import C_AGENT_STEPS, C_T, NANALYSIS, NCOUNTERS
     h2d = sum(v.nbytes for k, v in e2e_state.items() if k not in ("slot_map",))
-    from paper_2302_09334_gb300._lib import C_AGENT_STEPS, NCOUNTERS
-    counters_host = torch.empty((args.steps + 1, NCOUNTERS), dtype=torch.int64, pin_memory=True)
+    counter_log = torch.full((args.steps, NCOUNTERS), -1, dtype=torch.int64, pin_memory=True)
+    counters0 = torch.empty(NCOUNTERS, dtype=torch.int64, pin_memory=True)
     analysis_host = torch.empty((args.steps // 50 + 1, NANALYSIS), dtype=torch.int64,
                                 pin_memory=True)
+    world.counter_log(counter_log)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     world.load_state(e2e_state)
-    world.counters_async(counters_host[0])
-    d2h = 0
-    for k in range(args.steps):
-        world.step(1)
-        world.counters_async(counters_host[k + 1])
-        d2h += NCOUNTERS * 8
-        if (k + 1) % 50 == 0:
-            world.analysis_async(analysis_host[(k + 1) // 50 - 1])
+    world.counters_async(counters0)
+    d2h = NCOUNTERS * 8
+    done = 0
+    while done < args.steps:
+        n = min(50, args.steps - done)
+        world.step(n)
+        done += n
+        d2h += n * NCOUNTERS * 8
+        if n == 50:
+            world.analysis_async(analysis_host[done // 50 - 1])
             d2h += NANALYSIS * 8
     world.sync()
     e2e_dt = time.perf_counter() - t0
-    e2e_agent_steps = int(counters_host[args.steps, C_AGENT_STEPS] -
-                          counters_host[0, C_AGENT_STEPS])
+    world.counter_log(None)
+    t_first = int(counters0[C_T])
+    rows = counter_log.numpy()[[(t_first + k) % args.steps for k in range(args.steps)]]
+    if (rows[:, C_T] != np.arange(t_first + 1, t_first + args.steps + 1)).any():
+        raise RuntimeError("the counter log misses steps of the e2e leg")
+    e2e_agent_steps = int(rows[-1, C_AGENT_STEPS] - counters0[C_AGENT_STEPS])
     d2h //= args.steps
     from paper_2302_09334_gb300.world import analysis_record, life_expectancy
     windows = [analysis_record(r) for r in analysis_host[:args.steps // 50].numpy()]

@@ -220,6 +220,22 @@ int eco_world_load_state(EcoWorld *world, const EcoState *in, int set_counters);
  * stream its results without waiting for every step. */
 int eco_world_counters_async(EcoWorld *world, int64_t *out_host);
 
+/* Per-step counter log written by the step kernels themselves: from the
+ * work enqueued after this call on, the kernel that ends step t (t counted
+ * from 0, so counters[ECO_C_T] == t + 1 after it) writes the ECO_NCOUNTERS
+ * counters, in ECO_C_* order, to row t mod rows of log_host, an array of
+ * rows x ECO_NCOUNTERS int64 that the caller owns and keeps allocated and
+ * page-locked while the log is on.  It must be mapped into the device's
+ * address space (memory from cudaHostAlloc or cudaMallocHost, or a pinned
+ * torch tensor, on a system with unified addressing).  No copy or launch is
+ * added to a step, so a loop over many steps (graph chunks included) gets
+ * every step's counters on the host; a row is valid once the world's stream
+ * has passed that step (eco_world_sync, or an event).  log_host == NULL
+ * turns the log off.  Synchronous (waits for the world's stream).  Errors: ECO_EINVAL
+ * (world NULL; rows <= 0; log_host not 8-byte aligned, not page-locked or
+ * not mapped), ECO_ECUDA. */
+int eco_world_counter_log(EcoWorld *world, int64_t *log_host, int64_t rows);
+
 /* Metrics of the paper's analyses (App. C), for the window of steps since
  * the previous call (or since create / load_state, which start a window).
  * Life expectancy over several windows = sum(death_age_sum) / sum(deaths);

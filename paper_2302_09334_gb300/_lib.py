@@ -108,6 +108,7 @@ SIGNATURES = {
     "eco_world_load_state": (ctypes.c_int, [_P, ctypes.POINTER(CEcoState), ctypes.c_int]),
     "eco_world_sync": (ctypes.c_int, [_P]),
     "eco_world_counters_async": (ctypes.c_int, [_P, _P]),
+    "eco_world_counter_log": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
     "eco_world_analysis_async": (ctypes.c_int, [_P, _P]),
     "eco_world_lab_window": (ctypes.c_int, [_P]),
     "eco_world_lab_read": (ctypes.c_int, [_P, _P, _P]),

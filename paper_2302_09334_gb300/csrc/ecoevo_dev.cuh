@@ -124,6 +124,10 @@ struct Counters {            // mutable, updated by the kernels
   // summed ages at death since then
   long long snap_t, an_deaths;
   unsigned long long an_age_sum;
+  // per-step counter log in mapped page-locked host memory (null: off):
+  // the end of step t writes the first ECO_NCOUNTERS fields to row t % log_rows
+  long long *log;
+  long long log_rows;
 };
 
 // Record of the analysis kernels, in the order of the C ABI's EcoAnalysis.

@@ -786,6 +786,32 @@ int eco_world_counters_async(EcoWorld *w, int64_t *out_host) {
   return ECO_OK;
 }
 
+int eco_world_counter_log(EcoWorld *w, int64_t *log_host, int64_t rows) {
+  Trace trace("eco_world_counter_log");
+  if (!w) return ECO_EINVAL;
+  struct {
+    long long *log;
+    long long rows;
+  } v = {nullptr, 0};
+  static_assert(offsetof(Counters, log_rows) == offsetof(Counters, log) + sizeof(long long *),
+                "the log's pointer and row count are written together");
+  if (log_host) {
+    if (rows <= 0 || ((uintptr_t)log_host & 7u)) return ECO_EINVAL;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, log_host) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return ECO_EINVAL;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return ECO_EINVAL;
+    v.log = (long long *)a.devicePointer;
+    v.rows = rows;
+  }
+  ECO_CU(cudaMemcpyAsync(&w->hd.ctr->log, &v, sizeof v, cudaMemcpyHostToDevice, w->stream));
+  // the source is on the stack: the copy must have read it before returning
+  ECO_CU(cudaStreamSynchronize(w->stream));
+  return ECO_OK;
+}
+
 int eco_world_analysis_async(EcoWorld *w, EcoAnalysis *out_host) {
   Trace trace("eco_world_analysis_async");
   if (!w || !out_host) return ECO_EINVAL;

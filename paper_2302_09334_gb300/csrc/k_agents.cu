@@ -187,6 +187,19 @@ __device__ inline void finish_step(const WorldDev &wd, int S, int F, int pop, ui
   c.agent_steps += c.pop;  // the agents alive at the start of this step
   c.pop = pop;
   c.t = (long long)t + 1;
+  if (c.log) {  // posted stores to host memory; visible once the stream passes the step
+    long long *row = c.log + (size_t)((unsigned long long)t % (unsigned long long)c.log_rows) *
+                                 ECO_NCOUNTERS;
+    row[ECO_C_T] = c.t;
+    row[ECO_C_POP] = c.pop;
+    row[ECO_C_BIRTHS] = c.births;
+    row[ECO_C_DEATHS] = c.deaths;
+    row[ECO_C_DROPPED] = c.dropped;
+    row[ECO_C_BIRTHS_LAST] = c.births_last;
+    row[ECO_C_DEATHS_LAST] = c.deaths_last;
+    row[ECO_C_DROPPED_LAST] = c.dropped_last;
+    row[ECO_C_AGENT_STEPS] = c.agent_steps;
+  }
 }
 
 

@@ -105,6 +105,7 @@ class World(_Configurable):
         dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.device = dev
         self._h = None
+        self._counter_log = None
         with torch.cuda.device(dev):
             self.stream = stream if stream is not None else torch.cuda.Stream(dev)
             self.arena = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
@@ -183,6 +184,23 @@ class World(_Configurable):
         assert out.is_pinned() and out.numel() >= _lib.NCOUNTERS and out.element_size() == 8
         check(lib().eco_world_counters_async(self._h, ctypes.c_void_p(out.data_ptr())),
               "eco_world_counters_async")
+
+    def counter_log(self, log) -> None:
+        """Have the step kernels write every step's counters to `log`, a
+        page-locked int64 torch tensor of shape (rows, NCOUNTERS): step t
+        (counted from 0) fills row t % rows when it ends, with no copy added
+        to the step; rows are valid after sync().  None turns the log off.
+        The world keeps a reference to `log` while the log is on."""
+        if log is None:
+            check(lib().eco_world_counter_log(self._h, None, 0), "eco_world_counter_log")
+            self._counter_log = None
+            return
+        import torch
+        assert (log.is_pinned() and log.dtype == torch.int64 and log.dim() == 2
+                and log.shape[1] == _lib.NCOUNTERS and log.is_contiguous() and log.shape[0] > 0)
+        check(lib().eco_world_counter_log(self._h, ctypes.c_void_p(log.data_ptr()),
+                                          int(log.shape[0])), "eco_world_counter_log")
+        self._counter_log = log
 
     def analysis_async(self, out) -> None:
         """Enqueue the App. C metrics of the window that ends now into `out`,
