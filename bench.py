@@ -325,6 +325,10 @@ def bench_ours(args, params, rank, world_size, dist):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     world.load_state(e2e_state)
+    t_loaded = time.perf_counter()
+    e_steps0 = torch.cuda.Event(enable_timing=True)
+    e_steps1 = torch.cuda.Event(enable_timing=True)
+    e_steps0.record(stream)
     world.counters_async(counters0)
     d2h = NCOUNTERS * 8
     done = 0
@@ -336,8 +340,11 @@ def bench_ours(args, params, rank, world_size, dist):
         if n == 50:
             world.analysis_async(analysis_host[done // 50 - 1])
             d2h += NANALYSIS * 8
+    e_steps1.record(stream)
     world.sync()
     e2e_dt = time.perf_counter() - t0
+    e2e_load_s = t_loaded - t0
+    e2e_steps_ms = e_steps0.elapsed_time(e_steps1)
     world.counter_log(None)
     t_first = int(counters0[C_T])
     rows = counter_log.numpy()[[(t_first + k) % args.steps for k in range(args.steps)]]
@@ -378,7 +385,9 @@ def bench_ours(args, params, rank, world_size, dist):
         "gpu_launches": kps * args.steps,
         "launch_config": cfg,
         "e2e": {"value": e2e_agent_steps / e2e_dt, "unit": "agent-steps/s",
-                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h},
+                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h,
+                "load_state_ms": e2e_load_s * 1e3, "steps_device_ms": e2e_steps_ms,
+                "wall_ms": e2e_dt * 1e3},
         "clocks": clocks.summary(),
         "analysis": analysis_summary(windows, life_expectancy),
     }

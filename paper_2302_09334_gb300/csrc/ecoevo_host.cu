@@ -294,7 +294,9 @@ int capture(EcoBatch &b, int steps, cudaGraphExec_t *out) {
   if (e != cudaSuccess) return cuda_err(e);
   e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
-  return cuda_err(e);
+  if (e != cudaSuccess) return cuda_err(e);
+  // upload now, so that the first launch does not carry it
+  return cuda_err(cudaGraphUpload(*out, b.stream));
 }
 
 // Host side of a batch: device table of descriptors and work prefixes.
@@ -398,6 +400,22 @@ int profiled_step(EcoBatch &b, Profile &pr) {
   return ECO_OK;
 }
 
+// Capture (and upload) the graphs an unprofiled batch_step(b, n) launches:
+// chunks of steps_per_graph steps, then single steps.
+int prepare_graphs(EcoBatch &b, int64_t n) {
+  const int k = b.steps_per_graph;
+  if (k > 1 && n >= k && !b.gk) {
+    int rc = capture(b, k, &b.gk);
+    if (rc) return rc;
+  }
+  const int64_t chunks = k > 1 ? n / k : 0, singles = n - chunks * k;
+  if (singles && !b.g1) {
+    int rc = capture(b, 1, &b.g1);
+    if (rc) return rc;
+  }
+  return ECO_OK;
+}
+
 int batch_step(EcoBatch &b, int64_t n) {
   if (n < 0) return ECO_EINVAL;
   Profile *prof = b.prof;
@@ -421,16 +439,10 @@ int batch_step(EcoBatch &b, int64_t n) {
     }
     return cuda_err(cudaGetLastError());
   }
+  int rc = prepare_graphs(b, n);
+  if (rc) return rc;
   const int k = b.steps_per_graph;
-  if (k > 1 && n >= k && !b.gk) {
-    int rc = capture(b, k, &b.gk);
-    if (rc) return rc;
-  }
   const int64_t chunks = k > 1 ? n / k : 0, singles = n - chunks * k;
-  if (singles && !b.g1) {
-    int rc = capture(b, 1, &b.g1);
-    if (rc) return rc;
-  }
   for (int64_t i = 0; i < chunks; ++i) ECO_CU(cudaGraphLaunch(b.gk, b.stream));
   for (int64_t i = 0; i < singles; ++i) ECO_CU(cudaGraphLaunch(b.g1, b.stream));
   return ECO_OK;
@@ -464,7 +476,11 @@ int set_config(EcoBatch &b, int fused, int spawn_per_sm, int steps_per_graph) {
 }
 
 // Milliseconds per step of `steps` steps under the batch's current config.
+// The graphs are captured before the first event: a configuration change
+// drops them, and their capture is host work, not part of a step.
 int time_steps(EcoBatch &b, int64_t steps, cudaEvent_t e0, cudaEvent_t e1, double *ms) {
+  int rc0 = prepare_graphs(b, steps);
+  if (rc0) return rc0;
   ECO_CU(cudaEventRecord(e0, b.stream));
   int rc = batch_step(b, steps);
   if (rc) return rc;
