@@ -759,11 +759,15 @@ static_assert(REGROW_THREADS == SPAWN_THREADS, "one block size for the tail kern
 __global__ void __launch_bounds__(SPAWN_THREADS, 4) k_tail(const __grid_constant__ BatchDev b) {
   __shared__ uint32_t tile[TILE_ROWS_MAX][TILE_COLS];
   __shared__ int pre[1025];
-  pdl_wait_and_release();
-  if ((int)blockIdx.x < b.total_tiles)
-    regrow_tile(b, blockIdx.x, tile);
-  else
+  if ((int)blockIdx.x < b.total_tiles) {
+    // walls and thresholds are never written by a step: read before waiting
+    const RegrowFixed f = regrow_fixed(b, blockIdx.x);
+    pdl_wait_and_release();
+    regrow_run(f, tile);
+  } else {
+    pdl_wait_and_release();
     spawn_births(b, pre, blockIdx.x - b.total_tiles, gridDim.x - b.total_tiles);
+  }
 }
 
 // Initial weights of slots [0, n0): w_init_std * N_j of (TAG_INIT_W, 0, slot).
