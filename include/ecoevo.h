@@ -363,11 +363,12 @@ int eco_world_autotune(EcoWorld *world, int trial_steps, EcoTuneResult *out);
  * stream and returns the sums since enabling:
  * ms[k], launches[k] for k < ECO_NKERNELS (names: eco_kernel_name; a kernel
  * the world's step does not launch keeps 0 launches).  A step runs
- * "observe_lstm" (ECO_CTRL_PAPER: "observe_paper"), then the slot phases (moves, physiology, birth claims,
- * compaction) as one kernel "agents_fused" for worlds of capacity <= 16384
- * or as five kernels otherwise, then "regrow_spawn": the regrowth of the
- * next step's resource plane and the mutation of the births in one launch.
- * "regrow" is the first regrowth after creating or loading a world. */
+ * "regrow_spawn" (the regrowth of the step's resource plane and the mutation
+ * of the previous step's births in one launch), then "observe_lstm"
+ * (ECO_CTRL_PAPER: "observe_paper"), then the slot phases (moves,
+ * physiology, birth claims, compaction) as one kernel "agents_fused" for
+ * worlds of capacity <= 16384 or as five kernels otherwise.  "regrow" is no
+ * longer launched (kept so that the kernel ids stay stable). */
 #define ECO_NKERNELS 10
 int eco_world_profile(EcoWorld *world, int enable, int max_steps);
 int eco_world_profile_read(EcoWorld *world, double *ms, int64_t *launches);

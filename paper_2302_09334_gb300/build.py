@@ -23,7 +23,7 @@ LIB = os.path.join(LIBDIR, "libecoevo.so")
 # checked variant: every index read from device memory is range-checked
 # before use (a violation sets the world's status and skips the access)
 LIB_CHECKED = os.path.join(LIBDIR, "libecoevo_checked.so")
-SOURCES = ["k_regrow.cu", "k_lstm.cu", "k_agents.cu", "k_init.cu", "ecoevo_host.cu",
+SOURCES = ["k_lstm.cu", "k_agents.cu", "k_init.cu", "ecoevo_host.cu",
            "k_moves_noalloc.cu", "k_analysis.cu", "k_paper.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

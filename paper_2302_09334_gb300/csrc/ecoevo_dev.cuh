@@ -310,7 +310,6 @@ __device__ inline const WorldDev *world_ptr(const BatchDev &b, int w) {
 // Worlds up to this capacity run all slot phases of a step in one cluster.
 constexpr int FUSED_MAX_C = 16384;
 
-void launch_regrow(const BatchDev &b, cudaStream_t s);
 void launch_lstm(const BatchDev &b, cudaStream_t s);
 void launch_paper_ctrl(const BatchDev &b, cudaStream_t s);   // k_paper.cu
 void preload_paper();
@@ -322,12 +321,11 @@ void launch_scan_count(const BatchDev &b, cudaStream_t s);
 void launch_scan_prefix(const BatchDev &b, cudaStream_t s);
 void launch_scan_lists(const BatchDev &b, cudaStream_t s);
 void launch_scan_children(const BatchDev &b, cudaStream_t s);
-void launch_tail(const BatchDev &b, cudaStream_t s);   // regrowth of t+1 + births of t
+void launch_tail(const BatchDev &b, cudaStream_t s);   // regrowth of t + births of t-1
 void launch_agents_fused(const BatchDev &b, cudaStream_t s);
 void configure_lstm();   // once per device, before the first launch
 void launch_wait_selftest(int *status, unsigned long long limit_ns, cudaStream_t s);
 // Load every step kernel's code before a step is captured in a graph.
-void preload_regrow();
 void preload_lstm();
 void preload_agents();
 // set-up and state I/O

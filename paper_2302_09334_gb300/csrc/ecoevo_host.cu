@@ -229,31 +229,32 @@ int slot_blocks_of(const WorldDev &wd) { return (wd.C + SLOT_BLOCK - 1) / SLOT_B
 // Kernel ids for profiling (names: eco_kernel_name).
 enum { K_REGROW, K_LSTM, K_MOVE_CLAIM, K_MOVE_APPLY, K_PHYSIO, K_BIRTH_CLAIM, K_SCAN,
        K_TAIL, K_AGENTS_FUSED, K_PAPER };
-// A step starts with its resource plane already regrown (by the previous
-// step, or at creation/loading); the observation+controller kernel also
-// makes the move claims; it ends with the tail kernel: the regrowth
-// of the next step's plane in the same launch as the mutation of this
-// step's births (they touch disjoint data).
+// A step starts with the tail kernel: the regrowth of the step's resource
+// plane (App. B.1) in the same launch as the mutation of the previous step's
+// births (they touch disjoint data; newborns act from the step after their
+// birth, so their weights are needed only by this step's controller).  The
+// observation+controller kernel also makes the move claims; the slot phases
+// end the step.  In a graph, the tail kernel is thus followed by the
+// controller kernel, which starts its reads of slot state and non-newborn
+// weights while the tail runs (programmatic dependent launch).
 // (the four kernels of the split compaction are timed together as "scan")
 const StepKernel kSplitStep[] = {
-    {K_LSTM, launch_lstm},
+    {K_TAIL, launch_tail}, {K_LSTM, launch_lstm},
     {K_MOVE_APPLY, launch_move_apply}, {K_PHYSIO, launch_physio},
     {K_BIRTH_CLAIM, launch_birth_claim}, {K_SCAN, launch_scan_count},
-    {K_SCAN, launch_scan_prefix}, {K_SCAN, launch_scan_lists}, {K_SCAN, launch_scan_children},
-    {K_TAIL, launch_tail}};
-const StepKernel kFusedStep[] = {{K_LSTM, launch_lstm},
-                                 {K_AGENTS_FUSED, launch_agents_fused},
-                                 {K_TAIL, launch_tail}};
+    {K_SCAN, launch_scan_prefix}, {K_SCAN, launch_scan_lists}, {K_SCAN, launch_scan_children}};
+const StepKernel kFusedStep[] = {{K_TAIL, launch_tail},
+                                 {K_LSTM, launch_lstm},
+                                 {K_AGENTS_FUSED, launch_agents_fused}};
 // the same with the paper's controller
 const StepKernel kSplitStepPaper[] = {
-    {K_PAPER, launch_paper_ctrl},
+    {K_TAIL, launch_tail}, {K_PAPER, launch_paper_ctrl},
     {K_MOVE_APPLY, launch_move_apply}, {K_PHYSIO, launch_physio},
     {K_BIRTH_CLAIM, launch_birth_claim}, {K_SCAN, launch_scan_count},
-    {K_SCAN, launch_scan_prefix}, {K_SCAN, launch_scan_lists}, {K_SCAN, launch_scan_children},
-    {K_TAIL, launch_tail}};
-const StepKernel kFusedStepPaper[] = {{K_PAPER, launch_paper_ctrl},
-                                      {K_AGENTS_FUSED, launch_agents_fused},
-                                      {K_TAIL, launch_tail}};
+    {K_SCAN, launch_scan_prefix}, {K_SCAN, launch_scan_lists}, {K_SCAN, launch_scan_children}};
+const StepKernel kFusedStepPaper[] = {{K_TAIL, launch_tail},
+                                      {K_PAPER, launch_paper_ctrl},
+                                      {K_AGENTS_FUSED, launch_agents_fused}};
 
 static_assert(sizeof(kSplitStep) / sizeof(kSplitStep[0]) <= ECO_NKERNELS,
               "the profiler keeps two events per kernel of a step, for up to ECO_NKERNELS");
@@ -710,7 +711,6 @@ int eco_world_create(const EcoParams *params, uint64_t seed, void *arena,
     if ((rc = cuda_err(cudaDeviceGetAttribute(&w->n_sms, cudaDevAttrMultiProcessorCount,
                                               w->device)))) break;
     configure_lstm();
-    preload_regrow();
     preload_lstm();
     preload_paper();
     preload_agents();
@@ -747,9 +747,6 @@ int eco_world_create(const EcoParams *params, uint64_t seed, void *arena,
     if ((rc = cuda_err(cudaStreamSynchronize(s)))) break;
     EcoWorld *self[1] = {w};
     if ((rc = batch_init(w->self, self, 1, w->arena + L.tab_worlds))) break;
-    launch_regrow(w->self.bd, s);  // the plane the first step observes
-    if ((rc = cuda_err(cudaGetLastError()))) break;
-    if ((rc = cuda_err(cudaStreamSynchronize(s)))) break;
   } while (0);
   if (rc != ECO_OK) {
     if (w->owns_arena && w->arena) cudaFree(w->arena);
@@ -931,6 +928,17 @@ static int write_plane(uint32_t *plane, const EcoParams &p, const uint8_t *in) {
   return upload(plane, words.data(), words.size() * 4);
 }
 
+// The last step's births get their weights from the tail kernel that
+// starts the next step.  State I/O first runs that kernel (its regrowth part
+// writes the next plane from the current one: the same words the next step
+// writes again) and marks the births done, so it sees final weights.
+static int settle_births(EcoWorld *w) {
+  launch_tail(w->self.bd, w->stream);
+  ECO_CU(cudaGetLastError());
+  ECO_CU(cudaMemsetAsync(&w->hd.ctr->n_births, 0, sizeof(int), w->stream));
+  return ECO_OK;
+}
+
 int eco_world_read_state(EcoWorld *w, EcoState *out) {
   Trace trace("eco_world_read_state");
   if (!w || !out) return ECO_EINVAL;
@@ -941,9 +949,11 @@ int eco_world_read_state(EcoWorld *w, EcoState *out) {
       (out->weights_first < 0 || out->weights_count < 0 ||
        (size_t)out->weights_first + out->weights_count > C))
     return ECO_EINVAL;
+  int rc = settle_births(w);
+  if (rc) return rc;
   ECO_CU(cudaStreamSynchronize(w->stream));
   Counters c;
-  int rc = download(&c, d.ctr, sizeof(Counters));
+  rc = download(&c, d.ctr, sizeof(Counters));
   if (rc) return rc;
   counters_to_array(c, out->counters);
   const bool odd = (c.t & 1) != 0;
@@ -994,9 +1004,11 @@ int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
       (in->weights_first < 0 || in->weights_count < 0 ||
        (size_t)in->weights_first + in->weights_count > C))
     return ECO_EINVAL;
+  int rc = settle_births(w);
+  if (rc) return rc;
   ECO_CU(cudaStreamSynchronize(w->stream));
   Counters c;
-  int rc = download(&c, d.ctr, sizeof(Counters));
+  rc = download(&c, d.ctr, sizeof(Counters));
   if (rc) return rc;
   if (set_counters) {
     c.t = in->counters[ECO_C_T];
@@ -1052,7 +1064,6 @@ int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
   ECO_CU(cudaMemsetAsync(d.lab_t, 0, (C ? C : 1) * 4, w->stream));
   ECO_CU(cudaMemsetAsync(d.lab_c, 0, (C ? C : 1) * 4, w->stream));
   launch_rebuild(&w->hd, w->n_sms, w->stream);
-  launch_regrow(w->self.bd, w->stream);  // the plane the next step observes
   ECO_CU(cudaGetLastError());
   ECO_CU(cudaStreamSynchronize(w->stream));
   int st = 0;

@@ -17,9 +17,10 @@
 //               alive list for the next step rebuilt, counters, t += 1
 //   agents_cluster  all of the above for worlds of capacity <= 16384, one
 //               thread-block cluster per world
-//   tail        child weights = parent weights + sigma * N(0,1) (a grid-
-//               stride pass over every float4 of every birth) in the same
-//               launch as the regrowth of the next step's resource plane
+//   tail        the first kernel of a step: the regrowth of the step's
+//               resource plane in the same launch as the previous step's
+//               births, child weights = parent weights + sigma * N(0,1) (a
+//               grid-stride pass over every float4 of every birth)
 #include <climits>
 
 #include <cooperative_groups.h>
@@ -750,8 +751,9 @@ __device__ inline void spawn_births(const BatchDev &b, int *pre, int cta, int n_
   }
 }
 
-// The tail of a step: the regrowth of the next step's plane (the first
-// total_tiles CTAs) and the mutation of this step's births (the others), in
+// The tail of a step, launched first in the next one: the regrowth of that
+// step's plane (the first total_tiles CTAs) and the mutation of the births
+// of the step before (the others), in
 // one launch -- they touch disjoint data (resource planes / weights).
 constexpr int SPAWN_CTAS_PER_SM = 4;
 static_assert(REGROW_THREADS == SPAWN_THREADS, "one block size for the tail kernel");

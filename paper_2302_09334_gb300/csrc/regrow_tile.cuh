@@ -129,9 +129,4 @@ __device__ inline void regrow_run(const RegrowFixed &f, uint32_t (*tile)[REGROW_
   if (qd == 0 && y < H && ww < Wp) rout[y * Wp + ww] = word;
 }
 
-__device__ inline void regrow_tile(const BatchDev &b, int tile_id,
-                                   uint32_t (*tile)[REGROW_WORDS + 2]) {
-  regrow_run(regrow_fixed(b, tile_id), tile);
-}
-
 }  // namespace eco
