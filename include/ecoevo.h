@@ -199,7 +199,10 @@ int eco_world_step(EcoWorld *world, int64_t n_steps);
 int eco_world_step_forced(EcoWorld *world, const int32_t *actions,
                           int actions_on_host);
 
-/* Copy the state into `out` (see EcoState).  Synchronous. */
+/* Copy the state into `out` (see EcoState).  Synchronous.  The weights of
+ * the last step's births are written by the first kernel of the next step;
+ * when weights are requested, that kernel's work for them is done first
+ * (the next step then leaves them as they are). */
 int eco_world_read_state(EcoWorld *world, EcoState *out);
 
 /* Replace the state by `in`: every non-NULL field is written; slot_map,

@@ -929,9 +929,11 @@ static int write_plane(uint32_t *plane, const EcoParams &p, const uint8_t *in) {
 }
 
 // The last step's births get their weights from the tail kernel that
-// starts the next step.  State I/O first runs that kernel (its regrowth part
-// writes the next plane from the current one: the same words the next step
-// writes again) and marks the births done, so it sees final weights.
+// starts the next step.  Reading weights, and loading a state, first run
+// that kernel (its regrowth part writes the next plane from the current one:
+// the same words the next step writes again) and mark the births done, so
+// that they see final weights.  Nothing else a state read returns waits for
+// that kernel.
 static int settle_births(EcoWorld *w) {
   launch_tail(w->self.bd, w->stream);
   ECO_CU(cudaGetLastError());
@@ -949,8 +951,8 @@ int eco_world_read_state(EcoWorld *w, EcoState *out) {
       (out->weights_first < 0 || out->weights_count < 0 ||
        (size_t)out->weights_first + out->weights_count > C))
     return ECO_EINVAL;
-  int rc = settle_births(w);
-  if (rc) return rc;
+  int rc = ECO_OK;
+  if (out->weights_host && out->weights_count > 0 && (rc = settle_births(w))) return rc;
   ECO_CU(cudaStreamSynchronize(w->stream));
   Counters c;
   rc = download(&c, d.ctr, sizeof(Counters));
