@@ -412,6 +412,12 @@ def bench_ours(args, params, rank, world_size, dist):
             "sample": f"{args.workload}, {cores} independent worlds (seeds 0..{cores - 1}) on "
                       f"{cores} host processes, first {min(steps)}-{max(steps)} steps each "
                       f"({dt:.1f} s), single-threaded C oracle"}
+        # the parity configuration in full (20x40, 64 agents, 500 steps), one process
+        from paper_2302_09334_gb300.params import small_20x40
+        a_s, n_s, dt_s = _oracle_worker((small_20x40().asdict(), 0, 1e9, 0, 500))
+        line["cpu_baseline"]["small_20x40_full"] = {
+            "value": a_s / dt_s, "unit": "agent-steps/s", "cores": 1, "steps": n_s,
+            "seconds": dt_s}
     print(json.dumps(line), flush=True)
 
 
