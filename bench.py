@@ -404,6 +404,7 @@ def bench_ours(args, params, rank, world_size, dist):
         line["served"] = bench_served(args, local)
         line["paper_preset"] = bench_paper_preset(args, local)
         line["large"] = bench_large(args, local)
+        line["held"] = bench_held(args, local)
     if not args.no_cpu_baseline:
         cores = args.cpu_cores or os.cpu_count() or 1
         v, steps, dt = run_oracle_pool(params, args.cpu_budget, 0, 100000, cores)
@@ -597,6 +598,81 @@ def bench_large(args, local):
             "l2": "inputs larger than L2 (about 1.9 GB of weights per step), not flushed"}
 
 
+def bench_held(args, local):
+    """Held populations (no energy decay, no reproduction: the agent count
+    stays at n_agents0), the roofline microbenchmark: 1,000 agents at
+    200x400 (93 MB of weights, less than L2: flushed before every step),
+    20,000 agents at 1000x2000 and 131,072 (every slot) at 1000x2000 (1.9 and
+    12.2 GB per step, larger than L2: not flushed).  Plain steps timed with
+    CUDA events, per-kernel times from a profiled twin (same seed)."""
+    import torch
+    from paper_2302_09334_gb300.params import held, large_1000x2000, paper_200x400
+    from paper_2302_09334_gb300.world import World
+    peak, kind = load_peaks()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(local)
+    big = large_1000x2000()
+    cases = [("paper_200x400", held(paper_200x400()), True),
+             ("large_1000x2000", held(big), False),
+             ("large_1000x2000_full", held(big.replace(n_agents0=big.capacity)), False)]
+    out = []
+    for name, p, flushed in cases:
+        w = World(p, 0, device=local, stream=stream)
+        twin = World(p, 0, device=local, stream=stream)
+        w.set_config(steps_per_graph=1)
+        twin.set_config(steps_per_graph=1)
+        w.step(args.held_warmup)
+        twin.step(args.held_warmup)
+        n = int(w.counters()[1])
+        if flushed:
+            flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+            flush_read = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+            sink = torch.empty((), dtype=torch.float32, device=dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.held_steps if flushed else 1)]
+        twin.profile(True, max_steps=args.held_steps)
+        torch.cuda.synchronize()
+        if flushed:
+            for k in range(args.held_steps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(1)
+                    torch.sum(flush_read, dim=0, out=sink)
+                    twin.step(1)
+                    flush.fill_(1)
+                    torch.sum(flush_read, dim=0, out=sink)
+                ev[k][0].record(stream)
+                w.step(1)
+                ev[k][1].record(stream)
+        else:
+            ev[0][0].record(stream)
+            w.step(args.held_steps)
+            ev[0][1].record(stream)
+            twin.step(args.held_steps)
+        w.sync()
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        prof = twin.profile_read()
+        twin.profile(False)
+        if int(w.counters()[1]) != n or int(twin.counters()[1]) != n:
+            raise RuntimeError(f"held population changed in {name}")
+        w.close()
+        twin.close()
+        lstm_ms, lstm_n = prof["observe_lstm"]
+        bytes_lstm = lstm_n * lstm_bytes(n, p.H, p.W)
+        achieved = bytes_lstm / (lstm_ms / 1e3) / 1e9 if lstm_ms > 0 else None
+        out.append({"workload": name, "agents": n, "steps": args.held_steps,
+                    "ms_per_step": ms / args.held_steps,
+                    "agent_steps_per_s": n * args.held_steps / (ms / 1e3),
+                    "kernel_ms_per_step": {k: v[0] / v[1] for k, v in prof.items() if v[1]},
+                    "roofline": {"kernel": "observe_lstm", "bound": "hbm", "achieved": achieved,
+                                 "peak": peak, "peak_kind": f"{kind} hbm_gbs", "unit": "GB/s",
+                                 "frac": achieved / peak if achieved else None},
+                    "l2": ("flushed before every step" if flushed
+                           else "inputs larger than L2, not flushed")})
+        torch.cuda.empty_cache()
+    return out
+
+
 def bench_served(args, local):
     """Serving: Poisson request arrivals (20/s), admission by a 120 GB
     device-memory budget, continuous batching in chunks of 100 steps; the
@@ -630,6 +706,8 @@ def main():
     ap.add_argument("--cpu-cores", type=int, default=0,
                     help="host processes for the oracle (default: all cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--held-steps", type=int, default=50)
+    ap.add_argument("--held-warmup", type=int, default=3)
     ap.add_argument("--held", action="store_true",
                     help="no energy decay and no births: the population stays at n_agents0")
     ap.add_argument("--n-agents", type=int, default=None, help="override n_agents0")
