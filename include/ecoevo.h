@@ -304,7 +304,9 @@ void *eco_world_stream(const EcoWorld *world);
 /* Batch of independent worlds stepped together: every kernel of a step is
  * launched once for all of them (work lists over worlds and agents).  The
  * worlds must live on the current device and share one controller; the
- * batch uses the first world's stream.  The worlds must outlive the batch. */
+ * batch uses the first world's stream.  The worlds must outlive the batch.
+ * A member world's own calls (state I/O, counters, analysis) are ordered on
+ * that world's stream: call eco_batch_sync before them. */
 int eco_batch_create(EcoWorld *const *worlds, int n_worlds, EcoBatch **out);
 int eco_batch_step(EcoBatch *batch, int64_t n_steps);
 int eco_batch_sync(EcoBatch *batch);
