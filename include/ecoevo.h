@@ -12,6 +12,9 @@
  *   a5 physiology and death                 App. B.2 physiology, App. B.3 death
  *   a6 reproduction: slot compaction and    App. B.3 reproduction
  *      Gaussian mutation of the parent's weights
+ * The mutation of a step's births runs in the first kernel of the next step
+ * (the same launch as its a1), or before a state read that returns weights:
+ * newborns act from the step after their birth, so no result changes.
  *
  * Conventions, for every entry point:
  *   - Return ECO_OK (0) on success or a negative ECO_E* code.
