@@ -12,11 +12,15 @@
 //   physio      eat (atomicAnd clears the resource bit), energy update with
 //               exactly rounded float add/sub, death, reproduction counter
 //   birth_claim first free N/S/E/W cell of each parent, atomicMin(bclaim)
-//   scan        one CTA per world: successful parents, free slots, the k-th
-//               parent gets the k-th free slot, children initialised, the
-//               alive list for the next step rebuilt, counters, t += 1
+//   scan_count, scan_prefix, scan_lists, scan_children
+//               the compaction over 256-slot blocks: per-block counts of free
+//               slots, successful parents and survivors; one CTA per world
+//               scans them and writes the step's counters (t += 1); the free
+//               slots the births take and the next alive list; the k-th
+//               successful parent's child in the k-th free slot
 //   agents_cluster  all of the above for worlds of capacity <= 16384, one
-//               thread-block cluster per world
+//               thread-block cluster per world (agents_single: one CTA per
+//               world when every capacity is <= 2048)
 //   tail        the first kernel of a step: the regrowth of the step's
 //               resource plane in the same launch as the previous step's
 //               births, child weights = parent weights + sigma * N(0,1) (a
