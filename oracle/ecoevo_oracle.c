@@ -368,7 +368,13 @@ struct OrWorld {
   int64_t *agent_id, *snap_id;
   int32_t *snap_cell;
   int64_t next_id, snap_t, an_deaths, an_age_sum;
+  /* visiting order of the per-slot loops whose outcome the method leaves
+   * independent of it (NULL: ascending); a test hook, or_world_set_order */
+  int32_t *order;
 };
+
+/* Slot visited i-th by those loops. */
+static int slot_at(const OrWorld *w, int i) { return w->order ? w->order[i] : i; }
 
 static const int DY[5] = {0, -1, 1, 0, 0}; /* stay, N, S, E, W */
 static const int DX[5] = {0, 0, 0, 1, -1};
@@ -416,7 +422,37 @@ void or_world_destroy(OrWorld *w) {
   free(w->energy); free(w->weights); free(w->h); free(w->c); free(w->logits);
   free(w->thr);
   free(w->agent_id); free(w->snap_id); free(w->snap_cell);
+  free(w->order);
   free(w);
+}
+
+int or_world_set_order(OrWorld *w, const int32_t *perm) {
+  const int C = w->p.capacity;
+  if (!perm) {
+    free(w->order);
+    w->order = NULL;
+    return 0;
+  }
+  uint8_t *seen = calloc(C > 0 ? C : 1, 1);
+  int32_t *copy = malloc((C > 0 ? C : 1) * sizeof(int32_t));
+  if (!seen || !copy) {
+    free(seen);
+    free(copy);
+    return -2;
+  }
+  for (int i = 0; i < C; ++i) {
+    if (perm[i] < 0 || perm[i] >= C || seen[perm[i]]) {
+      free(seen);
+      free(copy);
+      return -1;
+    }
+    seen[perm[i]] = 1;
+    copy[i] = perm[i];
+  }
+  free(seen);
+  free(w->order);
+  w->order = copy;
+  return 0;
 }
 
 static int valid_params(const OrParams *p) {
@@ -642,7 +678,8 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
 
   /* 2-3. observation (new resources, start-of-step occupancy) and one
    * controller step per living agent */
-  for (int s = 0; s < C; ++s) {
+  for (int i = 0; i < C; ++i) {
+    const int s = slot_at(w, i);
     const int ate_last = w->ate[s];   /* the paper controller's input */
     w->ate[s] = 0;
     w->killed[s] = 0;
@@ -679,7 +716,8 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
    * start of the phase; among valid claimants of a cell the lowest slot
    * moves, every other agent stays. */
   for (int i = 0; i < H * W; ++i) w->claim[i] = -1;
-  for (int s = 0; s < C; ++s) {
+  for (int i = 0; i < C; ++i) {
+    const int s = slot_at(w, i);
     w->move_action[s] = 0;
     if (!w->alive[s]) continue;
     int a = forced ? forced[s] : w->action[s];
@@ -696,7 +734,8 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
     w->target[s] = cell;
     if (w->claim[cell] == -1 || s < w->claim[cell]) w->claim[cell] = s;
   }
-  for (int s = 0; s < C; ++s) {
+  for (int i = 0; i < C; ++i) {
+    const int s = slot_at(w, i);
     int cell = w->target[s];
     if (cell < 0 || w->claim[cell] != s) continue;
     w->slot_map[w->y[s] * W + w->x[s]] = -1;
@@ -706,7 +745,8 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
   }
 
   /* 5. eating: an agent on a resource cell consumes it */
-  for (int s = 0; s < C; ++s) {
+  for (int i = 0; i < C; ++i) {
+    const int s = slot_at(w, i);
     if (!w->alive[s] || w->killed[s]) continue;
     int cell = w->y[s] * W + w->x[s];
     if (w->res[cell]) {
@@ -720,7 +760,8 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
    * after t_death consecutive steps at or below e_death (at least one) or
    * past the maximum age; reproduction counter above e_repr. */
   int64_t deaths = 0;
-  for (int s = 0; s < C; ++s) {
+  for (int i = 0; i < C; ++i) {
+    const int s = slot_at(w, i);
     if (!w->alive[s]) continue;
     int dead = 0;
     if (w->killed[s]) {
@@ -754,7 +795,8 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
    * wins a contested cell; the k-th successful parent (ascending) gets the
    * k-th free slot (ascending); births past the free slots are dropped. */
   for (int i = 0; i < H * W; ++i) w->claim[i] = -1;
-  for (int s = 0; s < C; ++s) {
+  for (int i = 0; i < C; ++i) {
+    const int s = slot_at(w, i);
     if (!w->alive[s] || !w->wants[s]) continue;
     for (int a = 1; a < OR_NACT; ++a) {
       int ny = w->y[s] + DY[a], nx = w->x[s] + DX[a];

@@ -24,7 +24,8 @@
  *   or_observe         pinned: numpy padded-slice reconstruction
  *   or_lstm_step       pinned: torch.nn.LSTMCell (float64), bias-only closed form
  *   or_world_step      pinned: invariants, float32 energy closed forms,
- *                      brute force on <=4x4 worlds, slot-assignment rules
+ *                      brute force on <=4x4 worlds, slot-assignment rules,
+ *                      the same result for any slot visiting order
  *   or_world_analysis  pinned: hand-counted walks and lifetimes, closed
  *                      forms of the bin edges, age-based identity check
  *   or_pc_observe      pinned: numpy padded-slice reconstruction (15x15)
@@ -234,6 +235,14 @@ void or_world_destroy(OrWorld *w);
  * controller's own argmax (the controller still runs). */
 int or_world_step(OrWorld *w, const int32_t *forced);
 void *or_world_field(OrWorld *w, int field);
+/* Test hook: visit slots in the order perm[0..C-1] (a permutation of the
+ * slots; NULL restores ascending order) in the per-slot loops whose result
+ * the method defines independently of the order -- observation and
+ * controller, move claims and moves, eating, physiology and death, birth
+ * claims.  The ranking of births (k-th successful parent in ascending slot
+ * order, k-th free slot) is an order the method defines and stays
+ * ascending.  Returns 0, -1 (not a permutation), -2 (out of memory). */
+int or_world_set_order(OrWorld *w, const int32_t *perm);
 /* Rebuild slot_map from alive/y/x and the threshold table from the params,
  * after a caller has written state into the fields.  Returns 0, or -1 if
  * two agents share a cell, an agent sits on a wall or off the grid, or an

@@ -112,6 +112,8 @@ def lib():
         L.or_world_sync.argtypes = [ctypes.c_void_p]
         L.or_world_analysis.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.or_world_lab_window.argtypes = [ctypes.c_void_p]
+        L.or_world_set_order.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.or_world_set_order.restype = ctypes.c_int
         L.or_fill_normals_n.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                         ctypes.c_uint32, ctypes.c_float, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int]
@@ -347,6 +349,18 @@ class OracleWorld:
     def lab_window(self) -> None:
         """End a greediness window (or_world_lab_window)."""
         lib().or_world_lab_window(self._h)
+
+    def set_order(self, perm) -> None:
+        """Test hook (or_world_set_order): visit the slots in the order
+        `perm` in the loops whose result must not depend on it; None
+        restores ascending order."""
+        if perm is None:
+            rc = lib().or_world_set_order(self._h, None)
+        else:
+            a = np.ascontiguousarray(perm, dtype=np.int32)
+            rc = lib().or_world_set_order(self._h, a.ctypes.data)
+        if rc != 0:
+            raise ValueError(f"or_world_set_order failed ({rc})")
 
     def analysis(self) -> dict:
         """App. C metrics of the window that ends now (or_world_analysis);
