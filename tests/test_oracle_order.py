@@ -70,6 +70,16 @@ def test_contested_moves_and_births_independent_of_slot_order(oracle):
     b.close()
 
 
+def test_paper_controller_independent_of_slot_order(oracle):
+    # the paper's controller samples its actions from per-(slot, step) draws
+    p = EcoParams(H=20, W=40, capacity=120, n_agents0=60, res_init_p=0.2, t_repr=6,
+                  e_repr=0.5, e_decay=0.02, controller=1, max_age=80)
+    a, b, births = _run_pair(oracle, p, seed=9, steps=40)
+    assert births > 0
+    a.close()
+    b.close()
+
+
 def test_set_order_rejects_non_permutations(oracle):
     p = small_20x40()
     w = oracle.OracleWorld(p.asdict(), 0)
