@@ -213,7 +213,9 @@ int eco_world_read_state(EcoWorld *world, EcoState *out);
  * counters[ECO_C_T] and the cumulative counters are taken from `in` when
  * set_counters != 0.  h and c become the recurrent state for the next step.
  * A new analysis window (eco_world_analysis_async) starts at the loaded
- * state.  Synchronous.  Errors: ECO_EINVAL, ECO_ESTATE (two agents on one
+ * state.  The births of the world's last step get their weights first, so
+ * that rows `in` leaves out hold final weights.  Synchronous.  Errors:
+ * ECO_EINVAL, ECO_ESTATE (two agents on one
  * cell, an agent on a wall or off the grid, a negative age, res set on a
  * wall), ECO_ECUDA. */
 int eco_world_load_state(EcoWorld *world, const EcoState *in, int set_counters);
@@ -237,9 +239,9 @@ int eco_world_counters_async(EcoWorld *world, int64_t *out_host);
  * added to a step, so a loop over many steps (graph chunks included) gets
  * every step's counters on the host; a row is valid once the world's stream
  * has passed that step (eco_world_sync, or an event).  log_host == NULL
- * turns the log off.  Synchronous (waits for the world's stream).  Errors: ECO_EINVAL
- * (world NULL; rows <= 0; log_host not 8-byte aligned, not page-locked or
- * not mapped), ECO_ECUDA. */
+ * turns the log off.  Synchronous (waits for the world's stream).
+ * Errors: ECO_EINVAL (world NULL; rows <= 0; log_host not 8-byte aligned,
+ * not page-locked or not mapped), ECO_ECUDA. */
 int eco_world_counter_log(EcoWorld *world, int64_t *log_host, int64_t rows);
 
 /* Metrics of the paper's analyses (App. C), for the window of steps since
