@@ -343,6 +343,196 @@ int or_pc_sample(const double *logits, double u) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Error magnitudes of the controllers' outputs (test support).             */
+/* ------------------------------------------------------------------------ */
+/* Not part of the method: these functions give, for every output of one
+ * controller step, the first-order magnitude E that bounds how far an
+ * evaluation rounding each operation with relative error at most eps can be
+ * from the exact (here FP64) result: |computed - exact| <= eps * E, up to
+ * second-order terms, when eps covers the longest chain of roundings (a
+ * dot product of n terms: about n * 2^-24 in FP32).  It is a running error
+ * analysis (Wilkinson; Higham, "Accuracy and Stability of Numerical
+ * Algorithms", 2nd ed., sections 3.1-3.3): E of an exactly known input is
+ * 0; an input that is a previous step's output carries that step's E; then
+ *   dot product  z = b + sum_k w_k v_k:  E_z = |b| + sum_k |w_k| (|v_k| + E_vk)
+ *   activation   a = f(z):               E_a = |f'(z)| E_z + |a|
+ *   product      p = x y:                E_p = |x| E_y + |y| E_x + |p|
+ *   average of four  m = (x1+..+x4)/4:   E_m = (E_1 + E_2 + E_3 + E_4) / 4 + |m|
+ *   sum          s = x + y:              E_s = E_x + E_y + |s|
+ * (the |.| of an operation's own result, or |b| + sum |w_k v_k| of a dot
+ * product, is the rounding of that operation; the rest carries its inputs'
+ * magnitudes through the absolute values of the partial derivatives, so E
+ * is at least the first-order worst case over every choice of rounding
+ * errors).  The parity tests bound each recurrent output and logit of the
+ * CUDA path by a tolerance times E. */
+
+/* derivative of the logistic function from its value */
+static double dsigmoid_of(double s) { return s * (1.0 - s); }
+
+/* One gate-to-state update of unit j from pre-activations (z, E_z) of its
+ * gates i, f, g, o and the previous (c, E_c): writes (c', E_c'), (h', E_h'). */
+static void cell_mag(double zi, double ezi, double zf, double ezf, double zg, double ezg,
+                     double zo, double ezo, double c, double ec, double *cn, double *ecn,
+                     double *hn, double *ehn) {
+  const double gi = sigmoid(zi), gf = sigmoid(zf), gg = tanh(zg), go = sigmoid(zo);
+  const double ei = dsigmoid_of(gi) * ezi + fabs(gi);
+  const double ef = dsigmoid_of(gf) * ezf + fabs(gf);
+  const double eg = (1.0 - gg * gg) * ezg + fabs(gg);
+  const double eo = dsigmoid_of(go) * ezo + fabs(go);
+  const double fc = gf * c, ig = gi * gg;
+  *cn = fc + ig;
+  *ecn = (fabs(gf) * ec + fabs(c) * ef + fabs(fc)) + (fabs(gi) * eg + fabs(gg) * ei + fabs(ig)) +
+         fabs(*cn);
+  const double tc = tanh(*cn);
+  const double etc = (1.0 - tc * tc) * (*ecn) + fabs(tc);
+  *hn = go * tc;
+  *ehn = fabs(go) * etc + fabs(tc) * eo + fabs(*hn);
+}
+
+void or_lstm_mag(const float *w, const double *obs, const double *h, const double *c,
+                 const double *eh, const double *ec, double *eh_out, double *ec_out,
+                 double *el_out) {
+  double v[OR_NIN], ev[OR_NIN];
+  for (int k = 0; k < OR_NOBS; ++k) {
+    v[k] = obs[k];
+    ev[k] = 0.0;
+  }
+  for (int k = 0; k < OR_HID; ++k) {
+    v[OR_NOBS + k] = h[k];
+    ev[OR_NOBS + k] = eh[k];
+  }
+  double z[OR_NGATE], ez[OR_NGATE];
+  for (int r = 0; r < OR_NGATE; ++r) {
+    double acc = (double)w[OR_OFF_B + r], e = fabs((double)w[OR_OFF_B + r]);
+    for (int k = 0; k < OR_NIN; ++k) {
+      const double wk = (double)w[r * OR_NIN + k];
+      acc += wk * v[k];
+      e += fabs(wk) * (fabs(v[k]) + ev[k]);
+    }
+    z[r] = acc;
+    ez[r] = e;
+  }
+  double hn[OR_HID], ehn[OR_HID], ecn[OR_HID];
+  for (int j = 0; j < OR_HID; ++j) {
+    double cn;
+    cell_mag(z[j], ez[j], z[OR_HID + j], ez[OR_HID + j], z[2 * OR_HID + j],
+             ez[2 * OR_HID + j], z[3 * OR_HID + j], ez[3 * OR_HID + j], c[j], ec[j], &cn,
+             &ecn[j], &hn[j], &ehn[j]);
+  }
+  for (int a = 0; a < OR_NACT; ++a) {
+    double e = fabs((double)w[OR_OFF_BO + a]);
+    for (int j = 0; j < OR_HID; ++j)
+      e += fabs((double)w[OR_OFF_WO + a * OR_HID + j]) * (fabs(hn[j]) + ehn[j]);
+    el_out[a] = e;
+  }
+  for (int j = 0; j < OR_HID; ++j) {
+    eh_out[j] = ehn[j];
+    ec_out[j] = ecn[j];
+  }
+}
+
+/* conv3x3_s2 with magnitudes: E_in [n][n][ci] -> E_out [m][m][co] */
+static void conv3x3_s2_mag(const double *in, const double *ein, int n, int ci, const float *wt,
+                           const float *b, int co, double *out, double *eout, int m) {
+  for (int oy = 0; oy < m; ++oy)
+    for (int ox = 0; ox < m; ++ox)
+      for (int f = 0; f < co; ++f) {
+        double acc = (double)b[f], e = fabs((double)b[f]);
+        for (int ky = 0; ky < 3; ++ky)
+          for (int kx = 0; kx < 3; ++kx) {
+            int iy = 2 * oy + ky - 1, ix = 2 * ox + kx - 1;
+            if (iy < 0 || iy >= n || ix < 0 || ix >= n) continue;
+            for (int cc = 0; cc < ci; ++cc) {
+              const double wk = (double)wt[((f * 3 + ky) * 3 + kx) * ci + cc];
+              const int i = (iy * n + ix) * ci + cc;
+              acc += wk * in[i];
+              e += fabs(wk) * (fabs(in[i]) + ein[i]);
+            }
+          }
+        out[(oy * m + ox) * co + f] = acc;
+        eout[(oy * m + ox) * co + f] = e;
+      }
+}
+
+/* avgpool2_s1 of the magnitudes; out: the pooled values (avgpool2_s1) */
+static void avgpool2_s1_mag(const double *ein, int n, int c, const double *out, double *eout) {
+  for (int y = 0; y + 1 < n; ++y)
+    for (int x = 0; x + 1 < n; ++x)
+      for (int k = 0; k < c; ++k) {
+        const int o = (y * (n - 1) + x) * c + k;
+        eout[o] = 0.25 * (ein[(y * n + x) * c + k] + ein[(y * n + x + 1) * c + k] +
+                          ein[((y + 1) * n + x) * c + k] + ein[((y + 1) * n + x + 1) * c + k]) +
+                  fabs(out[o]);
+      }
+}
+
+void or_pc_mag(const float *w, const double *obs, int prev_action, int ate, const double *h,
+               const double *c, const double *eh, const double *ec, double *eh_out,
+               double *ec_out, double *el_out) {
+  static const double zero_obs[OR_PC_NOBS];   /* the view is exact */
+  double a1[8 * 8 * 4], ea1[8 * 8 * 4], p1[7 * 7 * 4], ep1[7 * 7 * 4];
+  double a2[4 * 4 * 8], ea2[4 * 4 * 8];
+  double emb[OR_PC_EMB + OR_PC_HID], eemb[OR_PC_EMB + OR_PC_HID];
+  conv3x3_s2_mag(obs, zero_obs, OR_PC_VIEW, 3, w + OR_PC_W1, w + OR_PC_B1, 4, a1, ea1, 8);
+  avgpool2_s1(a1, 8, 4, p1);
+  avgpool2_s1_mag(ea1, 8, 4, p1, ep1);
+  conv3x3_s2_mag(p1, ep1, 7, 4, w + OR_PC_W2, w + OR_PC_B2, 8, a2, ea2, 4);
+  avgpool2_s1(a2, 4, 8, emb);
+  avgpool2_s1_mag(ea2, 4, 8, emb, eemb);
+  for (int a = 0; a < OR_NACT; ++a) {
+    emb[72 + a] = (a == prev_action) ? 1.0 : 0.0;
+    eemb[72 + a] = 0.0;
+  }
+  emb[77] = ate ? 1.0 : 0.0;
+  eemb[77] = 0.0;
+  double z[4 * OR_PC_HID], ez[4 * OR_PC_HID];
+  for (int r = 0; r < 4 * OR_PC_HID; ++r) {
+    double acc = (double)w[OR_PC_BL + r], e = fabs((double)w[OR_PC_BL + r]);
+    for (int k = 0; k < OR_PC_EMB; ++k) {
+      const double wk = (double)w[OR_PC_WI + r * OR_PC_EMB + k];
+      acc += wk * emb[k];
+      e += fabs(wk) * (fabs(emb[k]) + eemb[k]);
+    }
+    for (int j = 0; j < OR_PC_HID; ++j) {
+      const double wk = (double)w[OR_PC_WH + r * OR_PC_HID + j];
+      acc += wk * h[j];
+      e += fabs(wk) * (fabs(h[j]) + eh[j]);
+    }
+    z[r] = acc;
+    ez[r] = e;
+  }
+  double ehn[OR_PC_HID], ecn[OR_PC_HID];
+  for (int j = 0; j < OR_PC_HID; ++j) {
+    double cn, hn;
+    cell_mag(z[j], ez[j], z[OR_PC_HID + j], ez[OR_PC_HID + j], z[2 * OR_PC_HID + j],
+             ez[2 * OR_PC_HID + j], z[3 * OR_PC_HID + j], ez[3 * OR_PC_HID + j], c[j], ec[j],
+             &cn, &ecn[j], &hn, &ehn[j]);
+    emb[OR_PC_EMB + j] = hn;
+    eemb[OR_PC_EMB + j] = ehn[j];
+  }
+  double d[8], ed[8];
+  for (int i = 0; i < 8; ++i) {
+    double acc = (double)w[OR_PC_DB1 + i], e = fabs((double)w[OR_PC_DB1 + i]);
+    for (int k = 0; k < OR_PC_EMB + OR_PC_HID; ++k) {
+      const double wk = (double)w[OR_PC_D1 + i * (OR_PC_EMB + OR_PC_HID) + k];
+      acc += wk * emb[k];
+      e += fabs(wk) * (fabs(emb[k]) + eemb[k]);
+    }
+    d[i] = tanh(acc);
+    ed[i] = (1.0 - d[i] * d[i]) * e + fabs(d[i]);
+  }
+  for (int a = 0; a < OR_NACT; ++a) {
+    double e = fabs((double)w[OR_PC_DB2 + a]);
+    for (int i = 0; i < 8; ++i) e += fabs((double)w[OR_PC_D2 + a * 8 + i]) * (fabs(d[i]) + ed[i]);
+    el_out[a] = e;
+  }
+  for (int j = 0; j < OR_PC_HID; ++j) {
+    eh_out[j] = ehn[j];
+    ec_out[j] = ecn[j];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* The world.                                                               */
 /* ------------------------------------------------------------------------ */
 struct OrWorld {
@@ -360,6 +550,8 @@ struct OrWorld {
   int32_t *lab_t, *lab_c;
   float *energy, *weights;
   double *h, *c, *logits;
+  /* test support: error magnitudes of h, c and the logits (or_lstm_mag) */
+  double *mag_h, *mag_c, *mag_l;
   uint32_t *thr;
   int64_t counters[OR_NCOUNTERS];
   /* analysis metrics, App. C: an identity for every agent (-1: empty slot),
@@ -406,6 +598,9 @@ void *or_world_field(OrWorld *w, int f) {
     case OR_F_LAB_FLAGS: return w->lab_flags;
     case OR_F_LAB_T: return w->lab_t;
     case OR_F_LAB_C: return w->lab_c;
+    case OR_F_MAG_H: return w->mag_h;
+    case OR_F_MAG_C: return w->mag_c;
+    case OR_F_MAG_LOGITS: return w->mag_l;
     default: return NULL;
   }
 }
@@ -420,6 +615,7 @@ void or_world_destroy(OrWorld *w) {
   free(w->move_action); free(w->prev_act);
   free(w->lab_flags); free(w->lab_t); free(w->lab_c);
   free(w->energy); free(w->weights); free(w->h); free(w->c); free(w->logits);
+  free(w->mag_h); free(w->mag_c); free(w->mag_l);
   free(w->thr);
   free(w->agent_id); free(w->snap_id); free(w->snap_cell);
   free(w->order);
@@ -588,6 +784,9 @@ int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
   w->h = calloc(C1 * OR_HID, sizeof(double));
   w->c = calloc(C1 * OR_HID, sizeof(double));
   w->logits = calloc(C1 * OR_NACT, sizeof(double));
+  w->mag_h = calloc(C1 * OR_HID, sizeof(double));
+  w->mag_c = calloc(C1 * OR_HID, sizeof(double));
+  w->mag_l = calloc(C1 * OR_NACT, sizeof(double));
   w->thr = calloc((size_t)p->H * 4, sizeof(uint32_t));
   w->agent_id = malloc(C1 * sizeof(int64_t));
   w->snap_id = malloc(C1 * sizeof(int64_t));
@@ -597,7 +796,8 @@ int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
       !w->repr_ctr || !w->low_ctr || !w->age || !w->action || !w->target ||
       !w->cand || !w->birth_parent || !w->birth_child || !w->free_list || !w->move_action ||
       !w->prev_act || !w->lab_flags || !w->lab_t || !w->lab_c ||
-      !w->energy || !w->weights || !w->h || !w->c || !w->logits || !w->thr) {
+      !w->energy || !w->weights || !w->h || !w->c || !w->logits || !w->thr ||
+      !w->mag_h || !w->mag_c || !w->mag_l) {
     or_world_destroy(w);
     return -2;
   }
@@ -655,6 +855,10 @@ int or_world_sync(OrWorld *w) {
     w->lab_t[s] = 0;
     w->lab_c[s] = 0;
   }
+  /* written state is exact */
+  memset(w->mag_h, 0, (size_t)(p->capacity ? p->capacity : 1) * OR_HID * sizeof(double));
+  memset(w->mag_c, 0, (size_t)(p->capacity ? p->capacity : 1) * OR_HID * sizeof(double));
+  memset(w->mag_l, 0, (size_t)(p->capacity ? p->capacity : 1) * OR_NACT * sizeof(double));
   return 0;
 }
 
@@ -694,6 +898,11 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
       or_pc_observe(p, w->res, w->wall, w->slot_map, w->y[s], w->x[s], obs);
       for (int k = 0; k < OR_PC_VIEW * OR_PC_VIEW; ++k)
         if (obs[3 * k] != 0.0) w->lab_flags[s] |= 1;   /* a resource in view */
+      or_pc_mag(w->weights + (size_t)s * OR_NPARAM, obs, w->prev_act[s], ate_last,
+                w->h + (size_t)s * OR_HID, w->c + (size_t)s * OR_HID,
+                w->mag_h + (size_t)s * OR_HID, w->mag_c + (size_t)s * OR_HID,
+                w->mag_h + (size_t)s * OR_HID, w->mag_c + (size_t)s * OR_HID,
+                w->mag_l + (size_t)s * OR_NACT);
       or_pc_forward(w->weights + (size_t)s * OR_NPARAM, obs, w->prev_act[s], ate_last,
                     w->h + (size_t)s * OR_HID, w->c + (size_t)s * OR_HID,
                     w->logits + (size_t)s * OR_NACT);
@@ -706,6 +915,10 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
                obs);
     for (int k = 0; k < OR_VIEW * OR_VIEW; ++k)
       if (obs[k] != 0.0) w->lab_flags[s] |= 1;     /* a resource in view */
+    or_lstm_mag(w->weights + (size_t)s * OR_NPARAM, obs, w->h + (size_t)s * OR_HID,
+                w->c + (size_t)s * OR_HID, w->mag_h + (size_t)s * OR_HID,
+                w->mag_c + (size_t)s * OR_HID, w->mag_h + (size_t)s * OR_HID,
+                w->mag_c + (size_t)s * OR_HID, w->mag_l + (size_t)s * OR_NACT);
     w->action[s] = or_lstm_step(w->weights + (size_t)s * OR_NPARAM, obs,
                                 w->h + (size_t)s * OR_HID,
                                 w->c + (size_t)s * OR_HID,
@@ -846,6 +1059,11 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
       w->c[(size_t)child * OR_HID + j] = 0.0;
     }
     for (int a = 0; a < OR_NACT; ++a) w->logits[(size_t)child * OR_NACT + a] = 0.0;
+    for (int j = 0; j < OR_HID; ++j) {
+      w->mag_h[(size_t)child * OR_HID + j] = 0.0;
+      w->mag_c[(size_t)child * OR_HID + j] = 0.0;
+    }
+    for (int a = 0; a < OR_NACT; ++a) w->mag_l[(size_t)child * OR_NACT + a] = 0.0;
     /* asexual reproduction: parent weights plus N(0, sigma) noise, App. B.3 */
     or_fill_normals_n(w->seed, OR_TAG_MUT, t, (uint32_t)parent, p->mut_std,
                       w->weights + (size_t)parent * OR_NPARAM,

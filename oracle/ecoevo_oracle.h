@@ -37,6 +37,11 @@
  *   or_action_uniform  pinned: numpy Philox reconstruction
  *   or_world_lab_window pinned: hand-counted walks past placed resources,
  *                      free-run recount from the views and meals
+ *   or_lstm_mag, or_pc_mag (test support: error magnitudes of the outputs)
+ *                      pinned: simulated low-precision evaluations (every
+ *                      operation rounded to a short mantissa) stay within
+ *                      the bound and come close to it; FP32 evaluations in
+ *                      several summation orders; bias-only closed form
  */
 #ifndef ECOEVO_ORACLE_H
 #define ECOEVO_ORACLE_H
@@ -154,6 +159,9 @@ enum {
                                     bit 1 ate                                */
   OR_F_LAB_T,        /* int32  [C]  windows with a resource in view (T_r)    */
   OR_F_LAB_C,        /* int32  [C]  windows with a consumption (C_r)         */
+  OR_F_MAG_H,        /* double [C*32] error magnitude of h (or_lstm_mag)     */
+  OR_F_MAG_C,        /* double [C*32] error magnitude of c                   */
+  OR_F_MAG_LOGITS,   /* double [C*5]  error magnitude of the logits          */
   OR_NFIELDS
 };
 enum {
@@ -223,6 +231,19 @@ void or_observe(const OrParams *p, const uint8_t *res, const uint8_t *wall,
  * h and c are updated in place; returns the action. */
 int or_lstm_step(const float *w /* [23333] */, const double *obs,
                  double *h, double *c, double *logits);
+
+/* Test support (not part of the method): first-order error magnitudes of
+ * one controller step's outputs by running error analysis, so that an
+ * evaluation whose operations each round with relative error <= eps lies
+ * within eps * E of the exact outputs.  eh, ec: magnitudes of the inputs h,
+ * c (0 when exact); writes E of h', c' and of the 5 logits.  The outputs
+ * may alias eh, ec.  or_world_step keeps them per slot (OR_F_MAG_*). */
+void or_lstm_mag(const float *w, const double *obs, const double *h, const double *c,
+                 const double *eh, const double *ec, double *eh_out, double *ec_out,
+                 double *el_out);
+void or_pc_mag(const float *w, const double *obs, int prev_action, int ate, const double *h,
+               const double *c, const double *eh, const double *ec, double *eh_out,
+               double *ec_out, double *el_out);
 
 /* Initial walls, resources and agent cells (cells[s] = y*W + x of slot s,
  * s < n_agents0) of a world created from `seed`; the first part of

@@ -24,7 +24,7 @@ PC_OFF = {"W1": 0, "B1": 108, "W2": 112, "B2": 400, "WI": 408, "WH": 1656, "BL":
 (F_RES, F_WALL, F_SLOT_MAP, F_ALIVE, F_Y, F_X, F_ENERGY, F_REPR_CTR, F_LOW_CTR,
  F_AGE, F_H, F_C, F_ACTION, F_LOGITS, F_ATE, F_WEIGHTS, F_COUNTERS, F_THR,
  F_BIRTH_PARENT, F_BIRTH_CHILD, F_MOVE_ACTION, F_PREV_ACTION, F_LAB_FLAGS, F_LAB_T,
- F_LAB_C) = range(25)
+ F_LAB_C, F_MAG_H, F_MAG_C, F_MAG_LOGITS) = range(28)
 (C_T, C_POP, C_BIRTHS, C_DEATHS, C_DROPPED, C_BIRTHS_LAST, C_DEATHS_LAST,
  C_DROPPED_LAST, C_AGENT_STEPS) = range(9)
 NCOUNTERS = 9
@@ -128,6 +128,9 @@ def lib():
         L.or_action_uniform.restype = ctypes.c_double
         L.or_pc_sample.argtypes = [ctypes.c_void_p, ctypes.c_double]
         L.or_pc_sample.restype = ctypes.c_int
+        L.or_lstm_mag.argtypes = [ctypes.c_void_p] * 9
+        L.or_pc_mag.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int] + \
+            [ctypes.c_void_p] * 7
         _lib = L
     return _lib
 
@@ -205,6 +208,37 @@ def lstm_step(w, obs, h, c):
     logits = np.zeros(NACT, np.float64)
     a = lib().or_lstm_step(_ptr(w), _ptr(obs), _ptr(h2), _ptr(c2), _ptr(logits))
     return a, h2, c2, logits
+
+
+def lstm_mag(w, obs, h, c, eh=None, ec=None):
+    """Error magnitudes (E_h', E_c', E_logits) of one LSTM step (test
+    support, or_lstm_mag); eh, ec: magnitudes of the inputs (default 0)."""
+    w = np.ascontiguousarray(w, np.float32)
+    obs = np.ascontiguousarray(obs, np.float64)
+    h = np.ascontiguousarray(h, np.float64)
+    c = np.ascontiguousarray(c, np.float64)
+    eh = np.zeros(HID) if eh is None else np.ascontiguousarray(eh, np.float64)
+    ec = np.zeros(HID) if ec is None else np.ascontiguousarray(ec, np.float64)
+    oh, oc, ol = np.zeros(HID), np.zeros(HID), np.zeros(NACT)
+    lib().or_lstm_mag(_ptr(w), _ptr(obs), _ptr(h), _ptr(c), _ptr(eh), _ptr(ec), _ptr(oh),
+                      _ptr(oc), _ptr(ol))
+    return oh, oc, ol
+
+
+def pc_mag(w, obs, prev_action, ate, h, c, eh=None, ec=None):
+    """Error magnitudes (E_h', E_c', E_logits) of one paper-controller step
+    (test support, or_pc_mag)."""
+    w = np.ascontiguousarray(np.asarray(w, np.float32)[:PC_NPARAM])
+    obs = np.ascontiguousarray(obs, np.float64).reshape(-1)
+    h = np.ascontiguousarray(np.asarray(h, np.float64)[:PC_HID])
+    c = np.ascontiguousarray(np.asarray(c, np.float64)[:PC_HID])
+    eh = np.zeros(PC_HID) if eh is None else np.ascontiguousarray(eh, np.float64)[:PC_HID]
+    ec = np.zeros(PC_HID) if ec is None else np.ascontiguousarray(ec, np.float64)[:PC_HID]
+    oh, oc, ol = np.zeros(PC_HID), np.zeros(PC_HID), np.zeros(NACT)
+    lib().or_pc_mag(_ptr(w), _ptr(obs), int(prev_action), int(ate), _ptr(h), _ptr(c),
+                    _ptr(np.ascontiguousarray(eh)), _ptr(np.ascontiguousarray(ec)), _ptr(oh),
+                    _ptr(oc), _ptr(ol))
+    return oh, oc, ol
 
 
 def param_count(controller: int) -> int:
@@ -315,6 +349,11 @@ class OracleWorld:
         self.lab_flags = f(F_LAB_FLAGS, np.uint8, (C,))
         self.lab_t = f(F_LAB_T, np.int32, (C,))
         self.lab_c = f(F_LAB_C, np.int32, (C,))
+        # test support: error magnitudes of h, c and the logits of the last
+        # step (or_lstm_mag / or_pc_mag; 0 for state written from outside)
+        self.mag_h = f(F_MAG_H, np.float64, (C, HID))
+        self.mag_c = f(F_MAG_C, np.float64, (C, HID))
+        self.mag_logits = f(F_MAG_LOGITS, np.float64, (C, NACT))
 
     def _field(self, fid, dtype, shape):
         addr = lib().or_world_field(self._h, fid)
