@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2302_09334_gb300.params import EcoParams, batched_64
-from tests.parity import compare, run_forced
+from tests.parity import compare, rnn_close, run_forced, small_margin, sync_weights
 
 pytestmark = pytest.mark.gpu
 
@@ -94,3 +94,35 @@ def test_served_cancel_mid_chunk_equals_alone(eco):
         for k in a:
             np.testing.assert_array_equal(a[k], r.final[k], err_msg=f"request {r.rid} {k}")
         alone.close()
+
+
+def test_served_trace_shaped_requests_match_oracle(eco, oracle):
+    """Three requests shaped like the serving trace's (grids 50x100, 100x200,
+    200x400; 250-400 agents, capacity 4x) served together for 20 steps in
+    one launch; each final state equals, bit for bit, a world of the same
+    spec stepped alone one step at a time, and that world matches the
+    oracle at every step: the oracle moves with the actions the GPU took and
+    is compared after each step from the same state (run_gpu_driven:
+    integer state and energies bit for bit, h, c and logits within the RNN
+    tolerance, an argmax difference only at a flagged near-tie)."""
+    from paper_2302_09334_gb300.serve import Server
+    from tests.parity import run_gpu_driven
+    specs = [(EcoParams(H=50, W=100, n_agents0=300, capacity=1200), 200),
+             (EcoParams(H=100, W=200, n_agents0=250, capacity=1000), 201),
+             (EcoParams(H=200, W=400, n_agents0=400, capacity=1600), 202)]
+    trace = [{"arrival": 0.0, "params": p, "seed": s, "steps": 20} for p, s in specs]
+    srv = Server(budget_bytes=3 * 2**30, chunk=100, keep_final=True)
+    rep = srv.run(trace)
+    srv.close()
+    assert rep["requests_completed"] == 3 and rep["batch_launches"] == 1
+    for r in srv.finished:
+        ow = oracle.OracleWorld(r.params.asdict(), r.seed)
+        alone = eco.World(r.params, r.seed)
+        st = run_gpu_driven(alone, ow, r.steps, f"served request {r.rid}")
+        a = alone.read_state()
+        for k in a:
+            np.testing.assert_array_equal(a[k], r.final[k], err_msg=f"request {r.rid} {k}")
+        print(f"served request {r.rid}: {st}")
+        assert st["flagged"] <= 2
+        alone.close()
+        ow.close()

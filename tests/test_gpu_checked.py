@@ -62,7 +62,7 @@ for w in ws:
 
 pc = EcoParams(H=30, W=60, capacity=400, n_agents0=100, controller=1, e0=3.0, e_max=3.0,
                e_decay=0.025, e_gain=1.0, e_repr=0.0, t_repr=30, e_death=0.0, t_death=20,
-               max_age=90, res_init_p=0.2, wall_kills=1)
+               max_age=90, res_init_p=0.2, wall_kills=1, w_init_std=0.5)
 w = world.World(pc, seed=2)
 w.step(120)
 w.sync()

@@ -1,18 +1,24 @@
 """Full-size parity: the 1000x2000 world (20,000 agents, capacity 131,072,
-the multi-CTA slot kernels), checked against the oracle on everything it can
-compute one piece at a time:
+the split slot kernels and their four-kernel compaction), against the
+oracle:
 
 * initial walls, resources and agent placement over the whole grid
   (or_initial_layout), initial weights of sampled agents (or_fill_normals);
-* one step: regrowth over the whole grid (or_regrow), the observation and
-  LSTM step of sampled agents (or_observe, or_lstm_step), the move rule and
-  the float32 energy update of every agent, population bookkeeping.
+* eight steps with the oracle's actions forced, compared with the oracle
+  world after every step (grid, slot map, positions, energies, counters,
+  h, c, logits, actions, children's weights): a churn variant (initial
+  energy 0.045, reproduction after 3 steps above 0) has two waves of about
+  20,000 and 26,000 births and one of about 14,000 deaths, so births, slot
+  assignment from the free list, the compaction and the mutation all run at
+  this size;
+* one free step whose regrowth, sampled observations + LSTM steps and
+  energies are recomputed piece by piece (an extra check).
 """
 import numpy as np
 import pytest
 
 from paper_2302_09334_gb300.params import large_1000x2000
-from tests.parity import RNN_TOL, rnn_close, small_margin, weights_close
+from tests.parity import RNN_TOL, compare, rnn_close, run_forced, small_margin, weights_close
 
 pytestmark = pytest.mark.gpu
 
@@ -78,11 +84,12 @@ def test_large_one_step(large, oracle):
                              before["y"][s], before["x"][s], before["energy"][s])
         w = gw.read_state(fields=(), weights=(int(s), 1))["weights"][0]
         a, h2, c2, lg = oracle.lstm_step(w, obs, before["h"][s], before["c"][s])
-        rnn_close(after["h"][s], h2, f"h of slot {s}")
-        rnn_close(after["c"][s], c2, f"c of slot {s}")
-        rnn_close(after["logits"][s], lg, f"logits of slot {s}")
+        Eh, Ec, El = oracle.lstm_mag(w, obs, before["h"][s], before["c"][s])
+        rnn_close(after["h"][s], h2, Eh, f"h of slot {s}")
+        rnn_close(after["c"][s], c2, Ec, f"c of slot {s}")
+        rnn_close(after["logits"][s], lg, El, f"logits of slot {s}")
         if after["action"][s] != a:
-            assert small_margin(lg[None])[0], f"action of slot {s}"
+            assert small_margin(lg[None], El[None])[0], f"action of slot {s}"
             flagged += 1
     assert flagged <= 2
 
@@ -127,3 +134,27 @@ def test_large_one_step(large, oracle):
     np.testing.assert_array_equal(sm[after["y"][alive] * W + after["x"][alive]], alive)
     assert (sm >= 0).sum() == len(alive)
     assert RNN_TOL > 0
+
+
+def test_large_forced_churn_equals_oracle(oracle):
+    """Eight steps of the full-size world under heavy churn, the GPU moving
+    with the oracle's actions, compared with the oracle after every step."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_09334_gb300 import build, world
+    build.build()
+    p = large_1000x2000().replace(e0=0.045, e_repr=0.0, t_repr=3)
+    gw = world.World(p, seed=0)
+    ow = oracle.OracleWorld(p.asdict(), 0)
+    try:
+        compare(gw.read_state(), ow, "churn init")
+        st = run_forced(gw, ow, 8, "1000x2000 churn", p.mut_std)
+        c = ow.counters
+        print("1000x2000 churn:", dict(births=int(c[2]), deaths=int(c[3]), pop=int(c[1]),
+                                       flagged=st["flagged"], budget=st["budget"], rel=st["rel"]))
+        assert c[2] > 40000 and c[3] > 10000, "two birth waves and a death wave expected"
+        assert st["flagged"] <= 4
+    finally:
+        gw.close()
+        ow.close()

@@ -35,7 +35,7 @@ def _check(gw, ow, where):
 @pytest.mark.parametrize("controller", [0, 1])
 def test_lab_counters_equal_oracle(eco, oracle, controller):
     p = EcoParams(H=24, W=48, capacity=300, n_agents0=80, t_repr=40, e_repr=0.6,
-                  max_age=150, controller=controller)
+                  max_age=150, controller=controller, w_init_std=0.5)
     gw = eco.World(p, seed=12)
     ow = oracle.OracleWorld(p.asdict(), 12)
     tot_t = tot_c = 0

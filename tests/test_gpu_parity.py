@@ -46,6 +46,18 @@ def test_small_world_500_steps_forced(eco, oracle):
     assert ow.counters[3] > 0  # deaths happened too
 
 
+def test_small_world_wide_weights_forced(eco, oracle):
+    """Initial weights N(0, 0.5^2): pre-activations of tens, saturated gates,
+    logits with large cancellations; the RNN tolerance is the same per-element
+    bound on the oracle's error magnitudes."""
+    p = small_20x40().replace(w_init_std=0.5)
+    gw, ow = _pair(eco, oracle, p, 1)
+    st = run_forced(gw, ow, 300, "20x40 std 0.5", p.mut_std)
+    print("std 0.5:", st)
+    assert st["births"] > 0 and st["budget"] <= 1.0
+    assert st["flagged"] <= 5
+
+
 EDGE_CASES = {
     "ragged_9x33": EcoParams(H=9, W=33, capacity=40, n_agents0=20),
     "paper_forms_24x100": EcoParams(H=24, W=100, capacity=120, n_agents0=60, nbr_shape=1,

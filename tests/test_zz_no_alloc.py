@@ -86,6 +86,75 @@ def test_moves_noalloc_matches_step(eco, params):
     assert moved.sum() > 0
 
 
+def test_moves_noalloc_wall_kills_match_step(eco):
+    """wall_kills = 1: an agent whose move leads into a wall or off the grid
+    is flagged in `killed`; the full step removes exactly those agents (and
+    no other), and every survivor ends where the full step puts it.  Two
+    calls in a row, the second from the state after the first step's
+    deaths."""
+    import torch
+    from paper_2302_09334_gb300._lib import check, lib
+
+    params = _held(EcoParams(H=12, W=30, capacity=128, n_agents0=120, wall_kills=1))
+    w = eco.World(params, seed=9)
+    st = w.read_state()
+    dev = w.device
+    H, W, C = params.H, params.W, params.capacity
+    as_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    wall_np = st["wall"].astype(np.uint8)
+    wall = as_dev(wall_np)
+    alive_np = st["alive"].copy()
+    y_np, x_np = st["y"].copy(), st["x"].copy()
+    alive, y, x = as_dev(alive_np), as_dev(y_np), as_dev(x_np)
+    slot_map = as_dev(st["slot_map"])
+    killed = torch.zeros(C, dtype=torch.uint8, device=dev)
+    rng = np.random.default_rng(4)
+    dy, dx = np.array([0, -1, 1, 0, 0]), np.array([0, 0, 0, 1, -1])
+    total_killed = 0
+    for call in range(2):
+        live = alive_np.astype(bool)
+        actions_np = rng.integers(0, 5, C).astype(np.int32)
+        # agents next to a wall move into it half of the time
+        for s in np.flatnonzero(live):
+            into = [a for a in range(1, 5)
+                    if wall_np[y_np[s] + dy[a], x_np[s] + dx[a]]]
+            if into and rng.random() < 0.5:
+                actions_np[s] = into[0]
+        w.step_forced(actions_np)
+        stream = torch.cuda.current_stream(dev)
+        check(lib().eco_moves_noalloc(H, W, C, 1, ctypes.c_void_p(wall.data_ptr()),
+                                      ctypes.c_void_p(alive.data_ptr()),
+                                      ctypes.c_void_p(as_dev(actions_np).data_ptr()),
+                                      ctypes.c_void_p(y.data_ptr()),
+                                      ctypes.c_void_p(x.data_ptr()),
+                                      ctypes.c_void_p(slot_map.data_ptr()),
+                                      ctypes.c_void_p(killed.data_ptr()),
+                                      ctypes.c_void_p(stream.cuda_stream)),
+              "eco_moves_noalloc")
+        torch.cuda.synchronize(dev)
+        ref = w.read_state(fields=("alive", "y", "x", "slot_map"))
+        k = killed.cpu().numpy().astype(bool)
+        died = live & ~ref["alive"].astype(bool)
+        np.testing.assert_array_equal(k & live, died, err_msg=f"call {call}: killed")
+        assert not (k & ~live).any()
+        surv = live & ~k
+        gy, gx = y.cpu().numpy(), x.cpu().numpy()
+        np.testing.assert_array_equal(gy[surv], ref["y"][surv], err_msg=f"call {call}")
+        np.testing.assert_array_equal(gx[surv], ref["x"][surv], err_msg=f"call {call}")
+        # the step also removes the killed agents from the grid
+        sm = slot_map.cpu().numpy()
+        for s in np.flatnonzero(k):
+            sm[gy[s], gx[s]] = -1
+        np.testing.assert_array_equal(sm, ref["slot_map"], err_msg=f"call {call}: slot_map")
+        total_killed += int(k.sum())
+        # the next call starts from the state after the deaths
+        alive_np = ref["alive"].copy()
+        y_np, x_np = ref["y"].copy(), ref["x"].copy()
+        alive.copy_(as_dev(alive_np))
+        slot_map.copy_(as_dev(ref["slot_map"]))
+    assert total_killed > 0
+
+
 def test_moves_noalloc_rejects_oversized_grid(eco):
     from paper_2302_09334_gb300._lib import ECO_EINVAL, lib
     rc = lib().eco_moves_noalloc(2048, 1025, 0, 0, None, None, None, None, None, None, None, None)
