@@ -675,14 +675,21 @@ def bench_held(args, local):
 
 def bench_served(args, local):
     """Serving: Poisson request arrivals (20/s), admission by a 120 GB
-    device-memory budget, continuous batching in chunks of 100 steps; the
-    same arrival trace processed one request at a time as the comparison."""
+    device-memory budget and a chunk-latency target, continuous batching
+    with reports every 100 steps of each request; the same arrival trace
+    processed one request at a time as the comparison.  The offered load
+    (about 20 requests/s x 1,600 agents x 10,500 steps) is several times what
+    one GPU steps, so the queue grows and admission decides the latency: the
+    line reports the p50/p99 report interval of all requests and of those
+    admitted after a warm-up (steady state) beside the target."""
     import torch
     from paper_2302_09334_gb300.params import serve_trace
     from paper_2302_09334_gb300.serve import Server, serve_sequential
     trace = serve_trace(duration_s=args.serve_seconds)
-    srv = Server(budget_bytes=120e9, chunk=100, device=local)
-    rep = srv.run(trace, duration_s=args.serve_seconds, max_wall_s=args.serve_seconds)
+    srv = Server(budget_bytes=120e9, chunk=100, device=local,
+                 target_chunk_s=args.serve_target)
+    srv.run(trace, duration_s=args.serve_seconds, max_wall_s=args.serve_seconds)
+    rep = srv.report(warm_s=min(args.serve_warm, args.serve_seconds / 2))
     srv.close()
     torch.cuda.empty_cache()
     seq = serve_sequential(trace, duration_s=args.serve_seconds,
@@ -715,7 +722,14 @@ def main():
                     help="skip the batched (64 worlds) and served measurements")
     ap.add_argument("--batched-steps", type=int, default=1000)
     ap.add_argument("--batched-warmup", type=int, default=10)
-    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-seconds", type=float, default=120.0,
+                    help="length of the served request trace and of the serving run "
+                         "(600: the whole 10-minute trace)")
+    ap.add_argument("--serve-warm", type=float, default=30.0,
+                    help="requests admitted after this many seconds give the steady-state "
+                         "latency")
+    ap.add_argument("--serve-target", type=float, default=0.1,
+                    help="chunk-latency target (s per 100-step report) for admission")
     ap.add_argument("--no-tune", action="store_true",
                     help="default launch configuration (no tuner world before the timed one)")
     ap.add_argument("--large-steps", type=int, default=100)

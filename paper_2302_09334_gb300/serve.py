@@ -4,16 +4,26 @@ batching.
 
 Every live world stays resident on the device (grid, agents, weights)
 between chunks.  Each iteration of the loop admits the requests that have
-arrived, in arrival order, while their arenas fit in the budget; steps every
-live world by one chunk (at most `chunk` steps, fewer when a request needs
-fewer) with one launch per kernel for all of them; reports each request's
-progress; and retires the requests that are done, freeing their memory for
-the queue.  A request's result does not depend on which others share its
-launches (every random draw is keyed by its own seed and step).
+arrived, in arrival order, while their arenas fit in the budget (and, with a
+chunk-latency target, while the live agents fit in it); steps every live
+world together, with one launch per kernel for all of them, up to the next
+step at which some live request reports (a request reports every `chunk`
+of its own steps and at its last step, so requests at different points of
+their 100-step cycles share shorter launches); reports; and retires the
+requests that are done, freeing their memory for the queue.  A request's
+result does not depend on which others share its launches (every random
+draw is keyed by its own seed and step).
 
 Latency accounting: a request's chunk latency is the time between two
-consecutive chunk reports (the first from its admission); the queueing
-delay is admission time minus arrival time.
+consecutive reports (the first from its admission); the queueing delay is
+admission time minus arrival time.
+
+Latency control: with target_chunk_s, a request is admitted only while the
+agents of the live worlds plus its own, stepped `chunk` times at the
+measured rate (agent-steps/s, a moving average over launches, from
+rate_prior until measured; fixed at rate_prior with learn_rate=False), fit
+in the target; the first request is always admitted.  The memory budget
+still applies.
 
 With `log` (a text file), every chunk appends one JSON record: its time,
 steps, live and queued requests, agent-steps, seconds, agent-steps/s and the
@@ -47,7 +57,7 @@ from .world import Batch, World
 class Request:
     __slots__ = ("rid", "arrival", "params", "seed", "steps", "nbytes", "world", "done",
                  "admitted", "last_report", "latencies", "agent_steps", "final",
-                 "cancel_after_steps", "outcome")
+                 "cancel_after_steps", "outcome", "pop")
 
     def __init__(self, rid, arrival, params, seed, steps, cancel_after_steps=None):
         self.rid, self.arrival, self.params, self.seed, self.steps = rid, arrival, params, seed, steps
@@ -63,6 +73,7 @@ class Request:
         self.last_report = None
         self.latencies = []
         self.agent_steps = 0
+        self.pop = int(params.n_agents0)   # population at the last launch
         self.final = None
         self.outcome = None   # "done" | "cancelled" | "rejected: <why>" | None (cut off)
 
@@ -79,9 +90,14 @@ class Server:
 
     def __init__(self, budget_bytes: float = 120e9, chunk: int = 100, device: int = 0,
                  keep_final: bool = False, world_factory=None, batch_factory=None,
-                 log=None):
+                 log=None, target_chunk_s: float | None = None, rate_prior: float = 5e7,
+                 learn_rate: bool = True):
         self.budget = float(budget_bytes)
         self.chunk = int(chunk)
+        self.target = None if target_chunk_s is None else float(target_chunk_s)
+        self.rate = float(rate_prior)   # agent-steps/s of a launch, moving average
+        self.learn_rate = learn_rate
+        self.live_agents = 0            # agents of the live worlds at the last launch
         self.device = device
         self.keep_final = keep_final
         if world_factory is None:
@@ -126,6 +142,7 @@ class Server:
         req.world.close()
         req.world = None
         self.used -= req.nbytes
+        self.live_agents -= req.pop
         self._wait_for_retire = False
         req.outcome = outcome
         (self.finished if outcome == "done" else self.cancelled).append(req)
@@ -134,19 +151,27 @@ class Server:
         req.outcome = f"rejected: {why}"
         self.rejected.append(req)
 
+    def _fits_target(self, req: Request) -> bool:
+        if self.target is None or not self.live:
+            return True
+        agents = self.live_agents + int(req.params.n_agents0)
+        return agents * self.chunk / self.rate <= self.target
+
     def _admit_queue(self, queue: deque, now: float) -> None:
         """Admit from the head of the queue, in arrival order, while the
-        arenas fit in the budget and the device has the memory."""
+        arenas fit in the budget, the live agents fit in the chunk-latency
+        target and the device has the memory."""
         while queue and not self._wait_for_retire:
             req = queue[0]
             if req.nbytes > self.budget:
                 queue.popleft()
                 self._reject(req, "arena larger than the memory budget")
                 continue
-            if self.used + req.nbytes > self.budget:
+            if self.used + req.nbytes > self.budget or not self._fits_target(req):
                 return
             try:
                 self._admit(req, now)
+                self.live_agents += int(req.params.n_agents0)
             except Exception as e:
                 if not _out_of_memory(e):
                     raise
@@ -157,6 +182,21 @@ class Server:
                 self._reject(req, "out of device memory with nothing live")
                 continue
             queue.popleft()
+
+    def _populations(self) -> list:
+        """Population of every live world: one asynchronous counter copy per
+        world into page-locked memory, one wait (fake worlds: counters())."""
+        worlds = [r.world for r in self.live]
+        if not worlds or not hasattr(worlds[0], "counters_async"):
+            return [int(w.counters()[1]) for w in worlds]
+        import torch
+        if getattr(self, "_ctr_host", None) is None or self._ctr_host.shape[0] < len(worlds):
+            self._ctr_host = torch.zeros((max(64, 2 * len(worlds)), _lib.NCOUNTERS),
+                                         dtype=torch.int64, pin_memory=True)
+        for i, w in enumerate(worlds):
+            w.counters_async(self._ctr_host[i])
+        worlds[0].stream.synchronize()
+        return [int(v) for v in self._ctr_host[:len(worlds), _lib.C_POP].tolist()]
 
     def _step_live(self, n: int) -> None:
         members = tuple(id(r) for r in self.live)
@@ -209,12 +249,17 @@ class Server:
                 if pending:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - now)))
                 continue
-            n = min(self.chunk, min(r.steps - r.done for r in self.live))
-            pops = [int(r.world.counters()[1]) for r in self.live]
+            # up to the next report of any live request
+            n = min(min(self.chunk - r.done % self.chunk, r.steps - r.done) for r in self.live)
+            pops = self._populations()
+            self.live_agents = sum(pops)
             t_chunk = time.perf_counter()
             self._step_live(n)
             chunks += 1
             t_rep = time.perf_counter() - t0
+            dt_launch = time.perf_counter() - t_chunk
+            if self.learn_rate and dt_launch > 0 and self.live_agents > 0:
+                self.rate += 0.2 * (self.live_agents * n / dt_launch - self.rate)
             if self.log is not None:
                 dt = time.perf_counter() - t_chunk
                 self.log.write(json.dumps({
@@ -225,7 +270,8 @@ class Server:
                     "used_gb": round(self.used / 1e9, 3)}) + "\n")
             for r, pop in zip(list(self.live), pops):
                 r.done += n
-                r.agent_steps += pop * n  # population at the chunk start
+                r.pop = pop
+                r.agent_steps += pop * n  # population at the launch start
                 if r.done % self.chunk == 0 or r.done == r.steps:
                     r.latencies.append(t_rep - r.last_report)
                     r.last_report = t_rep
@@ -240,17 +286,26 @@ class Server:
         self.chunks = chunks
         return self.report()
 
-    def report(self) -> dict:
+    def report(self, warm_s: float = 0.0) -> dict:
+        """Throughput and latency over the run; with warm_s, the steady-state
+        p50/p99 over the reports of requests admitted after warm_s."""
         reqs = self.finished + self.cancelled + [r for r in self.unfinished
                                                  if r.world is not None]
         lat = np.array([x for r in reqs for x in r.latencies], np.float64)
         agent_steps = sum(r.agent_steps for r in reqs)
         delays = [r.admitted - r.arrival for r in reqs if r.admitted is not None]
+        steady = np.array([x for r in reqs if r.admitted is not None and r.admitted >= warm_s
+                           for x in r.latencies], np.float64)
         return {
             "agent_steps_per_s": agent_steps / self.wall if self.wall > 0 else 0.0,
             "chunk_latency_p50_s": float(np.percentile(lat, 50)) if lat.size else None,
             "chunk_latency_p99_s": float(np.percentile(lat, 99)) if lat.size else None,
             "chunks_reported": int(lat.size),
+            "steady_after_s": warm_s,
+            "steady_chunk_latency_p50_s": float(np.percentile(steady, 50)) if steady.size else None,
+            "steady_chunk_latency_p99_s": float(np.percentile(steady, 99)) if steady.size else None,
+            "steady_chunks_reported": int(steady.size),
+            "target_chunk_s": self.target,
             "requests_admitted": sum(1 for r in reqs if r.admitted is not None),
             "requests_completed": len(self.finished),
             "requests_cancelled": len(self.cancelled),

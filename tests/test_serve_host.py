@@ -174,7 +174,39 @@ def test_chunk_log_is_jsonl():
     srv = _server(10 * _size(64), log=buf)
     srv.run([_req(0.0, 64, 250, seed=0), _req(0.0, 64, 120, seed=1)])
     recs = [json.loads(ln) for ln in buf.getvalue().splitlines()]
-    # chunks end where a request finishes: 100, 20 (request 1 done), 100, 30
-    assert [r["steps"] for r in recs] == [100, 20, 100, 30]
+    # launches end where a request reports or finishes: 100, 20 (request
+    # 1 done), 80 (request 0 reports at its step 200), 50
+    assert [r["steps"] for r in recs] == [100, 20, 80, 50]
     assert [r["live"] for r in recs] == [2, 2, 1, 1]
     assert all(r["agent_steps"] == 64 * r["steps"] * r["live"] for r in recs)
+
+
+def test_every_request_reports_every_chunk_of_its_own_steps():
+    """Requests whose step counts are not multiples of the chunk share
+    launches cut at the next report of any of them: each reports at every
+    multiple of 100 of its own steps and at its last step."""
+    srv = _server(1e12)
+    steps = (250, 420, 135, 999, 100)
+    trace = [_req(0.0, 64, s, seed=k) for k, s in enumerate(steps)]
+    trace.append(_req(0.0, 64, 330, seed=9))
+    rep = srv.run(trace)
+    assert rep["requests_completed"] == len(trace)
+    for r in srv.finished:
+        assert len(r.latencies) == r.steps // 100 + (1 if r.steps % 100 else 0), \
+            (r.steps, len(r.latencies))
+    # no launch crosses a report: launches end at a multiple of 100 of some request
+    assert all(n <= 100 for _, n in FakeBatch.log)
+    assert sum(n for _, n in FakeBatch.log) == 999
+
+
+def test_latency_target_bounds_the_live_agents():
+    """With a chunk-latency target, a request waits while the live agents
+    plus its own would take longer than the target per chunk at the
+    server's rate: here 2 x 64 agents x 100 steps / 1e4 agent-steps/s = 1.28 s
+    fits a 1.5 s target, 3 x 64 does not."""
+    srv = _server(1e12, target_chunk_s=1.5, rate_prior=1e4, learn_rate=False)
+    seen = []
+    FakeBatch.on_step = lambda: seen.append(len(srv.live))
+    rep = srv.run([_req(0.0, 64, 100, seed=k) for k in range(5)])
+    assert rep["requests_completed"] == 5
+    assert max(seen) <= 2
