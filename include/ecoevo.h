@@ -275,6 +275,12 @@ typedef struct EcoAnalysis {
  * share that stream.  Errors: ECO_EINVAL, ECO_ECUDA. */
 int eco_world_analysis_async(EcoWorld *world, EcoAnalysis *out_host);
 
+/* Life expectancy (App. C: mean age at death; the paper pools 500 steps)
+ * over n consecutive analysis records (host memory, as eco_world_analysis_async
+ * wrote them): sum of death_age_sum / sum of deaths, written to *out; NaN
+ * when nobody died.  Host only, synchronous.  Errors: ECO_EINVAL. */
+int eco_life_expectancy(const EcoAnalysis *records, int64_t n, double *out);
+
 /* Greediness in the lab environments (App. C): G = C_r / T_r, where T_r
  * counts the windows (the paper's are 20 steps) in which a resource was in
  * the agent's field of view at the observation of some step (7x7 or 15x15
@@ -286,6 +292,13 @@ int eco_world_analysis_async(EcoWorld *world, EcoAnalysis *out_host);
  * memory) after waiting for the stream.  Errors: ECO_EINVAL, ECO_ECUDA. */
 int eco_world_lab_window(EcoWorld *world);
 int eco_world_lab_read(EcoWorld *world, int32_t *seen_windows_host, int32_t *meal_windows_host);
+
+/* Greediness G = C_r / T_r of n agents (App. C) from the two window counts
+ * eco_world_lab_read returns (host memory): out[i] = meal_windows[i] /
+ * seen_windows[i], NaN where seen_windows[i] = 0.  Host only, synchronous.
+ * Errors: ECO_EINVAL. */
+int eco_greediness(const int32_t *seen_windows, const int32_t *meal_windows, int64_t n,
+                   double *out);
 
 /* Wait for the world's stream; returns ECO_ETIMEOUT if a device wait ran
  * out, ECO_ECUDA on a CUDA error, else ECO_OK.  Synchronous. */
@@ -341,17 +354,19 @@ typedef struct EcoTuneResult {
   int32_t fused, spawn_ctas_per_sm, steps_per_graph, reserved;
   int64_t steps_taken;          /* steps every world advanced while tuning  */
   double ms_per_step_initial;   /* one trial in the configuration it started from */
-  double ms_per_step_best;      /* median trial of the configuration it left */
+  double ms_per_step_best;      /* the chosen configuration, timed once more at
+                                   the end (at the population reached then)  */
 } EcoTuneResult;
 
 /* Choose the launch configuration for this batch's worlds by timing real
  * steps of the batch: one knob after the other (fused, then
  * spawn_ctas_per_sm, then steps_per_graph), every candidate value three
- * times round-robin, trial_steps steps per trial (the graph-length trials
- * use trial_steps rounded up to a multiple of 16); a knob moves to the
- * candidate with the lowest median time per step only if that median is
+ * times round-robin, trial_steps steps per trial (a graph-length trial
+ * takes trial_steps rounded up to a multiple of that length); a knob moves to
+ * the candidate with the lowest median time per step only if that median is
  * more than 3% below the current value's.  Candidates: fused {1, 0},
- * spawn_ctas_per_sm {2, 4, 8}, steps_per_graph {1, 4, 16}.  The worlds advance by
+ * spawn_ctas_per_sm {1, 2, 4, 8}, steps_per_graph {1, 4, 16, 50}.  Finally the
+ * chosen configuration is timed once more (ms_per_step_best).  The worlds advance by
  * out->steps_taken steps, exactly as eco_batch_step would have taken them.
  * Synchronous.  Errors: ECO_EINVAL (trial_steps outside 1..100000, profiling
  * on), ECO_ECUDA. */

@@ -132,6 +132,8 @@ SIGNATURES = {
     "eco_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
     "eco_kernels_per_step": (ctypes.c_int, [_P]),
     "eco_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "eco_life_expectancy": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
+    "eco_greediness": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "eco_moves_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]),
 }

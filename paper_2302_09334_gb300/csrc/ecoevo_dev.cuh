@@ -160,6 +160,8 @@ struct WorldDev {            // read-only while kernels run
   float *c;                  // [C][32]
   float *logits;             // [C][8]
   int32_t *alive_list;       // [C] slots alive at the start of the step
+  uint8_t *alive_new;        // [C] alive_list[i] received a child in the last step
+                             // (its weights come from the next step's tail kernel)
   int32_t *free_list, *birth_parent, *birth_child;  // [C]
   float *weights;            // [C][WSTRIDE], 256-B aligned
   Counters *ctr;
@@ -333,12 +335,16 @@ void launch_init_world(const WorldDev *wd_host, WorldDev *wd_dev, int n0,
                        const int32_t *place_y, const int32_t *place_x,
                        int border, uint32_t thr_init, int n_sms, cudaStream_t s);
 void launch_rebuild(const WorldDev *wd_host, int n_sms, cudaStream_t s);
-// Rows of `wstride` floats; ECO_CTRL_LSTM32 rows are permuted, ECO_CTRL_PAPER
-// rows are in logical order already (copied, padding zeroed).
-void launch_weights_to_physical(const float *logical, float *physical, int n, int controller,
-                                int n_sms, cudaStream_t s);
-void launch_weights_to_logical(const float *physical, float *logical, int n, int controller,
-                               int n_sms, cudaStream_t s);
+// Physical rows of `wstride` floats -> logical rows of `lpitch` floats
+// (device memory or the device address of page-locked host memory);
+// ECO_CTRL_LSTM32 rows are permuted, ECO_CTRL_PAPER rows are in logical order
+// already (copied).
+void launch_weights_to_logical(const float *physical, float *logical, size_t lpitch, int n,
+                               int controller, int n_sms, cudaStream_t s);
+// n rows of the weight array holding logical rows (copied there) -> physical
+// order, in place; returns a cudaError_t value.
+int launch_rows_to_physical_inplace(float *rows, int n, int controller, int n_sms,
+                                    cudaStream_t s);
 // analysis metrics of App. C (k_analysis.cu)
 void launch_analysis_reset(const WorldDev *wd_host, int n_sms, cudaStream_t s);
 void launch_analysis(const WorldDev *wd_host, int n_sms, cudaStream_t s);

@@ -66,7 +66,7 @@ struct Layout {
   size_t ctr, wdev, tab_worlds, tab_tiles, tab_blocks, thr, res0, res1, wall,
       slot_map, claim, bclaim, alive, killed, ate, flag, y, x, energy, repr_ctr,
       low_ctr, age, action, forced, target, birth_cell, arrive, h0, h1, c,
-      logits, alive_list, free_list, birth_parent, birth_child, snap_cell, analysis,
+      logits, alive_list, alive_new, free_list, birth_parent, birth_child, snap_cell, analysis,
       prev_act, lab_seen, lab_ate, lab_t, lab_c, scan_blocks, weights, staging, total;
 };
 
@@ -112,6 +112,7 @@ Layout layout_of(const EcoParams *p) {
   L.c = take(C1 * HID * 4);
   L.logits = take(C1 * 8 * 4);
   L.alive_list = take(C1 * 4);
+  L.alive_new = take(C1);
   L.free_list = take(C1 * 4);
   L.birth_parent = take(C1 * 4);
   L.birth_child = take(C1 * 4);
@@ -500,8 +501,10 @@ int time_steps(EcoBatch &b, int64_t steps, cudaEvent_t e0, cudaEvent_t e1, doubl
 // if it is faster by more than SWITCH_MARGIN: trials of a few steps are
 // noisy, and births (which some knobs act on) come in bursts.
 constexpr double SWITCH_MARGIN = 0.03;
-template <class Apply>
-int tune_knob(EcoBatch &b, const std::vector<int> &cand, int64_t trial, int rounds, Apply apply,
+// `trial_of(v)` is the number of steps a trial of candidate v takes (chunk
+// lengths are timed over a multiple of themselves).
+template <class Apply, class Trial>
+int tune_knob(EcoBatch &b, const std::vector<int> &cand, Trial trial_of, int rounds, Apply apply,
               cudaEvent_t e0, cudaEvent_t e1, int64_t *steps, int *best, double *best_ms) {
   std::vector<std::vector<double>> t(cand.size());
   for (int r = 0; r < rounds; ++r) {
@@ -509,6 +512,7 @@ int tune_knob(EcoBatch &b, const std::vector<int> &cand, int64_t trial, int roun
       int rc = apply(cand[i]);
       if (rc) return rc;
       double ms = 0.0;
+      const int64_t trial = trial_of(cand[i]);
       if ((rc = time_steps(b, trial, e0, e1, &ms))) return rc;
       *steps += trial;
       t[i].push_back(ms);
@@ -552,20 +556,30 @@ int autotune(EcoBatch &b, int trial_steps, EcoTuneResult *out) {
   if (!rc) rc = set_config(b, fused, spawn, k);
   if (!rc) rc = time_steps(b, trial_steps, e0, e1, &out->ms_per_step_initial);
   if (!rc) steps += trial_steps;
+  auto same = [&](int) { return (int64_t)trial_steps; };
   if (!rc && b.bd.max_capacity <= FUSED_MAX_C) {
-    rc = tune_knob(b, {1, 0}, trial_steps, rounds,
+    rc = tune_knob(b, {1, 0}, same, rounds,
                    [&](int v) { return set_config(b, v, spawn, k); }, e0, e1, &steps, &fused, &ms);
   }
   if (!rc) {
-    rc = tune_knob(b, {2, 4, 8}, trial_steps, rounds,
+    rc = tune_knob(b, {1, 2, 4, 8}, same, rounds,
                    [&](int v) { return set_config(b, fused, v, k); }, e0, e1, &steps, &spawn, &ms);
   }
   if (!rc) {
-    // chunk lengths are compared over the same number of steps, a multiple
-    // of every candidate
-    const int64_t chunk_trial = ((trial_steps + 15) / 16) * 16;
-    rc = tune_knob(b, {1, 4, 16}, chunk_trial, rounds,
+    // a chunk length is timed over whole chunks: the multiple of it closest
+    // to the trial length from above (steps per graph of the batched
+    // workload: 50)
+    auto whole = [&](int v) { return (int64_t)((trial_steps + v - 1) / v) * v; };
+    rc = tune_knob(b, {1, 4, 16, 50}, whole, rounds,
                    [&](int v) { return set_config(b, fused, spawn, v); }, e0, e1, &steps, &k, &ms);
+  }
+  // the record's best time: the chosen configuration timed again now, at
+  // the population the batch has reached (the knobs' medians were taken at
+  // earlier, different populations)
+  if (!rc) {
+    const int64_t trial = ((trial_steps + k - 1) / k) * k;
+    rc = time_steps(b, trial, e0, e1, &ms);
+    if (!rc) steps += trial;
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -640,6 +654,7 @@ static void fill_descriptor(EcoWorld *w) {
   d.c = (float *)(a + L.c);
   d.logits = (float *)(a + L.logits);
   d.alive_list = (int32_t *)(a + L.alive_list);
+  d.alive_new = (uint8_t *)(a + L.alive_new);
   d.free_list = (int32_t *)(a + L.free_list);
   d.birth_parent = (int32_t *)(a + L.birth_parent);
   d.birth_child = (int32_t *)(a + L.birth_child);
@@ -840,6 +855,26 @@ int eco_world_analysis_async(EcoWorld *w, EcoAnalysis *out_host) {
   return ECO_OK;
 }
 
+int eco_life_expectancy(const EcoAnalysis *records, int64_t n, double *out) {
+  if (!out || n < 0 || (n > 0 && !records)) return ECO_EINVAL;
+  int64_t deaths = 0, ages = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    deaths += records[i].deaths;
+    ages += records[i].death_age_sum;
+  }
+  *out = deaths > 0 ? (double)ages / (double)deaths : std::nan("");
+  return ECO_OK;
+}
+
+int eco_greediness(const int32_t *seen_windows, const int32_t *meal_windows, int64_t n,
+                   double *out) {
+  if (n < 0 || (n > 0 && (!seen_windows || !meal_windows || !out))) return ECO_EINVAL;
+  for (int64_t i = 0; i < n; ++i)
+    out[i] = seen_windows[i] > 0 ? (double)meal_windows[i] / (double)seen_windows[i]
+                                 : std::nan("");
+  return ECO_OK;
+}
+
 int eco_world_lab_window(EcoWorld *w) {
   if (!w) return ECO_EINVAL;
   launch_lab_window(&w->hd, w->n_sms, w->stream);
@@ -898,34 +933,54 @@ static void counters_to_array(const Counters &c, int64_t *out) {
   out[ECO_C_AGENT_STEPS] = c.agent_steps;
 }
 
-static int download(void *dst, const void *src, size_t bytes) {
-  if (!dst || !bytes) return ECO_OK;
-  return cuda_err(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
-}
-static int upload(void *dst, const void *src, size_t bytes) {
-  if (!src || !bytes) return ECO_OK;
-  return cuda_err(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+// State I/O.  Every copy is enqueued on the world's stream and the call
+// waits once at the end (a first version waited after each of ~20 copies).
+// A copy from or to page-locked host memory is a DMA transfer that overlaps
+// the others; from pageable memory the driver stages it.  Weights move
+// between the host's logical order and the device's physical order by a
+// permutation kernel: it reads or writes page-locked host memory directly
+// through its device address, and pageable memory through a staging region
+// of STAGING_AGENTS rows in the arena.
+struct StateIO {
+  cudaStream_t s;
+  int rc = ECO_OK;
+  explicit StateIO(cudaStream_t st) : s(st) {}
+  void d2h(void *dst, const void *src, size_t bytes) {
+    if (rc || !dst || !bytes) return;
+    rc = cuda_err(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+  }
+  void h2d(void *dst, const void *src, size_t bytes) {
+    if (rc || !src || !bytes) return;
+    rc = cuda_err(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+  }
+  int wait() {
+    if (rc) return rc;
+    return rc = cuda_err(cudaStreamSynchronize(s));
+  }
+};
+
+// Device address of a page-locked host buffer, or null for pageable memory.
+static void *pinned_device_view(const void *host) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
 }
 
-static int read_plane(const uint32_t *plane, const EcoParams &p, uint8_t *out) {
-  if (!out) return ECO_OK;
+static void pack_plane(const EcoParams &p, const uint8_t *in, std::vector<uint32_t> &words) {
   const int Wp = (p.W + 31) / 32;
-  std::vector<uint32_t> words((size_t)p.H * Wp);
-  int rc = download(words.data(), plane, words.size() * 4);
-  if (rc) return rc;
-  for (int y = 0; y < p.H; ++y)
-    for (int x = 0; x < p.W; ++x)
-      out[(size_t)y * p.W + x] = (words[(size_t)y * Wp + (x >> 5)] >> (x & 31)) & 1u;
-  return ECO_OK;
-}
-static int write_plane(uint32_t *plane, const EcoParams &p, const uint8_t *in) {
-  if (!in) return ECO_OK;
-  const int Wp = (p.W + 31) / 32;
-  std::vector<uint32_t> words((size_t)p.H * Wp, 0u);
+  words.assign((size_t)p.H * Wp, 0u);
   for (int y = 0; y < p.H; ++y)
     for (int x = 0; x < p.W; ++x)
       if (in[(size_t)y * p.W + x]) words[(size_t)y * Wp + (x >> 5)] |= 1u << (x & 31);
-  return upload(plane, words.data(), words.size() * 4);
+}
+static void unpack_plane(const EcoParams &p, const std::vector<uint32_t> &words, uint8_t *out) {
+  const int Wp = (p.W + 31) / 32;
+  for (int y = 0; y < p.H; ++y)
+    for (int x = 0; x < p.W; ++x)
+      out[(size_t)y * p.W + x] = (words[(size_t)y * Wp + (x >> 5)] >> (x & 31)) & 1u;
 }
 
 // The last step's births get their weights from the tail kernel that
@@ -952,47 +1007,71 @@ int eco_world_read_state(EcoWorld *w, EcoState *out) {
        (size_t)out->weights_first + out->weights_count > C))
     return ECO_EINVAL;
   int rc = ECO_OK;
-  if (out->weights_host && out->weights_count > 0 && (rc = settle_births(w))) return rc;
-  ECO_CU(cudaStreamSynchronize(w->stream));
+  const bool wts = out->weights_host && out->weights_count > 0;
+  if (wts && (rc = settle_births(w))) return rc;
+  StateIO io(w->stream);
   Counters c;
-  rc = download(&c, d.ctr, sizeof(Counters));
-  if (rc) return rc;
+  io.d2h(&c, d.ctr, sizeof(Counters));
+  if ((rc = io.wait())) return rc;
   counters_to_array(c, out->counters);
   const bool odd = (c.t & 1) != 0;
-  if ((rc = read_plane(odd ? d.res1 : d.res0, p, out->res_host))) return rc;
-  if ((rc = read_plane(d.wall, p, out->wall_host))) return rc;
-  if ((rc = download(out->slot_map_host, d.slot_map, HW * 4))) return rc;
-  if ((rc = download(out->alive_host, d.alive, C))) return rc;
-  if ((rc = download(out->y_host, d.y, C * 4))) return rc;
-  if ((rc = download(out->x_host, d.x, C * 4))) return rc;
-  if ((rc = download(out->energy_host, d.energy, C * 4))) return rc;
-  if ((rc = download(out->repr_ctr_host, d.repr_ctr, C * 4))) return rc;
-  if ((rc = download(out->low_ctr_host, d.low_ctr, C * 4))) return rc;
-  if ((rc = download(out->age_host, d.age, C * 4))) return rc;
-  if ((rc = download(out->h_host, odd ? d.h1 : d.h0, C * HID * 4))) return rc;
-  if ((rc = download(out->c_host, d.c, C * HID * 4))) return rc;
-  if ((rc = download(out->action_host, d.action, C * 4))) return rc;
-  if ((rc = download(out->prev_action_host, d.prev_act, C * 4))) return rc;
-  if ((rc = download(out->ate_host, d.ate, C))) return rc;
-  if (out->logits_host && C) {
-    std::vector<float> lg(C * 8);
-    if ((rc = download(lg.data(), d.logits, lg.size() * 4))) return rc;
-    for (size_t s = 0; s < C; ++s)
-      for (int a = 0; a < NACT; ++a) out->logits_host[s * NACT + a] = lg[s * 8 + a];
+  const size_t nwords = (size_t)p.H * ((p.W + 31) / 32);
+  std::vector<uint32_t> res_w, wall_w;
+  std::vector<float> lg;
+  if (out->res_host) {
+    res_w.resize(nwords);
+    io.d2h(res_w.data(), odd ? d.res1 : d.res0, nwords * 4);
   }
-  if (out->weights_host && out->weights_count > 0) {
-    float *staging = (float *)(w->arena + w->L.staging);
+  if (out->wall_host) {
+    wall_w.resize(nwords);
+    io.d2h(wall_w.data(), d.wall, nwords * 4);
+  }
+  io.d2h(out->slot_map_host, d.slot_map, HW * 4);
+  io.d2h(out->alive_host, d.alive, C);
+  io.d2h(out->y_host, d.y, C * 4);
+  io.d2h(out->x_host, d.x, C * 4);
+  io.d2h(out->energy_host, d.energy, C * 4);
+  io.d2h(out->repr_ctr_host, d.repr_ctr, C * 4);
+  io.d2h(out->low_ctr_host, d.low_ctr, C * 4);
+  io.d2h(out->age_host, d.age, C * 4);
+  io.d2h(out->h_host, odd ? d.h1 : d.h0, C * HID * 4);
+  io.d2h(out->c_host, d.c, C * HID * 4);
+  io.d2h(out->action_host, d.action, C * 4);
+  io.d2h(out->prev_action_host, d.prev_act, C * 4);
+  io.d2h(out->ate_host, d.ate, C);
+  if (out->logits_host && C) {
+    lg.resize(C * 8);
+    io.d2h(lg.data(), d.logits, lg.size() * 4);
+  }
+  if (wts && !io.rc) {
     const size_t ws = d.wstride, np = d.nparam;
-    for (int s0 = 0; s0 < out->weights_count; s0 += STAGING_AGENTS) {
-      const int n = std::min(STAGING_AGENTS, out->weights_count - s0);
-      launch_weights_to_logical(d.weights + (size_t)(out->weights_first + s0) * ws, staging, n,
-                                d.controller, w->n_sms, w->stream);
-      ECO_CU(cudaGetLastError());
-      ECO_CU(cudaMemcpy2DAsync(out->weights_host + (size_t)s0 * np, np * 4, staging, ws * 4,
-                               np * 4, n, cudaMemcpyDeviceToHost, w->stream));
-      ECO_CU(cudaStreamSynchronize(w->stream));
+    const float *src = d.weights + (size_t)out->weights_first * ws;
+    if (float *dev = (float *)pinned_device_view(out->weights_host)) {
+      launch_weights_to_logical(src, dev, np, out->weights_count, d.controller, w->n_sms,
+                                w->stream);
+      io.rc = cuda_err(cudaGetLastError());
+    } else {
+      float *staging = (float *)(w->arena + w->L.staging);
+      for (int s0 = 0; s0 < out->weights_count && !io.rc; s0 += STAGING_AGENTS) {
+        const int n = std::min(STAGING_AGENTS, out->weights_count - s0);
+        launch_weights_to_logical(src + (size_t)s0 * ws, staging, ws, n, d.controller, w->n_sms,
+                                  w->stream);
+        io.rc = cuda_err(cudaGetLastError());
+        if (!io.rc)
+          io.rc = cuda_err(cudaMemcpy2DAsync(out->weights_host + (size_t)s0 * np, np * 4,
+                                             staging, ws * 4, np * 4, n,
+                                             cudaMemcpyDeviceToHost, w->stream));
+        // the next chunk's permutation, which reuses the staging region, is
+        // ordered after this copy by the stream
+      }
     }
   }
+  if ((rc = io.wait())) return rc;
+  if (out->res_host) unpack_plane(p, res_w, out->res_host);
+  if (out->wall_host) unpack_plane(p, wall_w, out->wall_host);
+  if (out->logits_host)
+    for (size_t s = 0; s < C; ++s)
+      for (int a = 0; a < NACT; ++a) out->logits_host[s * NACT + a] = lg[s * 8 + a];
   return ECO_OK;
 }
 
@@ -1008,10 +1087,10 @@ int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
     return ECO_EINVAL;
   int rc = settle_births(w);
   if (rc) return rc;
-  ECO_CU(cudaStreamSynchronize(w->stream));
+  StateIO io(w->stream);
   Counters c;
-  rc = download(&c, d.ctr, sizeof(Counters));
-  if (rc) return rc;
+  io.d2h(&c, d.ctr, sizeof(Counters));
+  if ((rc = io.wait())) return rc;
   if (set_counters) {
     c.t = in->counters[ECO_C_T];
     c.births = in->counters[ECO_C_BIRTHS];
@@ -1026,53 +1105,64 @@ int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
   c.deaths_step = 0;
   c.n_births = 0;
   c.use_forced = 0;
-  if ((rc = upload(d.ctr, &c, sizeof(Counters)))) return rc;
+  // host buffers below live until the final wait
+  std::vector<uint32_t> res_w, wall_w;
+  std::vector<float> lg;
+  io.h2d(d.ctr, &c, sizeof(Counters));
   const bool odd = (c.t & 1) != 0;
-  if ((rc = write_plane(odd ? d.res1 : d.res0, p, in->res_host))) return rc;
-  if ((rc = write_plane(d.wall, p, in->wall_host))) return rc;
-  if ((rc = upload(d.alive, in->alive_host, C))) return rc;
-  if ((rc = upload(d.y, in->y_host, C * 4))) return rc;
-  if ((rc = upload(d.x, in->x_host, C * 4))) return rc;
-  if ((rc = upload(d.energy, in->energy_host, C * 4))) return rc;
-  if ((rc = upload(d.repr_ctr, in->repr_ctr_host, C * 4))) return rc;
-  if ((rc = upload(d.low_ctr, in->low_ctr_host, C * 4))) return rc;
-  if ((rc = upload(d.age, in->age_host, C * 4))) return rc;
-  if ((rc = upload(odd ? d.h1 : d.h0, in->h_host, C * HID * 4))) return rc;
-  if ((rc = upload(d.c, in->c_host, C * HID * 4))) return rc;
-  if ((rc = upload(d.action, in->action_host, C * 4))) return rc;
-  if ((rc = upload(d.prev_act, in->prev_action_host, C * 4))) return rc;
-  if ((rc = upload(d.ate, in->ate_host, C))) return rc;
+  if (in->res_host) {
+    pack_plane(p, in->res_host, res_w);
+    io.h2d(odd ? d.res1 : d.res0, res_w.data(), res_w.size() * 4);
+  }
+  if (in->wall_host) {
+    pack_plane(p, in->wall_host, wall_w);
+    io.h2d(d.wall, wall_w.data(), wall_w.size() * 4);
+  }
+  io.h2d(d.alive, in->alive_host, C);
+  io.h2d(d.y, in->y_host, C * 4);
+  io.h2d(d.x, in->x_host, C * 4);
+  io.h2d(d.energy, in->energy_host, C * 4);
+  io.h2d(d.repr_ctr, in->repr_ctr_host, C * 4);
+  io.h2d(d.low_ctr, in->low_ctr_host, C * 4);
+  io.h2d(d.age, in->age_host, C * 4);
+  io.h2d(odd ? d.h1 : d.h0, in->h_host, C * HID * 4);
+  io.h2d(d.c, in->c_host, C * HID * 4);
+  io.h2d(d.action, in->action_host, C * 4);
+  io.h2d(d.prev_act, in->prev_action_host, C * 4);
+  io.h2d(d.ate, in->ate_host, C);
   if (in->logits_host && C) {
-    std::vector<float> lg(C * 8, 0.f);
+    lg.assign(C * 8, 0.f);
     for (size_t s = 0; s < C; ++s)
       for (int a = 0; a < NACT; ++a) lg[s * 8 + a] = in->logits_host[s * NACT + a];
-    if ((rc = upload(d.logits, lg.data(), lg.size() * 4))) return rc;
+    io.h2d(d.logits, lg.data(), lg.size() * 4);
   }
-  if (in->weights_host && in->weights_count > 0) {
-    float *staging = (float *)(w->arena + w->L.staging);
+  if (in->weights_host && in->weights_count > 0 && !io.rc) {
+    // one 2-D copy of the logical rows into their own device rows (a DMA
+    // transfer from page-locked memory, staged by the driver from pageable
+    // memory), then the permutation to the physical order in place
     const size_t ws = d.wstride, np = d.nparam;
-    for (int s0 = 0; s0 < in->weights_count; s0 += STAGING_AGENTS) {
-      const int n = std::min(STAGING_AGENTS, in->weights_count - s0);
-      ECO_CU(cudaMemcpy2DAsync(staging, ws * 4, in->weights_host + (size_t)s0 * np, np * 4,
-                               np * 4, n, cudaMemcpyHostToDevice, w->stream));
-      launch_weights_to_physical(staging, d.weights + (size_t)(in->weights_first + s0) * ws, n,
-                                 d.controller, w->n_sms, w->stream);
-      ECO_CU(cudaGetLastError());
-    }
+    float *dst = d.weights + (size_t)in->weights_first * ws;
+    io.rc = cuda_err(cudaMemcpy2DAsync(dst, ws * 4, in->weights_host, np * 4, np * 4,
+                                       in->weights_count, cudaMemcpyHostToDevice, w->stream));
+    if (!io.rc)
+      io.rc = cuda_err((cudaError_t)launch_rows_to_physical_inplace(
+          dst, in->weights_count, d.controller, w->n_sms, w->stream));
   }
   // greediness counters start over with a loaded state
-  ECO_CU(cudaMemsetAsync(d.lab_seen, 0, C ? C : 1, w->stream));
-  ECO_CU(cudaMemsetAsync(d.lab_ate, 0, C ? C : 1, w->stream));
-  ECO_CU(cudaMemsetAsync(d.lab_t, 0, (C ? C : 1) * 4, w->stream));
-  ECO_CU(cudaMemsetAsync(d.lab_c, 0, (C ? C : 1) * 4, w->stream));
-  launch_rebuild(&w->hd, w->n_sms, w->stream);
-  ECO_CU(cudaGetLastError());
-  ECO_CU(cudaStreamSynchronize(w->stream));
+  if (!io.rc) io.rc = cuda_err(cudaMemsetAsync(d.lab_seen, 0, C ? C : 1, w->stream));
+  if (!io.rc) io.rc = cuda_err(cudaMemsetAsync(d.lab_ate, 0, C ? C : 1, w->stream));
+  if (!io.rc) io.rc = cuda_err(cudaMemsetAsync(d.lab_t, 0, (C ? C : 1) * 4, w->stream));
+  if (!io.rc) io.rc = cuda_err(cudaMemsetAsync(d.lab_c, 0, (C ? C : 1) * 4, w->stream));
+  if (!io.rc) {
+    launch_rebuild(&w->hd, w->n_sms, w->stream);
+    io.rc = cuda_err(cudaGetLastError());
+  }
   int st = 0;
-  if ((rc = read_status(w, &st))) return rc;
+  io.d2h(&st, &d.ctr->status, sizeof(int));
+  if ((rc = io.wait())) return rc;
   if (st & ST_STATE) {
     st &= ~ST_STATE;
-    upload(&d.ctr->status, &st, sizeof(int));
+    ECO_CU(cudaMemcpy(&d.ctr->status, &st, sizeof(int), cudaMemcpyHostToDevice));
     return ECO_ESTATE;
   }
   return ECO_OK;

@@ -329,7 +329,7 @@ __device__ __forceinline__ void phase_sync() {
     cg::this_cluster().sync();
 }
 
-template <int NCTA>
+template <int NCTA, int THREADS>
 __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
   __shared__ int sh[3 * 32 + 3];
   __shared__ int pub[3], ex[6];
@@ -340,7 +340,7 @@ __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
   const int C = wd.C, W = wd.W, Wp = wd.Wp;
   const int per_cta = (C + NCTA - 1) / NCTA;
   const int c0 = min(C, rank * per_cta), c1 = min(C, c0 + per_cta);
-  const int per = (c1 - c0 + SCAN_THREADS - 1) / SCAN_THREADS;
+  const int per = (c1 - c0 + THREADS - 1) / THREADS;
   const int s0 = min(c1, c0 + (int)threadIdx.x * per);
   const int ns = min(c1, s0 + per) - s0;
   if (threadIdx.x == 0) {
@@ -513,8 +513,10 @@ __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
     }
     // the next alive list: survivors and the free slots that receive a child
     if (al[k]) {
+      wd.alive_new[alive_pos] = 0;
       wd.alive_list[alive_pos++] = s;
     } else if (free_rank++ < births) {
+      wd.alive_new[alive_pos] = 1;
       wd.alive_list[alive_pos++] = s;
     }
   }
@@ -526,11 +528,11 @@ __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
 
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(SCAN_THREADS)
     k_agents_cluster(const __grid_constant__ BatchDev b) {
-  agents_fused_body<CLUSTER>(b);
+  agents_fused_body<CLUSTER, SCAN_THREADS>(b);
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_agents_single(const __grid_constant__ BatchDev b) {
-  agents_fused_body<1>(b);
+  agents_fused_body<1, SCAN_THREADS>(b);
 }
 
 // ---------------------------------------------------------------------------
@@ -626,9 +628,13 @@ __global__ void __launch_bounds__(SLOT_BLOCK) k_scan_lists(const __grid_constant
   const int pos = surv_before + min(free_before, births);
   if (a) {
     wd.alive_list[pos] = s;
+    wd.alive_new[pos] = 0;
   } else {
     if (free_before < S) wd.free_list[free_before] = s;
-    if (free_before < births) wd.alive_list[pos] = s;   // receives a child
+    if (free_before < births) {   // receives a child
+      wd.alive_list[pos] = s;
+      wd.alive_new[pos] = 1;
+    }
   }
 }
 
@@ -696,8 +702,13 @@ __device__ inline float4 mutate4(const WorldDev &wd, int vi, float4 base, uint32
   return make_float4(out[0], out[1], out[2], out[3]);
 }
 
-// Grid-stride over every float4 of every birth of the batch; each thread
-// issues the loads of SPAWN_UNROLL elements before any of their arithmetic.
+// Work items of the mutation: (birth, chunk of SPAWN_CHUNK float4s of its
+// weight row), dealt to the CTAs round-robin; a CTA's threads take the
+// float4s of an item in turn, each thread issuing the loads of SPAWN_UNROLL
+// float4s before any of their arithmetic.  The birth's world, parent, child
+// and step are looked up once per item (a first version looked them up, with
+// a 64-bit division, for every float4).
+constexpr int SPAWN_CHUNK = 1024;
 constexpr int SPAWN_UNROLL = 2;
 
 // Mutation of every birth of the batch by CTAs cta .. of n_cta.
@@ -715,42 +726,35 @@ __device__ inline void spawn_births(const BatchDev &b, int *pre, int cta, int n_
   }
   __syncthreads();
   const int nvec = b.wstride / 4;
-  const long long total = (long long)pre[b.n] * nvec;
-  const long long stride = (long long)n_cta * blockDim.x;
-  for (long long g0 = (long long)cta * blockDim.x + threadIdx.x; g0 < total;
-       g0 += SPAWN_UNROLL * stride) {
-    float4 in[SPAWN_UNROLL];
-    float4 *dst[SPAWN_UNROLL];
-    const WorldDev *wdu[SPAWN_UNROLL];
-    int vi[SPAWN_UNROLL], par[SPAWN_UNROLL];
-#pragma unroll
-    for (int u = 0; u < SPAWN_UNROLL; ++u) {
-      const long long g = g0 + u * stride;
-      dst[u] = nullptr;
-      if (g >= total) continue;
-      const int bi = (int)(g / nvec);
-      vi[u] = (int)(g % nvec);
-      int lo = 0, hi = b.n - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (pre[mid] <= bi) lo = mid; else hi = mid - 1;
-      }
-      const WorldDev &wd = *world_ptr(b, lo);
-      const int k = bi - pre[lo];
-      par[u] = wd.birth_parent[k];
-      const int child = wd.birth_child[k];
-      if (!ECO_IN_RANGE(wd, par[u] >= 0 && par[u] < wd.C && child >= 0 && child < wd.C))
-        continue;
-      wdu[u] = &wd;
-      in[u] = reinterpret_cast<const float4 *>(wd.weights + (size_t)par[u] * b.wstride)[vi[u]];
-      dst[u] = reinterpret_cast<float4 *>(wd.weights + (size_t)child * b.wstride) + vi[u];
+  const int per = (nvec + SPAWN_CHUNK - 1) / SPAWN_CHUNK;   // items per birth
+  const int items = pre[b.n] * per;
+  for (int item = cta; item < items; item += n_cta) {
+    const int bi = item / per, v0 = (item - bi * per) * SPAWN_CHUNK;
+    const int v1 = min(nvec, v0 + SPAWN_CHUNK);
+    int lo = 0, hi = b.n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (pre[mid] <= bi) lo = mid; else hi = mid - 1;
     }
+    const WorldDev &wd = *world_ptr(b, lo);
+    const int k = bi - pre[lo];
+    const int par = wd.birth_parent[k], child = wd.birth_child[k];
+    if (!ECO_IN_RANGE(wd, par >= 0 && par < wd.C && child >= 0 && child < wd.C)) continue;
+    const uint32_t t = wd.ctr->births_t;
+    const float4 *src = reinterpret_cast<const float4 *>(wd.weights + (size_t)par * b.wstride);
+    float4 *dst = reinterpret_cast<float4 *>(wd.weights + (size_t)child * b.wstride);
+    for (int vi = v0 + (int)threadIdx.x; vi < v1; vi += SPAWN_UNROLL * (int)blockDim.x) {
+      float4 in[SPAWN_UNROLL];
 #pragma unroll
-    for (int u = 0; u < SPAWN_UNROLL; ++u) {
-      if (!dst[u]) continue;
-      const WorldDev &wd = *wdu[u];
-      *dst[u] = mutate4(wd, vi[u], in[u], TAG_MUT, wd.ctr->births_t, (uint32_t)par[u],
-                        wd.mut_std);
+      for (int u = 0; u < SPAWN_UNROLL; ++u) {
+        const int v = vi + u * (int)blockDim.x;
+        if (v < v1) in[u] = src[v];
+      }
+#pragma unroll
+      for (int u = 0; u < SPAWN_UNROLL; ++u) {
+        const int v = vi + u * (int)blockDim.x;
+        if (v < v1) dst[v] = mutate4(wd, v, in[u], TAG_MUT, t, (uint32_t)par, wd.mut_std);
+      }
     }
   }
 }

@@ -139,7 +139,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_alive_list(WorldDev wd) {
   __syncthreads();
   int off = sh[warp] + inc - n;
   for (int s = s0; s < s1; ++s)
-    if (wd.alive[s]) wd.alive_list[off++] = s;
+    if (wd.alive[s]) {
+      wd.alive_new[off] = wd.age[s] == 0 ? 1 : 0;   // never stepped: treated as newborn
+      wd.alive_list[off++] = s;
+    }
   if (threadIdx.x == 0) wd.ctr->pop = sh[32];
 }
 
@@ -151,25 +154,37 @@ __device__ inline int logical_of(int controller, int p) {
   return logical_of_phys(p);
 }
 
-__global__ void k_weights_to_physical(const float *logical, float *physical, int n,
-                                      int controller, int stride) {
+// Weight rows from the physical order (rows of `stride` floats) to the
+// logical order (rows of `lpitch` floats, the first nparam written).  The
+// logical side may be page-locked host memory (its device address): writes
+// along a physical row are consecutive logical parameters within each
+// 180-weight gate row, so they coalesce.
+__global__ void k_weights_to_logical(const float *physical, float *logical, size_t lpitch,
+                                     int n, int controller, int stride) {
   const long long total = (long long)n * stride;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
     const int a = (int)(g / stride), p = (int)(g % stride);
     const int j = logical_of(controller, p);
-    physical[g] = j >= 0 ? logical[(size_t)a * stride + j] : 0.f;
+    if (j >= 0) logical[(size_t)a * lpitch + j] = physical[g];
   }
 }
 
-__global__ void k_weights_to_logical(const float *physical, float *logical, int n,
-                                     int controller, int stride) {
-  const long long total = (long long)n * stride;
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
-       g += (long long)gridDim.x * blockDim.x) {
-    const int a = (int)(g / stride), p = (int)(g % stride);
-    const int j = logical_of(controller, p);
-    if (j >= 0) logical[(size_t)a * stride + j] = physical[g];
+// Rows already on the device in logical order (the first nparam floats of
+// each `stride`-float row, copied there by DMA) permuted to the physical
+// order in place: each CTA stages a whole row in shared memory.
+__global__ void k_rows_to_physical_inplace(float *rows, int n, int controller, int stride,
+                                           int nparam) {
+  extern __shared__ float row[];
+  for (int a = blockIdx.x; a < n; a += gridDim.x) {
+    float *r = rows + (size_t)a * stride;
+    for (int i = threadIdx.x; i < stride; i += blockDim.x) row[i] = i < nparam ? r[i] : 0.f;
+    __syncthreads();
+    for (int p = threadIdx.x; p < stride; p += blockDim.x) {
+      const int j = logical_of(controller, p);
+      r[p] = j >= 0 ? row[j] : 0.f;
+    }
+    __syncthreads();
   }
 }
 
@@ -177,17 +192,25 @@ static int stride_of(int controller) {
   return controller == ECO_CTRL_PAPER ? PC_WSTRIDE : WSTRIDE;
 }
 
-void launch_weights_to_physical(const float *logical, float *physical, int n, int controller,
-                                int n_sms, cudaStream_t s) {
-  if (n > 0)
-    k_weights_to_physical<<<4 * n_sms, 256, 0, s>>>(logical, physical, n, controller,
-                                                    stride_of(controller));
+int launch_rows_to_physical_inplace(float *rows, int n, int controller, int n_sms,
+                                    cudaStream_t s) {
+  if (n <= 0) return 0;
+  const int stride = stride_of(controller);
+  const size_t smem = (size_t)stride * sizeof(float);
+  // a whole row of shared memory (the attribute is set on the current device)
+  cudaError_t e = cudaFuncSetAttribute(k_rows_to_physical_inplace,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(WSTRIDE * sizeof(float)));
+  if (e != cudaSuccess) return (int)e;
+  const int nparam = controller == ECO_CTRL_PAPER ? PC_NPARAM : NPARAM;
+  k_rows_to_physical_inplace<<<2 * n_sms, 512, smem, s>>>(rows, n, controller, stride, nparam);
+  return (int)cudaGetLastError();
 }
 
-void launch_weights_to_logical(const float *physical, float *logical, int n, int controller,
-                               int n_sms, cudaStream_t s) {
+void launch_weights_to_logical(const float *physical, float *logical, size_t lpitch, int n,
+                               int controller, int n_sms, cudaStream_t s) {
   if (n > 0)
-    k_weights_to_logical<<<4 * n_sms, 256, 0, s>>>(physical, logical, n, controller,
+    k_weights_to_logical<<<8 * n_sms, 256, 0, s>>>(physical, logical, lpitch, n, controller,
                                                    stride_of(controller));
 }
 

@@ -3,17 +3,24 @@
 //
 // Every agent has its own 93 KB of FP32 weights, used once per step, so the
 // step is a batched GEMV bound by HBM bandwidth (about 0.5 flop per byte).
-// A persistent grid of one CTA per SM; CTA b owns a contiguous range of the
-// agents of all worlds of the batch (world-major, alive-list order) and runs
-// a warp-specialised pipeline with no global synchronisation:
-//   * producer warp: streams each agent's four weight blocks (a block = the
-//     32 gate rows of 8 hidden units, 23,168 B; the last block also carries
-//     the read-out) with plain (non-multicast) cp.async.bulk copies into an
-//     8-stage shared-memory ring (two agents in flight, ~190 KB per SM);
-//   * two gather warps: build each agent's input [obs(148); h(32)] and its
-//     cell state into a 4-entry ring: the 7x7x3 window is staged through
-//     shared memory as 7-bit row masks of the bit planes; agent slots and
-//     positions are prefetched 32 agents at a time, one lane per agent;
+// A persistent grid of one CTA per SM runs a warp-specialised pipeline with
+// no global synchronisation:
+//   * CTA b takes the batch's agents b, b + G, b + 2G, ... (world-major,
+//     alive-list order; G CTAs), so its first agent is known before the
+//     population is: with one world its slot is requested together with the
+//     population, and the first copy waits for one round trip;
+//   * producer warp: slots and newborn flags of 32 agents at a time (one
+//     lane each), and each agent's four weight blocks (a block = the 32
+//     gate rows of 8 hidden units, 23,168 B; the last block also carries
+//     the read-out) streamed with plain (non-multicast) cp.async.bulk copies
+//     into an 8-stage shared-memory ring (two agents in flight, ~190 KB per
+//     SM);
+//   * four gather warps, taking the agents in turn: slots, positions and
+//     energies of 32 of their agents at a time, then per agent the 7x7x3
+//     window (row masks of the bit planes staged through shared memory),
+//     h and c in one round trip (about 4 us while the weight stream fills
+//     the memory system: four warps keep four in flight) into an 8-entry
+//     ring of inputs [obs(148); h(32)] and cell states;
 //   * four compute warps, warp q on block q: lane l computes gate row l with
 //     128-bit shared loads (conflict-free: rows are 720 B apart), the gate
 //     nonlinearity, and lanes 0, 4, .., 28 update the cell of their hidden
@@ -31,9 +38,9 @@
 namespace eco {
 
 constexpr int LSTAGES = 8;                 // two agents of four blocks
-constexpr int VRING = 4;                   // gathered inputs in flight
+constexpr int VRING = 8;                   // gathered inputs in flight
 constexpr int NCOMP = 4;                   // compute warps (one per block)
-constexpr int NGATH = 2;                   // gather warps
+constexpr int NGATH = 4;                   // gather warps
 constexpr int W_PROD = NCOMP + NGATH;      // producer warp index
 constexpr int LTHREADS = (NCOMP + NGATH + 1) * 32;
 constexpr int MAX_BATCH = 1024;
@@ -56,6 +63,15 @@ struct __align__(16) VEntry {
 };
 static_assert(sizeof(VEntry) % 16 == 0 && offsetof(VEntry, v) == 0,
               "ring entries keep v 16-byte aligned");
+
+// What the gather's window loads of one agent depend on: its slot, world,
+// position, energy, forced action (-1: its own) and the world's step counter.
+struct AgentDesc {
+  int slot, world, y, x;
+  float energy;
+  int forced;
+  uint32_t t;
+};
 
 struct __align__(128) LstmSmem {
   float stage[LSTAGES][STAGE_FLOATS];
@@ -141,37 +157,50 @@ __device__ inline uint32_t row7(const uint32_t *row, int Wp, int W, int xs,
 // the cell state.  The grid is the resource plane after this step's
 // regrowth, the agent channel is the start-of-step occupancy without the
 // agent itself, off-grid cells read as wall, the last observation is the
-// agent's energy.
-__device__ inline void gather_input(const WorldDev &wd, int slot, int y, int x,
-                                    float energy, uint32_t t, int forced, VEntry &e,
-                                    uint32_t *masks, int lane) {
+// agent's energy.  Every load depends only on the descriptor: gather_load
+// issues them all (one round trip) before the warp waits for its ring
+// entry, gather_store fills the entry.
+struct GatherRegs {
+  uint32_t mask;     // lanes 0..13: a row mask (resource rows, then wall rows)
+  float occ0, occ1, hp, cp;
+};
+
+__device__ inline GatherRegs gather_load(const WorldDev &wd, const AgentDesc &d, int lane) {
   const int H = wd.H, W = wd.W, Wp = wd.Wp;
-  const uint32_t *res = (t & 1u) ? wd.res0 : wd.res1;
-  const float *h_prev = (t & 1u) ? wd.h1 : wd.h0;
+  const uint32_t *res = (d.t & 1u) ? wd.res0 : wd.res1;
+  const float *h_prev = (d.t & 1u) ? wd.h1 : wd.h0;
+  GatherRegs g;
+  g.mask = 0u;
   if (lane < 14) {
     const bool is_wall = lane >= 7;
-    const int yy = y - 3 + (is_wall ? lane - 7 : lane);
-    uint32_t m;
+    const int yy = d.y - 3 + (is_wall ? lane - 7 : lane);
     if (yy < 0 || yy >= H)
-      m = is_wall ? 0x7Fu : 0u;
+      g.mask = is_wall ? 0x7Fu : 0u;
     else
-      m = row7((is_wall ? wd.wall : res) + (size_t)yy * Wp, Wp, W, x - 3, is_wall);
-    masks[lane] = m;
+      g.mask = row7((is_wall ? wd.wall : res) + (size_t)yy * Wp, Wp, W, d.x - 3, is_wall);
   }
-  float occ[2];
+  int occ[2];
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int k = lane + 32 * r;
-    const int yy = y + k / 7 - 3, xx = x + k % 7 - 3;
-    occ[r] = 0.f;
+    const int yy = d.y + k / 7 - 3, xx = d.x + k % 7 - 3;
+    occ[r] = -1;
     if (k < 49 && k != 24 && yy >= 0 && yy < H && xx >= 0 && xx < W)
-      occ[r] = wd.slot_map[(size_t)yy * W + xx] >= 0 ? 1.f : 0.f;
+      occ[r] = __ldcg(&wd.slot_map[(size_t)yy * W + xx]);
   }
-  const float hp = h_prev[(size_t)slot * HID + lane];
-  const float cp = wd.c[(size_t)slot * HID + lane];
+  g.occ0 = occ[0] >= 0 ? 1.f : 0.f;
+  g.occ1 = occ[1] >= 0 ? 1.f : 0.f;
+  g.hp = __ldcg(&h_prev[(size_t)d.slot * HID + lane]);
+  g.cp = __ldcg(&wd.c[(size_t)d.slot * HID + lane]);
+  return g;
+}
+
+__device__ inline void gather_store(const WorldDev &wd, const AgentDesc &d, const GatherRegs &g,
+                                    VEntry &e, uint32_t *masks, int lane) {
+  if (lane < 14) masks[lane] = g.mask;
   __syncwarp();
-  e.v[49 + lane] = occ[0];
-  if (lane + 32 < 49) e.v[49 + 32 + lane] = occ[1];
+  e.v[49 + lane] = g.occ0;
+  if (lane + 32 < 49) e.v[49 + 32 + lane] = g.occ1;
   for (int k = lane; k < 49; k += 32) {
     const int r = k / 7, cc = k % 7;
     e.v[k] = (float)((masks[r] >> cc) & 1u);
@@ -182,20 +211,55 @@ __device__ inline void gather_input(const WorldDev &wd, int slot, int y, int x,
     uint32_t any = 0u;
 #pragma unroll
     for (int r = 0; r < 7; ++r) any |= masks[r];
-    if (any) wd.lab_seen[slot] = 1;
-    e.v[147] = energy;
-    e.slot = slot;
-    e.y = y;
-    e.x = x;
-    e.forced = forced;
+    if (any) wd.lab_seen[d.slot] = 1;
+    e.v[147] = d.energy;
+    e.slot = d.slot;
+    e.y = d.y;
+    e.x = d.x;
+    e.forced = d.forced;
     e.wd = &wd;
-    e.c_row = wd.c + (size_t)slot * HID;
-    e.h_row = ((t & 1u) ? wd.h0 : wd.h1) + (size_t)slot * HID;
-    e.logits_row = wd.logits + (size_t)slot * 8;
-    e.action = wd.action + slot;
+    e.c_row = wd.c + (size_t)d.slot * HID;
+    e.h_row = ((d.t & 1u) ? wd.h0 : wd.h1) + (size_t)d.slot * HID;
+    e.logits_row = wd.logits + (size_t)d.slot * 8;
+    e.action = wd.action + d.slot;
   }
-  e.v[NOBS + lane] = hp;
-  e.c[lane] = cp;
+  e.v[NOBS + lane] = g.hp;
+  e.c[lane] = g.cp;
+}
+
+// Agent a of the batch (world-major, alive-list order): its world and its
+// position in that world's alive list.
+__device__ inline int local_index(const int *prefix, const BatchDev &b, int a, int *world) {
+  const int w = b.n == 1 ? 0 : world_of(prefix, b.n, a);
+  *world = w;
+  return a - (b.n == 1 ? 0 : prefix[w]);
+}
+
+// Slot and newborn flag of batch agent a, by one lane, as loaded: nothing
+// when a >= bound.  The bound is the population, or, for the loads issued
+// before the population is known (one world), the capacity: an entry past
+// the population is stale, so agent_valid() decides, once the population
+// is known, whether the lane's agent exists before anything uses its slot.
+struct AgentRef {
+  int slot, fresh, world;
+};
+__device__ inline AgentRef agent_ref(const int *prefix, const BatchDev &b, long long a,
+                                     long long bound) {
+  AgentRef r{0, 0, 0};
+  if (a < bound) {
+    const int li = local_index(prefix, b, (int)a, &r.world);
+    const WorldDev &wd = *world_ptr(b, r.world);
+    r.slot = __ldcg(&wd.alive_list[li]);
+    r.fresh = __ldcg(&wd.alive_new[li]);
+  }
+  return r;
+}
+// The reference of agent a if it exists (a < A, slot range-checked in the
+// checked build), else slot 0 of world 0 (never stepped, loads in range).
+__device__ inline AgentRef agent_valid(const BatchDev &b, AgentRef r, long long a, long long A) {
+  if (a >= A) return AgentRef{0, 0, 0};
+  r.slot = checked_index(*world_ptr(b, r.world), r.slot, world_ptr(b, r.world)->C);
+  return r;
 }
 
 __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ BatchDev b) {
@@ -203,7 +267,37 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
   LstmSmem &sm = *reinterpret_cast<LstmSmem *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned FULL = 0xFFFFFFFFu;
+  const int G = gridDim.x;
 
+  // The kernel before this one in a step is the tail (this step's
+  // regrowth, the mutation of the last step's births); the one before that
+  // (the slot phases) has completed by the time this kernel starts, since
+  // every tail CTA waits for it before it lets this kernel launch.  So the
+  // populations, alive lists and newborn flags, the weights of every agent
+  // not born in the last step, and everything the gather reads but the
+  // resource plane, are read before waiting for the tail (through L2,
+  // ld.cg); the resource plane and the newborns' weights only after.
+  pdl_release();
+
+  // CTA b steps the batch's agents b, b + G, b + 2G, ...  With one world the
+  // population and the first 32 slots of the producer and of each gather
+  // warp are requested at once, before the barriers are set up, so the
+  // first copy waits for one round trip.
+  const int role_first = warp == W_PROD ? 0 : (warp >= NCOMP ? warp - NCOMP : -1);
+  const int role_step = warp == W_PROD ? 1 : NGATH;   // CTA-local agents n = first + step k
+  AgentRef pre{0, 0, 0};
+  if (b.n == 1) {
+    const WorldDev &w0 = *world_ptr(b, 0);
+    const int pop = (warp == W_PROD && lane == 0) ? (int)__ldcg(&w0.ctr->pop) : 0;
+    if (role_first >= 0) {
+      const long long a = blockIdx.x + (long long)(role_first + role_step * lane) * G;
+      pre = agent_ref(sm.prefix, b, a, w0.C);   // guarded by the capacity only
+    }
+    if (warp == W_PROD && lane == 0) {
+      sm.prefix[0] = 0;
+      sm.prefix[1] = pop;
+    }
+  }
   if (threadIdx.x == 32) {
     for (int i = 0; i < LSTAGES; ++i) {
       mbar_init(&sm.full[i], 1);
@@ -218,17 +312,9 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
     sm.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // The kernel before this one in a step is the tail (this step's
-  // regrowth, the mutation of the last step's births); the one before that
-  // (the slot phases) has completed by the time this kernel starts, since
-  // every tail CTA waits for it before it lets this kernel launch.  So the
-  // populations, alive lists and ages, and the weights of every agent not
-  // born in the last step, are read before waiting for the tail (through
-  // L2, ld.cg); the resource plane and the newborns' weights only after.
-  pdl_release();
-
-  // agents per world (= alive-list length at the start of the step)
-  if (warp == 0) {
+  // agents per world (= alive-list length at the start of the step), for
+  // batches of several worlds
+  if (warp == 0 && b.n > 1) {
     const int per = (b.n + 31) / 32;
     int local = 0;
     for (int i = 0; i < per; ++i) {
@@ -254,36 +340,31 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
   __syncthreads();
 
   const long long A = sm.prefix[b.n];
-  const int a_begin = (int)(A * blockIdx.x / gridDim.x);
-  const int a_end = (int)(A * (blockIdx.x + 1) / gridDim.x);
-  const int n_agents = a_end - a_begin;
+  const int n_agents = A > blockIdx.x ? (int)((A - blockIdx.x + G - 1) / G) : 0;
   int *status = &world_ptr(b, 0)->ctr->status;
 
   if (warp == W_PROD) {
     // ------------------------------------------------ producer -------------
-    int my_slot = 0, my_new = 0;
-    const float *my_w = nullptr;
+    // Slots of 32 agents at a time, one lane per agent (the first 32 were
+    // requested at the start with one world); lane 0 issues the copies.
     int issued = 0;
-    bool waited = false;
-    for (int n = 0; n < n_agents; ++n) {
+    bool waited = false, abort = false;
+    AgentRef mine = pre;
+    for (int n = 0; n < n_agents && !abort; ++n) {
       if ((n & 31) == 0) {
-        const int a = a_begin + n + lane;
-        if (a < a_end) {
-          const int w = world_of(sm.prefix, b.n, a);
-          const WorldDev *wd = world_ptr(b, w);
-          my_slot = checked_index(*wd, __ldcg(&wd->alive_list[a - sm.prefix[w]]), wd->C);
-          my_new = __ldcg(&wd->age[my_slot]) == 0;  // born in the last step (or never stepped)
-          my_w = wd->weights;
-        }
+        const long long a = blockIdx.x + (long long)(n + lane) * G;
+        if (n > 0 || b.n > 1) mine = agent_ref(sm.prefix, b, a, A);
+        mine = agent_valid(b, mine, a, A);
       }
-      const int slot = __shfl_sync(FULL, my_slot, n & 31);
-      const float *wts = reinterpret_cast<const float *>(
-          __shfl_sync(FULL, reinterpret_cast<unsigned long long>(my_w), n & 31));
-      if (!waited && __shfl_sync(FULL, my_new, n & 31)) {
-        pdl_wait();   // its weights are written by the tail kernel
+      const int slot = __shfl_sync(FULL, mine.slot, n & 31);
+      const int fresh = __shfl_sync(FULL, mine.fresh, n & 31);
+      const int world = __shfl_sync(FULL, mine.world, n & 31);
+      if (!waited && fresh) {
+        pdl_wait();   // a newborn's weights are written by the tail kernel
         waited = true;
       }
       if (lane == 0) {
+        const float *wts = world_ptr(b, world)->weights + (size_t)slot * WSTRIDE;
         for (int q = 0; q < NBLK; ++q) {
           const int u = NBLK * n + q, st = u % LSTAGES, k = u / LSTAGES;
           if (k > 0 && !mbar_wait(&sm.empty[st], (k - 1) & 1)) {
@@ -293,48 +374,56 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
           }
           const uint32_t bytes = (q == NBLK - 1) ? STAGE_FLOATS * 4 : BLK_BYTES;
           mbar_expect_tx(&sm.full[st], bytes);
-          bulk_copy_g2s(sm.stage[st], wts + (size_t)slot * WSTRIDE + q * BLK_FLOATS, bytes,
-                        &sm.full[st]);
+          bulk_copy_g2s(sm.stage[st], wts + q * BLK_FLOATS, bytes, &sm.full[st]);
           issued = u + 1;
         }
       }
       __syncwarp();
-      if (sm.abort_flag) break;
+      abort = sm.abort_flag != 0;
     }
     if (lane == 0) sm.issued = issued;
   } else if (warp >= NCOMP) {
     // ------------------------------------------------ gather ---------------
-    pdl_wait();   // the resource plane of this step is the tail kernel's
+    // Gather warp gw takes the CTA's agents gw, gw + NGATH, ...: their slots,
+    // then positions, energies and forced actions, 32 agents at a time (one
+    // lane per agent); then per agent the window's loads (one round trip),
+    // issued before the warp waits for its ring entry.
     const int gw = warp - NCOMP;
-    int my_slot = 0, my_y = 0, my_x = 0, my_f = -1;
-    float my_e = 0.f;
-    uint32_t my_t = 0;
-    const WorldDev *my_wd = nullptr;
+    bool waited = false;
+    AgentRef ref = pre;
+    AgentDesc mine{};
     for (int m = 0;; ++m) {
       const int n = gw + NGATH * m;
       if (n >= n_agents) break;
       if ((m & 31) == 0) {
-        const int a = a_begin + gw + NGATH * (m + lane);
-        if (a < a_end) {
-          const int w = world_of(sm.prefix, b.n, a);
-          my_wd = world_ptr(b, w);
-          my_slot = checked_index(*my_wd, my_wd->alive_list[a - sm.prefix[w]], my_wd->C);
-          my_y = my_wd->y[my_slot];
-          my_x = my_wd->x[my_slot];
-          my_e = my_wd->energy[my_slot];
-          my_t = (uint32_t)my_wd->ctr->t;
-          my_f = my_wd->ctr->use_forced ? my_wd->forced[my_slot] : -1;
-        }
+        const long long a = blockIdx.x + (long long)(gw + NGATH * (m + lane)) * G;
+        if (m > 0 || b.n > 1) ref = agent_ref(sm.prefix, b, a, A);
+        ref = agent_valid(b, ref, a, A);
+        const WorldDev &wd = *world_ptr(b, ref.world);
+        mine.slot = ref.slot;
+        mine.world = ref.world;
+        mine.y = __ldcg(&wd.y[ref.slot]);
+        mine.x = __ldcg(&wd.x[ref.slot]);
+        mine.energy = __ldcg(&wd.energy[ref.slot]);
+        const int forced = __ldcg(&wd.forced[ref.slot]);
+        mine.forced = __ldcg(&wd.ctr->use_forced) ? forced : -1;
+        mine.t = (uint32_t)__ldcg(&wd.ctr->t);
       }
       const int src = m & 31;
-      const int slot = __shfl_sync(FULL, my_slot, src);
-      const int y = __shfl_sync(FULL, my_y, src);
-      const int x = __shfl_sync(FULL, my_x, src);
-      const float e = __shfl_sync(FULL, my_e, src);
-      const uint32_t t = __shfl_sync(FULL, my_t, src);
-      const int fa = __shfl_sync(FULL, my_f, src);
-      const WorldDev *wd = reinterpret_cast<const WorldDev *>(
-          __shfl_sync(FULL, reinterpret_cast<unsigned long long>(my_wd), src));
+      AgentDesc d;
+      d.slot = __shfl_sync(FULL, mine.slot, src);
+      d.world = __shfl_sync(FULL, mine.world, src);
+      d.y = __shfl_sync(FULL, mine.y, src);
+      d.x = __shfl_sync(FULL, mine.x, src);
+      d.energy = __shfl_sync(FULL, mine.energy, src);
+      d.forced = __shfl_sync(FULL, mine.forced, src);
+      d.t = __shfl_sync(FULL, mine.t, src);
+      if (!waited) {
+        pdl_wait();   // the resource plane of this step is the tail kernel's
+        waited = true;
+      }
+      const WorldDev &wd = *world_ptr(b, d.world);
+      const GatherRegs g = gather_load(wd, d, lane);
       const int ei = n % VRING, k = n / VRING;
       bool ok = true;
       if (lane == 0 && k > 0) ok = mbar_wait(&sm.vempty[ei], (k - 1) & 1);
@@ -343,7 +432,7 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
         sm.abort_flag = 1;
         break;
       }
-      gather_input(*wd, slot, y, x, e, t, fa, sm.ring[ei], sm.masks[gw], lane);
+      gather_store(wd, d, g, sm.ring[ei], sm.masks[gw], lane);
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.vfull[ei]);
       if (sm.abort_flag) break;
@@ -356,12 +445,17 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
       if (sm.abort_flag) break;
       const int ei = n % VRING, kv = n / VRING;
       const int u = NBLK * n + q, st = u % LSTAGES, ks = u / LSTAGES;
-      if (!mbar_wait(&sm.vfull[ei], kv & 1) || !mbar_wait(&sm.full[st], ks & 1)) {
+      if (!mbar_wait(&sm.vfull[ei], kv & 1)) {
         if (lane == 0) atomicOr(status, ST_TIMEOUT);
         sm.abort_flag = 1;
         break;
       }
       VEntry &E = sm.ring[ei];
+      if (!mbar_wait(&sm.full[st], ks & 1)) {
+        if (lane == 0) atomicOr(status, ST_TIMEOUT);
+        sm.abort_flag = 1;
+        break;
+      }
       const float *stg = sm.stage[st];
       // gate row `lane` of block q: z = W_row . [obs; h] + b_row
       const float4 *W4 = reinterpret_cast<const float4 *>(stg + lane * NIN);
@@ -441,8 +535,12 @@ __global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ Ba
   }
 
   // Drain: wait (bounded) for every copy this CTA issued, so that no bulk
-  // copy into shared memory is still in flight when the CTA exits.
+  // copy into shared memory is still in flight when the CTA exits.  A CTA
+  // that had no agent has not waited for the tail kernel yet: it does so
+  // here, so that this kernel never completes before the tail (the next
+  // kernel waits on this one).
   __syncthreads();
+  pdl_wait();
   if (threadIdx.x == 0) {
     const int issued = sm.issued;
     for (int st = 0; st < LSTAGES && st < issued; ++st) {

@@ -40,7 +40,8 @@ struct __align__(16) PcSmem {
   float z[4 * PC_HID];                   // LSTM gate pre-activations
   float d[8];                            // dense 1 after tanh
   int prefix[1025];                      // agents before world w of the batch
-  int first_slot;                        // one world: slot of this CTA's first agent
+  int first_slot, first_new;              // one world: this CTA's first agent and its
+                                         // newborn flag
 };
 
 __device__ inline void cp_async16(void *smem, const void *gmem) {
@@ -111,9 +112,11 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
       const WorldDev &w0 = *world_ptr(b, 0);
       const int pop = (int)__ldcg(&w0.ctr->pop);
       const int first = (int)blockIdx.x < w0.C ? __ldcg(&w0.alive_list[blockIdx.x]) : 0;
+      const int first_new = (int)blockIdx.x < w0.C ? __ldcg(&w0.alive_new[blockIdx.x]) : 1;
       S.prefix[0] = 0;
       S.prefix[1] = pop;
       S.first_slot = first;
+      S.first_new = first_new;
     }
   } else if (warp == 0) {
     const int per = (b.n + 31) / 32;
@@ -144,15 +147,14 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
   for (int a = blockIdx.x; a < A; a += gridDim.x) {
     const int wi = world_of(S.prefix, b.n, a);
     const WorldDev &wd = *world_ptr(b, wi);
+    const bool first = b.n == 1 && a == (int)blockIdx.x;
     const int s = checked_index(
-        wd,
-        (b.n == 1 && a == (int)blockIdx.x) ? S.first_slot
-                                           : __ldcg(&wd.alive_list[a - S.prefix[wi]]),
-        wd.C);
+        wd, first ? S.first_slot : __ldcg(&wd.alive_list[a - S.prefix[wi]]), wd.C);
+    const int fresh = first ? S.first_new : __ldcg(&wd.alive_new[a - S.prefix[wi]]);
     const uint32_t t = (uint32_t)__ldcg(&wd.ctr->t);
     const int y = __ldcg(&wd.y[s]), x = __ldcg(&wd.x[s]);
     // a newborn's parameters are written by the tail kernel
-    if (__ldcg(&wd.age[s]) == 0) pdl_wait();
+    if (fresh) pdl_wait();
 
     // parameters -> shared memory, asynchronously
     const float4 *src = reinterpret_cast<const float4 *>(wd.weights + (size_t)s * PC_WSTRIDE);
@@ -312,6 +314,10 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
     }
     __syncthreads();   // the shared buffers are reused by the next agent
   }
+  // a CTA without agents has not waited for the tail kernel: it does so
+  // here, so that this kernel never completes before the tail (the next
+  // kernel waits on this one)
+  pdl_wait();
 }
 
 void preload_paper() {

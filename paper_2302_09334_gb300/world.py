@@ -34,6 +34,16 @@ def _ptr(a):
     return ctypes.c_void_p(a.ctypes.data) if a is not None else None
 
 
+def _host_weights(count: int, nparam: int) -> np.ndarray:
+    """Host array for weight rows: page-locked (a numpy view of a pinned
+    torch tensor, which the array keeps alive) when large, so that the
+    library's permutation kernel writes it directly."""
+    if count * nparam * 4 < (1 << 20):
+        return np.zeros((count, nparam), np.float32)
+    import torch
+    return torch.empty((count, nparam), dtype=torch.float32, pin_memory=True).numpy()
+
+
 def analysis_record(a) -> dict:
     """EcoAnalysis as int64 values -> dict (move_bins: int64 array of 17)."""
     a = np.asarray(a, np.int64)
@@ -44,18 +54,27 @@ def analysis_record(a) -> dict:
 
 
 def greediness(seen_windows, meal_windows):
-    """G = C_r / T_r per agent (App. C); NaN where T_r = 0."""
-    T = np.asarray(seen_windows, np.float64)
-    C = np.asarray(meal_windows, np.float64)
-    with np.errstate(invalid="ignore", divide="ignore"):
-        return np.where(T > 0, C / np.maximum(T, 1), np.nan)
+    """G = C_r / T_r per agent (App. C, eco_greediness); NaN where T_r = 0."""
+    T = np.ascontiguousarray(seen_windows, np.int32)
+    C = np.ascontiguousarray(meal_windows, np.int32)
+    assert T.shape == C.shape
+    out = np.empty(T.shape, np.float64)
+    check(lib().eco_greediness(_ptr(T), _ptr(C), T.size, _ptr(out)), "eco_greediness")
+    return out
 
 
 def life_expectancy(records) -> float | None:
     """Mean age at death over consecutive analysis windows (App. C: the
-    paper pools 500 steps); None when nobody died."""
-    deaths = sum(r["deaths"] for r in records)
-    return sum(r["death_age_sum"] for r in records) / deaths if deaths else None
+    paper pools 500 steps; eco_life_expectancy); None when nobody died."""
+    rec = np.zeros((len(records), _lib.NANALYSIS), np.int64)
+    n = len(_lib.ANALYSIS_KEYS)
+    for i, r in enumerate(records):
+        rec[i, :n] = [r[k] for k in _lib.ANALYSIS_KEYS]
+        rec[i, n:] = r["move_bins"]
+    out = ctypes.c_double()
+    check(lib().eco_life_expectancy(_ptr(rec) if len(records) else None, len(records),
+                                    ctypes.byref(out)), "eco_life_expectancy")
+    return None if np.isnan(out.value) else out.value
 
 
 class _Configurable:
@@ -147,7 +166,7 @@ class World(_Configurable):
             setattr(st, f + "_host", out[f].ctypes.data)
         if weights is not None:
             first, count = weights
-            out["weights"] = np.zeros((count, self.nparam), np.float32)
+            out["weights"] = _host_weights(count, self.nparam)
             st.weights_host = out["weights"].ctypes.data
             st.weights_first, st.weights_count = int(first), int(count)
         check(lib().eco_world_read_state(self._h, ctypes.byref(st)), "eco_world_read_state")

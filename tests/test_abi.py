@@ -117,3 +117,20 @@ def test_new_entry_points_validate_arguments_without_gpu(L):
     paper = _lib.to_c_params(P.paper_natural())
     assert L.eco_world_bytes(ctypes.byref(lstm)) > 5 * L.eco_world_bytes(ctypes.byref(paper))
     assert p.value is None
+
+
+def test_greediness_and_life_expectancy_host_functions():
+    """The App. C ratios computed by the library's host functions (no GPU):
+    G = C_r / T_r with NaN where T_r = 0; life expectancy pooled over
+    analysis records, None when nobody died."""
+    import numpy as np
+    from paper_2302_09334_gb300.world import greediness, life_expectancy
+    g = greediness([0, 2, 4, 5], [0, 1, 4, 0])
+    assert np.isnan(g[0]) and g[1] == 0.5 and g[2] == 1.0 and g[3] == 0.0
+    rec = lambda d, s: {"t": 0, "window": 50, "population": 0, "resources": 0, "deaths": d,
+                        "death_age_sum": s, "movers": 0, "move_bins": np.zeros(17, np.int64)}
+    assert life_expectancy([rec(2, 100), rec(0, 0), rec(3, 50)]) == 30.0
+    assert life_expectancy([rec(0, 0)]) is None and life_expectancy([]) is None
+    from paper_2302_09334_gb300._lib import ECO_EINVAL, lib
+    assert lib().eco_greediness(None, None, -1, None) == ECO_EINVAL
+    assert lib().eco_life_expectancy(None, 1, None) == ECO_EINVAL
