@@ -550,8 +550,10 @@ struct OrWorld {
   int32_t *lab_t, *lab_c;
   float *energy, *weights;
   double *h, *c, *logits;
-  /* test support: error magnitudes of h, c and the logits (or_lstm_mag) */
+  /* test support: error magnitudes of h, c and the logits (or_lstm_mag),
+   * computed while track_mag is set (the default) */
   double *mag_h, *mag_c, *mag_l;
+  int track_mag;
   uint32_t *thr;
   int64_t counters[OR_NCOUNTERS];
   /* analysis metrics, App. C: an identity for every agent (-1: empty slot),
@@ -621,6 +623,8 @@ void or_world_destroy(OrWorld *w) {
   free(w->order);
   free(w);
 }
+
+void or_world_track_magnitudes(OrWorld *w, int on) { w->track_mag = on ? 1 : 0; }
 
 int or_world_set_order(OrWorld *w, const int32_t *perm) {
   const int C = w->p.capacity;
@@ -762,6 +766,7 @@ int or_world_create(const OrParams *p, uint64_t seed, OrWorld **out) {
   if (!w) return -2;
   w->p = *p;
   w->seed = seed;
+  w->track_mag = 1;
   const size_t HW = (size_t)p->H * (size_t)p->W, C = (size_t)p->capacity;
   const size_t C1 = C ? C : 1;
   w->res = calloc(HW, 1); w->wall = calloc(HW, 1); w->res_tmp = calloc(HW, 1);
@@ -898,7 +903,8 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
       or_pc_observe(p, w->res, w->wall, w->slot_map, w->y[s], w->x[s], obs);
       for (int k = 0; k < OR_PC_VIEW * OR_PC_VIEW; ++k)
         if (obs[3 * k] != 0.0) w->lab_flags[s] |= 1;   /* a resource in view */
-      or_pc_mag(w->weights + (size_t)s * OR_NPARAM, obs, w->prev_act[s], ate_last,
+      if (w->track_mag)
+        or_pc_mag(w->weights + (size_t)s * OR_NPARAM, obs, w->prev_act[s], ate_last,
                 w->h + (size_t)s * OR_HID, w->c + (size_t)s * OR_HID,
                 w->mag_h + (size_t)s * OR_HID, w->mag_c + (size_t)s * OR_HID,
                 w->mag_h + (size_t)s * OR_HID, w->mag_c + (size_t)s * OR_HID,
@@ -915,7 +921,8 @@ int or_world_step(OrWorld *w, const int32_t *forced) {
                obs);
     for (int k = 0; k < OR_VIEW * OR_VIEW; ++k)
       if (obs[k] != 0.0) w->lab_flags[s] |= 1;     /* a resource in view */
-    or_lstm_mag(w->weights + (size_t)s * OR_NPARAM, obs, w->h + (size_t)s * OR_HID,
+    if (w->track_mag)
+      or_lstm_mag(w->weights + (size_t)s * OR_NPARAM, obs, w->h + (size_t)s * OR_HID,
                 w->c + (size_t)s * OR_HID, w->mag_h + (size_t)s * OR_HID,
                 w->mag_c + (size_t)s * OR_HID, w->mag_h + (size_t)s * OR_HID,
                 w->mag_c + (size_t)s * OR_HID, w->mag_l + (size_t)s * OR_NACT);

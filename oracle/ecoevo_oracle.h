@@ -244,6 +244,9 @@ void or_lstm_mag(const float *w, const double *obs, const double *h, const doubl
 void or_pc_mag(const float *w, const double *obs, int prev_action, int ate, const double *h,
                const double *c, const double *eh, const double *ec, double *eh_out,
                double *ec_out, double *el_out);
+/* Whether or_world_step keeps the magnitudes (on at create).  Off, they
+ * keep their last values and nothing else of a step changes. */
+void or_world_track_magnitudes(OrWorld *w, int on);
 
 /* Initial walls, resources and agent cells (cells[s] = y*W + x of slot s,
  * s < n_agents0) of a world created from `seed`; the first part of

@@ -129,6 +129,7 @@ def lib():
         L.or_pc_sample.argtypes = [ctypes.c_void_p, ctypes.c_double]
         L.or_pc_sample.restype = ctypes.c_int
         L.or_lstm_mag.argtypes = [ctypes.c_void_p] * 9
+        L.or_world_track_magnitudes.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.or_pc_mag.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int] + \
             [ctypes.c_void_p] * 7
         _lib = L
@@ -314,7 +315,7 @@ def analysis_record(a) -> dict:
 class OracleWorld:
     """One oracle world; the fields are numpy views into the C arrays."""
 
-    def __init__(self, params, seed: int):
+    def __init__(self, params, seed: int, magnitudes: bool = True):
         self.p = make_params(params)
         self.seed = int(seed)
         h = ctypes.c_void_p()
@@ -322,6 +323,8 @@ class OracleWorld:
         if rc != 0:
             raise ValueError(f"or_world_create failed ({rc})")
         self._h = h
+        if not magnitudes:   # test support only; the step itself is the same
+            lib().or_world_track_magnitudes(h, 0)
         H, W, C = self.p.H, self.p.W, max(self.p.capacity, 1)
         f = self._field
         self.res = f(F_RES, np.uint8, (H, W))

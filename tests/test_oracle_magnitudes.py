@@ -328,3 +328,20 @@ def test_world_keeps_magnitudes_per_slot():
     assert ow.counters[orc.C_BIRTHS] > 0
     ow.sync()
     assert not ow.mag_h.any() and not ow.mag_c.any() and not ow.mag_logits.any()
+
+
+def test_magnitude_tracking_leaves_the_step_unchanged():
+    """The magnitudes are test support: a world stepped without them has
+    exactly the same state."""
+    from paper_2302_09334_gb300.params import small_20x40
+    p = small_20x40().replace(t_repr=5)
+    a = orc.OracleWorld(p.asdict(), 5)
+    b = orc.OracleWorld(p.asdict(), 5, magnitudes=False)
+    for _ in range(30):
+        a.step()
+        b.step()
+    for f in ("res", "slot_map", "alive", "y", "x", "energy", "h", "c", "logits", "weights",
+              "counters", "action"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f), err_msg=f)
+    assert a.counters[orc.C_BIRTHS] > 0
+    assert not b.mag_h.any() and a.mag_h[a.alive.astype(bool)].any()
