@@ -380,11 +380,12 @@ int eco_world_get_config(const EcoWorld *world, int *fused, int *spawn_ctas_per_
 int eco_world_autotune(EcoWorld *world, int trial_steps, EcoTuneResult *out);
 
 /* Per-kernel timing with CUDA events on the world's stream.  While enabled,
- * each step (up to max_steps after each read) runs as a one-step CUDA graph
- * with an event-record node before and after every kernel; the elapsed
- * times of a step are added to their kernels when the next profiled step is
- * launched (the events are reused, so that launch first waits for the
- * previous one) or when they are read.  eco_world_profile_read waits for the
+ * each step (up to max_steps after each read) launches its kernels on the
+ * stream with an event recorded before and after every kernel (no graph, no
+ * programmatic overlap between the kernels); the elapsed times of a step are
+ * added to their kernels when the next profiled step is launched (the
+ * events are reused, so that launch first waits for the previous one) or
+ * when they are read.  eco_world_profile_read waits for the
  * stream and returns the sums since enabling:
  * ms[k], launches[k] for k < ECO_NKERNELS (names: eco_kernel_name; a kernel
  * the world's step does not launch keeps 0 launches).  A step runs

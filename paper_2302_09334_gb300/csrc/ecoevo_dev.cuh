@@ -119,7 +119,9 @@ struct Counters {            // mutable, updated by the kernels
   unsigned births_t;         // step index the births belong to
   int use_forced;            // moves read `forced` instead of `action`
   int status;                // ST_* bits
-  int pad[3];
+  int cand_step;             // CTAs of the fused slot phases with a reproduction
+                             // candidate this step (reset at the step's end)
+  int pad[2];
   // analysis window (App. C): the step it started at, and the deaths and
   // summed ages at death since then
   long long snap_t, an_deaths;
@@ -198,23 +200,65 @@ __host__ __device__ inline U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
 }
 
 #ifdef __CUDACC__
-// Box-Muller pair from two words, in float.  ln(u1) is taken on the side of
-// 1/2 where it is well conditioned (log of u1, or log1p of -(1 - u1) built
-// from the complement word), and the angle is reduced by quadrant from the
-// top two bits of x2 so that sincospi sees an argument below 1/2.
-__device__ inline void box_muller_f(uint32_t x1, uint32_t x2, float &z0,
-                                    float &z1) {
-  const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
-  float ln_u1;
-  if (x1 < 0x80000000u)
-    ln_u1 = logf(((float)x1 + 0.5f) * two_m32);
-  else
-    ln_u1 = log1pf(-(((float)(~x1) + 0.5f) * two_m32));
-  float r = sqrtf(-2.0f * ln_u1);
-  uint32_t quad = x2 >> 30;
-  float f = ((float)(x2 & 0x3FFFFFFFu) + 0.5f) * 9.313225746154785e-10f;  // 2^-30
-  float s, c;
-  sincospif(0.5f * f, &s, &c);  // angle = pi/2 * (quad + f)
+// ln(u), u = (x1 + 1/2) 2^-32, in float with no branch.  u = 2^e (1 + f),
+// f in [sqrt(1/2) - 1, sqrt(2) - 1), taken from the integer word: from u
+// itself when x1 < 2^31 (u < 1/2); when u >= 1/2 from 1 - u = (~x1 + 1/2)
+// 2^-32, which a float holds exactly, so that ln of a u close to 1 keeps its
+// relative accuracy (e = 0, f = u - 1 = -(1 - u), or e = -1, f = 2u - 1).
+// Then ln(1 + f) = 2 atanh(s) with s = f / (2 + f), |s| < 0.1716, by the
+// Taylor series of atanh up to s^9 (the next term is below 2e-10 of the
+// sum), and e ln 2 with ln 2 split in two (Cody and Waite) so that e ln2_hi
+// is exact.
+__device__ inline float ln_unit_word(uint32_t x1) {
+  const bool upper = x1 >= 0x80000000u;
+  const float v = ((float)(upper ? ~x1 : x1) + 0.5f) * 2.3283064365386963e-10f;  // 2^-32
+  // u = v < 1/2: exponent and mantissa of v
+  const uint32_t bits = __float_as_uint(v);
+  int e_lo = (int)((bits >> 23) & 0xFFu) - 127;
+  float m = __uint_as_float((bits & 0x7FFFFFu) | 0x3F800000u);   // [1, 2)
+  const bool big = m >= 1.41421356f;
+  m = big ? 0.5f * m : m;
+  e_lo += big ? 1 : 0;
+  const float f_lo = m - 1.0f;                                     // exact
+  // u = 1 - v >= 1/2
+  const bool near_one = v <= 0.29289322f;                          // 1 - sqrt(1/2)
+  const float f_up = near_one ? -v : 1.0f - 2.0f * v;              // exact
+  const int e_up = near_one ? 0 : -1;
+  const float f = upper ? f_up : f_lo;
+  const float e = (float)(upper ? e_up : e_lo);
+  const float s = f / (2.0f + f);
+  const float s2 = s * s;
+  float q = fmaf(s2, 1.0f / 9.0f, 1.0f / 7.0f);
+  q = fmaf(s2, q, 1.0f / 5.0f);
+  q = fmaf(s2, q, 1.0f / 3.0f);
+  const float two_s = 2.0f * s;
+  const float l = fmaf(two_s * s2, q, two_s);                      // ln(1 + f)
+  return fmaf(e, 0.693145751953125f, fmaf(e, 1.4286067653e-06f, l));
+}
+
+// Box-Muller pair from two words, in float, with no branch: r = sqrt(-2 ln
+// u1); the angle (pi/2)(quad + g), quad = the top two bits of x2 and g =
+// (low 30 bits + 1/2) 2^-30, is reduced to a in (0, pi/4): a = (pi/2) g when
+// g < 1/2, else the complement (pi/2)(1 - g) with 1 - g taken exactly from
+// the complemented bits (and cos and sin swapped); sin a and cos a by their
+// Taylor series up to a^9 and a^10 (next terms below 2e-9).
+__device__ inline void box_muller_f(uint32_t x1, uint32_t x2, float &z0, float &z1) {
+  const float r = sqrtf(-2.0f * ln_unit_word(x1));
+  const uint32_t quad = x2 >> 30;
+  const bool upper = (x2 >> 29) & 1u;
+  const uint32_t y = (upper ? ~x2 : x2) & 0x1FFFFFFFu;
+  const float a = ((float)y + 0.5f) * (1.5707963705062866f * 9.313225746154785e-10f);
+  const float a2 = a * a;
+  float ps = fmaf(a2, 1.0f / 362880.0f, -1.0f / 5040.0f);
+  ps = fmaf(a2, ps, 1.0f / 120.0f);
+  ps = fmaf(a2, ps, -1.0f / 6.0f);
+  const float sa = fmaf(a * a2, ps, a);
+  float pc = fmaf(a2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+  pc = fmaf(a2, pc, -1.0f / 720.0f);
+  pc = fmaf(a2, pc, 1.0f / 24.0f);
+  pc = fmaf(a2, pc, -0.5f);
+  const float ca = fmaf(a2, pc, 1.0f);
+  const float c = upper ? sa : ca, s = upper ? ca : sa;   // cos, sin of (pi/2) g
   float cs, sn;
   switch (quad) {
     case 0: cs = c; sn = s; break;
@@ -267,6 +311,8 @@ struct BatchDev {
   int n_sms;
   int fused;                 // slot phases in one cluster kernel (capacity <= FUSED_MAX_C)
   int spawn_ctas;            // CTAs of the tail kernel that mutate births
+  int tail_early;            // the tail kernel lets the next kernel launch at its start
+                             // (its grid is at most 2 CTAs per SM), else at its end
   int controller, wstride;   // shared by every world of the batch
 };
 
@@ -341,6 +387,11 @@ void launch_rebuild(const WorldDev *wd_host, int n_sms, cudaStream_t s);
 // already (copied).
 void launch_weights_to_logical(const float *physical, float *logical, size_t lpitch, int n,
                                int controller, int n_sms, cudaStream_t s);
+// n packed logical rows in page-locked host memory (its device address,
+// 16-byte aligned) -> the physical rows; returns a cudaError_t value
+// (cudaErrorMisalignedAddress: not 16-byte aligned, nothing launched).
+int launch_weights_from_host(const float *host_dev, float *rows, int n, int controller,
+                             int n_sms, cudaStream_t s);
 // n rows of the weight array holding logical rows (copied there) -> physical
 // order, in place; returns a cudaError_t value.
 int launch_rows_to_physical_inplace(float *rows, int n, int controller, int n_sms,

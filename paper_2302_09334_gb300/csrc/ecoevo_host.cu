@@ -156,11 +156,12 @@ std::vector<uint32_t> threshold_table(const EcoParams *p) {
 typedef void (*Launcher)(const BatchDev &, cudaStream_t);
 struct StepKernel { int id; Launcher fn; };
 
-// Per-kernel timing of graph-launched steps: the one-step graph is captured
-// with an event-record node before and after every kernel.  A profiled
-// step launches the graph and returns; the times of a launch are added just
-// before the graph is launched again (its events are reused) or when they
-// are read.
+// Per-kernel timing: a profiled step launches its kernels on the stream
+// with an event recorded before and after every kernel (an earlier version
+// launched a one-step graph with event-record nodes, which added about 7 us
+// of node latency to every kernel's time).  A profiled step returns at
+// once; the times of a step are added just before the next profiled step
+// (its events are reused) or when they are read.
 struct Profile {
   bool on = false;
   int max_steps = 0, used = 0;
@@ -168,8 +169,7 @@ struct Profile {
   long long launches[ECO_NKERNELS] = {0};
   cudaEvent_t ev[2 * ECO_NKERNELS] = {nullptr};
   int n_ev = 0;
-  cudaGraphExec_t exec = nullptr;
-  const void *owner = nullptr;   // the batch the graph steps
+  const void *owner = nullptr;   // the batch whose kernels the events bracket
   const StepKernel *list = nullptr;
   int nk = 0;
   bool pending = false;      // a launch whose times are not yet added
@@ -271,14 +271,14 @@ int step_kernels(const BatchDev &bd, const StepKernel **list) {
 }
 
 // One step, kernel by kernel; with `ev`, a pair of events around every
-// kernel.
+// kernel (not while capturing a graph).
 void launch_step(const EcoBatch &b, cudaStream_t s, cudaEvent_t *ev) {
   const StepKernel *list;
   const int nk = step_kernels(b.bd, &list);
   for (int k = 0; k < nk; ++k) {
-    if (ev) cudaEventRecordWithFlags(ev[2 * k], s, cudaEventRecordExternal);
+    if (ev) cudaEventRecord(ev[2 * k], s);
     list[k].fn(b.bd, s);
-    if (ev) cudaEventRecordWithFlags(ev[2 * k + 1], s, cudaEventRecordExternal);
+    if (ev) cudaEventRecord(ev[2 * k + 1], s);
   }
 }
 
@@ -299,6 +299,12 @@ int capture(EcoBatch &b, int steps, cudaGraphExec_t *out) {
   if (e != cudaSuccess) return cuda_err(e);
   // upload now, so that the first launch does not carry it
   return cuda_err(cudaGraphUpload(*out, b.stream));
+}
+
+// The tail kernel's grid (regrowth tiles + mutation CTAs) leaves room on
+// every SM for a controller CTA when it is at most 2 CTAs per SM.
+int tail_early(const BatchDev &bd) {
+  return bd.total_tiles + bd.spawn_ctas <= 2 * bd.n_sms ? 1 : 0;
 }
 
 // Host side of a batch: device table of descriptors and work prefixes.
@@ -340,14 +346,15 @@ int batch_init(EcoBatch &b, EcoWorld *const *worlds, int n, void *table_dev) {
   b.bd.n_sms = worlds[0]->n_sms;
   b.bd.fused = maxc <= FUSED_MAX_C ? 1 : 0;
   b.bd.spawn_ctas = DEFAULT_SPAWN_PER_SM * b.bd.n_sms;
+  b.bd.tail_early = tail_early(b.bd);
   b.bd.controller = worlds[0]->hd.controller;
   b.bd.wstride = worlds[0]->hd.wstride;
   b.prof = &worlds[0]->prof;
   return ECO_OK;
 }
 
-// One-step graph with external event-record nodes around every kernel.
-int capture_profiled(EcoBatch &b, Profile &pr) {
+// Events for the kernels of the batch's step.
+int profile_setup(EcoBatch &b, Profile &pr) {
   const StepKernel *list;
   const int nk = step_kernels(b.bd, &list);
   for (int k = 0; k < 2 * nk; ++k) ECO_CU(cudaEventCreate(&pr.ev[k]));
@@ -355,23 +362,12 @@ int capture_profiled(EcoBatch &b, Profile &pr) {
   pr.owner = &b;
   pr.list = list;
   pr.nk = nk;
-  cudaGraph_t g = nullptr;
-  int rc = cuda_err(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
-  if (rc == ECO_OK) {
-    launch_step(b, b.stream, pr.ev);
-    const int rc_end = cuda_err(cudaStreamEndCapture(b.stream, &g));
-    if (rc == ECO_OK) rc = rc_end;
-  }
-  if (rc == ECO_OK) rc = cuda_err(cudaGraphInstantiate(&pr.exec, g, 0));
-  if (g) cudaGraphDestroy(g);
-  return rc;
+  return ECO_OK;
 }
 
 void profile_release(Profile &pr) {
   for (int k = 0; k < pr.n_ev; ++k) cudaEventDestroy(pr.ev[k]);
   pr.n_ev = 0;
-  if (pr.exec) cudaGraphExecDestroy(pr.exec);
-  pr.exec = nullptr;
   pr.owner = nullptr;
   pr.list = nullptr;
   pr.nk = 0;
@@ -396,7 +392,8 @@ int profile_collect(Profile &pr) {
 int profiled_step(EcoBatch &b, Profile &pr) {
   int rc = profile_collect(pr);
   if (rc) return rc;
-  ECO_CU(cudaGraphLaunch(pr.exec, b.stream));
+  launch_step(b, b.stream, pr.ev);
+  ECO_CU(cudaGetLastError());
   pr.pending = true;
   pr.used += 1;
   return ECO_OK;
@@ -422,13 +419,13 @@ int batch_step(EcoBatch &b, int64_t n) {
   if (n < 0) return ECO_EINVAL;
   Profile *prof = b.prof;
   if (prof && prof->on) {
-    if (prof->exec && prof->owner != &b) {  // profiled last as part of another batch
+    if (prof->owner && prof->owner != &b) {  // profiled last as part of another batch
       int rc = profile_collect(*prof);
       if (rc) return rc;
       profile_release(*prof);
     }
-    if (!prof->exec) {
-      int rc = capture_profiled(b, *prof);
+    if (!prof->owner) {
+      int rc = profile_setup(b, *prof);
       if (rc) return rc;
     }
     for (int64_t i = 0; i < n; ++i) {
@@ -466,13 +463,14 @@ int set_config(EcoBatch &b, int fused, int spawn_per_sm, int steps_per_graph) {
     return ECO_OK;
   ECO_CU(cudaStreamSynchronize(b.stream));
   destroy_graphs(b);
-  if (b.prof && b.prof->owner == &b) {  // its profiled graph holds the old launches
+  if (b.prof && b.prof->owner == &b) {  // its events bracket the old kernel list
     int rc = profile_collect(*b.prof);
     if (rc) return rc;
     profile_release(*b.prof);
   }
   b.bd.fused = fused;
   b.bd.spawn_ctas = spawn;
+  b.bd.tail_early = tail_early(b.bd);
   b.steps_per_graph = steps_per_graph;
   return ECO_OK;
 }
@@ -1103,6 +1101,7 @@ int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
     if (c.t < 0 || c.t > 0xFFFFFFFFll) return ECO_EINVAL;
   }
   c.deaths_step = 0;
+  c.cand_step = 0;
   c.n_births = 0;
   c.use_forced = 0;
   // host buffers below live until the final wait
@@ -1137,16 +1136,24 @@ int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
     io.h2d(d.logits, lg.data(), lg.size() * 4);
   }
   if (in->weights_host && in->weights_count > 0 && !io.rc) {
-    // one 2-D copy of the logical rows into their own device rows (a DMA
-    // transfer from page-locked memory, staged by the driver from pageable
-    // memory), then the permutation to the physical order in place
     const size_t ws = d.wstride, np = d.nparam;
     float *dst = d.weights + (size_t)in->weights_first * ws;
-    io.rc = cuda_err(cudaMemcpy2DAsync(dst, ws * 4, in->weights_host, np * 4, np * 4,
-                                       in->weights_count, cudaMemcpyHostToDevice, w->stream));
-    if (!io.rc)
-      io.rc = cuda_err((cudaError_t)launch_rows_to_physical_inplace(
-          dst, in->weights_count, d.controller, w->n_sms, w->stream));
+    // page-locked rows (16-byte aligned): read by a kernel through their
+    // device address, stored in physical order (faster over the host link
+    // than a copy engine); otherwise one 2-D copy of the logical rows into
+    // their own device rows (staged by the driver from pageable memory),
+    // then the permutation to the physical order in place
+    const float *dev = (const float *)pinned_device_view(in->weights_host);
+    if (dev && ((uintptr_t)dev & 15u) == 0) {
+      io.rc = cuda_err((cudaError_t)launch_weights_from_host(dev, dst, in->weights_count,
+                                                             d.controller, w->n_sms, w->stream));
+    } else {
+      io.rc = cuda_err(cudaMemcpy2DAsync(dst, ws * 4, in->weights_host, np * 4, np * 4,
+                                         in->weights_count, cudaMemcpyHostToDevice, w->stream));
+      if (!io.rc)
+        io.rc = cuda_err((cudaError_t)launch_rows_to_physical_inplace(
+            dst, in->weights_count, d.controller, w->n_sms, w->stream));
+    }
   }
   // greediness counters start over with a loaded state
   if (!io.rc) io.rc = cuda_err(cudaMemsetAsync(d.lab_seen, 0, C ? C : 1, w->stream));

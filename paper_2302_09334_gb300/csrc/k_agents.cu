@@ -187,6 +187,7 @@ __device__ inline void finish_step(const WorldDev &wd, int S, int F, int pop, ui
   c.deaths += c.deaths_step;
   c.an_deaths += c.deaths_step;
   c.deaths_step = 0;
+  c.cand_step = 0;
   c.n_births = births;
   c.births_t = t;
   c.agent_steps += c.pop;  // the agents alive at the start of this step
@@ -333,7 +334,7 @@ template <int NCTA, int THREADS>
 __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
   __shared__ int sh[3 * 32 + 3];
   __shared__ int pub[3], ex[6];
-  __shared__ int cta_deaths;
+  __shared__ int cta_deaths, cta_cand;
   __shared__ unsigned long long cta_age_sum;
   const WorldDev &wd = *world_ptr(b, blockIdx.x / NCTA);
   const int rank = NCTA == 1 ? 0 : (int)cg::this_cluster().block_rank();
@@ -345,6 +346,7 @@ __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
   const int ns = min(c1, s0 + per) - s0;
   if (threadIdx.x == 0) {
     cta_deaths = 0;
+    cta_cand = 0;
     cta_age_sum = 0ull;
   }
   // The slot state below was last written by the previous step's slot
@@ -433,6 +435,7 @@ __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
       if (!dead) {
         rep[k] = (e > wd.e_repr) ? rep[k] + 1 : 0;
         wd.repr_ctr[s] = rep[k];
+        if (rep[k] >= wd.t_repr) cta_cand = 1;   // will try to give birth
       }
     }
     wd.ate[s] = ate ? 1 : 0;  // an input of the paper's controller next step
@@ -450,7 +453,21 @@ __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
     atomicAdd(&wd.ctr->deaths_step, cta_deaths);
     atomicAdd(&wd.ctr->an_age_sum, cta_age_sum);
   }
+  if (threadIdx.x == 0 && cta_cand) atomicAdd(&wd.ctr->cand_step, 1);
   phase_sync<NCTA>();
+  // A quiet step -- no death and no reproduction candidate in the whole
+  // world (every CTA's counts are in after the barrier) -- leaves the alive
+  // list as it is (survivors in slot order, no child): the birth and
+  // compaction phases are skipped, last step's newborns are newborns no
+  // more.  The counters read here are reset by finish_step, which in a
+  // quiet step changes nothing another CTA can still read (both are 0).
+  if (__ldcg(&wd.ctr->deaths_step) == 0 && __ldcg(&wd.ctr->cand_step) == 0) {
+    const int pop = (int)__ldcg(&wd.ctr->pop);   // agents at the step's start
+    for (int i = rank * THREADS + (int)threadIdx.x; i < pop; i += NCTA * THREADS)
+      wd.alive_new[i] = 0;
+    if (rank == 0 && threadIdx.x == 0) finish_step(wd, 0, 0, pop, t);
+    return;
+  }
   // ---- birth claims: first free N, S, E, W cell; lowest parent slot wins
 #pragma unroll
   for (int k = 0; k < CL_SPT; ++k) {
@@ -769,15 +786,23 @@ static_assert(REGROW_THREADS == SPAWN_THREADS, "one block size for the tail kern
 __global__ void __launch_bounds__(SPAWN_THREADS, 4) k_tail(const __grid_constant__ BatchDev b) {
   __shared__ uint32_t tile[TILE_ROWS_MAX][TILE_COLS];
   __shared__ int pre[1025];
+  // The controller kernel after this one starts its reads early when this
+  // grid is small enough (b.tail_early) to leave room for it beside the
+  // tail's CTAs; a larger grid (many worlds' regrowth tiles) lets it launch
+  // only as its CTAs finish, since controller CTAs taking SMs early would
+  // halve the tail's occupancy while their gather warps wait for it anyway.
   if ((int)blockIdx.x < b.total_tiles) {
     // walls and thresholds are never written by a step: read before waiting
     const RegrowFixed f = regrow_fixed(b, blockIdx.x);
-    pdl_wait_and_release();
+    pdl_wait();
+    if (b.tail_early) pdl_release();
     regrow_run(f, tile);
   } else {
-    pdl_wait_and_release();
+    pdl_wait();
+    if (b.tail_early) pdl_release();
     spawn_births(b, pre, blockIdx.x - b.total_tiles, gridDim.x - b.total_tiles);
   }
+  if (!b.tail_early) pdl_release();
 }
 
 // Initial weights of slots [0, n0): w_init_std * N_j of (TAG_INIT_W, 0, slot).

@@ -170,6 +170,39 @@ __global__ void k_weights_to_logical(const float *physical, float *logical, size
   }
 }
 
+// Packed logical rows (n rows of nparam floats, back to back) in page-locked
+// host memory, read through its device address as one flat array: 16-byte
+// loads over the host link (the buffer is 16-byte aligned), the last 1..3
+// floats one by one; each float is stored at its physical place in the
+// device rows, and the holder of a row's last parameter zeroes the row's
+// padding.
+template <int CTRL>
+__global__ void k_weights_from_host(const float *src, size_t total, float *rows) {
+  constexpr int NP = CTRL == ECO_CTRL_PAPER ? PC_NPARAM : NPARAM;
+  constexpr int STRIDE = CTRL == ECO_CTRL_PAPER ? PC_WSTRIDE : WSTRIDE;
+  const size_t n_vec = (total + 3) / 4;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n_vec;
+       i += (size_t)gridDim.x * blockDim.x) {
+    float f[4];
+    if (4 * i + 4 <= total) {
+      const float4 v = reinterpret_cast<const float4 *>(src)[i];
+      f[0] = v.x; f[1] = v.y; f[2] = v.z; f[3] = v.w;
+    } else {
+      for (int c = 0; c < 4; ++c) f[c] = 4 * i + c < total ? src[4 * i + c] : 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const size_t g = 4 * i + c;
+      if (g >= total) break;
+      const int a = (int)(g / NP), j = (int)(g % NP);
+      float *r = rows + (size_t)a * STRIDE;
+      r[CTRL == ECO_CTRL_PAPER ? j : phys_of_logical(j)] = f[c];
+      if (j == NP - 1)
+        for (int q = NP; q < STRIDE; ++q) r[q] = 0.f;
+    }
+  }
+}
+
 // Rows already on the device in logical order (the first nparam floats of
 // each `stride`-float row, copied there by DMA) permuted to the physical
 // order in place: each CTA stages a whole row in shared memory.
@@ -204,6 +237,19 @@ int launch_rows_to_physical_inplace(float *rows, int n, int controller, int n_sm
   if (e != cudaSuccess) return (int)e;
   const int nparam = controller == ECO_CTRL_PAPER ? PC_NPARAM : NPARAM;
   k_rows_to_physical_inplace<<<2 * n_sms, 512, smem, s>>>(rows, n, controller, stride, nparam);
+  return (int)cudaGetLastError();
+}
+
+int launch_weights_from_host(const float *host_dev, float *rows, int n, int controller,
+                             int n_sms, cudaStream_t s) {
+  if (n <= 0) return 0;
+  if (((uintptr_t)host_dev & 15u) != 0) return (int)cudaErrorMisalignedAddress;
+  const size_t np = controller == ECO_CTRL_PAPER ? PC_NPARAM : NPARAM;
+  const size_t total = (size_t)n * np;
+  if (controller == ECO_CTRL_PAPER)
+    k_weights_from_host<ECO_CTRL_PAPER><<<8 * n_sms, 256, 0, s>>>(host_dev, total, rows);
+  else
+    k_weights_from_host<ECO_CTRL_LSTM32><<<8 * n_sms, 256, 0, s>>>(host_dev, total, rows);
   return (int)cudaGetLastError();
 }
 

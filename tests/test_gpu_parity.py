@@ -105,6 +105,40 @@ def test_paper_scale_world_forced(eco, oracle):
     run_forced(gw, ow, 60, "200x400", p.mut_std, compare_every=10)
 
 
+def test_load_state_pinned_equals_pageable(eco):
+    """A state loaded from page-locked host memory (weights read by the
+    device through its address) equals the same state loaded from pageable
+    memory (2-D copy and in-place permutation), for both controllers and a
+    weight count whose floats are not a multiple of four."""
+    import torch
+    for p in (EcoParams(H=30, W=60, capacity=300, n_agents0=120),
+              EcoParams(H=30, W=60, capacity=300, n_agents0=120, controller=1)):
+        src = eco.World(p, 3)
+        src.step(30)
+        n = 117                                    # 117 * 23333 and 117 * 2445 are odd
+        st = src.read_state(weights=(0, n))
+        pinned = {}
+        for k, v in st.items():
+            t = torch.empty(v.shape, dtype=torch.from_numpy(v[:0].copy()).dtype, pin_memory=True)
+            pinned[k] = t.numpy()
+            pinned[k][...] = v
+        a, b = eco.World(p, 9), eco.World(p, 9)
+        a.load_state(pinned)
+        b.load_state({k: np.array(v) for k, v in st.items()})
+        ra, rb = a.read_state(weights=(0, n)), b.read_state(weights=(0, n))
+        for k in ra:
+            np.testing.assert_array_equal(ra[k], rb[k], err_msg=k)
+        np.testing.assert_array_equal(ra["weights"], st["weights"])
+        a.step(10)
+        b.step(10)
+        ra, rb = a.read_state(weights=(0, p.capacity)), b.read_state(weights=(0, p.capacity))
+        live = ra["alive"].astype(bool)
+        np.testing.assert_array_equal(ra["weights"][live], rb["weights"][live])
+        np.testing.assert_array_equal(ra["h"], rb["h"])
+        for w in (src, a, b):
+            w.close()
+
+
 def test_free_run_is_deterministic(eco):
     p = small_20x40()
     a = eco.World(p, 3)

@@ -1,5 +1,5 @@
-"""Per-kernel profiling (graph-launched steps with event nodes) and graph
-stepping give the same states as kernel-by-kernel forced steps."""
+"""Per-kernel profiling (kernels launched on the stream with events around
+each) and graph stepping give the same states as plain steps."""
 import numpy as np
 import pytest
 
