@@ -35,10 +35,10 @@ sys.path.insert(0, ROOT)
 LSTM_BYTES_PER_AGENT = 93332 + 512 + 36
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one observation+LSTM launch per agent, from an
-# ncu capture of this kernel on the 200x400 world with 3,440 agents held
-# (327.55 MB, mean of two launches); traffic grows with the agents of a
+# ncu capture of this kernel on the 200x400 world with 1,000 agents held
+# (97.17 MB, mean of two launches); traffic grows with the agents of a
 # launch, so it is scaled by them.
-LSTM_TRAFFIC_PER_AGENT = 327.55e6 / 3440
+LSTM_TRAFFIC_PER_AGENT = 97.17e6 / 1000
 
 
 # the same for the paper's controller: 2,445 FP32 parameters, h and c of 4
@@ -118,7 +118,9 @@ def _oracle_worker(args):
     params_dict, seed, budget_s, warmup, max_steps = args
     sys.path.insert(0, ROOT)
     from oracle import pyoracle
-    ow = pyoracle.OracleWorld(params_dict, seed)
+    # the error magnitudes the oracle keeps for the parity tests are not part
+    # of the step: off for the timing
+    ow = pyoracle.OracleWorld(params_dict, seed, magnitudes=False)
     for _ in range(warmup):
         ow.step()
     agent_steps, steps = 0, 0
@@ -246,8 +248,9 @@ def bench_ours(args, params, rank, world_size, dist):
         del tuner
         cfg = {k: tuned[k] for k in ("fused", "spawn_ctas_per_sm", "steps_per_graph")}
     # the timed world steps by plain one-step CUDA graphs; its twin (same
-    # seed, hence the same states step by step) runs the profiled graphs
-    # whose event nodes give the per-kernel times
+    # seed, hence the same states step by step) launches each step's kernels
+    # on the stream with CUDA events around every kernel for the per-kernel
+    # times
     world = World(params, seed=rank, device=local)
     twin = World(params, seed=rank, device=local, stream=world.stream)
     world.set_config(**cfg)
@@ -435,9 +438,13 @@ def bench_batched(args, local):
     from paper_2302_09334_gb300.world import Batch, World
     specs = batched_64()
     stream = torch.cuda.Stream(local)
-    # tuner: a twin batch of the same worlds with seeds 1000+
+    # tuner: a twin batch of the same worlds with seeds 1000+, first stepped
+    # past the first births (step 50) so that its trials see the mutation
+    # load the timed steps have
     tw = [World(p, 1000 + s, device=local, stream=stream) for p, s in specs]
     tb = Batch(tw)
+    tb.step(args.batched_warmup + 60)
+    tb.sync()
     tuned = tb.autotune(trial_steps=4)
     tb.close()
     for w in tw:
@@ -460,7 +467,20 @@ def bench_batched(args, local):
     end.synchronize()
     total_ms = start.elapsed_time(end)
     agent_steps = sum(int(w.counters()[C_AGENT_STEPS]) for w in worlds) - as0
-    # then as many profiled steps for the per-kernel times
+    batch.close()
+    for w in worlds:
+        w.close()
+    del worlds, batch
+    torch.cuda.empty_cache()
+    # per-kernel times over the same steps: a twin batch (same worlds and
+    # seeds, hence the same states step by step) repeats warm-up and timed
+    # steps with its kernels bracketed by events
+    worlds = [World(p, s, device=local, stream=stream) for p, s in specs]
+    batch = Batch(worlds)
+    batch.set_config(fused=tuned["fused"], spawn_ctas_per_sm=tuned["spawn_ctas_per_sm"],
+                     steps_per_graph=tuned["steps_per_graph"])
+    batch.step(args.batched_warmup)
+    batch.sync()
     worlds[0].profile(True, max_steps=args.batched_steps)
     as1 = sum(int(w.counters()[C_AGENT_STEPS]) for w in worlds)
     batch.step(args.batched_steps)
@@ -468,6 +488,8 @@ def bench_batched(args, local):
     prof = worlds[0].profile_read()
     worlds[0].profile(False)
     prof_agent_steps = sum(int(w.counters()[C_AGENT_STEPS]) for w in worlds) - as1
+    if prof_agent_steps != agent_steps:
+        raise RuntimeError("the profiled twin batch diverged from the timed batch")
     lstm_ms, _ = prof["observe_lstm"]
     cells = sum(p.H * p.W for p, _ in specs)
     bytes_lstm = prof_agent_steps * LSTM_BYTES_PER_AGENT + \
@@ -486,6 +508,9 @@ def bench_batched(args, local):
                      "ms_per_step_initial": tuned["ms_per_step_initial"],
                      "ms_per_step_best": tuned["ms_per_step_best"]},
            "kernel_ms_per_step": {k: v[0] / v[1] for k, v in prof.items() if v[1]},
+           "kernel_sum_ms_per_step": sum(v[0] for v in prof.values()) / args.batched_steps,
+           "kernel_times": "twin batch over the same steps, kernels on the stream between "
+                           "CUDA events (no overlap between them)",
            "roofline": {"kernel": "observe_lstm", "bound": "hbm", "achieved": achieved,
                         "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak if achieved else None},
@@ -619,8 +644,9 @@ def bench_held(args, local):
     for name, p, flushed in cases:
         w = World(p, 0, device=local, stream=stream)
         twin = World(p, 0, device=local, stream=stream)
-        w.set_config(steps_per_graph=1)
-        twin.set_config(steps_per_graph=1)
+        # no births in a held population: one mutation CTA per SM
+        w.set_config(steps_per_graph=1, spawn_ctas_per_sm=1)
+        twin.set_config(steps_per_graph=1, spawn_ctas_per_sm=1)
         w.step(args.held_warmup)
         twin.step(args.held_warmup)
         n = int(w.counters()[1])

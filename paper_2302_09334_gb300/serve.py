@@ -22,7 +22,8 @@ Latency control: with target_chunk_s, a request is admitted only while the
 agents of the live worlds plus its own, stepped `chunk` times at the
 measured rate (agent-steps/s, a moving average over launches, from
 rate_prior until measured; fixed at rate_prior with learn_rate=False), fit
-in the target; the first request is always admitted.  The memory budget
+in 70 % of the target (the rest is left for the births of admitted worlds);
+the first request is always admitted.  The memory budget
 still applies.
 
 With `log` (a text file), every chunk appends one JSON record: its time,
@@ -151,11 +152,15 @@ class Server:
         req.outcome = f"rejected: {why}"
         self.rejected.append(req)
 
+    # share of the target left for the growth of admitted populations
+    # (births after admission; capacities are 4x the initial populations)
+    TARGET_HEADROOM = 0.7
+
     def _fits_target(self, req: Request) -> bool:
         if self.target is None or not self.live:
             return True
         agents = self.live_agents + int(req.params.n_agents0)
-        return agents * self.chunk / self.rate <= self.target
+        return agents * self.chunk / self.rate <= self.TARGET_HEADROOM * self.target
 
     def _admit_queue(self, queue: deque, now: float) -> None:
         """Admit from the head of the queue, in arrival order, while the
