@@ -183,6 +183,17 @@ def config_of(args, params):
             "parallelism": f"replicas{args.gpus}"}
 
 
+CONFIG_KEYS = ("fused", "spawn_ctas_per_sm", "steps_per_graph")
+SHAPE_KEYS = ("regrow_rows_per_cta", "lstm_ctas_per_sm")
+
+
+def configure(target, cfg: dict) -> None:
+    """Launch configuration and kernel shapes (a tuner record, or the
+    get_config() + get_shape() of a world) applied to a world or batch."""
+    target.set_config(**{k: cfg[k] for k in CONFIG_KEYS})
+    target.set_shape(**{k: cfg[k] for k in SHAPE_KEYS})
+
+
 def to_pinned(state: dict) -> dict:
     """The same arrays in page-locked host memory (numpy views of pinned
     torch tensors), so that host-to-device copies from them are DMA
@@ -239,22 +250,22 @@ def bench_ours(args, params, rank, world_size, dist):
     # so that the measured world starts from step 0
     if args.no_tune:
         probe = World(params, seed=1000 + rank, device=local)
-        cfg = probe.get_config()
+        cfg = {**probe.get_config(), **probe.get_shape()}
         probe.close()
     else:
         tuner = World(params, seed=1000 + rank, device=local)
         tuned = tuner.autotune(trial_steps=8)
         tuner.close()
         del tuner
-        cfg = {k: tuned[k] for k in ("fused", "spawn_ctas_per_sm", "steps_per_graph")}
+        cfg = {k: tuned[k] for k in CONFIG_KEYS + SHAPE_KEYS}
     # the timed world steps by plain one-step CUDA graphs; its twin (same
     # seed, hence the same states step by step) launches each step's kernels
     # on the stream with CUDA events around every kernel for the per-kernel
     # times
     world = World(params, seed=rank, device=local)
     twin = World(params, seed=rank, device=local, stream=world.stream)
-    world.set_config(**cfg)
-    twin.set_config(**cfg)
+    configure(world, cfg)
+    configure(twin, cfg)
     stream = world.stream
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     flush_read = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -328,10 +339,16 @@ def bench_ours(args, params, rank, world_size, dist):
     world.counter_log(counter_log)
     e_steps0 = torch.cuda.Event(enable_timing=True)
     e_steps1 = torch.cuda.Event(enable_timing=True)
-    # warm-up of the path (its first call loads kernels and touches the
-    # buffers), then the timed region without Python's cyclic collector
+    # warm-up of the path (its first calls load kernels, touch the buffers
+    # and capture the step graphs the timed calls replay), then the timed
+    # region without Python's cyclic collector
     world.load_state(e2e_state)
-    world.step(1)
+    done = 0
+    while done < args.steps:
+        n = min(50, args.steps - done)
+        world.step(n)
+        done += n
+    world.sync()
     gc.collect()
     gc.disable()
     torch.cuda.synchronize()
@@ -453,8 +470,7 @@ def bench_batched(args, local):
     torch.cuda.empty_cache()
     worlds = [World(p, s, device=local, stream=stream) for p, s in specs]
     batch = Batch(worlds)
-    batch.set_config(fused=tuned["fused"], spawn_ctas_per_sm=tuned["spawn_ctas_per_sm"],
-                     steps_per_graph=tuned["steps_per_graph"])
+    configure(batch, tuned)
     batch.step(args.batched_warmup)
     batch.sync()
     pops0 = [int(w.counters()[1]) for w in worlds]
@@ -477,8 +493,7 @@ def bench_batched(args, local):
     # steps with its kernels bracketed by events
     worlds = [World(p, s, device=local, stream=stream) for p, s in specs]
     batch = Batch(worlds)
-    batch.set_config(fused=tuned["fused"], spawn_ctas_per_sm=tuned["spawn_ctas_per_sm"],
-                     steps_per_graph=tuned["steps_per_graph"])
+    configure(batch, tuned)
     batch.step(args.batched_warmup)
     batch.sync()
     worlds[0].profile(True, max_steps=args.batched_steps)
@@ -502,8 +517,7 @@ def bench_batched(args, local):
            "cell_steps_per_s": cells * args.batched_steps / (total_ms / 1e3),
            "mean_population": agent_steps / args.batched_steps,
            "initial_population": sum(pops0),
-           "launch_config": {k: tuned[k] for k in ("fused", "spawn_ctas_per_sm",
-                                                   "steps_per_graph")},
+           "launch_config": {k: tuned[k] for k in CONFIG_KEYS + SHAPE_KEYS},
            "tuner": {"steps_taken": tuned["steps_taken"],
                      "ms_per_step_initial": tuned["ms_per_step_initial"],
                      "ms_per_step_best": tuned["ms_per_step_best"]},
@@ -539,9 +553,9 @@ def bench_paper_preset(args, local):
     tuner = World(p, 1000, device=local, stream=stream)
     tuned = tuner.autotune(trial_steps=16)
     tuner.close()
-    cfg = {k: tuned[k] for k in ("fused", "spawn_ctas_per_sm", "steps_per_graph")}
+    cfg = {k: tuned[k] for k in CONFIG_KEYS + SHAPE_KEYS}
     w = World(p, 0, device=local, stream=stream)
-    w.set_config(**cfg)
+    configure(w, cfg)
     w.step(args.paper_warmup)
     w.sync()
     c0 = w.counters()

@@ -349,23 +349,43 @@ int eco_batch_set_config(EcoBatch *batch, int fused, int spawn_ctas_per_sm,
 int eco_batch_get_config(const EcoBatch *batch, int *fused, int *spawn_ctas_per_sm,
                          int *steps_per_graph);
 
+/* Kernel shapes of a batch (or of a world stepped alone); like the launch
+ * configuration, no choice changes any result:
+ *   regrow_rows_per_cta  8-row x 128-cell regrowth tiles stacked in one CTA
+ *                        of the tail kernel: 1, 2, 4 or 8, or 0 to choose by
+ *                        size (the fewest that leave at most two regrowth
+ *                        CTAs per SM; the default).
+ *   lstm_ctas_per_sm     CTAs per SM of the controller kernel of the LSTM(32)
+ *                        controller: 1 (an 8-block weight ring, two agents in
+ *                        flight; the default) or 2 (a 4-block ring each).
+ * set_shape waits for the stream when a shape changes; get_shape reports
+ * the stacking in use (never 0).  Errors: ECO_EINVAL (a value out of range),
+ * ECO_ECUDA. */
+int eco_batch_set_shape(EcoBatch *batch, int regrow_rows_per_cta, int lstm_ctas_per_sm);
+int eco_batch_get_shape(const EcoBatch *batch, int *regrow_rows_per_cta,
+                        int *lstm_ctas_per_sm);
+
 /* Result of the tuner. */
 typedef struct EcoTuneResult {
-  int32_t fused, spawn_ctas_per_sm, steps_per_graph, reserved;
+  int32_t fused, spawn_ctas_per_sm, steps_per_graph;
+  int32_t regrow_rows_per_cta, lstm_ctas_per_sm, reserved;
   int64_t steps_taken;          /* steps every world advanced while tuning  */
   double ms_per_step_initial;   /* one trial in the configuration it started from */
   double ms_per_step_best;      /* the chosen configuration, timed once more at
                                    the end (at the population reached then)  */
 } EcoTuneResult;
 
-/* Choose the launch configuration for this batch's worlds by timing real
- * steps of the batch: one knob after the other (fused, then
- * spawn_ctas_per_sm, then steps_per_graph), every candidate value three
+/* Choose the launch configuration and kernel shapes for this batch's worlds
+ * by timing real steps of the batch: one knob after the other (fused, then
+ * spawn_ctas_per_sm, lstm_ctas_per_sm (LSTM(32) controller only),
+ * regrow_rows_per_cta, then steps_per_graph), every candidate value three
  * times round-robin, trial_steps steps per trial (a graph-length trial
  * takes trial_steps rounded up to a multiple of that length); a knob moves to
  * the candidate with the lowest median time per step only if that median is
  * more than 3% below the current value's.  Candidates: fused {1, 0},
- * spawn_ctas_per_sm {1, 2, 4, 8}, steps_per_graph {1, 4, 16, 50}.  Finally the
+ * spawn_ctas_per_sm {1, 2, 4, 8}, lstm_ctas_per_sm {1, 2},
+ * regrow_rows_per_cta {1, 2, .., the default} (none when the default is 1),
+ * steps_per_graph {1, 4, 16, 50}.  Finally the
  * chosen configuration is timed once more (ms_per_step_best).  The worlds advance by
  * out->steps_taken steps, exactly as eco_batch_step would have taken them.
  * Synchronous.  Errors: ECO_EINVAL (trial_steps outside 1..100000, profiling
@@ -377,6 +397,9 @@ int eco_world_set_config(EcoWorld *world, int fused, int spawn_ctas_per_sm,
                          int steps_per_graph);
 int eco_world_get_config(const EcoWorld *world, int *fused, int *spawn_ctas_per_sm,
                          int *steps_per_graph);
+int eco_world_set_shape(EcoWorld *world, int regrow_rows_per_cta, int lstm_ctas_per_sm);
+int eco_world_get_shape(const EcoWorld *world, int *regrow_rows_per_cta,
+                        int *lstm_ctas_per_sm);
 int eco_world_autotune(EcoWorld *world, int trial_steps, EcoTuneResult *out);
 
 /* Per-kernel timing with CUDA events on the world's stream.  While enabled,

@@ -90,7 +90,8 @@ class CEcoState(ctypes.Structure):
 # name -> (restype, argtypes)
 class CEcoTuneResult(ctypes.Structure):
     _fields_ = [("fused", ctypes.c_int32), ("spawn_ctas_per_sm", ctypes.c_int32),
-                ("steps_per_graph", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("steps_per_graph", ctypes.c_int32), ("regrow_rows_per_cta", ctypes.c_int32),
+                ("lstm_ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("steps_taken", ctypes.c_int64), ("ms_per_step_initial", ctypes.c_double),
                 ("ms_per_step_best", ctypes.c_double)]
 
@@ -122,9 +123,13 @@ SIGNATURES = {
     "eco_batch_destroy": (None, [_P]),
     "eco_batch_set_config": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "eco_batch_get_config": (ctypes.c_int, [_P, _I, _I, _I]),
+    "eco_batch_set_shape": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "eco_batch_get_shape": (ctypes.c_int, [_P, _I, _I]),
     "eco_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(CEcoTuneResult)]),
     "eco_world_set_config": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "eco_world_get_config": (ctypes.c_int, [_P, _I, _I, _I]),
+    "eco_world_set_shape": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "eco_world_get_shape": (ctypes.c_int, [_P, _I, _I]),
     "eco_world_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(CEcoTuneResult)]),
     "eco_world_profile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "eco_world_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),

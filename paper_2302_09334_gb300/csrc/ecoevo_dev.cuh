@@ -119,9 +119,7 @@ struct Counters {            // mutable, updated by the kernels
   unsigned births_t;         // step index the births belong to
   int use_forced;            // moves read `forced` instead of `action`
   int status;                // ST_* bits
-  int cand_step;             // CTAs of the fused slot phases with a reproduction
-                             // candidate this step (reset at the step's end)
-  int pad[2];
+  int pad[3];
   // analysis window (App. C): the step it started at, and the deaths and
   // summed ages at death since then
   long long snap_t, an_deaths;
@@ -205,7 +203,8 @@ __host__ __device__ inline U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
 // itself when x1 < 2^31 (u < 1/2); when u >= 1/2 from 1 - u = (~x1 + 1/2)
 // 2^-32, which a float holds exactly, so that ln of a u close to 1 keeps its
 // relative accuracy (e = 0, f = u - 1 = -(1 - u), or e = -1, f = 2u - 1).
-// Then ln(1 + f) = 2 atanh(s) with s = f / (2 + f), |s| < 0.1716, by the
+// Then ln(1 + f) = 2 atanh(s) with s = f / (2 + f), |s| < 0.1716 (the
+// quotient by the hardware's approximate division, within 2 ulp), by the
 // Taylor series of atanh up to s^9 (the next term is below 2e-10 of the
 // sum), and e ln 2 with ln 2 split in two (Cody and Waite) so that e ln2_hi
 // is exact.
@@ -226,7 +225,7 @@ __device__ inline float ln_unit_word(uint32_t x1) {
   const int e_up = near_one ? 0 : -1;
   const float f = upper ? f_up : f_lo;
   const float e = (float)(upper ? e_up : e_lo);
-  const float s = f / (2.0f + f);
+  const float s = __fdividef(f, 2.0f + f);
   const float s2 = s * s;
   float q = fmaf(s2, 1.0f / 9.0f, 1.0f / 7.0f);
   q = fmaf(s2, q, 1.0f / 5.0f);
@@ -236,14 +235,23 @@ __device__ inline float ln_unit_word(uint32_t x1) {
   return fmaf(e, 0.693145751953125f, fmaf(e, 1.4286067653e-06f, l));
 }
 
+// Square root of x > 0: x rsqrt(x) from the hardware's approximate
+// reciprocal square root, then one Newton-Raphson (Heron) step, r + (x -
+// r^2) / (2 r) with 1/r taken as rsqrt(x).
+__device__ inline float sqrt_pos(float x) {
+  const float y = rsqrtf(x);
+  const float r = x * y;
+  return fmaf(fmaf(-r, r, x), 0.5f * y, r);
+}
+
 // Box-Muller pair from two words, in float, with no branch: r = sqrt(-2 ln
-// u1); the angle (pi/2)(quad + g), quad = the top two bits of x2 and g =
+// u1) (-2 ln u1 > 2e-10: u1 < 1 - 2^-33); the angle (pi/2)(quad + g), quad = the top two bits of x2 and g =
 // (low 30 bits + 1/2) 2^-30, is reduced to a in (0, pi/4): a = (pi/2) g when
 // g < 1/2, else the complement (pi/2)(1 - g) with 1 - g taken exactly from
 // the complemented bits (and cos and sin swapped); sin a and cos a by their
 // Taylor series up to a^9 and a^10 (next terms below 2e-9).
 __device__ inline void box_muller_f(uint32_t x1, uint32_t x2, float &z0, float &z1) {
-  const float r = sqrtf(-2.0f * ln_unit_word(x1));
+  const float r = sqrt_pos(-2.0f * ln_unit_word(x1));
   const uint32_t quad = x2 >> 30;
   const bool upper = (x2 >> 29) & 1u;
   const uint32_t y = (upper ? ~x2 : x2) & 0x1FFFFFFFu;
@@ -284,16 +292,6 @@ __device__ inline bool bit_at(const uint32_t *plane, int Wp, int y, int x) {
   return (plane[y * Wp + (x >> 5)] >> (x & 31)) & 1u;
 }
 
-// Bits of a (2R+1)-bit row window that belong to the neighbourhood at row
-// offset dy (centre excluded): square or diamond, App. B.1.
-__device__ inline uint32_t nbr_mask(int shape, int R, int dy) {
-  const int ady = dy < 0 ? -dy : dy;
-  const int reach = (shape == 1) ? R - ady : R;
-  uint32_t m = 0;
-  if (reach >= 0) m = ((1u << (2 * reach + 1)) - 1u) << (R - reach);
-  if (dy == 0) m &= ~(1u << R);
-  return m;
-}
 
 #endif
 
@@ -305,6 +303,9 @@ struct BatchDev {
   WorldDev *const *worlds;   // device array [n]
   int n;
   int *tile_prefix;          // device [n+1]: regrowth tiles per world
+  int regrow_k;              // 8-row tiles stacked in one regrowth CTA (1, 2, 4, 8)
+  int lstm_ctas;             // controller-kernel CTAs per SM (1 or 2)
+  int pdl;                   // host side: launch with programmatic dependent launch
   int *slot_block_prefix;    // device [n+1]: 256-slot blocks per world
   int total_tiles, total_slot_blocks;
   int max_capacity;
@@ -330,7 +331,8 @@ __device__ inline void pdl_release() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Launch a step kernel with the programmatic-stream-serialization attribute.
+// Launch a step kernel, with the programmatic-stream-serialization
+// attribute unless b.pdl is 0 (kernels timed one by one between events).
 template <typename Kernel>
 inline void launch_step_kernel(Kernel k, int grid, int block, size_t smem, cudaStream_t s,
                                const BatchDev &b) {
@@ -343,7 +345,7 @@ inline void launch_step_kernel(Kernel k, int grid, int block, size_t smem, cudaS
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = b.pdl ? 1 : 0;
   cudaLaunchKernelEx(&cfg, k, b);
 }
 
@@ -396,6 +398,27 @@ int launch_weights_from_host(const float *host_dev, float *rows, int n, int cont
 // order, in place; returns a cudaError_t value.
 int launch_rows_to_physical_inplace(float *rows, int n, int controller, int n_sms,
                                     cudaStream_t s);
+// Counters of a loaded state: with set, the cumulative ones (t .. agent_steps
+// but pop, which the rebuild counts); always the per-step ones zeroed.
+struct LoadCounters {
+  long long t, births, deaths, dropped, births_last, deaths_last, dropped_last, agent_steps;
+  int set;
+};
+void launch_load_counters(Counters *ctr, const LoadCounters &v, cudaStream_t s);
+// A plane of one byte per cell (nonzero: set; device memory or the device
+// address of page-locked host memory) -> H x Wp words.
+void launch_pack_plane(const uint8_t *cells, int H, int W, int Wp, uint32_t *words,
+                       cudaStream_t s);
+// Slot arrays of a loaded state read from page-locked host memory through
+// their device addresses (null: not read here); logits are C x NACT on the
+// host, C x 8 on the device; h goes to h_dst (the current buffer).
+struct SlotSources {
+  const uint8_t *alive, *ate;
+  const int32_t *y, *x, *repr, *low, *age, *action, *prev;
+  const float *energy, *logits, *h, *c;
+};
+void launch_load_slots(const WorldDev &wd, const SlotSources &src, float *h_dst, int n_sms,
+                       cudaStream_t s);
 // analysis metrics of App. C (k_analysis.cu)
 void launch_analysis_reset(const WorldDev *wd_host, int n_sms, cudaStream_t s);
 void launch_analysis(const WorldDev *wd_host, int n_sms, cudaStream_t s);
@@ -404,5 +427,12 @@ void launch_lab_window(const WorldDev *wd_host, int n_sms, cudaStream_t s);
 constexpr int SCAN_THREADS = 1024;
 constexpr int SLOT_BLOCK = 256;
 constexpr int REGROW_ROWS = 8, REGROW_WORDS = 4;
+constexpr int REGROW_KMAX = 8;   // 8-row tiles stacked in one regrowth CTA, at most
+
+// Regrowth CTAs of a world (columns of k stacked tiles).
+inline int regrow_tiles_of(int H, int Wp, int k) {
+  const int rows = REGROW_ROWS * k;
+  return ((H + rows - 1) / rows) * ((Wp + REGROW_WORDS - 1) / REGROW_WORDS);
+}
 
 }  // namespace eco

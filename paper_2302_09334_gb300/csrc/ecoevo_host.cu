@@ -188,6 +188,7 @@ struct EcoBatch {
   bool owns_table = false;
   cudaGraphExec_t g1 = nullptr, gk = nullptr;
   int steps_per_graph = STEPS_PER_GRAPH;  // steps in the chunk graph gk
+  int regrow_cfg = 0;     // regrowth tiles stacked per CTA as set (0: chosen by size)
   Profile *prof = nullptr;  // the first world's profiler
 };
 
@@ -205,6 +206,10 @@ struct EcoWorld {
   WorldDev *dd = nullptr; // device descriptor
   EcoBatch self;          // batch of one: this world
   Profile prof;
+  // second stream of state loads (the weight rows' upload runs on it beside
+  // the rest), created at the first load
+  cudaStream_t io_stream = nullptr;
+  cudaEvent_t io_fork = nullptr, io_join = nullptr;
 };
 
 namespace {
@@ -221,9 +226,18 @@ int cuda_err_at(cudaError_t e, const char *what) {
     if (rc__ != ECO_OK) return rc__;                  \
   } while (0)
 
-int tiles_of(const WorldDev &wd) {
-  return ((wd.H + REGROW_ROWS - 1) / REGROW_ROWS) *
-         ((wd.Wp + REGROW_WORDS - 1) / REGROW_WORDS);
+// 8-row tiles stacked per regrowth CTA by default: the fewest (1, 2, 4, 8)
+// that leave at most four CTAs per SM (one wave of the tail kernel), so that
+// a large world's regrowth does not queue in waves behind itself.
+int regrow_k_for(EcoWorld *const *worlds, int n, int n_sms) {
+  int k = 1;
+  for (; k < REGROW_KMAX; k *= 2) {
+    long long tiles = 0;
+    for (int i = 0; i < n; ++i)
+      tiles += regrow_tiles_of(worlds[i]->hd.H, worlds[i]->hd.Wp, k);
+    if (tiles <= 4ll * n_sms) break;
+  }
+  return k;
 }
 int slot_blocks_of(const WorldDev &wd) { return (wd.C + SLOT_BLOCK - 1) / SLOT_BLOCK; }
 
@@ -272,12 +286,17 @@ int step_kernels(const BatchDev &bd, const StepKernel **list) {
 
 // One step, kernel by kernel; with `ev`, a pair of events around every
 // kernel (not while capturing a graph).
+// The kernels of one step; with events (profiling) each kernel is
+// bracketed by two and launched without programmatic dependent launch,
+// which the events between kernels rule out anyway.
 void launch_step(const EcoBatch &b, cudaStream_t s, cudaEvent_t *ev) {
   const StepKernel *list;
   const int nk = step_kernels(b.bd, &list);
+  BatchDev bd = b.bd;
+  if (ev) bd.pdl = 0;
   for (int k = 0; k < nk; ++k) {
     if (ev) cudaEventRecord(ev[2 * k], s);
-    list[k].fn(b.bd, s);
+    list[k].fn(bd, s);
     if (ev) cudaEventRecord(ev[2 * k + 1], s);
   }
 }
@@ -323,12 +342,14 @@ int batch_init(EcoBatch &b, EcoWorld *const *worlds, int n, void *table_dev) {
   WorldDev **wp = reinterpret_cast<WorldDev **>(host.data());
   int *tiles = reinterpret_cast<int *>(host.data() + n * sizeof(WorldDev *));
   int *blocks = tiles + (n + 1);
+  const int rk = regrow_k_for(worlds, n, worlds[0]->n_sms);
+  b.regrow_cfg = 0;
   int tt = 0, bb = 0, maxc = 0;
   for (int i = 0; i < n; ++i) {
     wp[i] = worlds[i]->dd;
     tiles[i] = tt;
     blocks[i] = bb;
-    tt += tiles_of(worlds[i]->hd);
+    tt += regrow_tiles_of(worlds[i]->hd.H, worlds[i]->hd.Wp, rk);
     bb += slot_blocks_of(worlds[i]->hd);
     maxc = std::max(maxc, worlds[i]->hd.C);
   }
@@ -341,6 +362,9 @@ int batch_init(EcoBatch &b, EcoWorld *const *worlds, int n, void *table_dev) {
   b.bd.tile_prefix = reinterpret_cast<int *>((char *)b.table + n * sizeof(WorldDev *));
   b.bd.slot_block_prefix = b.bd.tile_prefix + (n + 1);
   b.bd.total_tiles = tt;
+  b.bd.regrow_k = rk;
+  b.bd.lstm_ctas = 1;
+  b.bd.pdl = 1;
   b.bd.total_slot_blocks = bb;
   b.bd.max_capacity = maxc;
   b.bd.n_sms = worlds[0]->n_sms;
@@ -453,6 +477,19 @@ int batch_step(EcoBatch &b, int64_t n) {
 // split into launches and CTAs differs), so the tuner times real steps of the
 // batch it tunes.
 // ---------------------------------------------------------------------------
+// Before a launch configuration changes: the stream idle, the graphs (which
+// hold the old one) dropped, the profiler's events released.
+int reconfigure(EcoBatch &b) {
+  ECO_CU(cudaStreamSynchronize(b.stream));
+  destroy_graphs(b);
+  if (b.prof && b.prof->owner == &b) {  // its events bracket the old kernel list
+    int rc = profile_collect(*b.prof);
+    if (rc) return rc;
+    profile_release(*b.prof);
+  }
+  return ECO_OK;
+}
+
 int set_config(EcoBatch &b, int fused, int spawn_per_sm, int steps_per_graph) {
   if (fused != 0 && fused != 1) return ECO_EINVAL;
   if (fused && b.bd.max_capacity > FUSED_MAX_C) return ECO_EINVAL;
@@ -461,17 +498,44 @@ int set_config(EcoBatch &b, int fused, int spawn_per_sm, int steps_per_graph) {
   const int spawn = spawn_per_sm * b.bd.n_sms;
   if (fused == b.bd.fused && spawn == b.bd.spawn_ctas && steps_per_graph == b.steps_per_graph)
     return ECO_OK;
-  ECO_CU(cudaStreamSynchronize(b.stream));
-  destroy_graphs(b);
-  if (b.prof && b.prof->owner == &b) {  // its events bracket the old kernel list
-    int rc = profile_collect(*b.prof);
-    if (rc) return rc;
-    profile_release(*b.prof);
-  }
+  int rc = reconfigure(b);
+  if (rc) return rc;
   b.bd.fused = fused;
   b.bd.spawn_ctas = spawn;
   b.bd.tail_early = tail_early(b.bd);
   b.steps_per_graph = steps_per_graph;
+  return ECO_OK;
+}
+
+// Kernel shapes: regrowth tiles stacked per CTA (0: chosen by size; 1, 2,
+// 4, 8) and controller-kernel CTAs per SM (1, 2).  A new stacking rewrites
+// the batch's tile prefix in its device table.
+int set_shape(EcoBatch &b, int regrow_rows, int lstm_ctas) {
+  if (regrow_rows != 0 && regrow_rows != 1 && regrow_rows != 2 && regrow_rows != 4 &&
+      regrow_rows != 8)
+    return ECO_EINVAL;
+  if (lstm_ctas != 1 && lstm_ctas != 2) return ECO_EINVAL;
+  const int n = (int)b.worlds.size();
+  const int k = regrow_rows ? regrow_rows : regrow_k_for(b.worlds.data(), n, b.bd.n_sms);
+  b.regrow_cfg = regrow_rows;
+  if (k == b.bd.regrow_k && lstm_ctas == b.bd.lstm_ctas) return ECO_OK;
+  int rc = reconfigure(b);
+  if (rc) return rc;
+  if (k != b.bd.regrow_k) {
+    std::vector<int> tiles(n + 1);
+    int tt = 0;
+    for (int i = 0; i < n; ++i) {
+      tiles[i] = tt;
+      tt += regrow_tiles_of(b.worlds[i]->hd.H, b.worlds[i]->hd.Wp, k);
+    }
+    tiles[n] = tt;
+    ECO_CU(cudaMemcpy(b.bd.tile_prefix, tiles.data(), (n + 1) * sizeof(int),
+                      cudaMemcpyHostToDevice));
+    b.bd.total_tiles = tt;
+    b.bd.regrow_k = k;
+    b.bd.tail_early = tail_early(b.bd);
+  }
+  b.bd.lstm_ctas = lstm_ctas;
   return ECO_OK;
 }
 
@@ -550,6 +614,7 @@ int autotune(EcoBatch &b, int trial_steps, EcoTuneResult *out) {
   const int rounds = 3;
   int64_t steps = 0;
   int fused = b.bd.fused, spawn = b.bd.spawn_ctas / b.bd.n_sms, k = b.steps_per_graph;
+  int regrow = b.regrow_cfg ? b.regrow_cfg : b.bd.regrow_k, lstm = b.bd.lstm_ctas;
   double ms = 0.0;
   if (!rc) rc = set_config(b, fused, spawn, k);
   if (!rc) rc = time_steps(b, trial_steps, e0, e1, &out->ms_per_step_initial);
@@ -562,6 +627,21 @@ int autotune(EcoBatch &b, int trial_steps, EcoTuneResult *out) {
   if (!rc) {
     rc = tune_knob(b, {1, 2, 4, 8}, same, rounds,
                    [&](int v) { return set_config(b, fused, v, k); }, e0, e1, &steps, &spawn, &ms);
+  }
+  if (!rc && b.bd.controller == ECO_CTRL_LSTM32) {
+    rc = tune_knob(b, {1, 2}, same, rounds,
+                   [&](int v) { return set_shape(b, b.regrow_cfg, v); }, e0, e1, &steps, &lstm,
+                   &ms);
+  }
+  // stacking beyond the default (the fewest tiles per CTA that fit one wave)
+  // only lengthens each CTA: the candidates stop there, and a batch that
+  // fits one wave unstacked has no choice to make
+  const int regrow_max = regrow_k_for(b.worlds.data(), (int)b.worlds.size(), b.bd.n_sms);
+  if (!rc && regrow_max > 1) {
+    std::vector<int> cand;
+    for (int v = 1; v <= regrow_max; v *= 2) cand.push_back(v);
+    rc = tune_knob(b, cand, same, rounds,
+                   [&](int v) { return set_shape(b, v, lstm); }, e0, e1, &steps, &regrow, &ms);
   }
   if (!rc) {
     // a chunk length is timed over whole chunks: the multiple of it closest
@@ -585,6 +665,8 @@ int autotune(EcoBatch &b, int trial_steps, EcoTuneResult *out) {
   out->fused = fused;
   out->spawn_ctas_per_sm = spawn;
   out->steps_per_graph = k;
+  out->regrow_rows_per_cta = regrow;
+  out->lstm_ctas_per_sm = lstm;
   out->steps_taken = steps;
   out->ms_per_step_best = ms;
   return ECO_OK;
@@ -773,6 +855,12 @@ int eco_world_create(const EcoParams *params, uint64_t seed, void *arena,
 void eco_world_destroy(EcoWorld *w) {
   if (!w) return;
   cudaStreamSynchronize(w->stream);
+  if (w->io_stream) {
+    cudaStreamSynchronize(w->io_stream);
+    cudaStreamDestroy(w->io_stream);
+  }
+  if (w->io_fork) cudaEventDestroy(w->io_fork);
+  if (w->io_join) cudaEventDestroy(w->io_join);
   destroy_graphs(w->self);
   profile_release(w->prof);
   if (w->owns_arena) cudaFree(w->arena);
@@ -1083,78 +1171,120 @@ int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
       (in->weights_first < 0 || in->weights_count < 0 ||
        (size_t)in->weights_first + in->weights_count > C))
     return ECO_EINVAL;
+  if (set_counters && (in->counters[ECO_C_T] < 0 || in->counters[ECO_C_T] > 0xFFFFFFFFll))
+    return ECO_EINVAL;
   int rc = settle_births(w);
   if (rc) return rc;
-  StateIO io(w->stream);
-  Counters c;
-  io.d2h(&c, d.ctr, sizeof(Counters));
-  if ((rc = io.wait())) return rc;
-  if (set_counters) {
-    c.t = in->counters[ECO_C_T];
-    c.births = in->counters[ECO_C_BIRTHS];
-    c.deaths = in->counters[ECO_C_DEATHS];
-    c.dropped = in->counters[ECO_C_DROPPED];
-    c.births_last = in->counters[ECO_C_BIRTHS_LAST];
-    c.deaths_last = in->counters[ECO_C_DEATHS_LAST];
-    c.dropped_last = in->counters[ECO_C_DROPPED_LAST];
-    c.agent_steps = in->counters[ECO_C_AGENT_STEPS];
-    if (c.t < 0 || c.t > 0xFFFFFFFFll) return ECO_EINVAL;
-  }
-  c.deaths_step = 0;
-  c.cand_step = 0;
-  c.n_births = 0;
-  c.use_forced = 0;
-  // host buffers below live until the final wait
-  std::vector<uint32_t> res_w, wall_w;
-  std::vector<float> lg;
-  io.h2d(d.ctr, &c, sizeof(Counters));
-  const bool odd = (c.t & 1) != 0;
-  if (in->res_host) {
-    pack_plane(p, in->res_host, res_w);
-    io.h2d(odd ? d.res1 : d.res0, res_w.data(), res_w.size() * 4);
-  }
-  if (in->wall_host) {
-    pack_plane(p, in->wall_host, wall_w);
-    io.h2d(d.wall, wall_w.data(), wall_w.size() * 4);
-  }
-  io.h2d(d.alive, in->alive_host, C);
-  io.h2d(d.y, in->y_host, C * 4);
-  io.h2d(d.x, in->x_host, C * 4);
-  io.h2d(d.energy, in->energy_host, C * 4);
-  io.h2d(d.repr_ctr, in->repr_ctr_host, C * 4);
-  io.h2d(d.low_ctr, in->low_ctr_host, C * 4);
-  io.h2d(d.age, in->age_host, C * 4);
-  io.h2d(odd ? d.h1 : d.h0, in->h_host, C * HID * 4);
-  io.h2d(d.c, in->c_host, C * HID * 4);
-  io.h2d(d.action, in->action_host, C * 4);
-  io.h2d(d.prev_act, in->prev_action_host, C * 4);
-  io.h2d(d.ate, in->ate_host, C);
-  if (in->logits_host && C) {
-    lg.assign(C * 8, 0.f);
-    for (size_t s = 0; s < C; ++s)
-      for (int a = 0; a < NACT; ++a) lg[s * 8 + a] = in->logits_host[s * NACT + a];
-    io.h2d(d.logits, lg.data(), lg.size() * 4);
-  }
-  if (in->weights_host && in->weights_count > 0 && !io.rc) {
+  // The weight rows, the bulk of a state (93 KB per agent over a host link
+  // of about 0.2 TB/s), go first, on the world's second stream, while the
+  // rest of the state is written on the world's stream; the rows' slots
+  // wait for the tail kernel just launched (it writes pending children).
+  const bool wts = in->weights_host && in->weights_count > 0;
+  if (wts) {
+    if (!w->io_stream) {
+      ECO_CU(cudaStreamCreateWithFlags(&w->io_stream, cudaStreamNonBlocking));
+      ECO_CU(cudaEventCreateWithFlags(&w->io_fork, cudaEventDisableTiming));
+      ECO_CU(cudaEventCreateWithFlags(&w->io_join, cudaEventDisableTiming));
+    }
+    ECO_CU(cudaEventRecord(w->io_fork, w->stream));
+    ECO_CU(cudaStreamWaitEvent(w->io_stream, w->io_fork, 0));
     const size_t ws = d.wstride, np = d.nparam;
     float *dst = d.weights + (size_t)in->weights_first * ws;
     // page-locked rows (16-byte aligned): read by a kernel through their
-    // device address, stored in physical order (faster over the host link
-    // than a copy engine); otherwise one 2-D copy of the logical rows into
-    // their own device rows (staged by the driver from pageable memory),
-    // then the permutation to the physical order in place
+    // device address, stored in physical order; otherwise one 2-D copy of
+    // the logical rows into their own device rows (staged by the driver
+    // from pageable memory), then the permutation to the physical order in
+    // place
     const float *dev = (const float *)pinned_device_view(in->weights_host);
+    int wrc;
     if (dev && ((uintptr_t)dev & 15u) == 0) {
-      io.rc = cuda_err((cudaError_t)launch_weights_from_host(dev, dst, in->weights_count,
-                                                             d.controller, w->n_sms, w->stream));
+      wrc = cuda_err((cudaError_t)launch_weights_from_host(dev, dst, in->weights_count,
+                                                           d.controller, w->n_sms, w->io_stream));
     } else {
-      io.rc = cuda_err(cudaMemcpy2DAsync(dst, ws * 4, in->weights_host, np * 4, np * 4,
-                                         in->weights_count, cudaMemcpyHostToDevice, w->stream));
-      if (!io.rc)
-        io.rc = cuda_err((cudaError_t)launch_rows_to_physical_inplace(
-            dst, in->weights_count, d.controller, w->n_sms, w->stream));
+      wrc = cuda_err(cudaMemcpy2DAsync(dst, ws * 4, in->weights_host, np * 4, np * 4,
+                                       in->weights_count, cudaMemcpyHostToDevice, w->io_stream));
+      if (!wrc)
+        wrc = cuda_err((cudaError_t)launch_rows_to_physical_inplace(
+            dst, in->weights_count, d.controller, w->n_sms, w->io_stream));
+    }
+    // joined by the world's stream before its final wait, whatever happens
+    const int jrc = cuda_err(cudaEventRecord(w->io_join, w->io_stream));
+    if (wrc || jrc) {
+      cudaStreamSynchronize(w->io_stream);
+      return wrc ? wrc : jrc;
     }
   }
+  StateIO io(w->stream);
+  // The step counter says which buffer of the plane and h pairs is current:
+  // the caller's, or (counters kept) the device's, read back first.
+  LoadCounters lc{};
+  lc.set = set_counters ? 1 : 0;
+  long long t_now = in->counters[ECO_C_T];
+  if (set_counters) {
+    lc.t = in->counters[ECO_C_T];
+    lc.births = in->counters[ECO_C_BIRTHS];
+    lc.deaths = in->counters[ECO_C_DEATHS];
+    lc.dropped = in->counters[ECO_C_DROPPED];
+    lc.births_last = in->counters[ECO_C_BIRTHS_LAST];
+    lc.deaths_last = in->counters[ECO_C_DEATHS_LAST];
+    lc.dropped_last = in->counters[ECO_C_DROPPED_LAST];
+    lc.agent_steps = in->counters[ECO_C_AGENT_STEPS];
+  } else {
+    io.d2h(&t_now, &d.ctr->t, sizeof(long long));
+    if ((rc = io.wait())) {
+      if (wts) cudaStreamSynchronize(w->io_stream);
+      return rc;
+    }
+  }
+  launch_load_counters(d.ctr, lc, w->stream);
+  const bool odd = (t_now & 1) != 0;
+  // Planes: the cells' bytes are staged in the slot map (rebuilt below) or
+  // read from page-locked memory, and packed into words on the device.
+  const size_t HW = (size_t)p.H * p.W;
+  uint8_t *stage = reinterpret_cast<uint8_t *>(d.slot_map);   // 4 HW bytes
+  const uint8_t *planes_in[2] = {in->res_host, in->wall_host};
+  uint32_t *planes_out[2] = {odd ? d.res1 : d.res0, d.wall};
+  for (int k = 0; k < 2 && !io.rc; ++k) {
+    if (!planes_in[k]) continue;
+    const uint8_t *cells = (const uint8_t *)pinned_device_view(planes_in[k]);
+    if (!cells) {
+      io.h2d(stage + k * HW, planes_in[k], HW);
+      cells = stage + k * HW;
+    }
+    launch_pack_plane(cells, p.H, p.W, d.Wp, planes_out[k], w->stream);
+  }
+  // Slot arrays: page-locked ones read by one kernel, the others copied.
+  SlotSources src{};
+  std::vector<float> lg;   // pageable logits repacked to C x 8, alive until the wait
+  auto slot_in = [&](const void *host, void *dev, size_t bytes) -> const void * {
+    if (!host || !C) return nullptr;
+    if (const void *v = pinned_device_view(host)) return v;
+    io.h2d(dev, host, bytes);
+    return nullptr;
+  };
+  src.alive = (const uint8_t *)slot_in(in->alive_host, d.alive, C);
+  src.y = (const int32_t *)slot_in(in->y_host, d.y, C * 4);
+  src.x = (const int32_t *)slot_in(in->x_host, d.x, C * 4);
+  src.energy = (const float *)slot_in(in->energy_host, d.energy, C * 4);
+  src.repr = (const int32_t *)slot_in(in->repr_ctr_host, d.repr_ctr, C * 4);
+  src.low = (const int32_t *)slot_in(in->low_ctr_host, d.low_ctr, C * 4);
+  src.age = (const int32_t *)slot_in(in->age_host, d.age, C * 4);
+  float *h_dst = odd ? d.h1 : d.h0;
+  src.h = (const float *)slot_in(in->h_host, h_dst, C * HID * 4);
+  src.c = (const float *)slot_in(in->c_host, d.c, C * HID * 4);
+  src.action = (const int32_t *)slot_in(in->action_host, d.action, C * 4);
+  src.prev = (const int32_t *)slot_in(in->prev_action_host, d.prev_act, C * 4);
+  src.ate = (const uint8_t *)slot_in(in->ate_host, d.ate, C);
+  if (in->logits_host && C) {
+    src.logits = (const float *)pinned_device_view(in->logits_host);
+    if (!src.logits) {
+      lg.assign(C * 8, 0.f);
+      for (size_t s = 0; s < C; ++s)
+        for (int a = 0; a < NACT; ++a) lg[s * 8 + a] = in->logits_host[s * NACT + a];
+      io.h2d(d.logits, lg.data(), lg.size() * 4);
+    }
+  }
+  if (!io.rc) launch_load_slots(d, src, h_dst, w->n_sms, w->stream);
   // greediness counters start over with a loaded state
   if (!io.rc) io.rc = cuda_err(cudaMemsetAsync(d.lab_seen, 0, C ? C : 1, w->stream));
   if (!io.rc) io.rc = cuda_err(cudaMemsetAsync(d.lab_ate, 0, C ? C : 1, w->stream));
@@ -1164,9 +1294,16 @@ int eco_world_load_state(EcoWorld *w, const EcoState *in, int set_counters) {
     launch_rebuild(&w->hd, w->n_sms, w->stream);
     io.rc = cuda_err(cudaGetLastError());
   }
+  if (wts) {
+    const int jrc = cuda_err(cudaStreamWaitEvent(w->stream, w->io_join, 0));
+    if (!io.rc) io.rc = jrc;
+  }
   int st = 0;
   io.d2h(&st, &d.ctr->status, sizeof(int));
-  if ((rc = io.wait())) return rc;
+  if ((rc = io.wait())) {
+    if (wts) cudaStreamSynchronize(w->io_stream);
+    return rc;
+  }
   if (st & ST_STATE) {
     st &= ~ST_STATE;
     ECO_CU(cudaMemcpy(&d.ctr->status, &st, sizeof(int), cudaMemcpyHostToDevice));
@@ -1215,6 +1352,18 @@ int eco_batch_get_config(const EcoBatch *b, int *fused, int *spawn_ctas_per_sm,
   return ECO_OK;
 }
 
+int eco_batch_set_shape(EcoBatch *b, int regrow_rows_per_cta, int lstm_ctas_per_sm) {
+  if (!b) return ECO_EINVAL;
+  return set_shape(*b, regrow_rows_per_cta, lstm_ctas_per_sm);
+}
+
+int eco_batch_get_shape(const EcoBatch *b, int *regrow_rows_per_cta, int *lstm_ctas_per_sm) {
+  if (!b || !regrow_rows_per_cta || !lstm_ctas_per_sm) return ECO_EINVAL;
+  *regrow_rows_per_cta = b->bd.regrow_k;
+  *lstm_ctas_per_sm = b->bd.lstm_ctas;
+  return ECO_OK;
+}
+
 int eco_batch_autotune(EcoBatch *b, int trial_steps, EcoTuneResult *out) {
   Trace trace("eco_batch_autotune");
   if (!b || !out) return ECO_EINVAL;
@@ -1230,6 +1379,16 @@ int eco_world_get_config(const EcoWorld *w, int *fused, int *spawn_ctas_per_sm,
                          int *steps_per_graph) {
   if (!w) return ECO_EINVAL;
   return eco_batch_get_config(&w->self, fused, spawn_ctas_per_sm, steps_per_graph);
+}
+
+int eco_world_set_shape(EcoWorld *w, int regrow_rows_per_cta, int lstm_ctas_per_sm) {
+  if (!w) return ECO_EINVAL;
+  return set_shape(w->self, regrow_rows_per_cta, lstm_ctas_per_sm);
+}
+
+int eco_world_get_shape(const EcoWorld *w, int *regrow_rows_per_cta, int *lstm_ctas_per_sm) {
+  if (!w) return ECO_EINVAL;
+  return eco_batch_get_shape(&w->self, regrow_rows_per_cta, lstm_ctas_per_sm);
 }
 
 int eco_world_autotune(EcoWorld *w, int trial_steps, EcoTuneResult *out) {

@@ -187,7 +187,6 @@ __device__ inline void finish_step(const WorldDev &wd, int S, int F, int pop, ui
   c.deaths += c.deaths_step;
   c.an_deaths += c.deaths_step;
   c.deaths_step = 0;
-  c.cand_step = 0;
   c.n_births = births;
   c.births_t = t;
   c.agent_steps += c.pop;  // the agents alive at the start of this step
@@ -335,9 +334,14 @@ __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
   __shared__ int sh[3 * 32 + 3];
   __shared__ int pub[3], ex[6];
   __shared__ int cta_deaths, cta_cand;
+  __shared__ int busy[NCTA];   // CTA r of the cluster had a death or a candidate
   __shared__ unsigned long long cta_age_sum;
   const WorldDev &wd = *world_ptr(b, blockIdx.x / NCTA);
   const int rank = NCTA == 1 ? 0 : (int)cg::this_cluster().block_rank();
+  // Every CTA of the cluster writes its quiet-step flag into the shared
+  // memory of every other after the first phase; this arrival (completed
+  // before those writes) makes sure they have all started.
+  if constexpr (NCTA > 1) asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
   const int C = wd.C, W = wd.W, Wp = wd.Wp;
   const int per_cta = (C + NCTA - 1) / NCTA;
   const int c0 = min(C, rank * per_cta), c1 = min(C, c0 + per_cta);
@@ -355,6 +359,7 @@ __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
   // L2, before waiting for the observation+controller kernel; its outputs
   // (targets, kills, claims) after.
   const uint32_t t = (uint32_t)__ldcg(&wd.ctr->t);
+  const int pop0 = (int)__ldcg(&wd.ctr->pop);      // agents at the step's start
   uint32_t *res = (t & 1u) ? wd.res0 : wd.res1;  // plane after this step's regrowth
   float *h_next = (t & 1u) ? wd.h0 : wd.h1;
 
@@ -453,19 +458,27 @@ __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
     atomicAdd(&wd.ctr->deaths_step, cta_deaths);
     atomicAdd(&wd.ctr->an_age_sum, cta_age_sum);
   }
-  if (threadIdx.x == 0 && cta_cand) atomicAdd(&wd.ctr->cand_step, 1);
+  if constexpr (NCTA > 1) {
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+    if (threadIdx.x < NCTA)
+      *cg::this_cluster().map_shared_rank(&busy[rank], (int)threadIdx.x) =
+          (cta_deaths || cta_cand) ? 1 : 0;
+  } else if (threadIdx.x == 0) {
+    busy[0] = (cta_deaths || cta_cand) ? 1 : 0;
+  }
   phase_sync<NCTA>();
   // A quiet step -- no death and no reproduction candidate in the whole
-  // world (every CTA's counts are in after the barrier) -- leaves the alive
+  // world (every CTA's flag is in after the barrier) -- leaves the alive
   // list as it is (survivors in slot order, no child): the birth and
   // compaction phases are skipped, last step's newborns are newborns no
-  // more.  The counters read here are reset by finish_step, which in a
-  // quiet step changes nothing another CTA can still read (both are 0).
-  if (__ldcg(&wd.ctr->deaths_step) == 0 && __ldcg(&wd.ctr->cand_step) == 0) {
-    const int pop = (int)__ldcg(&wd.ctr->pop);   // agents at the step's start
-    for (int i = rank * THREADS + (int)threadIdx.x; i < pop; i += NCTA * THREADS)
+  // more.
+  bool quiet = true;
+#pragma unroll
+  for (int r = 0; r < NCTA; ++r) quiet = quiet && busy[r] == 0;
+  if (quiet) {
+    for (int i = rank * THREADS + (int)threadIdx.x; i < pop0; i += NCTA * THREADS)
       wd.alive_new[i] = 0;
-    if (rank == 0 && threadIdx.x == 0) finish_step(wd, 0, 0, pop, t);
+    if (rank == 0 && threadIdx.x == 0) finish_step(wd, 0, 0, pop0, t);
     return;
   }
   // ---- birth claims: first free N, S, E, W cell; lowest parent slot wins
@@ -684,49 +697,74 @@ __global__ void __launch_bounds__(SLOT_BLOCK) k_scan_children(const __grid_const
 // bias rows of a block are permuted and take one draw per element.
 constexpr int SPAWN_THREADS = 256;
 
+// Four consecutive logical parameters j .. j+3 (j a multiple of 4, or -1:
+// padding) plus scale * N of one Philox draw; parameters from np on are
+// padding (zero).
+__device__ inline float4 mutate_quad(const WorldDev &wd, float4 base, int j, int np,
+                                     uint32_t tag, uint32_t t, uint32_t id, float scale) {
+  if (j < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+  float z[4];
+  normals4(wd.key0, wd.key1, (uint32_t)j >> 2, t, tag, id, z);
+  float out[4] = {base.x, base.y, base.z, base.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    out[i] = (j + i < np) ? __fadd_rn(out[i], __fmul_rn(scale, z[i])) : 0.f;
+  return make_float4(out[0], out[1], out[2], out[3]);
+}
+
+// One parameter j plus scale * N_j (normal j & 3 of draw j >> 2).
+__device__ inline float mutate_one(const WorldDev &wd, float base, int j, uint32_t tag,
+                                   uint32_t t, uint32_t id, float scale) {
+  float z[4];
+  normals4(wd.key0, wd.key1, (uint32_t)j >> 2, t, tag, id, z);
+  const int i = j & 3;
+  const float zi = i == 0 ? z[0] : i == 1 ? z[1] : i == 2 ? z[2] : z[3];
+  return __fadd_rn(base, __fmul_rn(scale, zi));
+}
+
+// The bias float4 number b4 (0..7) of block q: rows 4 b4 .. 4 b4 + 3, whose
+// logical rows are not consecutive, so each takes its own draw.
+__device__ inline float4 mutate_bias4(const WorldDev &wd, float4 base, int q, int b4,
+                                      uint32_t tag, uint32_t t, uint32_t id, float scale) {
+  float in[4] = {base.x, base.y, base.z, base.w}, out[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    out[i] = mutate_one(wd, in[i], OFF_B + blk_row_to_logical(q, 4 * b4 + i), tag, t, id, scale);
+  return make_float4(out[0], out[1], out[2], out[3]);
+}
+
 // Float4 number vi of an agent's physical weights after adding scale * N_j
-// (stream tag, t, id) to `base`.  The paper controller's rows are in
+// (stream tag, t, id) to `base` (initial weights; the mutation of births
+// walks the row by parts, below).  The paper controller's rows are in
 // logical order, so every float4 is four consecutive parameters.
 __device__ inline float4 mutate4(const WorldDev &wd, int vi, float4 base, uint32_t tag,
                                  uint32_t t, uint32_t id, float scale) {
   const int p = vi * 4;
-  float out[4] = {base.x, base.y, base.z, base.w};
-  const bool paper = wd.controller == ECO_CTRL_PAPER;
+  if (wd.controller == ECO_CTRL_PAPER)
+    return mutate_quad(wd, base, p < PC_NPARAM ? p : -1, PC_NPARAM, tag, t, id, scale);
   const int o = p % BLK_FLOATS;
-  const bool bias_vec = !paper && p < TAIL && o >= BLK_ROWS * NIN;
-  if (!bias_vec) {
-    // multiple of 4, or -1 for padding
-    const int j = paper ? (p < PC_NPARAM ? p : -1) : logical_of_phys(p);
-    const int np = paper ? PC_NPARAM : NPARAM;
-    if (j >= 0) {
-      float z[4];
-      normals4(wd.key0, wd.key1, (uint32_t)j >> 2, t, tag, id, z);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        out[i] = (j + i < np) ? __fadd_rn(out[i], __fmul_rn(scale, z[i])) : 0.f;
-    } else {
-      out[0] = out[1] = out[2] = out[3] = 0.f;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int j = logical_of_phys(p + i);
-      float z[4];
-      normals4(wd.key0, wd.key1, (uint32_t)j >> 2, t, tag, id, z);
-      out[i] = __fadd_rn(out[i], __fmul_rn(scale, z[j & 3]));
-    }
-  }
-  return make_float4(out[0], out[1], out[2], out[3]);
+  if (p < TAIL && o >= BLK_ROWS * NIN)
+    return mutate_bias4(wd, base, p / BLK_FLOATS, (o - BLK_ROWS * NIN) / 4, tag, t, id, scale);
+  return mutate_quad(wd, base, logical_of_phys(p), NPARAM, tag, t, id, scale);
 }
 
-// Work items of the mutation: (birth, chunk of SPAWN_CHUNK float4s of its
-// weight row), dealt to the CTAs round-robin; a CTA's threads take the
-// float4s of an item in turn, each thread issuing the loads of SPAWN_UNROLL
-// float4s before any of their arithmetic.  The birth's world, parent, child
-// and step are looked up once per item (a first version looked them up, with
-// a 64-bit division, for every float4).
+// Work items of the mutation: (birth, part of its weight row), dealt to the
+// CTAs round-robin.  With the LSTM(32) controller the parts are the four
+// hidden-unit blocks (1,440 float4s of gate rows, a row's 45 float4s being
+// consecutive logical parameters, then 8 float4s of biases) and the
+// read-out; with the paper's controller, chunks of SPAWN_CHUNK float4s.  A
+// CTA's threads take the float4s of an item in turn, each thread issuing the
+// loads of SPAWN_UNROLL float4s before any of their arithmetic.  The birth's
+// world, parent, child and step are looked up once per item (a first version
+// looked them up, with a 64-bit division, for every float4; the next one
+// derived each float4's logical index from its physical offset with two
+// divisions).
 constexpr int SPAWN_CHUNK = 1024;
 constexpr int SPAWN_UNROLL = 2;
+constexpr int ROW_VECS = NIN / 4;                 // 45 float4s per gate row
+constexpr int BLK_VECS = BLK_FLOATS / 4;          // 1,448 float4s per block
+constexpr int BLK_W_VECS = BLK_ROWS * ROW_VECS;   // 1,440 of them gate rows
+static_assert(NIN % 4 == 0 && BLK_FLOATS % 4 == 0 && TAIL % 4 == 0, "float4 parts");
 
 // Mutation of every birth of the batch by CTAs cta .. of n_cta.
 __device__ inline void spawn_births(const BatchDev &b, int *pre, int cta, int n_cta) {
@@ -742,12 +780,20 @@ __device__ inline void spawn_births(const BatchDev &b, int *pre, int cta, int n_
     pre[b.n] = run;
   }
   __syncthreads();
+  const bool lstm = b.controller != ECO_CTRL_PAPER;
   const int nvec = b.wstride / 4;
-  const int per = (nvec + SPAWN_CHUNK - 1) / SPAWN_CHUNK;   // items per birth
+  const int per = lstm ? NBLK + 1 : (nvec + SPAWN_CHUNK - 1) / SPAWN_CHUNK;  // parts per birth
   const int items = pre[b.n] * per;
   for (int item = cta; item < items; item += n_cta) {
-    const int bi = item / per, v0 = (item - bi * per) * SPAWN_CHUNK;
-    const int v1 = min(nvec, v0 + SPAWN_CHUNK);
+    const int bi = item / per, part = item - bi * per;
+    int v0, v1;
+    if (lstm) {
+      v0 = part * BLK_VECS;
+      v1 = part < NBLK ? v0 + BLK_VECS : nvec;
+    } else {
+      v0 = part * SPAWN_CHUNK;
+      v1 = min(nvec, v0 + SPAWN_CHUNK);
+    }
     int lo = 0, hi = b.n - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -758,6 +804,7 @@ __device__ inline void spawn_births(const BatchDev &b, int *pre, int cta, int n_
     const int par = wd.birth_parent[k], child = wd.birth_child[k];
     if (!ECO_IN_RANGE(wd, par >= 0 && par < wd.C && child >= 0 && child < wd.C)) continue;
     const uint32_t t = wd.ctr->births_t;
+    const float sigma = wd.mut_std;
     const float4 *src = reinterpret_cast<const float4 *>(wd.weights + (size_t)par * b.wstride);
     float4 *dst = reinterpret_cast<float4 *>(wd.weights + (size_t)child * b.wstride);
     for (int vi = v0 + (int)threadIdx.x; vi < v1; vi += SPAWN_UNROLL * (int)blockDim.x) {
@@ -770,7 +817,25 @@ __device__ inline void spawn_births(const BatchDev &b, int *pre, int cta, int n_
 #pragma unroll
       for (int u = 0; u < SPAWN_UNROLL; ++u) {
         const int v = vi + u * (int)blockDim.x;
-        if (v < v1) dst[v] = mutate4(wd, v, in[u], TAG_MUT, t, (uint32_t)par, wd.mut_std);
+        if (v >= v1) continue;
+        float4 r;
+        if (!lstm) {
+          const int j = 4 * v;
+          r = mutate_quad(wd, in[u], j < PC_NPARAM ? j : -1, PC_NPARAM, TAG_MUT, t, par, sigma);
+        } else if (part == NBLK) {   // read-out, in logical order; then padding
+          const int j = 4 * v;
+          r = mutate_quad(wd, in[u], j < NPARAM ? j : -1, NPARAM, TAG_MUT, t, par, sigma);
+        } else {
+          const int f = v - v0;
+          if (f < BLK_W_VECS) {
+            const int l = f / ROW_VECS, k4 = f - l * ROW_VECS;
+            const int j = blk_row_to_logical(part, l) * NIN + 4 * k4;
+            r = mutate_quad(wd, in[u], j, NPARAM, TAG_MUT, t, par, sigma);
+          } else {
+            r = mutate_bias4(wd, in[u], part, f - BLK_W_VECS, TAG_MUT, t, par, sigma);
+          }
+        }
+        dst[v] = r;
       }
     }
   }
@@ -784,8 +849,10 @@ constexpr int SPAWN_CTAS_PER_SM = 4;
 static_assert(REGROW_THREADS == SPAWN_THREADS, "one block size for the tail kernel");
 
 __global__ void __launch_bounds__(SPAWN_THREADS, 4) k_tail(const __grid_constant__ BatchDev b) {
-  __shared__ uint32_t tile[TILE_ROWS_MAX][TILE_COLS];
-  __shared__ int pre[1025];
+  __shared__ union {
+    RegrowSmem rg;    // regrowth CTAs
+    int pre[1025];    // mutation CTAs: births per world, prefix
+  } sm;
   // The controller kernel after this one starts its reads early when this
   // grid is small enough (b.tail_early) to leave room for it beside the
   // tail's CTAs; a larger grid (many worlds' regrowth tiles) lets it launch
@@ -793,14 +860,14 @@ __global__ void __launch_bounds__(SPAWN_THREADS, 4) k_tail(const __grid_constant
   // halve the tail's occupancy while their gather warps wait for it anyway.
   if ((int)blockIdx.x < b.total_tiles) {
     // walls and thresholds are never written by a step: read before waiting
-    const RegrowFixed f = regrow_fixed(b, blockIdx.x);
+    const RegrowPlace f = regrow_fixed(b, blockIdx.x, sm.rg);
     pdl_wait();
     if (b.tail_early) pdl_release();
-    regrow_run(f, tile);
+    regrow_run(f, b.regrow_k, sm.rg);
   } else {
     pdl_wait();
     if (b.tail_early) pdl_release();
-    spawn_births(b, pre, blockIdx.x - b.total_tiles, gridDim.x - b.total_tiles);
+    spawn_births(b, sm.pre, blockIdx.x - b.total_tiles, gridDim.x - b.total_tiles);
   }
   if (!b.tail_early) pdl_release();
 }
@@ -828,9 +895,16 @@ void preload_agents() {
   cudaFuncGetAttributes(&a, k_scan_prefix);
   cudaFuncGetAttributes(&a, k_scan_lists);
   cudaFuncGetAttributes(&a, k_scan_children);
-  cudaFuncGetAttributes(&a, k_tail);
   cudaFuncGetAttributes(&a, k_agents_cluster);
   cudaFuncGetAttributes(&a, k_agents_single);
+  // The tail kernel asks for the shared-memory carveout of the controller
+  // kernel that follows it (the largest), so that an SM running tail CTAs
+  // need not change its split between L1 and shared memory before the
+  // controller kernel's CTAs start beside them (programmatic dependent
+  // launch).
+  cudaFuncGetAttributes(&a, k_tail);
+  cudaFuncSetAttribute(k_tail, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
 }
 
 void launch_move_apply(const BatchDev &b, cudaStream_t s) {

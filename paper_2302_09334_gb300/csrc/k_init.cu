@@ -253,6 +253,80 @@ int launch_weights_from_host(const float *host_dev, float *rows, int n, int cont
   return (int)cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// State loads.
+// ---------------------------------------------------------------------------
+__global__ void k_load_counters(Counters *ctr, LoadCounters v) {
+  if (v.set) {
+    ctr->t = v.t;
+    ctr->births = v.births;
+    ctr->deaths = v.deaths;
+    ctr->dropped = v.dropped;
+    ctr->births_last = v.births_last;
+    ctr->deaths_last = v.deaths_last;
+    ctr->dropped_last = v.dropped_last;
+    ctr->agent_steps = v.agent_steps;
+  }
+  ctr->deaths_step = 0;
+  ctr->n_births = 0;
+  ctr->use_forced = 0;
+}
+
+void launch_load_counters(Counters *ctr, const LoadCounters &v, cudaStream_t s) {
+  k_load_counters<<<1, 1, 0, s>>>(ctr, v);
+}
+
+// One thread per word: bit b of word (y, w) is cell (y, 32 w + b).
+__global__ void k_pack_plane(const uint8_t *cells, int H, int W, int Wp, uint32_t *words) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= H * Wp) return;
+  const int y = i / Wp, x0 = (i % Wp) * 32;
+  const uint8_t *row = cells + (size_t)y * W;
+  uint32_t v = 0u;
+  for (int b = 0; b < 32 && x0 + b < W; ++b)
+    if (row[x0 + b]) v |= 1u << b;
+  words[i] = v;
+}
+
+void launch_pack_plane(const uint8_t *cells, int H, int W, int Wp, uint32_t *words,
+                       cudaStream_t s) {
+  const int n = H * Wp;
+  if (n > 0) k_pack_plane<<<(n + 255) / 256, 256, 0, s>>>(cells, H, W, Wp, words);
+}
+
+// Grid-stride over the C slots (scalars and logits) and over the C x HID
+// elements of h and c.
+__global__ void k_load_slots(WorldDev wd, SlotSources src, float *h_dst) {
+  const int C = wd.C;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (long long i = i0; i < C; i += stride) {
+    if (src.alive) wd.alive[i] = src.alive[i];
+    if (src.ate) wd.ate[i] = src.ate[i];
+    if (src.y) wd.y[i] = src.y[i];
+    if (src.x) wd.x[i] = src.x[i];
+    if (src.repr) wd.repr_ctr[i] = src.repr[i];
+    if (src.low) wd.low_ctr[i] = src.low[i];
+    if (src.age) wd.age[i] = src.age[i];
+    if (src.action) wd.action[i] = src.action[i];
+    if (src.prev) wd.prev_act[i] = src.prev[i];
+    if (src.energy) wd.energy[i] = src.energy[i];
+    if (src.logits)
+      for (int a = 0; a < 8; ++a)
+        wd.logits[i * 8 + a] = a < NACT ? src.logits[i * NACT + a] : 0.f;
+  }
+  const long long n = (long long)C * HID;
+  for (long long i = i0; i < n; i += stride) {
+    if (src.h) h_dst[i] = src.h[i];
+    if (src.c) wd.c[i] = src.c[i];
+  }
+}
+
+void launch_load_slots(const WorldDev &wd, const SlotSources &src, float *h_dst, int n_sms,
+                       cudaStream_t s) {
+  if (wd.C > 0) k_load_slots<<<4 * n_sms, 256, 0, s>>>(wd, src, h_dst);
+}
+
 void launch_weights_to_logical(const float *physical, float *logical, size_t lpitch, int n,
                                int controller, int n_sms, cudaStream_t s) {
   if (n > 0)

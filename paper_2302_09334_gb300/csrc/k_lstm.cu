@@ -3,8 +3,9 @@
 //
 // Every agent has its own 93 KB of FP32 weights, used once per step, so the
 // step is a batched GEMV bound by HBM bandwidth (about 0.5 flop per byte).
-// A persistent grid of one CTA per SM runs a warp-specialised pipeline with
-// no global synchronisation:
+// A persistent grid of one CTA per SM (or two, each with half the ring: a
+// launch-shape choice) runs a warp-specialised pipeline with no global
+// synchronisation:
 //   * CTA b takes the batch's agents b, b + G, b + 2G, ... (world-major,
 //     alive-list order; G CTAs), so its first agent is known before the
 //     population is: with one world its slot is requested together with the
@@ -13,8 +14,8 @@
 //     lane each), and each agent's four weight blocks (a block = the 32
 //     gate rows of 8 hidden units, 23,168 B; the last block also carries
 //     the read-out) streamed with plain (non-multicast) cp.async.bulk copies
-//     into an 8-stage shared-memory ring (two agents in flight, ~190 KB per
-//     SM);
+//     into a shared-memory ring of LSTAGES blocks (8: two agents in flight,
+//     ~190 KB; 4 with two CTAs per SM);
 //   * four gather warps, taking the agents in turn: slots, positions and
 //     energies of 32 of their agents at a time, then per agent the 7x7x3
 //     window (row masks of the bit planes staged through shared memory),
@@ -37,7 +38,6 @@
 
 namespace eco {
 
-constexpr int LSTAGES = 8;                 // two agents of four blocks
 constexpr int VRING = 8;                   // gathered inputs in flight
 constexpr int NCOMP = 4;                   // compute warps (one per block)
 constexpr int NGATH = 4;                   // gather warps
@@ -73,6 +73,7 @@ struct AgentDesc {
   uint32_t t;
 };
 
+template <int LSTAGES>
 struct __align__(128) LstmSmem {
   float stage[LSTAGES][STAGE_FLOATS];
   VEntry ring[VRING];
@@ -83,7 +84,8 @@ struct __align__(128) LstmSmem {
   int issued;
   volatile int abort_flag;
 };
-static_assert(offsetof(LstmSmem, ring) % 16 == 0 && (STAGE_FLOATS * 4) % 16 == 0,
+static_assert(offsetof(LstmSmem<4>, ring) % 16 == 0 && offsetof(LstmSmem<8>, ring) % 16 == 0 &&
+                  (STAGE_FLOATS * 4) % 16 == 0,
               "bulk-copy stages and ring entries are 16-byte aligned");
 
 __device__ inline uint32_t smem_u32(const void *p) {
@@ -262,9 +264,11 @@ __device__ inline AgentRef agent_valid(const BatchDev &b, AgentRef r, long long 
   return r;
 }
 
-__global__ void __launch_bounds__(LTHREADS, 1) k_lstm(const __grid_constant__ BatchDev b) {
+// LSTAGES weight blocks in the ring, MINB CTAs per SM.
+template <int LSTAGES, int MINB>
+__global__ void __launch_bounds__(LTHREADS, MINB) k_lstm(const __grid_constant__ BatchDev b) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  LstmSmem &sm = *reinterpret_cast<LstmSmem *>(smem_raw);
+  LstmSmem<LSTAGES> &sm = *reinterpret_cast<LstmSmem<LSTAGES> *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned FULL = 0xFFFFFFFFu;
   const int G = gridDim.x;
@@ -570,18 +574,28 @@ void launch_wait_selftest(int *status, unsigned long long limit_ns, cudaStream_t
   k_wait_selftest<<<1, 32, 0, s>>>(status, limit_ns);
 }
 
+// Two shapes: one CTA per SM with an 8-block ring (~199 KB of shared
+// memory), or two CTAs per SM with a 4-block ring each (~108 KB).
+static_assert(2 * (sizeof(LstmSmem<4>) + 1024) <= 228 * 1024, "two 4-stage CTAs fit an SM");
+
 void configure_lstm() {
-  cudaFuncSetAttribute(k_lstm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(LstmSmem));
+  cudaFuncSetAttribute(k_lstm<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(LstmSmem<8>));
+  cudaFuncSetAttribute(k_lstm<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(LstmSmem<4>));
 }
 
 void preload_lstm() {
   cudaFuncAttributes a;
-  cudaFuncGetAttributes(&a, k_lstm);
+  cudaFuncGetAttributes(&a, k_lstm<8, 1>);
+  cudaFuncGetAttributes(&a, k_lstm<4, 2>);
 }
 
 void launch_lstm(const BatchDev &b, cudaStream_t s) {
-  launch_step_kernel(k_lstm, b.n_sms, LTHREADS, sizeof(LstmSmem), s, b);
+  if (b.lstm_ctas == 2)
+    launch_step_kernel(k_lstm<4, 2>, 2 * b.n_sms, LTHREADS, sizeof(LstmSmem<4>), s, b);
+  else
+    launch_step_kernel(k_lstm<8, 1>, b.n_sms, LTHREADS, sizeof(LstmSmem<8>), s, b);
 }
 
 }  // namespace eco

@@ -323,6 +323,8 @@ __global__ void __launch_bounds__(PC_THREADS, PC_CTAS_PER_SM)
 void preload_paper() {
   cudaFuncSetAttribute(k_paper, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sizeof(PcSmem));
+  cudaFuncSetAttribute(k_paper, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
 }
 
 void launch_paper_ctrl(const BatchDev &b, cudaStream_t s) {

@@ -97,6 +97,21 @@ class _Configurable:
         check(self._fn("set_config")(self._h, int(c["fused"]), int(c["spawn_ctas_per_sm"]),
                                      int(c["steps_per_graph"])), f"eco_{self._prefix}_set_config")
 
+    def get_shape(self) -> dict:
+        rk, lc = ctypes.c_int(), ctypes.c_int()
+        check(self._fn("get_shape")(self._h, ctypes.byref(rk), ctypes.byref(lc)),
+              f"eco_{self._prefix}_get_shape")
+        return {"regrow_rows_per_cta": rk.value, "lstm_ctas_per_sm": lc.value}
+
+    def set_shape(self, regrow_rows_per_cta=None, lstm_ctas_per_sm=None) -> None:
+        """Kernel shapes (results unchanged): regrowth tiles stacked per CTA
+        (0: chosen by size, or 1, 2, 4, 8) and controller CTAs per SM (1, 2);
+        None keeps a shape as it is."""
+        c = self.get_shape()
+        rk = c["regrow_rows_per_cta"] if regrow_rows_per_cta is None else regrow_rows_per_cta
+        lc = c["lstm_ctas_per_sm"] if lstm_ctas_per_sm is None else lstm_ctas_per_sm
+        check(self._fn("set_shape")(self._h, int(rk), int(lc)), f"eco_{self._prefix}_set_shape")
+
     def autotune(self, trial_steps: int = 16) -> dict:
         """Time real steps under each candidate configuration and keep the
         fastest; the worlds advance by the returned steps_taken."""

@@ -55,12 +55,46 @@ def test_every_config_gives_the_same_state(eco):
         w.close()
 
 
+# 70 rows: 9 tiles of 8 rows, stacked 2, 4 and 8 per CTA leave ragged columns
+PS = EcoParams(H=70, W=200, capacity=1200, n_agents0=300, t_repr=25, e_repr=0.4, max_age=140)
+
+
+def test_every_shape_gives_the_same_state(eco):
+    shapes = [(1, 1), (2, 2), (4, 1), (8, 2), (0, 2)]
+    worlds = []
+    for rk, lc in shapes:
+        w = eco.World(PS, seed=23)
+        w.set_shape(regrow_rows_per_cta=rk, lstm_ctas_per_sm=lc)
+        got = w.get_shape()
+        assert got["lstm_ctas_per_sm"] == lc
+        assert got["regrow_rows_per_cta"] == (rk if rk else got["regrow_rows_per_cta"])
+        assert got["regrow_rows_per_cta"] in (1, 2, 4, 8)
+        worlds.append(w)
+    for n in (30, 90):
+        for w in worlds:
+            w.step(n)
+        ref = _state(worlds[0], PS)
+        assert ref["counters"][2] > 0          # births happened
+        for (sh, w) in zip(shapes[1:], worlds[1:]):
+            _equal(ref, _state(w, PS), f"shape {sh} after {int(ref['counters'][0])} steps")
+    # a shape changed between steps continues the same run
+    worlds[0].set_shape(regrow_rows_per_cta=8, lstm_ctas_per_sm=2)
+    worlds[1].set_shape(regrow_rows_per_cta=1, lstm_ctas_per_sm=1)
+    for w in worlds[:2]:
+        w.step(20)
+    _equal(_state(worlds[0], PS), _state(worlds[1], PS), "shapes swapped")
+    for w in worlds:
+        w.close()
+
+
 def test_world_autotune_steps_are_plain_steps(eco):
     a, b = eco.World(P, seed=5), eco.World(P, seed=5)
     r = a.autotune(trial_steps=4)
     assert r["steps_taken"] > 0 and r["ms_per_step_best"] > 0
     cfg = a.get_config()
     assert cfg == {k: r[k] for k in cfg}
+    shape = a.get_shape()
+    assert shape == {k: r[k] for k in shape}
     b.step(r["steps_taken"])
     _equal(_state(a, P), _state(b, P), "after tuning")
     a.step(40)
@@ -97,6 +131,11 @@ def test_invalid_configs_refused(eco):
                {"spawn_ctas_per_sm": 33}):
         with pytest.raises(EcoError) as e:
             big.set_config(**kw)
+        assert e.value.code == ECO_EINVAL
+    for kw in ({"regrow_rows_per_cta": 3}, {"regrow_rows_per_cta": 16},
+               {"lstm_ctas_per_sm": 0}, {"lstm_ctas_per_sm": 3}):
+        with pytest.raises(EcoError) as e:
+            big.set_shape(**kw)
         assert e.value.code == ECO_EINVAL
     r = big.autotune(trial_steps=1)          # the fused candidate is skipped
     assert r["fused"] == 0
