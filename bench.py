@@ -298,14 +298,19 @@ def bench_ours(args, params, rank, world_size, dist):
         tuner = World(params, seed=1000 + rank, device=local)
         tuned = tuner.autotune(trial_steps=8)
         cfg = {k: tuned[k] for k in CONFIG_KEYS + SHAPE_KEYS}
-        if params.controller == 0:
-            # the tuner's trials run back to back, with the weights left in
-            # L2 from step to step; the timed steps start from a flushed L2,
-            # where the controller kernel's shape matters more: both shapes
-            # are timed again that way (one-step graphs, flush before each)
-            cfg, shape_check = flushed_shape_check(tuner, cfg, flush, flush_read, flush_sink)
         tuner.close()
         del tuner
+        if params.controller == 0:
+            # the tuner's trials run back to back, with the weights left in
+            # L2 from step to step, and reach populations the timed steps do
+            # not; the timed steps start from a flushed L2, where the
+            # controller kernel's shape matters more: both shapes are timed
+            # again that way on another fresh world of the same shape (one-step
+            # graphs, flush before each)
+            probe = World(params, seed=2000 + rank, device=local)
+            cfg, shape_check = flushed_shape_check(probe, cfg, flush, flush_read, flush_sink)
+            probe.close()
+            del probe
     # the timed world steps by plain one-step CUDA graphs; its twin (same
     # seed, hence the same states step by step) launches each step's kernels
     # on the stream with CUDA events around every kernel for the per-kernel
