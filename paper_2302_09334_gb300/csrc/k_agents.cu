@@ -363,6 +363,27 @@ __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
   uint32_t *res = (t & 1u) ? wd.res0 : wd.res1;  // plane after this step's regrowth
   float *h_next = (t & 1u) ? wd.h0 : wd.h1;
 
+  // In a cluster the first phase takes the slots in chunks of 32, dealt
+  // round-robin to the CTAs and within a CTA to its warps (chunk c = (k WARPS
+  // + warp) NCTA + rank), so that the live agents, which fill the lowest
+  // slots, spread over every SM of the cluster: their scattered slot-map,
+  // claim and resource accesses are what the phase's time goes to, and one SM
+  // took them all at 1,000 agents (5.6 µs against 2.4 spread).  The later
+  // phases take contiguous ranges (their scans follow slot order) and reload
+  // the slot state the first one wrote.  One CTA keeps its contiguous slots
+  // throughout.
+  constexpr int WARPS = THREADS / 32;
+  const int lane = (int)threadIdx.x & 31, warp = (int)threadIdx.x >> 5;
+  int ms[CL_SPT];   // first-phase slot of k, or -1
+#pragma unroll
+  for (int k = 0; k < CL_SPT; ++k) {
+    if constexpr (NCTA > 1) {
+      const int s = ((k * WARPS + warp) * NCTA + rank) * 32 + lane;
+      ms[k] = s < C ? s : -1;
+    } else {
+      ms[k] = k < ns ? s0 + k : -1;
+    }
+  }
   int al[CL_SPT], py[CL_SPT], px[CL_SPT], tgt[CL_SPT], age[CL_SPT], low[CL_SPT],
       rep[CL_SPT], bcell[CL_SPT];
   float en[CL_SPT];
@@ -370,8 +391,8 @@ __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
 #pragma unroll
   for (int k = 0; k < CL_SPT; ++k) {
     al[k] = 0;
-    if (k < ns) {
-      const int s = s0 + k;
+    if (ms[k] >= 0) {
+      const int s = ms[k];
       al[k] = __ldcg(&wd.alive[s]);
       py[k] = __ldcg(&wd.y[s]);
       px[k] = __ldcg(&wd.x[s]);
@@ -384,8 +405,8 @@ __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
   pdl_wait_and_release();
 #pragma unroll
   for (int k = 0; k < CL_SPT; ++k) {
-    if (k < ns) {
-      const int s = s0 + k;
+    if (ms[k] >= 0) {
+      const int s = ms[k];
       tgt[k] = wd.target[s];
       kil[k] = wd.killed[s] != 0;
     }
@@ -395,9 +416,10 @@ __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
 #pragma unroll
   for (int k = 0; k < CL_SPT; ++k) {
     if (!al[k]) continue;
-    const int s = s0 + k;
+    const int s = ms[k];
     if (!ECO_IN_RANGE(wd, py[k] >= 0 && py[k] < wd.H && px[k] >= 0 && px[k] < W)) {
       al[k] = 0;
+      wd.alive[s] = 0;   // (range-checked build) out of the step from here on
       continue;
     }
     // The claim and the resource words of both possible final cells are
@@ -480,6 +502,21 @@ __device__ __forceinline__ void agents_fused_body(const BatchDev &b) {
       wd.alive_new[i] = 0;
     if (rank == 0 && threadIdx.x == 0) finish_step(wd, 0, 0, pop0, t);
     return;
+  }
+  // slot state of the contiguous range, as the first phase left it (the
+  // barrier above makes every CTA's writes visible)
+  if constexpr (NCTA > 1) {
+#pragma unroll
+    for (int k = 0; k < CL_SPT; ++k) {
+      al[k] = 0;
+      if (k < ns) {
+        const int s = s0 + k;
+        al[k] = __ldcg(&wd.alive[s]);
+        py[k] = __ldcg(&wd.y[s]);
+        px[k] = __ldcg(&wd.x[s]);
+        rep[k] = __ldcg(&wd.repr_ctr[s]);
+      }
+    }
   }
   // ---- birth claims: first free N, S, E, W cell; lowest parent slot wins
 #pragma unroll

@@ -154,7 +154,7 @@ class Server:
 
     # share of the target left for the growth of admitted populations
     # (births after admission; capacities are 4x the initial populations)
-    TARGET_HEADROOM = 0.7
+    TARGET_HEADROOM = 0.65
 
     def _fits_target(self, req: Request) -> bool:
         if self.target is None or not self.live:
