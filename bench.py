@@ -294,13 +294,17 @@ def bench_ours(args, params, rank, world_size, dist):
         probe = World(params, seed=1000 + rank, device=local)
         cfg = {**probe.get_config(), **probe.get_shape()}
         probe.close()
+        if args.lstm_ctas:
+            cfg["lstm_ctas_per_sm"] = args.lstm_ctas
     else:
         tuner = World(params, seed=1000 + rank, device=local)
         tuned = tuner.autotune(trial_steps=8)
         cfg = {k: tuned[k] for k in CONFIG_KEYS + SHAPE_KEYS}
         tuner.close()
         del tuner
-        if params.controller == 0:
+        if args.lstm_ctas:
+            cfg["lstm_ctas_per_sm"] = args.lstm_ctas
+        elif params.controller == 0:
             # the tuner's trials run back to back, with the weights left in
             # L2 from step to step, and reach populations the timed steps do
             # not; the timed steps start from a flushed L2, where the
@@ -823,6 +827,9 @@ def main():
                     help="chunk-latency target (s per 100-step report) for admission")
     ap.add_argument("--no-tune", action="store_true",
                     help="default launch configuration (no tuner world before the timed one)")
+    ap.add_argument("--lstm-ctas", type=int, choices=(1, 2), default=None,
+                    help="controller-kernel CTAs per SM of the headline world (default: "
+                         "the tuner's choice checked with flushed steps, or 1 with --no-tune)")
     ap.add_argument("--large-steps", type=int, default=100)
     ap.add_argument("--large-warmup", type=int, default=10)
     ap.add_argument("--paper-steps", type=int, default=20000)
