@@ -169,6 +169,42 @@ def test_batch_equals_alone(eco):
             np.testing.assert_array_equal(sa[k], sb[k], err_msg=k)
 
 
+def test_load_state_keeping_counters_and_a_weight_range(eco):
+    """load_state with set_counters=False keeps the device's counters (the
+    step counter, read back, decides which buffer of the plane and h pairs
+    is current), and a weight range starting past slot 0 replaces exactly
+    those rows: the world then steps as the one the state was read from."""
+    p = EcoParams(H=30, W=60, capacity=400, n_agents0=150, t_repr=20, e_repr=0.4)
+    src = eco.World(p, 21)
+    src.step(37)                                  # odd step counter
+    st = src.read_state(weights=(0, p.capacity))
+    dst = eco.World(p, 22)
+    dst.step(37)                                  # same step counter, another history
+    c_dst = dst.read_state(fields=())["counters"]
+    dst.load_state({k: v for k, v in st.items() if k != "weights"}, set_counters=False)
+    c_after = dst.read_state(fields=())["counters"]
+    np.testing.assert_array_equal(c_after[[0, 2, 3, 4]], c_dst[[0, 2, 3, 4]])  # t, cumulative
+    assert c_after[1] == st["counters"][1]        # population: the loaded alive flags
+    # weights in two ranges, the second starting past slot 0
+    lo = 137
+    dst.load_state({"weights": st["weights"][:lo]}, set_counters=False, weights_first=0)
+    dst.load_state({"weights": st["weights"][lo:]}, set_counters=False, weights_first=lo)
+    mid = dst.read_state(weights=(0, p.capacity))
+    for k in ("alive", "y", "x", "energy", "h", "c", "res", "wall", "weights"):
+        np.testing.assert_array_equal(mid[k], st[k], err_msg=k)
+    src.step(25)
+    dst.step(25)
+    a, b = src.read_state(weights=(0, p.capacity)), dst.read_state(weights=(0, p.capacity))
+    assert a["counters"][2] > st["counters"][2]   # births in the 25 steps
+    for k in a:
+        if k == "counters":
+            np.testing.assert_array_equal(a[k][[0, 1, 5, 6, 7]], b[k][[0, 1, 5, 6, 7]])
+        else:
+            np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    src.close()
+    dst.close()
+
+
 def test_load_rejects_inconsistent_state(eco):
     from paper_2302_09334_gb300._lib import EcoError, ECO_ESTATE
     p = EcoParams(H=8, W=8, capacity=4, n_agents0=2)
