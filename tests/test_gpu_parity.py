@@ -173,14 +173,21 @@ def test_load_state_keeping_counters_and_a_weight_range(eco):
     """load_state with set_counters=False keeps the device's counters (the
     step counter, read back, decides which buffer of the plane and h pairs
     is current), and a weight range starting past slot 0 replaces exactly
-    those rows: the world then steps as the one the state was read from."""
+    those rows: the world then steps as the one the state was read from
+    (same seed, so the same random streams)."""
     p = EcoParams(H=30, W=60, capacity=400, n_agents0=150, t_repr=20, e_repr=0.4)
     src = eco.World(p, 21)
     src.step(37)                                  # odd step counter
     st = src.read_state(weights=(0, p.capacity))
-    dst = eco.World(p, 22)
-    dst.step(37)                                  # same step counter, another history
+    # the same seed (the random streams are keyed by it, not by the state),
+    # another history: the initial state of seed 22, then as many steps
+    other = eco.World(p, 22)
+    dst = eco.World(p, 21)
+    dst.load_state(other.read_state(weights=(0, p.capacity)))
+    other.close()
+    dst.step(37)                                  # same step counter
     c_dst = dst.read_state(fields=())["counters"]
+    assert c_dst[0] == st["counters"][0] and c_dst[2] != st["counters"][2]
     dst.load_state({k: v for k, v in st.items() if k != "weights"}, set_counters=False)
     c_after = dst.read_state(fields=())["counters"]
     np.testing.assert_array_equal(c_after[[0, 2, 3, 4]], c_dst[[0, 2, 3, 4]])  # t, cumulative
