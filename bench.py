@@ -475,11 +475,11 @@ def bench_ours(args, params, rank, world_size, dist):
         "analysis": analysis_summary(windows, life_expectancy),
     }
     if world_size == 1 and not args.no_many:
-        line["batched"] = bench_batched(args, local)
-        line["served"] = bench_served(args, local)
-        line["paper_preset"] = bench_paper_preset(args, local)
-        line["large"] = bench_large(args, local)
-        line["held"] = bench_held(args, local)
+        legs = {"batched": bench_batched, "served": bench_served,
+                "paper_preset": bench_paper_preset, "large": bench_large, "held": bench_held}
+        for name, leg in legs.items():
+            if args.legs is None or name in args.legs:
+                line[name] = leg(args, local)
     if not args.no_cpu_baseline:
         cores = args.cpu_cores or os.cpu_count() or 1
         v, steps, dt = run_oracle_pool(params, args.cpu_budget, 0, 100000, cores)
@@ -813,6 +813,9 @@ def main():
     ap.add_argument("--held", action="store_true",
                     help="no energy decay and no births: the population stays at n_agents0")
     ap.add_argument("--n-agents", type=int, default=None, help="override n_agents0")
+    ap.add_argument("--legs", nargs="+", default=None,
+                    choices=("batched", "served", "paper_preset", "large", "held"),
+                    help="run only these extra legs (default: all)")
     ap.add_argument("--no-many", action="store_true",
                     help="skip the batched (64 worlds) and served measurements")
     ap.add_argument("--batched-steps", type=int, default=1000)
