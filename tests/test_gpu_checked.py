@@ -1,6 +1,7 @@
 """The range-checked build (libecoevo_checked.so, ECO_CHECKED=1): every index
 the kernels read from device memory is checked before use.  Forced parity
-runs on both slot-phase paths, free runs at 200x400, a mixed batch, the
+runs on both slot-phase paths, free runs at 200x400 (in both kernel shapes),
+a mixed batch, the
 paper's controller, the analysis and lab calls all finish with no index out
 of range (eco_world_sync / eco_batch_sync would return ECO_EBOUNDS), and the
 checked library's results equal the regular one's.  Runs in a child process
@@ -41,6 +42,8 @@ states = []
 for fused in (1, 0):
     w = world.World(big, seed=1)
     w.set_config(fused=fused, spawn_ctas_per_sm=2 if fused else 8)
+    if not fused:   # the other kernel shapes too
+        w.set_shape(regrow_rows_per_cta=2, lstm_ctas_per_sm=2)
     w.step(100)
     w.analysis()
     w.lab_window()
@@ -54,6 +57,7 @@ specs = [(EcoParams(H=20 + 7 * i, W=40 + 11 * i, n_agents0=30 + 20 * i,
                     capacity=4 * (30 + 20 * i)), i) for i in range(6)]
 ws = [world.World(q, s) for q, s in specs]
 b = world.Batch(ws)
+b.set_shape(regrow_rows_per_cta=4, lstm_ctas_per_sm=2)
 b.step(100)
 b.sync()
 b.close()
