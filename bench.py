@@ -195,12 +195,12 @@ def configure(target, cfg: dict) -> None:
 
 
 def flushed_shape_check(w, cfg: dict, flush, flush_read, sink, steps: int = 8,
-                        rounds: int = 3, margin: float = 0.03):
+                        rounds: int = 5):
     """Controller CTAs per SM (1 or 2) timed on world `w` with L2 flushed
-    before every step, as the timed region runs: three rounds of `steps`
-    one-step graphs per shape, round-robin; the median decides, and the
-    tuned shape is left only for one more than `margin` faster.  Returns the
-    configuration and the medians."""
+    before every step, as the timed region runs: `rounds` rounds of `steps`
+    one-step graphs per shape, round-robin; the lower median decides (the
+    tuner's own choice, made with the weights left in L2, gets no
+    precedence).  Returns the configuration and the medians."""
     import statistics
     import torch
     stream = w.stream
@@ -222,11 +222,8 @@ def flushed_shape_check(w, cfg: dict, flush, flush_read, sink, steps: int = 8,
                 e1.synchronize()
                 times[lc].append(e0.elapsed_time(e1))
     med = {lc: statistics.median(v) for lc, v in times.items()}
-    cur = cfg["lstm_ctas_per_sm"]
-    other = 3 - cur
     out = dict(cfg)
-    if med[other] < (1.0 - margin) * med[cur]:
-        out["lstm_ctas_per_sm"] = other
+    out["lstm_ctas_per_sm"] = min(med, key=med.get)
     configure(w, out)
     return out, {"flushed_step_ms_lstm_ctas_1": med[1], "flushed_step_ms_lstm_ctas_2": med[2],
                  "chosen": out["lstm_ctas_per_sm"]}
