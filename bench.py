@@ -194,22 +194,28 @@ def configure(target, cfg: dict) -> None:
     target.set_shape(**{k: cfg[k] for k in SHAPE_KEYS})
 
 
-def flushed_shape_check(w, cfg: dict, flush, flush_read, sink, steps: int = 8,
-                        rounds: int = 5):
-    """Controller CTAs per SM (1 or 2) timed on world `w` with L2 flushed
-    before every step, as the timed region runs: `rounds` rounds of `steps`
-    one-step graphs per shape, round-robin; the lower median decides (the
-    tuner's own choice, made with the weights left in L2, gets no
-    precedence).  Returns the configuration and the medians."""
+def flushed_shape_check(make_world, cfg: dict, flush, flush_read, sink, steps: int = 8,
+                        rounds: int = 4):
+    """Controller CTAs per SM (1 or 2) timed with L2 flushed before every
+    step, as the timed region runs: one fresh world per shape (from
+    `make_world()`, the same seed), `rounds` rounds of `steps` one-step
+    graphs each, round-robin between the two, all before the first births
+    (so both time the population the timed steps have); the lower median
+    decides (the tuner's own choice, made with the weights left in L2, gets
+    no precedence).  Returns the configuration and the medians."""
     import statistics
     import torch
-    stream = w.stream
+    worlds = {}
+    for lc in (1, 2):
+        w = make_world()
+        configure(w, {**cfg, "steps_per_graph": 1, "lstm_ctas_per_sm": lc})
+        w.step(1)   # the one-step graph captured before the timing
+        w.sync()
+        worlds[lc] = w
     times = {1: [], 2: []}
     for _ in range(rounds):
-        for lc in (1, 2):
-            configure(w, {**cfg, "steps_per_graph": 1, "lstm_ctas_per_sm": lc})
-            w.step(1)   # graphs captured before the timing
-            w.sync()
+        for lc, w in worlds.items():
+            stream = w.stream
             for _ in range(steps):
                 with torch.cuda.stream(stream):
                     flush.fill_(1)
@@ -221,10 +227,11 @@ def flushed_shape_check(w, cfg: dict, flush, flush_read, sink, steps: int = 8,
                 e1.record(stream)
                 e1.synchronize()
                 times[lc].append(e0.elapsed_time(e1))
+    for w in worlds.values():
+        w.close()
     med = {lc: statistics.median(v) for lc, v in times.items()}
     out = dict(cfg)
     out["lstm_ctas_per_sm"] = min(med, key=med.get)
-    configure(w, out)
     return out, {"flushed_step_ms_lstm_ctas_1": med[1], "flushed_step_ms_lstm_ctas_2": med[2],
                  "chosen": out["lstm_ctas_per_sm"]}
 
@@ -308,10 +315,9 @@ def bench_ours(args, params, rank, world_size, dist):
             # controller kernel's shape matters more: both shapes are timed
             # again that way on another fresh world of the same shape (one-step
             # graphs, flush before each)
-            probe = World(params, seed=2000 + rank, device=local)
-            cfg, shape_check = flushed_shape_check(probe, cfg, flush, flush_read, flush_sink)
-            probe.close()
-            del probe
+            cfg, shape_check = flushed_shape_check(
+                lambda: World(params, seed=2000 + rank, device=local), cfg, flush, flush_read,
+                flush_sink)
     # the timed world steps by plain one-step CUDA graphs; its twin (same
     # seed, hence the same states step by step) launches each step's kernels
     # on the stream with CUDA events around every kernel for the per-kernel
