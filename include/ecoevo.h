@@ -214,7 +214,12 @@ int eco_world_read_state(EcoWorld *world, EcoState *out);
  * set_counters != 0.  h and c become the recurrent state for the next step.
  * A new analysis window (eco_world_analysis_async) starts at the loaded
  * state.  The births of the world's last step get their weights first, so
- * that rows `in` leaves out hold final weights.  Synchronous.  Errors:
+ * that rows `in` leaves out hold final weights.  Page-locked host buffers
+ * are read by kernels through their device addresses (a weight buffer must
+ * then start on a 16-byte boundary, else it is copied like pageable memory);
+ * the weight rows go on a second stream of the world, created at the first
+ * call, beside the rest of the state.  Synchronous: both streams are done
+ * when the call returns.  Errors:
  * ECO_EINVAL, ECO_ESTATE (two agents on one
  * cell, an agent on a wall or off the grid, a negative age, res set on a
  * wall), ECO_ECUDA. */
