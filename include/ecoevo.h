@@ -358,8 +358,9 @@ int eco_batch_get_config(const EcoBatch *batch, int *fused, int *spawn_ctas_per_
  * configuration, no choice changes any result:
  *   regrow_rows_per_cta  8-row x 128-cell regrowth tiles stacked in one CTA
  *                        of the tail kernel: 1, 2, 4 or 8, or 0 to choose by
- *                        size (the fewest that leave at most two regrowth
- *                        CTAs per SM; the default).
+ *                        size (the fewest that leave at most four regrowth
+ *                        CTAs per SM, one wave of the tail kernel; the
+ *                        default).
  *   lstm_ctas_per_sm     CTAs per SM of the controller kernel of the LSTM(32)
  *                        controller: 1 (an 8-block weight ring, two agents in
  *                        flight; the default) or 2 (a 4-block ring each).
