@@ -517,10 +517,13 @@ int set_shape(EcoBatch &b, int regrow_rows, int lstm_ctas) {
   if (lstm_ctas != 1 && lstm_ctas != 2) return ECO_EINVAL;
   const int n = (int)b.worlds.size();
   const int k = regrow_rows ? regrow_rows : regrow_k_for(b.worlds.data(), n, b.bd.n_sms);
-  b.regrow_cfg = regrow_rows;
-  if (k == b.bd.regrow_k && lstm_ctas == b.bd.lstm_ctas) return ECO_OK;
+  if (k == b.bd.regrow_k && lstm_ctas == b.bd.lstm_ctas) {
+    b.regrow_cfg = regrow_rows;
+    return ECO_OK;
+  }
   int rc = reconfigure(b);
   if (rc) return rc;
+  b.regrow_cfg = regrow_rows;
   if (k != b.bd.regrow_k) {
     std::vector<int> tiles(n + 1);
     int tt = 0;
